@@ -1,0 +1,496 @@
+"""Pins of the CPU oracle against things other than itself: closed forms
+derived from the paper's definitions, published hash test vectors, dense brute
+force, textbook eigenvalues and invariants.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+
+def csr(p):
+    return sp.csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(p["n"], p["n"]))
+
+
+def as_dict(M):
+    M = sp.csr_matrix(M)
+    M.sort_indices()
+    return dict(nrows=M.shape[0], ncols=M.shape[1], row_ptr=M.indptr.astype(np.int64),
+                col=M.indices.astype(np.int32), val=M.data.astype(np.float64))
+
+
+def to_sp(d):
+    return sp.csr_matrix((d["val"], d["col"], d["row_ptr"]), shape=(d["nrows"], d["ncols"]))
+
+
+def entry(p, arr, i, j):
+    rp, ci = p["row_ptr"], p["col"]
+    for q in range(rp[i], rp[i + 1]):
+        if ci[q] == j:
+            return arr[q]
+    raise KeyError((i, j))
+
+
+# ---------------------------------------------------------------------------
+# hash: MurmurHash3_x86_32 of the empty input with seed s equals fmix32(s);
+# published test vectors: seed 1 -> 0x514E28B7, seed 0xFFFFFFFF -> 0x81F16F39
+# ---------------------------------------------------------------------------
+def test_mis_key_is_murmur3_finaliser(orc):
+    c1 = 0x9E3779B9  # level-0 salt
+    assert orc.mis_key(0, 0, 1 ^ c1) >> 32 == 0x514E28B7
+    assert orc.mis_key(0, 0, 0xFFFFFFFF ^ c1) >> 32 == 0x81F16F39
+    assert orc.mis_key(0, 0, c1) >> 32 == 0  # fmix32(0) = 0
+    assert orc.mis_key(12345, 3, 7) & 0xFFFFFFFF == 12345
+
+
+def test_start_vector_range(orc):
+    v = np.array([orc.start_value(i, 1, 0) for i in range(2000)])
+    assert v.min() >= -1.0 and v.max() < 1.0
+    assert abs(v.mean()) < 0.1 and 0.25 < v.var() < 0.42  # uniform on [-1,1): var 1/3
+
+
+# ---------------------------------------------------------------------------
+# Worked example (Sec. 3, Fig. test_problem / neighbor_node_naming): S values
+# of nodes 12, 13, 14 derived in closed form from L_d and the max-symmetrised
+# material distance, scalar pointwise sigma: sigma_low for x<=1, kappa for x>=2
+# ---------------------------------------------------------------------------
+def closed_forms(k):
+    r24 = math.sqrt(24.0)
+    return {
+        (12, 11): 1 / r24, (12, 6): 0.5 / r24, (12, 7): 1 / 6,
+        (12, 13): 1 / math.sqrt(12 + 24 * k), (12, 8): 0.5 / math.sqrt(12 + 24 * k),
+        (13, 8): k / (2 + 4 * k), (13, 7): 0.5 / math.sqrt(12 + 24 * k),
+        (13, 14): 1 / math.sqrt(6 * (4 + 2 / k)),
+        (14, 9): 1 / 6, (14, 15): 1 / r24,
+    }
+
+
+@pytest.mark.parametrize("kappa", [1.0, 10.0, 100.0, 1e4, 1e8])
+@pytest.mark.parametrize("sig_low", [1.0, 1e-3])
+def test_worked_example_material_soc(orc, gen_mod, kappa, sig_low):
+    p = gen_mod.worked_example(sig_low=sig_low, kappa=kappa)
+    sinv = orc.invert_tensors(2, p["tensors"])
+    w, D, keep = orc.strength_material(2, p["n"], p["row_ptr"], p["col"], None, p["coords"], sinv, 0.0)
+    for (a, b), s in closed_forms(kappa).items():
+        i, j = a - 1, b - 1  # paper numbers nodes from 1
+        S = entry(p, w, i, j) / math.sqrt(D[i] * D[j])
+        assert S == pytest.approx(s, rel=1e-13), (a, b)
+
+
+def test_worked_example_asymptotics(orc, gen_mod):
+    # S_low,high ~ kappa^{-1/2} (Eq. low_high_soc_parameter_relation)
+    for kappa in [1e6, 1e8, 1e10]:
+        p = gen_mod.worked_example(kappa=kappa)
+        sinv = orc.invert_tensors(2, p["tensors"])
+        w, D, _ = orc.strength_material(2, p["n"], p["row_ptr"], p["col"], None, p["coords"], sinv, 0.0)
+        S = entry(p, w, 11, 12) / math.sqrt(D[11] * D[12])
+        assert S * math.sqrt(kappa) == pytest.approx(1 / math.sqrt(24.0), rel=1e-4)
+
+
+def test_worked_example_drops_interface(orc, gen_mod):
+    # with theta between the interface value and the in-region values the
+    # low-high edges are dropped and the in-region edges are kept
+    kappa = 1e4
+    p = gen_mod.worked_example(kappa=kappa)
+    sinv = orc.invert_tensors(2, p["tensors"])
+    _, _, keep = orc.strength_material(2, p["n"], p["row_ptr"], p["col"], None, p["coords"], sinv, 0.05)
+    assert entry(p, keep, 11, 12) == 0 and entry(p, keep, 11, 7) == 0  # 12-13, 12-right diag
+    assert entry(p, keep, 11, 10) == 1 and entry(p, keep, 12, 13) == 1  # 12-left, 13-14
+
+
+# ---------------------------------------------------------------------------
+# classical measure: closed forms of isotropic Q1 stencils (Sec. 2.1)
+# ---------------------------------------------------------------------------
+def test_classical_2d_isotropic(orc, gen_mod):
+    # interior 2D Q1: a_ii = 8/3, every off-diagonal -1/3 -> S = 1/8
+    p = gen_mod.layered_serving(2, 8, 1.0)
+    A = csr(p)
+    n = p["n"]
+    for theta, expect in [(0.125 * (1 - 1e-12), 1), (0.125 * (1 + 1e-12), 0)]:
+        keep = orc.strength_classical(n, p["row_ptr"], p["col"], p["val"], p["dir_mask"], theta)
+        i = 4 + 9 * 4  # interior node (4,4)
+        for q in range(p["row_ptr"][i], p["row_ptr"][i + 1]):
+            if p["col"][q] != i:
+                assert keep[q] == expect
+    assert A[40, 40] == pytest.approx(8 / 3)
+
+
+def test_classical_3d_isotropic(orc, gen_mod):
+    # interior 3D Q1 (h): diag 8h/3, axis 0, face diagonals -h/6, body -h/12
+    # -> S in {0, 1/16, 1/32}
+    p = gen_mod.layered_serving(3, 6, 1.0)
+    n = p["n"]
+    N = 7
+    i = 3 + N * (3 + N * 3)
+    got = {}
+    for theta in [1 / 32 * (1 - 1e-12), 1 / 32 * (1 + 1e-12), 1 / 16 * (1 - 1e-12), 1 / 16 * (1 + 1e-12)]:
+        keep = orc.strength_classical(n, p["row_ptr"], p["col"], p["val"], None, theta)
+        row = [(p["col"][q], keep[q]) for q in range(p["row_ptr"][i], p["row_ptr"][i + 1])]
+        got[theta] = sum(k for c, k in row if c != i)
+    vals = list(got.values())
+    assert vals == [20, 12, 12, 0]  # 12 face + 8 body kept; then 12 face; then none
+
+
+def test_material_3d_isotropic_closed_form(orc, gen_mod):
+    # uniform cubes: w = 1/h^2, 1/(2h^2), 1/(3h^2); D = 44/(3h^2)
+    # -> S = 3/44 (axis), 3/88 (face), 1/44 (body)
+    p = gen_mod.layered_serving(3, 6, 1.0)
+    sig = orc.nodal_from_elements(3, p["n"], p["elem_nodes"], p["elem_measure"], p["tensors"])
+    sinv = orc.invert_tensors(3, sig)
+    w, D, _ = orc.strength_material(3, p["n"], p["row_ptr"], p["col"], None, p["coords"], sinv, 0.0)
+    N = 7
+    i = 3 + N * (3 + N * 3)
+    expect = {1: 3 / 44, 2: 3 / 88, 3: 1 / 44}
+    for q in range(p["row_ptr"][i], p["row_ptr"][i + 1]):
+        j = p["col"][q]
+        if j == i:
+            continue
+        off = sum(abs(a - b) for a, b in zip(np.unravel_index(i, (N, N, N)), np.unravel_index(j, (N, N, N))))
+        assert w[q] / math.sqrt(D[i] * D[j]) == pytest.approx(expect[off], rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# nodal tensors (Clement average) and inversion, checked by brute force
+# ---------------------------------------------------------------------------
+def test_nodal_tensors_brute_force(orc, gen_mod):
+    p = gen_mod.voronoi_3d(6, nseeds=5, seed=3)
+    sig = orc.nodal_from_elements(3, p["n"], p["elem_nodes"], p["elem_measure"], p["tensors"])
+    en = p["elem_nodes"].reshape(-1, 8)
+    K = p["tensors"].reshape(-1, 6)
+    num = np.zeros((p["n"], 6))
+    den = np.zeros(p["n"])
+    for e in range(en.shape[0]):
+        for a in en[e]:
+            num[a] += p["elem_measure"][e] * K[e]
+            den[a] += p["elem_measure"][e]
+    np.testing.assert_allclose(sig.reshape(-1, 6), num / den[:, None], rtol=1e-13, atol=0)
+    sinv = orc.invert_tensors(3, sig).reshape(-1, 6)
+    idx = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    for i in range(0, p["n"], 17):
+        M = np.zeros((3, 3))
+        Mi = np.zeros((3, 3))
+        for c, (a, b) in enumerate(idx):
+            M[a, b] = M[b, a] = sig[6 * i + c]
+            Mi[a, b] = Mi[b, a] = sinv[i, c]
+        np.testing.assert_allclose(M @ Mi, np.eye(3), atol=1e-9)
+        np.testing.assert_allclose(Mi, np.linalg.inv(M), rtol=1e-8, atol=1e-8 * abs(Mi).max())
+
+
+# ---------------------------------------------------------------------------
+# invariants of the strength measures
+# ---------------------------------------------------------------------------
+def test_material_soc_symmetric_and_scale_invariant(orc, gen_mod):
+    p = gen_mod.voronoi_3d(8, nseeds=6, seed=1)
+    n = p["n"]
+    sig = orc.nodal_from_elements(3, n, p["elem_nodes"], p["elem_measure"], p["tensors"])
+    sinv = orc.invert_tensors(3, sig)
+    w, D, keep = orc.strength_material(3, n, p["row_ptr"], p["col"], p["dir_mask"], p["coords"], sinv, 0.05)
+    W = sp.csr_matrix((w, p["col"], p["row_ptr"]), shape=(n, n))
+    assert (W != W.T).nnz == 0  # bitwise symmetric
+    K = sp.csr_matrix((keep.astype(float), p["col"], p["row_ptr"]), shape=(n, n))
+    assert (K != K.T).nnz == 0
+    # scaling coordinates by c and sigma by s scales every w (and D) by s/c^2
+    sinv2 = orc.invert_tensors(3, sig * 7.5)
+    w2, D2, keep2 = orc.strength_material(3, n, p["row_ptr"], p["col"], p["dir_mask"], p["coords"] * 0.3,
+                                          sinv2, 0.05)
+    rows = np.repeat(np.arange(n), np.diff(p["row_ptr"]))
+    off = p["col"] != rows
+    S1 = w[off] / np.sqrt(D[rows[off]] * D[p["col"][off]])
+    S2 = w2[off] / np.sqrt(D2[rows[off]] * D2[p["col"][off]])
+    # exact in real arithmetic; rounding is amplified by the 1e3 anisotropy of sigma^-1
+    np.testing.assert_allclose(S1, S2, rtol=1e-9)
+    border = np.abs(S1 - 0.05) < 1e-8
+    assert np.array_equal(keep[off][~border], keep2[off][~border])
+
+
+def test_classical_matches_definition_brute_force(orc, gen_mod):
+    p = gen_mod.voronoi_3d(6, nseeds=4, seed=2)
+    A = csr(p).toarray()
+    d = np.diag(A)
+    keep = orc.strength_classical(p["n"], p["row_ptr"], p["col"], p["val"], p["dir_mask"], 0.04)
+    rows = np.repeat(np.arange(p["n"]), np.diff(p["row_ptr"]))
+    S = np.abs(p["val"]) / np.sqrt(np.abs(d[rows] * d[p["col"]]))
+    dm = p["dir_mask"].astype(bool)
+    expect = np.where(rows == p["col"], 1, (S >= 0.04) & ~dm[rows] & ~dm[p["col"]])
+    border = np.abs(S - 0.04) < 1e-12
+    assert np.array_equal(keep[~border], expect[~border].astype(np.uint8))
+
+
+# ---------------------------------------------------------------------------
+# MIS-2 and aggregation: brute force on small graphs
+# ---------------------------------------------------------------------------
+def _graph(orc, p, theta, measure="classical"):
+    n = p["n"]
+    if measure == "classical":
+        keep = orc.strength_classical(n, p["row_ptr"], p["col"], p["val"], p["dir_mask"], theta)
+    else:
+        sig = orc.nodal_from_elements(p["dim"], n, p["elem_nodes"], p["elem_measure"], p["tensors"])
+        sinv = orc.invert_tensors(p["dim"], sig)
+        keep = orc.strength_material(p["dim"], n, p["row_ptr"], p["col"], p["dir_mask"], p["coords"], sinv,
+                                     theta)[2]
+    grp, gci = orc.filtered_graph(n, p["row_ptr"], p["col"], keep, p["dir_mask"])
+    return keep, grp, gci
+
+
+def _adj(n, grp, gci):
+    return [set(gci[grp[i]:grp[i + 1]].tolist()) for i in range(n)]
+
+
+def _ball2(adj, i):
+    s = {i} | adj[i]
+    for j in adj[i]:
+        s |= adj[j]
+    return s
+
+
+@pytest.mark.parametrize("case", ["c1", "two_domain", "voronoi"])
+def test_mis2_equals_sequential_greedy(orc, gen_mod, case):
+    if case == "c1":
+        p = gen_mod.layered_2d(16)
+        keep, grp, gci = _graph(orc, p, 0.08, "material")
+    elif case == "two_domain":
+        p = gen_mod.two_domain(16, 1e4)
+        keep, grp, gci = _graph(orc, p, 0.08, "classical")
+    else:
+        p = gen_mod.voronoi_3d(6, nseeds=5, seed=4)
+        keep, grp, gci = _graph(orc, p, 0.05, "material")
+    n = p["n"]
+    dm = p["dir_mask"].astype(bool)
+    adj = _adj(n, grp, gci)
+    # brute force: the test's own greedy over G^2 in descending key order
+    keys = sorted((orc.mis_key(i, 2, 5), i) for i in range(n) if not dm[i])
+    sel = set()
+    for _, i in reversed(keys):
+        if not (_ball2(adj, i) & sel):
+            sel.add(i)
+    root = orc.mis2(n, grp, gci, p["dir_mask"], level=2, seed=5)
+    assert set(np.flatnonzero(root).tolist()) == sel
+    # distance >= 3 and maximality
+    for i in sel:
+        assert _ball2(adj, i) & sel == {i}
+    for i in range(n):
+        if not dm[i]:
+            assert _ball2(adj, i) & sel
+
+
+def test_aggregates_partition_and_rules(orc, gen_mod):
+    p = gen_mod.voronoi_3d(7, nseeds=5, seed=9)
+    keep, grp, gci = _graph(orc, p, 0.05, "material")
+    n = p["n"]
+    dm = p["dir_mask"].astype(bool)
+    root = orc.mis2(n, grp, gci, p["dir_mask"], 0, 0)
+    nc, agg = orc.aggregate(n, grp, gci, p["dir_mask"], root)
+    adj = _adj(n, grp, gci)
+    roots = np.flatnonzero(root)
+    assert nc == len(roots)
+    assert np.all(agg[dm] == -1) and np.all(agg[~dm] >= 0)  # partition of non-Dirichlet nodes
+    assert np.array_equal(agg[roots], np.arange(nc))  # ids by ascending root index
+    phase1 = np.full(n, -1)
+    for a, r in enumerate(roots):
+        phase1[r] = a
+        for j in adj[r]:
+            assert phase1[j] == -1  # roots >= 3 apart: disjoint
+            phase1[j] = a
+    for i in range(n):
+        if dm[i]:
+            continue
+        if phase1[i] >= 0:
+            assert agg[i] == phase1[i]
+        else:
+            cnt = {}
+            for j in adj[i]:
+                if phase1[j] >= 0:
+                    cnt[phase1[j]] = cnt.get(phase1[j], 0) + 1
+            best = min(cnt, key=lambda a: (-cnt[a], a))
+            assert agg[i] == best
+
+
+def test_two_domain_no_aggregate_straddles_interface(orc, gen_mod):
+    # Sec. 3, Fig. academic_test_problem_coarsening: material-aware dropping
+    # removes every edge across x=0, so no aggregate straddles it
+    p = gen_mod.two_domain(32, 1e4)
+    h = orc.Hierarchy(p, 0.08, "material", max_coarse=64)
+    lv = h.level(0)
+    x = p["coords"].reshape(-1, 2)[:, 0]
+    for a in range(lv["nc"]):
+        xs = x[lv["agg"] == a]
+        assert xs.max() <= 0 or xs.min() >= 0 or (np.all(xs <= 1e-12) or np.all(xs >= -1e-12))
+    # anisotropic half: semi-coarsening along x (the strong direction)
+    y = p["coords"].reshape(-1, 2)[:, 1]
+    spans_y = [np.ptp(y[lv["agg"] == a]) for a in range(lv["nc"]) if x[lv["agg"] == a].min() > 0.1]
+    assert np.median(spans_y) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# prolongator pieces
+# ---------------------------------------------------------------------------
+def test_tentative_and_filter_invariants(orc, gen_mod):
+    p = gen_mod.voronoi_3d(6, nseeds=4, seed=5)
+    keep, grp, gci = _graph(orc, p, 0.05, "material")
+    n = p["n"]
+    root = orc.mis2(n, grp, gci, p["dir_mask"], 0, 0)
+    nc, agg = orc.aggregate(n, grp, gci, p["dir_mask"], root)
+    Pt = to_sp(orc.tentative(n, nc, agg))
+    rs = np.asarray(Pt.sum(axis=1)).ravel()
+    assert np.all(rs[agg >= 0] == 1.0) and np.all(rs[agg < 0] == 0.0)
+    F, Dt = orc.filter_matrix(n, p["row_ptr"], p["col"], p["val"], keep)
+    Fs = to_sp(F)
+    A = csr(p)
+    # row sums preserved by lumping (Sec. 2.2)
+    np.testing.assert_allclose(np.asarray(Fs.sum(1)).ravel(), np.asarray(A.sum(1)).ravel(),
+                               atol=1e-12 * abs(A).max())
+    fin = np.isfinite(Dt)
+    np.testing.assert_allclose(Dt[fin], np.asarray(abs(Fs).sum(1)).ravel()[fin], rtol=1e-14)
+    assert np.all(np.asarray(abs(Fs).sum(1)).ravel()[~fin] <= 1e-12 * np.asarray(abs(A).sum(1)).ravel()[~fin])
+    assert (Fs != Fs.T).nnz == 0
+    # Gershgorin: rho(D~^-1 A_F) <= 1 for the 1-norm diagonal
+    s = 1 / np.sqrt(Dt)
+    lam = orc.power_estimate(F, s, 10, 1, 0)
+    assert 0 < lam <= 1 + 1e-12
+    # dense check of the smoothed prolongator
+    omega = 4 / 3 / lam
+    P = to_sp(orc.smooth_prolongator(F, Dt, omega, agg, nc)).toarray()
+    Pd = Pt.toarray()
+    dense = Pd - omega * (np.diag(np.where(fin, 1 / Dt, 0.0)) @ Fs.toarray() @ Pd)
+    dense[agg < 0] = 0
+    np.testing.assert_allclose(P, dense, atol=1e-14)
+    # P 1 = 1 where the row of A sums to zero (interpolates the near nullspace)
+    arow = np.asarray(A.sum(1)).ravel()
+    ok = (np.abs(arow) < 1e-12 * abs(A).max()) & (agg >= 0)
+    nbr_ok = np.array([np.all(agg[p["col"][p["row_ptr"][i]:p["row_ptr"][i + 1]]] >= 0) for i in range(n)])
+    np.testing.assert_allclose(P.sum(1)[ok & nbr_ok], 1.0, atol=1e-12)
+
+
+def test_power_method_1d_laplacian(orc):
+    # eigenvalues of tridiag(-1,2,-1): 2 - 2 cos(k pi / (n+1))
+    n = 40
+    T = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    lmax = 2 - 2 * math.cos(n * math.pi / (n + 1))
+    d = as_dict(T)
+    est = [orc.power_estimate(d, np.ones(n), k, 3, 0) for k in (5, 10, 50, 4000)]
+    assert all(e <= lmax * (1 + 1e-12) for e in est)
+    assert est[-1] == pytest.approx(lmax, rel=1e-6)
+    assert est[1] > 0.9 * lmax
+
+
+def test_spgemm_transpose_galerkin_dense(orc, gen_mod):
+    rng = np.random.default_rng(0)
+    A = sp.random(30, 25, density=0.2, random_state=1, format="csr")
+    B = sp.random(25, 17, density=0.3, random_state=2, format="csr")
+    C = to_sp(orc.spgemm(as_dict(A), as_dict(B)))
+    np.testing.assert_allclose(C.toarray(), (A @ B).toarray(), rtol=1e-14, atol=1e-15)
+    R = to_sp(orc.transpose(as_dict(B)))
+    assert (R != B.T).nnz == 0
+    # Galerkin on a real level: dense P^T A P, exact symmetry
+    p = gen_mod.layered_2d(12)
+    h = orc.Hierarchy(p, 0.08, "material", max_coarse=20)
+    l0, l1 = h.level(0), h.level(1)
+    A0 = sp.csr_matrix((l0["A_v"], l0["A_ci"], l0["A_rp"]), shape=(l0["n"],) * 2).toarray()
+    P0 = sp.csr_matrix((l0["P_v"], l0["P_ci"], l0["P_rp"]), shape=(l0["n"], l0["nc"])).toarray()
+    A1 = sp.csr_matrix((l1["A_v"], l1["A_ci"], l1["A_rp"]), shape=(l1["n"],) * 2).toarray()
+    np.testing.assert_allclose(A1, P0.T @ A0 @ P0, rtol=0, atol=1e-13 * abs(A1).max())
+    assert np.array_equal(A1, A1.T)
+    del rng
+
+
+def test_galerkin_kills_constants_on_pure_neumann(orc, gen_mod):
+    # no Dirichlet rows: A 1 = 0 and P 1 = 1 imply A_c 1 = 0 (two levels of
+    # the step chain; the full setup would stop at the singular coarse solve)
+    xc = np.linspace(0, 1, 17)
+    K = np.tile([1.0, 0.3, 0.1], (256, 1))
+    q = gen_mod.assemble(2, 16, 16, 0, xc, xc, None, K, None, np.zeros(289, np.uint8))
+    n, rp, ci, v = q["n"], q["row_ptr"], q["col"], q["val"]
+    A = dict(nrows=n, ncols=n, row_ptr=rp, col=ci, val=v)
+    assert np.abs(csr(q) @ np.ones(n)).max() < 1e-13
+    dm = orc.dirichlet(n, rp, ci, v)
+    assert not dm.any()
+    for level in range(2):
+        keep = orc.strength_classical(n, A["row_ptr"], A["col"], A["val"], dm, 0.02)
+        grp, gci = orc.filtered_graph(n, A["row_ptr"], A["col"], keep, dm)
+        root = orc.mis2(n, grp, gci, dm, level, 0)
+        nc, agg = orc.aggregate(n, grp, gci, dm, root)
+        F, Dt = orc.filter_matrix(n, A["row_ptr"], A["col"], A["val"], keep)
+        lam = orc.power_estimate(F, 1 / np.sqrt(Dt), 10, 1, 0)
+        P = orc.smooth_prolongator(F, Dt, 4 / 3 / lam, agg, nc)
+        np.testing.assert_allclose(to_sp(P) @ np.ones(nc), 1.0, atol=1e-12)
+        Ac = orc.galerkin(A, P)
+        As = to_sp(Ac)
+        assert np.abs(As @ np.ones(nc)).max() < 1e-12 * abs(As).max()
+        assert (As != As.T).nnz == 0
+        A, n, dm = Ac, nc, np.zeros(nc, np.uint8)
+
+
+# ---------------------------------------------------------------------------
+# solve phase
+# ---------------------------------------------------------------------------
+def test_chebyshev_polynomial_on_diagonal(orc):
+    # with A = diag(a) and D^-1 = I, x_k = (I - p(A)) A^-1 b, where
+    # p(t) = T_k((theta - t)/delta) / T_k(theta/delta)  (Chebyshev iteration)
+    a = np.linspace(0.05, 2.0, 23)
+    A = as_dict(sp.diags(a).tocsr())
+    b = np.linspace(1, 2, 23)
+    lmax, lmin = 2.0, 0.1
+    th, de = (lmax + lmin) / 2, (lmax - lmin) / 2
+    for deg in (1, 2, 3):
+        x = orc.chebyshev(A, np.ones(23), lmax, lmin, deg, b)
+        Tk = np.polynomial.chebyshev.Chebyshev.basis(deg)
+        pvals = Tk((th - a) / de) / Tk(th / de)
+        np.testing.assert_allclose(b / a - x, pvals * (b / a), rtol=1e-12, atol=1e-13)
+
+
+def test_dense_cholesky(orc, gen_mod):
+    p = gen_mod.layered_2d(6)
+    A = as_dict(csr(p))
+    st, L = orc.dense_cholesky(A)
+    assert st == 0
+    np.testing.assert_allclose(L @ L.T, to_sp(A).toarray(), atol=1e-13)
+    assert np.all(np.triu(L, 1) == 0)
+    bad = as_dict(-csr(p))
+    assert orc.dense_cholesky(bad)[0] == orc.ERR_NOT_SPD
+
+
+@pytest.mark.parametrize("measure", ["classical", "material"])
+def test_pcg_matches_dense_solve(orc, gen_mod, measure):
+    p = gen_mod.layered_2d(16, contrast=1e-3)
+    h = orc.Hierarchy(p, 0.08, measure, max_coarse=30)
+    assert h.nlev >= 2
+    x, info = h.solve(p["b"], tol=1e-10)
+    assert info["status"] == 0 and info["iters"] <= p["n"]
+    xd = np.linalg.solve(csr(p).toarray(), p["b"])
+    cond = np.linalg.cond(csr(p).toarray())
+    assert np.linalg.norm(x - xd) <= 10 * cond * 1e-10 * np.linalg.norm(xd)
+    assert info["rel_res"] <= 1e-10
+
+
+def test_vcycle_is_symmetric_positive(orc, gen_mod):
+    p = gen_mod.voronoi_3d(6, nseeds=4, seed=6)
+    h = orc.Hierarchy(p, 0.05, "material", max_coarse=40)
+    assert h.nlev >= 2
+    rng = np.random.default_rng(3)
+    u, v = rng.standard_normal(p["n"]), rng.standard_normal(p["n"])
+    Mu, Mv = h.vcycle(u), h.vcycle(v)
+    assert u @ Mv == pytest.approx(v @ Mu, rel=1e-10)
+    assert v @ Mv > 0 and u @ Mu > 0
+
+
+def test_flexible_cg_converges(orc, gen_mod):
+    p = gen_mod.layered_2d(32)
+    h = orc.Hierarchy(p, 0.08, "material", max_coarse=64)
+    _, a = h.solve(p["b"])
+    _, b = h.solve(p["b"], flexible=True)
+    assert a["status"] == b["status"] == 0
+    assert abs(a["iters"] - b["iters"]) <= 1
+
+
+def test_two_domain_material_robust_in_kappa(orc, gen_mod):
+    # Sec. 4.1: classical SA degrades with the contrast, the material-aware
+    # measure stays near its kappa = 1 baseline
+    it = {}
+    for kappa in (1.0, 1e4):
+        p = gen_mod.two_domain(32, kappa)
+        for m in ("classical", "material"):
+            h = orc.Hierarchy(p, 0.08, m, max_coarse=64)
+            it[(m, kappa)] = h.solve(p["b"])[1]["iters"]
+    assert it[("material", 1e4)] <= 1.5 * it[("material", 1.0)]
+    assert it[("classical", 1e4)] >= 2 * it[("classical", 1.0)]
+    assert it[("material", 1e4)] < it[("classical", 1e4)]
