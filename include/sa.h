@@ -1,0 +1,226 @@
+/*
+ * sa.h -- C ABI of the GB300 smoothed-aggregation AMG library.
+ *
+ * Smoothed-aggregation algebraic multigrid (arXiv 2602.05686, Sec. 2) used as
+ * the preconditioner of conjugate gradients (Sec. 4) for the material-weighted
+ * Laplacian -div(sigma(x) grad u) = f discretised by finite elements
+ * (Sec. 1, Eq. model_problem and linear_system).  Coarsening is driven by the
+ * classical strength-of-connection measure S^sa = D^-1/2 A D^-1/2
+ * (Sec. 2.1) or the material-aware distance Laplacian
+ * S^dlap_sigma = D_sigma^-1/2 L_sigma D_sigma^-1/2 (Sec. 3), with pointwise
+ * dropping.  Every step runs as a CUDA kernel on one GPU.
+ *
+ * Conventions for every call:
+ *   - the return value is a status (SA_OK or a negative SA_ERR_*); no call
+ *     aborts, traps or spins without a bound;
+ *   - "device pointer" means memory of the current CUDA device; "host
+ *     pointer" means ordinary or pinned host memory; calls that accept
+ *     either detect the kind with cudaPointerGetAttributes;
+ *   - all GPU work of a handle is ordered on options.stream (a
+ *     cudaStream_t; NULL = the legacy default stream); a handle must not be
+ *     used from two host threads at once;
+ *   - indices are 0-based; CSR row pointers are int64, column indices int32.
+ */
+#ifndef SA_GB300_H
+#define SA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sa_handle_s* sa_handle;
+
+enum {
+  SA_OK = 0,
+  SA_ERR_INVALID_ARG = -1,    /* bad size, NULL pointer, unsupported option */
+  SA_ERR_OOM = -2,            /* device allocation (or the allocator callback) failed */
+  SA_ERR_CUDA = -3,           /* a CUDA runtime call failed; see sa_last_error() */
+  SA_ERR_NOT_SPD = -4,        /* non-positive pivot in the coarse Cholesky factor */
+  SA_ERR_STAGNATION = -5,     /* coarsening stagnated above the coarse-solve limit */
+  SA_ERR_NO_CONVERGENCE = -6, /* maxit reached; x holds the last iterate */
+  SA_ERR_BREAKDOWN = -7,      /* p^T A p <= 0 or NaN in CG */
+  SA_ERR_CAPACITY = -8        /* an internal fixed-size table was exceeded */
+};
+
+typedef enum {
+  SA_MEASURE_CLASSICAL = 0, /* |a_ij| / sqrt(|a_ii a_jj|) >= theta (Sec. 2.1) */
+  SA_MEASURE_MATERIAL = 1,  /* material-weighted distance Laplacian (Sec. 3) */
+  SA_MEASURE_DISTANCE = 2   /* Euclidean distance Laplacian (Sec. 2.1), sigma = I */
+} sa_measure;
+
+typedef enum {
+  SA_PREC_FP64 = 0,        /* FP64 PCG with an FP64 V-cycle */
+  SA_PREC_FP32_VCYCLE = 1  /* FP64 flexible CG with an FP32 V-cycle on the
+                              symmetrically diagonal-scaled hierarchy */
+} sa_precision;
+
+typedef enum {
+  SA_TENSOR_NODE = 0,    /* tensors: n * kp values, one tensor per node */
+  SA_TENSOR_ELEMENT = 1  /* tensors: n_elem * kp values, one per element,
+                            averaged to nodes by the Clement interpolant (Sec. 3) */
+} sa_tensor_loc;
+
+/*
+ * Problem statement (Sec. 1: A u = b from Q1/trilinear finite elements).
+ * All arrays are caller-owned and only read during sa_setup; they may be
+ * device or host pointers (one kind for all arrays, see `host`).
+ *   A: SPD, structurally symmetric CSR, columns sorted ascending, diagonal
+ *      stored.  Dirichlet rows carry only their diagonal and their columns
+ *      are eliminated from the other rows (a row whose stored off-diagonals
+ *      are all exactly zero is treated as Dirichlet and never aggregated).
+ *   coords: n * dim node coordinates (row-major); required for the
+ *      MATERIAL and DISTANCE measures, ignored for CLASSICAL.
+ *   tensors: packed symmetric sigma, kp = 3 in 2D (xx, yy, xy), kp = 6 in
+ *      3D (xx, yy, zz, xy, xz, yz); required for MATERIAL.
+ *   elem_nodes / elem_measure: element connectivity (n_elem * nodes_per_elem)
+ *      and element measures |e|, required for SA_TENSOR_ELEMENT.
+ */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int host;                /* 1 if every array below is a host pointer */
+  int64_t n, nnz;
+  const int64_t* row_ptr;  /* n + 1 */
+  const int32_t* col;      /* nnz */
+  const double* val;       /* nnz */
+  const double* coords;    /* n * dim */
+  sa_tensor_loc tloc;
+  const double* tensors;
+  int64_t n_elem;
+  int nodes_per_elem;
+  const int32_t* elem_nodes;
+  const double* elem_measure;
+} sa_problem;
+
+/*
+ * Options.  sa_default_options fills the paper's settings (Sec. 4):
+ *   theta = 0.08, measure MATERIAL, precision FP64, max_coarse = 5000,
+ *   max_levels = 10, Chebyshev degree 2 with lambda_max boost 1.1 and ratio
+ *   30, 10 power steps, omega_sym = 4/3, maxit = 500.
+ * alloc/dealloc: optional device allocator (e.g. a caching allocator);
+ *   NULL = stream-ordered cudaMallocAsync/cudaFreeAsync on `stream`.
+ */
+typedef struct {
+  double theta;
+  sa_measure measure;
+  sa_precision precision;
+  int max_coarse, max_levels;
+  int cheb_degree;
+  double cheb_ratio, cheb_boost;
+  int power_iters;
+  double omega_sym;
+  uint32_t seed;           /* salts the MIS-2 priorities and power-method starts */
+  int maxit;
+  void* stream;            /* cudaStream_t */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*dealloc)(void* ptr, void* ctx);
+  void* alloc_ctx;
+  int keep_setup_data;     /* 1: keep strength masks and roots for sa_export_strength */
+} sa_options;
+
+typedef struct {
+  int iters;               /* CG iterations (operator products with p) */
+  double rel_res_true;     /* ||b - A x|| / ||b - A x0|| at exit, recomputed in FP64 */
+  double setup_ms, solve_ms;
+  int status;
+} sa_solve_info;
+
+/* fills *o with the defaults listed above; returns SA_OK */
+int sa_default_options(sa_options* o);
+
+/*
+ * Builds the hierarchy (Sec. 2 and 3; steps a1-a15 of the hot path): copies
+ * the inputs into handle-owned device memory, then per level computes the
+ * strength mask, filtered graph, MIS-2 aggregates, tentative and smoothed
+ * prolongators, coarse auxiliary data and the Galerkin product, then the
+ * smoother and coarse-solve data.  *out receives the handle on SA_OK and is
+ * NULL otherwise.  Blocks the calling thread until setup has finished
+ * (sizes are read back between steps).
+ */
+int sa_setup(const sa_problem* prob, const sa_options* opt, sa_handle* out);
+
+/*
+ * Solves A x = b by CG preconditioned with one V(1,1) cycle per iteration
+ * (Sec. 4; flexible CG for SA_PREC_FP32_VCYCLE) until
+ * ||b - A x_k|| <= tol ||b - A x_0||.  b and x are n-vectors, both device or
+ * both host pointers; x holds the initial guess on entry and the solution on
+ * exit (also on SA_ERR_NO_CONVERGENCE).  info may be NULL.
+ */
+int sa_solve(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info);
+
+/*
+ * k independent solves with the same hierarchy; B and X are column-major
+ * n x k (column c starts at B + c*n); infos (may be NULL) receives k entries.
+ */
+int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos);
+
+/*
+ * One application of the preconditioner z = M r (the V-cycle of
+ * Algorithm 1 in the handle's precision); r, z device n-vectors.
+ */
+int sa_vcycle(sa_handle h, const double* r, double* z);
+
+/*
+ * Hierarchy statistics: *levels; n_l[levels], nnz_l[levels] (arrays of at
+ * least 32 entries, may be NULL); *op_complexity = sum nnz(A_l) / nnz(A_1)
+ * (Sec. 2.2); *device_bytes = device memory held by the handle.
+ */
+int sa_hierarchy_stats(sa_handle h, int* levels, int64_t* n_l, int64_t* nnz_l, double* op_complexity,
+                       int64_t* device_bytes);
+
+/*
+ * Sizes of level l: out[0] = n_l, out[1] = nnz(A_l), out[2] = nnz(P_l),
+ * out[3] = n_{l+1} (0 on the coarsest level), out[4] = nnz of the filtered graph.
+ */
+int sa_level_sizes(sa_handle h, int l, int64_t* out);
+
+/*
+ * Copies level l to HOST arrays (any pointer may be NULL to skip it):
+ * aggregate map agg[n_l] (-1 = Dirichlet), P_l in CSR (n_l x n_{l+1}) and A_l
+ * in CSR.  Used by the parity tests.
+ */
+int sa_export_level(sa_handle h, int l, int32_t* agg, int64_t* P_rowptr, int32_t* P_col, double* P_val,
+                    int64_t* A_rowptr, int32_t* A_col, double* A_val);
+
+/*
+ * Copies the strength data of level l to HOST arrays (NULL skips): keep mask
+ * per stored entry of A_l, MIS-2 roots and Dirichlet flags per node (needs
+ * options.keep_setup_data = 1), coordinates n_l*dim and inverse tensors
+ * n_l*kp (material/distance measures), and scalars[4] = {omega,
+ * lambda_omega, cheb_lambda_max, cheb_lambda_min}.
+ */
+int sa_export_strength(sa_handle h, int l, uint8_t* keep, uint8_t* root, uint8_t* dirichlet, double* coords,
+                       double* sigma_inv, double* scalars);
+
+/* releases every device buffer of the handle (stream-ordered) */
+int sa_free(sa_handle h);
+
+/* static description of a status code */
+const char* sa_status_string(int status);
+
+/* text of the last CUDA error seen by this thread (empty if none) */
+const char* sa_last_error(void);
+
+/*
+ * Single steps on caller-provided DEVICE buffers, for stepwise parity checks
+ * and for callers that build their own pipeline.  Ordered on `stream`.
+ *
+ * sa_strength: the per-edge strength filter of Sec. 2.1 / Sec. 3 with
+ *   pointwise dropping on CSR (n, row_ptr, col, val).  keep[nnz] receives
+ *   1 for the diagonal and for kept off-diagonals.  dirichlet[n] (may be
+ *   NULL) excludes nodes.  CLASSICAL reads val; MATERIAL reads coords
+ *   (n*dim) and sigma_inv (n*kp, inverse nodal tensors); DISTANCE reads
+ *   coords only.  Scratch: the MATERIAL/DISTANCE measures need
+ *   nnz + n doubles of device scratch, allocated and freed inside the call
+ *   with cudaMallocAsync on `stream`.
+ */
+int sa_strength(sa_measure measure, int dim, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                const double* val, const double* coords, const double* sigma_inv, const uint8_t* dirichlet,
+                double theta, uint8_t* keep, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -473,6 +473,7 @@ double or_power_estimate(const csr_t* A, const double* s, int steps, uint32_t ta
   for (int it = 0; it < steps; ++it) {
     spmv_scaled(A, s, v, w);
     double nrm = sqrt(dot(n, w, w));
+    if (nrm == 0.0) { lam = 0.0; break; } /* M v = 0: no spectral information */
     lam = nrm / sqrt(dot(n, v, v));
     for (int64_t i = 0; i < n; ++i) v[i] = w[i] / nrm;
   }
@@ -778,7 +779,7 @@ or_hier_t* or_setup(int dim, int64_t n, const int64_t* rp, const int32_t* ci, co
     double* s = (double*)malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1));
     for (int64_t i = 0; i < nl; ++i) s[i] = 1.0 / sqrt(Dt[i]);
     Lc->lam_omega = or_power_estimate(&F, s, o->power_iters, (uint32_t)(2 * l + 1), o->seed);
-    Lc->omega = o->omega_sym / Lc->lam_omega;
+    Lc->omega = Lc->lam_omega > 0.0 ? o->omega_sym / Lc->lam_omega : 0.0;
     free(s);
     Lc->P = or_smooth_prolongator(&F, Dt, &Pt, Lc->omega, Lc->agg);
     csr_del(&F); csr_del(&Pt); free(Dt);

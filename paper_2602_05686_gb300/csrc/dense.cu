@@ -1,0 +1,288 @@
+// Coarsest level (Sec. 4: "the coarsest level is solved with a direct
+// method").  A_L (n_L <= a few thousand) is densified and factored
+// A_L = L L^T by a blocked right-looking Cholesky in FP64 (32 x 32 tiles);
+// then W = L^-1 is formed by blocked forward substitution on the identity,
+// so that every coarse solve is x = W^T (W b): two triangular matrix-vector
+// products that use every SM, instead of two sequential triangular sweeps.
+// W^T is stored explicitly so both products read contiguous rows.
+#include <math.h>
+
+#include "common.cuh"
+#include "solve.cuh"
+
+namespace sa {
+
+constexpr int NB = 32;
+
+__global__ void k_densify(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ v, double* __restrict__ M) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) M[i * n + ci[p]] = v[p];
+}
+
+__global__ void k_set_identity(int64_t n, double* __restrict__ W) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n * n) W[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
+// factor the diagonal tile (k,k) in place; err = 1 on a non-positive pivot
+__global__ void k_potrf_diag(int64_t n, double* __restrict__ M, int k, int* __restrict__ err) {
+  __shared__ double T[NB][NB + 1];
+  const int64_t o = (int64_t)k * NB;
+  const int bs = (int)((n - o) < NB ? (n - o) : NB);
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    int r = t / NB, c = t % NB;
+    T[r][c] = (r < bs && c < bs) ? M[(o + r) * n + o + c] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < bs; ++j) {
+    if (threadIdx.x == 0) {
+      double d = T[j][j];
+      if (!(d > 0.0)) { atomicOr(err, 1); d = 1.0; }
+      T[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int r = j + 1 + threadIdx.x; r < bs; r += blockDim.x) T[r][j] /= T[j][j];
+    __syncthreads();
+    const int m = bs - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      int r = j + 1 + t / m, c = j + 1 + t % m;
+      if (c <= r) T[r][c] -= T[r][j] * T[c][j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
+    int r = t / bs, c = t % bs;
+    M[(o + r) * n + o + c] = (c <= r) ? T[r][c] : 0.0;
+  }
+}
+
+// L_ik = A_ik L_kk^-T for block rows i > k (one CTA of NB threads per block row)
+__global__ void k_trsm_panel(int64_t n, double* __restrict__ M, int k) {
+  __shared__ double L[NB][NB + 1];
+  __shared__ double X[NB][NB + 1];
+  const int64_t ok = (int64_t)k * NB;
+  const int bk = (int)((n - ok) < NB ? (n - ok) : NB);
+  const int64_t oi = (int64_t)(k + 1 + blockIdx.x) * NB;
+  const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    int r = t / NB, c = t % NB;
+    L[r][c] = (r < bk && c < bk) ? M[(ok + r) * n + ok + c] : 0.0;
+    X[r][c] = (r < bi && c < bk) ? M[(oi + r) * n + ok + c] : 0.0;
+  }
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < bi) {
+    for (int c = 0; c < bk; ++c) {
+      double x = X[r][c];
+      for (int m = 0; m < c; ++m) x -= X[r][m] * L[c][m];
+      X[r][c] = x / L[c][c];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < bi * bk; t += blockDim.x) {
+    int rr = t / bk, c = t % bk;
+    M[(oi + rr) * n + ok + c] = X[rr][c];
+  }
+}
+
+__device__ __forceinline__ void tri_index(int64_t idx, int* ti, int* tj) {
+  // idx -> (ti, tj) with 0 <= tj <= ti, idx = ti (ti+1) / 2 + tj
+  int t = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(t + 1) * (t + 2) / 2 <= idx) ++t;
+  while ((int64_t)t * (t + 1) / 2 > idx) --t;
+  *ti = t;
+  *tj = (int)(idx - (int64_t)t * (t + 1) / 2);
+}
+
+// C -= A B^T on one NB x NB tile; 256 threads, 4 outputs each
+__device__ __forceinline__ void tile_gemm_nt_sub(int64_t n, double* __restrict__ M, int64_t oc_r, int64_t oc_c,
+                                                 int br, int bc, const double* __restrict__ Abase, int64_t oa_r,
+                                                 int64_t oa_c, const double* __restrict__ Bbase, int64_t ob_r,
+                                                 int64_t ob_c, int bkk, int64_t lda, int64_t ldb) {
+  __shared__ double As[NB][NB + 1];
+  __shared__ double Bs[NB][NB + 1];
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    int r = t / NB, c = t % NB;
+    As[r][c] = (r < br && c < bkk) ? Abase[(oa_r + r) * lda + oa_c + c] : 0.0;
+    Bs[r][c] = (r < bc && c < bkk) ? Bbase[(ob_r + r) * ldb + ob_c + c] : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    int r = t / NB, c = t % NB;
+    if (r < br && c < bc) {
+      double s = 0.0;
+#pragma unroll 8
+      for (int m = 0; m < NB; ++m) s += As[r][m] * Bs[c][m];
+      M[(oc_r + r) * n + oc_c + c] -= s;
+    }
+  }
+}
+
+// trailing update after panel k: A_ij -= L_ik L_jk^T, k < j <= i
+__global__ void k_syrk_update(int64_t n, double* __restrict__ M, int k) {
+  int ti, tj;
+  tri_index(blockIdx.x, &ti, &tj);
+  const int i = k + 1 + ti, j = k + 1 + tj;
+  const int64_t oi = (int64_t)i * NB, oj = (int64_t)j * NB, ok = (int64_t)k * NB;
+  const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
+  const int bj = (int)((n - oj) < NB ? (n - oj) : NB);
+  const int bk = (int)((n - ok) < NB ? (n - ok) : NB);
+  tile_gemm_nt_sub(n, M, oi, oj, bi, bj, M, oi, ok, M, oj, ok, bk, n, n);
+}
+
+// W_ij <- L_ii^-1 W_ij for block columns j <= i (CTA of NB threads per j)
+__global__ void k_trsm_lower_left(int64_t n, const double* __restrict__ L, double* __restrict__ W, int i) {
+  __shared__ double Ls[NB][NB + 1];
+  __shared__ double X[NB][NB + 1];
+  const int j = blockIdx.x;
+  const int64_t oi = (int64_t)i * NB, oj = (int64_t)j * NB;
+  const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
+  const int bj = (int)((n - oj) < NB ? (n - oj) : NB);
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    int r = t / NB, c = t % NB;
+    Ls[r][c] = (r < bi && c < bi) ? L[(oi + r) * n + oi + c] : 0.0;
+    X[r][c] = (r < bi && c < bj) ? W[(oi + r) * n + oj + c] : 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < bj) {
+    for (int r = 0; r < bi; ++r) {
+      double x = X[r][c];
+      for (int m = 0; m < r; ++m) x -= Ls[r][m] * X[m][c];
+      X[r][c] = x / Ls[r][r];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < bi * bj; t += blockDim.x) {
+    int r = t / bj, cc = t % bj;
+    W[(oi + r) * n + oj + cc] = X[r][cc];
+  }
+}
+
+// W_mj -= L_mi W_ij for m > i, j <= i
+__global__ void k_gemm_left(int64_t n, const double* __restrict__ L, double* __restrict__ W, int i, int ncolb) {
+  const int m = i + 1 + blockIdx.x / ncolb;
+  const int j = blockIdx.x % ncolb;
+  const int64_t om = (int64_t)m * NB, oi = (int64_t)i * NB, oj = (int64_t)j * NB;
+  const int bm = (int)((n - om) < NB ? (n - om) : NB);
+  const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
+  const int bj = (int)((n - oj) < NB ? (n - oj) : NB);
+  __shared__ double As[NB][NB + 1];
+  __shared__ double Bs[NB][NB + 1];
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    int r = t / NB, c = t % NB;
+    As[r][c] = (r < bm && c < bi) ? L[(om + r) * n + oi + c] : 0.0;   // L_mi
+    Bs[r][c] = (r < bi && c < bj) ? W[(oi + r) * n + oj + c] : 0.0;   // W_ij
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    int r = t / NB, c = t % NB;
+    if (r < bm && c < bj) {
+      double s = 0.0;
+#pragma unroll 8
+      for (int q = 0; q < NB; ++q) s += As[r][q] * Bs[q][c];
+      W[(om + r) * n + oj + c] -= s;
+    }
+  }
+}
+
+__global__ void k_transpose_dense(int64_t n, const double* __restrict__ W, double* __restrict__ WT) {
+  __shared__ double t[32][33];
+  int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  int x = threadIdx.x, y = threadIdx.y;
+  for (int k = y; k < 32; k += 8) {
+    int64_t r = by + k, c = bx + x;
+    t[k][x] = (r < n && c < n) ? W[r * n + c] : 0.0;
+  }
+  __syncthreads();
+  for (int k = y; k < 32; k += 8) {
+    int64_t r = bx + k, c = by + x;
+    if (r < n && c < n) WT[r * n + c] = t[x][k];
+  }
+}
+
+int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                             Buf<double>& W, Buf<double>& WT) {
+  cudaStream_t s = al.stream;
+  if (n <= 0) return SA_OK;
+  Buf<double> M;
+  Buf<int> err;
+  SA_TRY(M.alloc(&al, n * n));
+  SA_TRY(W.alloc(&al, n * n));
+  SA_TRY(WT.alloc(&al, n * n));
+  SA_TRY(err.alloc(&al, 1));
+  SA_TRY(memset_d(M.p, 0, M.bytes(), s));
+  SA_TRY(memset_d(err.p, 0, sizeof(int), s));
+  k_densify<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, v, M.p);
+  SA_LAUNCHED();
+  const int nb = (int)((n + NB - 1) / NB);
+  for (int k = 0; k < nb; ++k) {
+    k_potrf_diag<<<1, 256, 0, s>>>(n, M.p, k, err.p);
+    SA_LAUNCHED();
+    const int m = nb - k - 1;
+    if (m > 0) {
+      k_trsm_panel<<<m, NB, 0, s>>>(n, M.p, k);
+      SA_LAUNCHED();
+      k_syrk_update<<<(unsigned)((int64_t)m * (m + 1) / 2), 256, 0, s>>>(n, M.p, k);
+      SA_LAUNCHED();
+    }
+  }
+  int h_err = 0;
+  SA_TRY(copy_d2h(&h_err, err.p, sizeof(int), s));
+  if (h_err) return SA_ERR_NOT_SPD;
+  // strict upper triangle of M outside the diagonal tiles still holds A: W
+  // reads only the lower triangle of L, so it is left as is.
+  k_set_identity<<<blocks_for(n * n, 256), 256, 0, s>>>(n, W.p);
+  SA_LAUNCHED();
+  for (int i = 0; i < nb; ++i) {
+    k_trsm_lower_left<<<i + 1, NB, 0, s>>>(n, M.p, W.p, i);
+    SA_LAUNCHED();
+    const int m = nb - i - 1;
+    if (m > 0) {
+      k_gemm_left<<<(unsigned)(m * (i + 1)), 256, 0, s>>>(n, M.p, W.p, i, i + 1);
+      SA_LAUNCHED();
+    }
+  }
+  dim3 tb(32, 8), tg((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+  k_transpose_dense<<<tg, tb, 0, s>>>(n, W.p, WT.p);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+// y = W b (W lower triangular): warp per row over j <= i
+__global__ void k_trmv_lower(int64_t n, const double* __restrict__ W, const double* __restrict__ b,
+                             double* __restrict__ y) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    double s = 0.0;
+    for (int64_t j = lane; j <= i; j += 32) s += W[i * n + j] * b[j];
+    s = warp_sum(s);
+    if (lane == 0) y[i] = s;
+  }
+}
+
+// x = W^T y: row j of W^T over i >= j
+__global__ void k_trmv_upper(int64_t n, const double* __restrict__ WT, const double* __restrict__ y,
+                             double* __restrict__ x) {
+  const int lane = lane_id();
+  for (int64_t j = global_warp(); j < n; j += warp_stride()) {
+    double s = 0.0;
+    for (int64_t i = j + lane; i < n; i += 32) s += WT[j * n + i] * y[i];
+    s = warp_sum(s);
+    if (lane == 0) x[j] = s;
+  }
+}
+
+int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
+                        double* x) {
+  if (n <= 0) return SA_OK;
+  k_trmv_lower<<<warp_rows_grid(n), 256, 0, st>>>(n, W, b, y);
+  SA_LAUNCHED();
+  k_trmv_upper<<<warp_rows_grid(n), 256, 0, st>>>(n, WT, y, x);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+}  // namespace sa

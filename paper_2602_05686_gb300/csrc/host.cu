@@ -1,0 +1,764 @@
+// Host orchestration behind the C ABI: hierarchy setup (Sec. 2-3), the
+// V-cycle of Algorithm 1 with Chebyshev smoothing and the dense coarse
+// solve, and (flexible) CG (Sec. 4).  Every numerical step is a kernel; the
+// host only sequences launches and reads back sizes and convergence flags.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "mixed.cuh"
+#include "solve.cuh"
+
+namespace sa {
+
+struct Level {
+  int64_t n = 0, nnz = 0;
+  Buf<int64_t> rp;
+  Buf<int32_t> ci;
+  Buf<double> v;
+  Buf<double> diag, dinv;
+  int sw = 8;
+  // transfer operators (levels above the coarsest)
+  int64_t nc = 0, nnzP = 0, nnz_gc = 0;
+  int mis_rounds = 0;
+  Buf<int32_t> agg;
+  Buf<int64_t> Prp, Rrp;
+  Buf<int32_t> Pci, Rci;
+  Buf<double> Pv, Rv;
+  // auxiliary data (material / distance measures)
+  Buf<double> x, sigma, sinv;
+  // optional diagnostics
+  Buf<uint8_t> keep, root, dir;
+  double omega = 0, lam_omega = 0, lmax = 0, lmin = 0;
+  // FP64 V-cycle workspace
+  Buf<double> vb, vx, vx2, vr, vd;
+
+  CsrView A() const {
+    CsrView c;
+    c.n = n; c.nnz = nnz; c.rp = rp.p; c.ci = ci.p; c.v = v.p; c.sw = sw;
+    return c;
+  }
+  CsrView P() const {
+    CsrView c;
+    c.n = n; c.nnz = nnzP; c.rp = Prp.p; c.ci = Pci.p; c.v = Pv.p; c.sw = pick_sw(n, nnzP);
+    return c;
+  }
+  CsrView R() const {
+    CsrView c;
+    c.n = nc; c.nnz = nnzP; c.rp = Rrp.p; c.ci = Rci.p; c.v = Rv.p; c.sw = pick_sw(nc, nnzP);
+    return c;
+  }
+};
+
+}  // namespace sa
+
+struct sa_handle_s {
+  sa::Alloc al;
+  sa_options opt;
+  int dim = 0;
+  int64_t n = 0;
+  std::vector<std::unique_ptr<sa::Level>> lev;
+  sa::Buf<double> W, WT, cy;
+  int64_t nL = 0;
+  // Krylov workspace (FP64, fine level)
+  sa::Buf<double> r, p, q, rprev, t, part, dots, xb, bb;
+  sa::Buf<sa::CgScalars> cg;
+  double* host_pin = nullptr;  // pinned readback buffer
+  sa::MixedHierarchy* mixed = nullptr;
+  double setup_ms = 0;
+};
+
+namespace sa {
+
+static int level_diag(sa_handle h, Level& L, uint8_t* dir, int* err) {
+  SA_TRY(L.diag.alloc(&h->al, L.n));
+  SA_TRY(launch_dirichlet_diag(h->al.stream, L.n, L.rp.p, L.ci.p, L.v.p, dir, L.diag.p, err));
+  L.sw = pick_sw(L.n, L.nnz);
+  return SA_OK;
+}
+
+static int read_i64(cudaStream_t s, const int64_t* d, int64_t* h) { return copy_d2h(h, d, sizeof(int64_t), s); }
+
+// one coarsening step: level l -> level l+1.  *stop = 1 when level l is the
+// coarsest (stagnation or nothing to coarsen).
+static int coarsen(sa_handle h, int l, int* err, int* stop) {
+  Alloc& al = h->al;
+  cudaStream_t s = al.stream;
+  const sa_options& o = h->opt;
+  Level& L = *h->lev[l];
+  const int64_t n = L.n, nnz = L.nnz;
+  const uint8_t* dir = (l == 0) ? L.dir.p : nullptr;
+  const bool aux = o.measure != SA_MEASURE_CLASSICAL;
+  *stop = 0;
+
+  // a3/a4: strength + pointwise dropping; kept counts per row -> rpF
+  Buf<uint8_t> keep;
+  Buf<int64_t> rpF;
+  SA_TRY(keep.alloc(&al, nnz));
+  SA_TRY(rpF.alloc(&al, n + 1));
+  SA_TRY(memset_d(rpF.p, 0, sizeof(int64_t), s));
+  if (!aux) {
+    SA_TRY(launch_strength_classical(s, n, L.rp.p, L.ci.p, L.v.p, L.diag.p, dir, o.theta, keep.p, rpF.p));
+  } else {
+    Buf<double> w, D;
+    SA_TRY(w.alloc(&al, nnz));
+    SA_TRY(D.alloc(&al, n));
+    SA_TRY(launch_strength_material(s, h->dim, n, L.rp.p, L.ci.p, L.x.p, L.sinv.p, dir, o.theta, w.p, D.p, keep.p,
+                                    rpF.p));
+  }
+  SA_TRY(scan_inplace(al, rpF.p + 1, n));
+  int64_t nnzF = 0;
+  SA_TRY(read_i64(s, rpF.p + n, &nnzF));
+
+  // a5: filtered graph
+  Buf<int64_t> gcrp;
+  Buf<int32_t> gcci;
+  L.nnz_gc = nnzF - n;
+  SA_TRY(gcrp.alloc(&al, n + 1));
+  SA_TRY(gcci.alloc(&al, L.nnz_gc));
+  SA_TRY(launch_graph_rowptr(s, n, rpF.p, gcrp.p));
+  SA_TRY(launch_graph_compact(s, n, L.rp.p, L.ci.p, keep.p, gcrp.p, gcci.p));
+
+  // a6/a7: MIS-2 and aggregates
+  Buf<uint64_t> tag;
+  SA_TRY(tag.alloc(&al, n));
+  SA_TRY(run_mis2(al, n, gcrp.p, gcci.p, dir, l, o.seed, tag.p, &L.mis_rounds, 100000));
+  SA_TRY(L.agg.alloc(&al, n));
+  Buf<uint8_t> root;
+  if (o.keep_setup_data) SA_TRY(root.alloc(&al, n));
+  int64_t nc = 0;
+  SA_TRY(run_aggregate(al, n, gcrp.p, gcci.p, dir, tag.p, L.agg.p, o.keep_setup_data ? root.p : nullptr, &nc, err));
+  if (o.keep_setup_data) {
+    L.keep = std::move(keep);
+    L.root = std::move(root);
+  }
+  if (nc == 0 || (double)nc > 0.9 * (double)n) {
+    L.agg.release();
+    *stop = 1;
+    return SA_OK;
+  }
+  L.nc = nc;
+
+  // a8: tentative prolongator
+  Buf<int64_t> Trp;
+  Buf<int32_t> Tci;
+  Buf<double> Tv;
+  SA_TRY(Trp.alloc(&al, n + 1));
+  SA_TRY(memset_d(Trp.p, 0, sizeof(int64_t), s));
+  SA_TRY(launch_tentative_count(s, n, L.agg.p, Trp.p));
+  SA_TRY(scan_inplace(al, Trp.p + 1, n));
+  int64_t nnzT = 0;
+  SA_TRY(read_i64(s, Trp.p + n, &nnzT));
+  SA_TRY(Tci.alloc(&al, nnzT));
+  SA_TRY(Tv.alloc(&al, nnzT));
+  SA_TRY(launch_tentative(s, n, L.agg.p, Trp.p, Tci.p, Tv.p));
+
+  // a10: filtered matrix and 1-norm diagonal
+  Buf<int32_t> ciF;
+  Buf<double> vF, Dt, sc, scal;
+  SA_TRY(ciF.alloc(&al, nnzF));
+  SA_TRY(vF.alloc(&al, nnzF));
+  SA_TRY(Dt.alloc(&al, n));
+  const uint8_t* keep_p = o.keep_setup_data ? L.keep.p : keep.p;
+  SA_TRY(launch_filter(s, n, L.rp.p, L.ci.p, L.v.p, keep_p, rpF.p, ciF.p, vF.p, Dt.p));
+
+  // a11: omega = omega_sym / rho(D~^-1 A_F)
+  SA_TRY(sc.alloc(&al, n));
+  SA_TRY(scal.alloc(&al, 2));
+  SA_TRY(launch_rsqrt_scale(s, n, Dt.p, sc.p));
+  SA_TRY(run_power(al, n, rpF.p, ciF.p, vF.p, sc.p, o.power_iters, (uint32_t)(2 * l + 1), o.seed, scal.p));
+  SA_TRY(launch_omega(s, scal.p, o.omega_sym, scal.p + 1));
+
+  // a12: P = P^ - omega D~^-1 A_F P^
+  SA_TRY(run_spgemm(al, n, nc, rpF.p, ciF.p, vF.p, Trp.p, Tci.p, Tv.p, L.Prp, L.Pci, L.Pv, &L.nnzP));
+  SA_TRY(launch_smooth_p_values(s, n, L.Prp.p, L.Pci.p, L.Pv.p, L.agg.p, Dt.p, scal.p + 1, L.Pv.p));
+  double hs[2];
+  SA_TRY(copy_d2h(hs, scal.p, sizeof(hs), s));
+  L.lam_omega = hs[0];
+  L.omega = hs[1];
+
+  // a13: R = P^T, A_{l+1} = R (A P), exactly symmetric
+  SA_TRY(run_transpose(al, n, nc, L.Prp.p, L.Pci.p, L.Pv.p, L.Rrp, L.Rci, &L.Rv));
+  Buf<int64_t> APrp;
+  Buf<int32_t> APci;
+  Buf<double> APv;
+  int64_t nnzAP = 0;
+  SA_TRY(run_spgemm(al, n, nc, L.rp.p, L.ci.p, L.v.p, L.Prp.p, L.Pci.p, L.Pv.p, APrp, APci, APv, &nnzAP));
+  std::unique_ptr<Level> N(new Level());
+  N->n = nc;
+  SA_TRY(run_spgemm(al, nc, nc, L.Rrp.p, L.Rci.p, L.Rv.p, APrp.p, APci.p, APv.p, N->rp, N->ci, N->v, &N->nnz));
+  SA_TRY(launch_symmetrize(s, nc, N->rp.p, N->ci.p, N->v.p, err));
+  SA_TRY(level_diag(h, *N, nullptr, err));
+
+  // a9: coarse coordinates and tensors
+  if (aux) {
+    Buf<int64_t> Mrp;
+    Buf<int32_t> Mci;
+    SA_TRY(run_transpose(al, n, nc, Trp.p, Tci.p, nullptr, Mrp, Mci, nullptr));
+    const int kp = h->dim == 3 ? 6 : 3;
+    SA_TRY(N->x.alloc(&al, nc * h->dim));
+    SA_TRY(N->sigma.alloc(&al, nc * kp));
+    SA_TRY(N->sinv.alloc(&al, nc * kp));
+    SA_TRY(launch_coarse_aux(s, nc, h->dim, Mrp.p, Mci.p, L.x.p, L.sigma.p, N->x.p, N->sigma.p, N->sinv.p));
+  }
+  h->lev.push_back(std::move(N));
+  return SA_OK;
+}
+
+static int alloc_workspace(sa_handle h) {
+  Alloc& al = h->al;
+  for (auto& Lp : h->lev) {
+    Level& L = *Lp;
+    SA_TRY(L.vb.alloc(&al, L.n));
+    SA_TRY(L.vx.alloc(&al, L.n));
+    SA_TRY(L.vx2.alloc(&al, L.n));
+    SA_TRY(L.vr.alloc(&al, L.n));
+    SA_TRY(L.vd.alloc(&al, L.n));
+  }
+  const int64_t n = h->n;
+  SA_TRY(h->r.alloc(&al, n));
+  SA_TRY(h->p.alloc(&al, n));
+  SA_TRY(h->q.alloc(&al, n));
+  SA_TRY(h->rprev.alloc(&al, n));
+  SA_TRY(h->t.alloc(&al, n));
+  SA_TRY(h->xb.alloc(&al, n));
+  SA_TRY(h->bb.alloc(&al, n));
+  int64_t np = blocks_for(n * 32, 256) + RED_BLOCKS;
+  SA_TRY(h->part.alloc(&al, 3 * np));
+  SA_TRY(h->dots.alloc(&al, 8));
+  SA_TRY(h->cg.alloc(&al, 1));
+  SA_TRY(h->cy.alloc(&al, h->nL > 0 ? h->nL : 1));
+  return SA_OK;
+}
+
+// FP64 V-cycle (Algorithm 1) on level l: returns the buffer with x_l.
+static int vcycle64(sa_handle h, int l, const double* b, double** xout) {
+  cudaStream_t s = h->al.stream;
+  Level& L = *h->lev[l];
+  const int last = (int)h->lev.size() - 1;
+  if (l == last) {
+    SA_TRY(launch_coarse_solve(s, L.n, h->W.p, h->WT.p, b, h->cy.p, L.vx.p));
+    *xout = L.vx.p;
+    return SA_OK;
+  }
+  const int deg = h->opt.cheb_degree;
+  const double th = 0.5 * (L.lmax + L.lmin), de = 0.5 * (L.lmax - L.lmin);
+  const double s1 = th / de;
+  double* xa = L.vx.p;
+  double* xb = L.vx2.p;
+  const CsrView A = L.A();
+  // pre-smoothing from x = 0
+  SA_TRY(launch_cheb_first(s, L.n, L.dinv.p, b, 1.0 / th, xa, L.vd.p));
+  double rho = 1.0 / s1;
+  for (int k = 1; k < deg; ++k) {
+    double rn = 1.0 / (2.0 * s1 - rho);
+    SA_TRY(launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, rn * rho, 2.0 * rn / de, 0));
+    double* t = xa; xa = xb; xb = t;
+    rho = rn;
+  }
+  // restriction of the residual, coarse correction, prolongation
+  Level& C = *h->lev[l + 1];
+  SA_TRY(launch_residual(s, A, b, xa, L.vr.p));
+  SA_TRY(launch_spmv(s, L.R(), L.vr.p, C.vb.p));
+  double* xc = nullptr;
+  SA_TRY(vcycle64(h, l + 1, C.vb.p, &xc));
+  SA_TRY(launch_spmv_add(s, L.P(), xc, xa));
+  // post-smoothing
+  SA_TRY(launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, 0.0, 1.0 / th, 1));
+  { double* t = xa; xa = xb; xb = t; }
+  rho = 1.0 / s1;
+  for (int k = 1; k < deg; ++k) {
+    double rn = 1.0 / (2.0 * s1 - rho);
+    SA_TRY(launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, rn * rho, 2.0 * rn / de, 0));
+    double* t = xa; xa = xb; xb = t;
+    rho = rn;
+  }
+  *xout = xa;
+  return SA_OK;
+}
+
+static int precondition(sa_handle h, const double* r, double** z) {
+  if (h->opt.precision == SA_PREC_FP32_VCYCLE) return mixed_vcycle(h->mixed, h->al.stream, r, z);
+  return vcycle64(h, 0, r, z);
+}
+
+struct HostScal {
+  double rr, pad0, pad1;
+};
+
+// CG / flexible CG on device buffers b, x (Sec. 4)
+static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
+  cudaStream_t s = h->al.stream;
+  Level& L0 = *h->lev[0];
+  const CsrView A = L0.A();
+  const int64_t n = h->n;
+  const int flexible = h->opt.precision == SA_PREC_FP32_VCYCLE;
+  double* hp = h->host_pin;
+  auto t0 = std::chrono::steady_clock::now();
+  int status = SA_ERR_NO_CONVERGENCE, it = 0;
+  double r0 = 0.0;
+  SA_TRY(launch_residual(s, A, b, x, h->r.p));
+  SA_TRY(launch_dots(s, n, h->r.p, h->r.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p));
+  SA_CUDA(cudaMemcpyAsync(hp, h->dots.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SA_CUDA(cudaStreamSynchronize(s));
+  r0 = sqrt(hp[0]);
+  if (r0 > 0.0) {
+    double* z = nullptr;
+    SA_TRY(precondition(h, h->r.p, &z));
+    SA_TRY(launch_cg_pupdate(s, n, h->cg.p, z, h->p.p, 1));
+    SA_TRY(launch_dots(s, n, h->r.p, z, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p));
+    SA_TRY(launch_cg_beta(s, h->cg.p, h->dots.p, -1));
+    const int maxit = h->opt.maxit;
+    for (it = 1; it <= maxit; ++it) {
+      int np = 0;
+      SA_TRY(launch_spmv_dot(s, A, h->p.p, h->q.p, h->part.p, &np));
+      SA_TRY(launch_finish(s, h->part.p, np, h->dots.p));
+      SA_TRY(launch_cg_alpha(s, h->cg.p, h->dots.p));
+      SA_TRY(launch_cg_update(s, n, h->cg.p, h->p.p, h->q.p, x, h->r.p, flexible ? h->rprev.p : nullptr,
+                              h->part.p));
+      SA_TRY(launch_finish(s, h->part.p, RED_BLOCKS, h->dots.p + 4));
+      SA_CUDA(cudaMemcpyAsync(hp, h->dots.p + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+      SA_CUDA(cudaMemcpyAsync(hp + 1, &h->cg.p->breakdown, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SA_CUDA(cudaStreamSynchronize(s));
+      int brk = 0;
+      memcpy(&brk, hp + 1, sizeof(int));
+      if (brk) { status = SA_ERR_BREAKDOWN; break; }
+      if (sqrt(hp[0]) <= tol * r0) {
+        SA_TRY(launch_residual(s, A, b, x, h->t.p));
+        SA_TRY(launch_dots(s, n, h->t.p, h->t.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p + 4));
+        SA_CUDA(cudaMemcpyAsync(hp, h->dots.p + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SA_CUDA(cudaStreamSynchronize(s));
+        if (sqrt(hp[0]) <= tol * r0) { status = SA_OK; break; }
+        SA_CUDA(cudaMemcpyAsync(h->r.p, h->t.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      }
+      SA_TRY(precondition(h, h->r.p, &z));
+      SA_TRY(launch_dots(s, n, h->r.p, z, flexible ? z : nullptr, flexible ? h->rprev.p : nullptr, nullptr,
+                         nullptr, h->part.p, h->dots.p));
+      SA_TRY(launch_cg_beta(s, h->cg.p, h->dots.p, flexible));
+      SA_TRY(launch_cg_pupdate(s, n, h->cg.p, z, h->p.p, 0));
+    }
+    if (it > maxit) it = maxit;
+  } else {
+    status = SA_OK;
+  }
+  // true residual at exit
+  SA_TRY(launch_residual(s, A, b, x, h->t.p));
+  SA_TRY(launch_dots(s, n, h->t.p, h->t.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p + 4));
+  SA_CUDA(cudaMemcpyAsync(hp, h->dots.p + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SA_CUDA(cudaStreamSynchronize(s));
+  auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    info->iters = it;
+    info->rel_res_true = r0 > 0.0 ? sqrt(hp[0]) / r0 : 0.0;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->status = status;
+  }
+  return status;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static int upload(Alloc& al, Buf<T>& dst, const T* src, int64_t count) {
+  SA_TRY(dst.alloc(&al, count));
+  if (count > 0) SA_CUDA(cudaMemcpyAsync(dst.p, src, sizeof(T) * (size_t)count, cudaMemcpyDefault, al.stream));
+  return SA_OK;
+}
+
+static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
+  Alloc& al = h->al;
+  cudaStream_t s = al.stream;
+  auto t0 = std::chrono::steady_clock::now();
+  h->dim = P->dim;
+  h->n = P->n;
+  Buf<int> err;
+  SA_TRY(err.alloc(&al, 1));
+  SA_TRY(memset_d(err.p, 0, sizeof(int), s));
+  std::unique_ptr<Level> L0(new Level());
+  L0->n = P->n;
+  L0->nnz = P->nnz;
+  SA_TRY(upload(al, L0->rp, P->row_ptr, P->n + 1));
+  SA_TRY(upload(al, L0->ci, P->col, P->nnz));
+  SA_TRY(upload(al, L0->v, P->val, P->nnz));
+  SA_TRY(launch_validate_csr(s, P->n, P->nnz, L0->rp.p, L0->ci.p, err.p));
+  {
+    int e0 = 0;
+    SA_TRY(copy_d2h(&e0, err.p, sizeof(int), s));
+    if (e0) {
+      set_error_text("row pointers or column indices invalid (range, order)");
+      return SA_ERR_INVALID_ARG;
+    }
+  }
+  SA_TRY(L0->dir.alloc(&al, P->n));
+  SA_TRY(level_diag(h, *L0, L0->dir.p, err.p));
+  {
+    int e0 = 0;
+    SA_TRY(copy_d2h(&e0, err.p, sizeof(int), s));
+    if (e0) {
+      set_error_text("a row has no stored diagonal");
+      return SA_ERR_INVALID_ARG;
+    }
+  }
+  const int kp = P->dim == 3 ? 6 : 3;
+  if (o->measure != SA_MEASURE_CLASSICAL) {
+    SA_TRY(upload(al, L0->x, P->coords, P->n * P->dim));
+    SA_TRY(L0->sigma.alloc(&al, P->n * kp));
+    SA_TRY(L0->sinv.alloc(&al, P->n * kp));
+    if (o->measure == SA_MEASURE_DISTANCE) {
+      SA_TRY(launch_nodal_tensors(al, P->dim, P->n, 0, nullptr, 0, 0, nullptr, nullptr, L0->sigma.p, L0->sinv.p,
+                                  err.p));
+    } else if (P->tloc == SA_TENSOR_NODE) {
+      Buf<double> t;
+      SA_TRY(upload(al, t, P->tensors, P->n * kp));
+      SA_TRY(launch_nodal_tensors(al, P->dim, P->n, 0, t.p, 0, 0, nullptr, nullptr, L0->sigma.p, L0->sinv.p, err.p));
+    } else {
+      Buf<double> t, m;
+      Buf<int32_t> en;
+      SA_TRY(upload(al, t, P->tensors, P->n_elem * kp));
+      SA_TRY(upload(al, m, P->elem_measure, P->n_elem));
+      SA_TRY(upload(al, en, P->elem_nodes, P->n_elem * P->nodes_per_elem));
+      SA_TRY(launch_nodal_tensors(al, P->dim, P->n, 1, t.p, P->n_elem, P->nodes_per_elem, en.p, m.p, L0->sigma.p,
+                                  L0->sinv.p, err.p));
+    }
+  }
+  h->lev.push_back(std::move(L0));
+  for (int l = 0;; ++l) {
+    Level& L = *h->lev[l];
+    if (L.n <= o->max_coarse || l + 1 >= o->max_levels) break;
+    int stop = 0;
+    SA_TRY(coarsen(h, l, err.p, &stop));
+    if (stop) break;
+  }
+  int h_err = 0;
+  SA_TRY(copy_d2h(&h_err, err.p, sizeof(int), s));
+  if (h_err) {
+    char msg[64];
+    snprintf(msg, sizeof(msg), "setup validation flags 0x%x", h_err);
+    set_error_text(msg);
+    return SA_ERR_INVALID_ARG;
+  }
+  const int nlev = (int)h->lev.size();
+  Level& Lc = *h->lev[nlev - 1];
+  if (Lc.n > 16384) return SA_ERR_STAGNATION;
+  // a15: smoother data (Chebyshev bounds from 10 power steps on D^-1/2 A D^-1/2)
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = *h->lev[l];
+    SA_TRY(L.dinv.alloc(&al, L.n));
+    SA_TRY(launch_reciprocal(s, L.n, L.diag.p, L.dinv.p));
+    if (l + 1 < nlev) {
+      Buf<double> sc, lam;
+      SA_TRY(sc.alloc(&al, L.n));
+      SA_TRY(lam.alloc(&al, 1));
+      SA_TRY(launch_rsqrt_scale(s, L.n, L.diag.p, sc.p));
+      SA_TRY(run_power(al, L.n, L.rp.p, L.ci.p, L.v.p, sc.p, o->power_iters, (uint32_t)(2 * l + 2), o->seed, lam.p));
+      double hl = 0;
+      SA_TRY(copy_d2h(&hl, lam.p, sizeof(double), s));
+      L.lmax = o->cheb_boost * hl;
+      L.lmin = L.lmax / o->cheb_ratio;
+    }
+  }
+  h->nL = Lc.n;
+  SA_TRY(run_dense_inverse_factor(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT));
+  SA_TRY(alloc_workspace(h));
+  if (o->precision == SA_PREC_FP32_VCYCLE) {
+    std::vector<MixedLevelIn> in(nlev);
+    for (int l = 0; l < nlev; ++l) {
+      Level& L = *h->lev[l];
+      in[l].n = L.n; in[l].nnz = L.nnz; in[l].rp = L.rp.p; in[l].ci = L.ci.p; in[l].v = L.v.p;
+      in[l].diag = L.diag.p; in[l].lmax = L.lmax; in[l].lmin = L.lmin;
+      in[l].nc = (l + 1 < nlev) ? L.nc : 0; in[l].nnzP = L.nnzP;
+      in[l].Prp = L.Prp.p; in[l].Pci = L.Pci.p; in[l].Pv = L.Pv.p;
+      in[l].Rrp = L.Rrp.p; in[l].Rci = L.Rci.p; in[l].Rv = L.Rv.p;
+    }
+    SA_TRY(mixed_build(al, in.data(), nlev, h->opt.cheb_degree, h->W.p, h->WT.p, &h->mixed));
+  }
+  SA_CUDA(cudaStreamSynchronize(s));
+  auto t1 = std::chrono::steady_clock::now();
+  h->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  return SA_OK;
+}
+
+}  // namespace sa
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int sa_default_options(sa_options* o) {
+  if (!o) return SA_ERR_INVALID_ARG;
+  memset(o, 0, sizeof(*o));
+  o->theta = 0.08;
+  o->measure = SA_MEASURE_MATERIAL;
+  o->precision = SA_PREC_FP64;
+  o->max_coarse = 5000;
+  o->max_levels = 10;
+  o->cheb_degree = 2;
+  o->cheb_ratio = 30.0;
+  o->cheb_boost = 1.1;
+  o->power_iters = 10;
+  o->omega_sym = 4.0 / 3.0;
+  o->seed = 0;
+  o->maxit = 500;
+  return SA_OK;
+}
+
+static int validate(const sa_problem* P, const sa_options* o) {
+  if (!P || !o) return SA_ERR_INVALID_ARG;
+  if (P->dim != 2 && P->dim != 3) return SA_ERR_INVALID_ARG;
+  if (P->n <= 0 || P->nnz < P->n || P->n >= (int64_t)0x7fffffff) return SA_ERR_INVALID_ARG;
+  if (!P->row_ptr || !P->col || !P->val) return SA_ERR_INVALID_ARG;
+  if ((int)o->measure < 0 || (int)o->measure > 2) return SA_ERR_INVALID_ARG;
+  if ((int)o->precision < 0 || (int)o->precision > 1) return SA_ERR_INVALID_ARG;
+  if (o->measure != SA_MEASURE_CLASSICAL && !P->coords) return SA_ERR_INVALID_ARG;
+  if (o->measure == SA_MEASURE_MATERIAL) {
+    if (!P->tensors) return SA_ERR_INVALID_ARG;
+    if (P->tloc == SA_TENSOR_ELEMENT &&
+        (P->n_elem <= 0 || P->nodes_per_elem <= 0 || !P->elem_nodes || !P->elem_measure))
+      return SA_ERR_INVALID_ARG;
+  }
+  if (!(o->theta >= 0.0) || o->cheb_degree < 1 || o->power_iters < 1 || o->max_levels < 1 || o->maxit < 1 ||
+      !(o->cheb_ratio > 1.0) || !(o->cheb_boost > 0.0) || o->max_coarse < 1)
+    return SA_ERR_INVALID_ARG;
+  return SA_OK;
+}
+
+int sa_setup(const sa_problem* prob, const sa_options* opt, sa_handle* out) {
+  if (!out) return SA_ERR_INVALID_ARG;
+  *out = nullptr;
+  int st = validate(prob, opt);
+  if (st) return st;
+  sa_handle h = new (std::nothrow) sa_handle_s();
+  if (!h) return SA_ERR_OOM;
+  h->opt = *opt;
+  h->al.stream = (cudaStream_t)opt->stream;
+  h->al.fn_alloc = opt->alloc;
+  h->al.fn_free = opt->dealloc;
+  h->al.ctx = opt->alloc_ctx;
+  if (cudaMallocHost(&h->host_pin, 64) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return SA_ERR_OOM;
+  }
+  st = sa::setup_impl(prob, opt, h);
+  if (st != SA_OK) {
+    cudaStreamSynchronize(h->al.stream);
+    sa_free(h);
+    return st;
+  }
+  *out = h;
+  return SA_OK;
+}
+
+int sa_solve(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
+  if (!h || !b || !x || !(tol > 0.0)) return SA_ERR_INVALID_ARG;
+  cudaStream_t s = h->al.stream;
+  const int64_t n = h->n;
+  const bool dev = sa::is_device_ptr(b) && sa::is_device_ptr(x);
+  const double* bd = b;
+  double* xd = x;
+  if (!dev) {
+    SA_CUDA(cudaMemcpyAsync(h->bb.p, b, sizeof(double) * n, cudaMemcpyDefault, s));
+    SA_CUDA(cudaMemcpyAsync(h->xb.p, x, sizeof(double) * n, cudaMemcpyDefault, s));
+    bd = h->bb.p;
+    xd = h->xb.p;
+  }
+  int st = sa::cg_device(h, bd, xd, tol, info);
+  if (!dev) {
+    SA_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDefault, s));
+    SA_CUDA(cudaStreamSynchronize(s));
+  }
+  return st;
+}
+
+int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos) {
+  if (!h || k < 0 || (k > 0 && (!B || !X))) return SA_ERR_INVALID_ARG;
+  int worst = SA_OK;
+  for (int c = 0; c < k; ++c) {
+    int st = sa_solve(h, B + (int64_t)c * h->n, X + (int64_t)c * h->n, tol, infos ? infos + c : nullptr);
+    if (st != SA_OK && worst == SA_OK) worst = st;
+    if (st != SA_OK && st != SA_ERR_NO_CONVERGENCE) return st;
+  }
+  return worst;
+}
+
+int sa_vcycle(sa_handle h, const double* r, double* z) {
+  if (!h || !r || !z) return SA_ERR_INVALID_ARG;
+  double* zz = nullptr;
+  SA_TRY(sa::precondition(h, r, &zz));
+  SA_CUDA(cudaMemcpyAsync(z, zz, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->al.stream));
+  SA_CUDA(cudaStreamSynchronize(h->al.stream));
+  return SA_OK;
+}
+
+int sa_hierarchy_stats(sa_handle h, int* levels, int64_t* n_l, int64_t* nnz_l, double* op_complexity,
+                       int64_t* device_bytes) {
+  if (!h) return SA_ERR_INVALID_ARG;
+  const int nlev = (int)h->lev.size();
+  if (levels) *levels = nlev;
+  double tot = 0;
+  for (int l = 0; l < nlev && l < 32; ++l) {
+    if (n_l) n_l[l] = h->lev[l]->n;
+    if (nnz_l) nnz_l[l] = h->lev[l]->nnz;
+    tot += (double)h->lev[l]->nnz;
+  }
+  if (op_complexity) *op_complexity = tot / (double)h->lev[0]->nnz;
+  if (device_bytes) *device_bytes = h->al.live_bytes;
+  return SA_OK;
+}
+
+int sa_level_sizes(sa_handle h, int l, int64_t* out) {
+  if (!h || !out || l < 0 || l >= (int)h->lev.size()) return SA_ERR_INVALID_ARG;
+  const sa::Level& L = *h->lev[l];
+  const bool has_p = l + 1 < (int)h->lev.size();
+  out[0] = L.n;
+  out[1] = L.nnz;
+  out[2] = has_p ? L.nnzP : 0;
+  out[3] = has_p ? L.nc : 0;
+  out[4] = L.nnz_gc;
+  return SA_OK;
+}
+
+int sa_export_level(sa_handle h, int l, int32_t* agg, int64_t* P_rowptr, int32_t* P_col, double* P_val,
+                    int64_t* A_rowptr, int32_t* A_col, double* A_val) {
+  if (!h || l < 0 || l >= (int)h->lev.size()) return SA_ERR_INVALID_ARG;
+  const sa::Level& L = *h->lev[l];
+  cudaStream_t s = h->al.stream;
+  const bool has_p = l + 1 < (int)h->lev.size();
+  auto d2h = [&](void* dst, const void* src, size_t bytes) -> int {
+    if (dst && src && bytes) SA_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+    return SA_OK;
+  };
+  SA_TRY(d2h(A_rowptr, L.rp.p, sizeof(int64_t) * (L.n + 1)));
+  SA_TRY(d2h(A_col, L.ci.p, sizeof(int32_t) * L.nnz));
+  SA_TRY(d2h(A_val, L.v.p, sizeof(double) * L.nnz));
+  if (has_p) {
+    SA_TRY(d2h(agg, L.agg.p, sizeof(int32_t) * L.n));
+    SA_TRY(d2h(P_rowptr, L.Prp.p, sizeof(int64_t) * (L.n + 1)));
+    SA_TRY(d2h(P_col, L.Pci.p, sizeof(int32_t) * L.nnzP));
+    SA_TRY(d2h(P_val, L.Pv.p, sizeof(double) * L.nnzP));
+  }
+  SA_CUDA(cudaStreamSynchronize(s));
+  return SA_OK;
+}
+
+int sa_export_strength(sa_handle h, int l, uint8_t* keep, uint8_t* root, uint8_t* dirichlet, double* coords,
+                       double* sigma_inv, double* scalars) {
+  if (!h || l < 0 || l >= (int)h->lev.size()) return SA_ERR_INVALID_ARG;
+  const sa::Level& L = *h->lev[l];
+  cudaStream_t s = h->al.stream;
+  const int kp = h->dim == 3 ? 6 : 3;
+  auto d2h = [&](void* dst, const void* src, size_t bytes) -> int {
+    if (dst && src && bytes) SA_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+    return SA_OK;
+  };
+  if ((keep && !L.keep.p) || (root && !L.root.p)) {
+    if (l + 1 < (int)h->lev.size() || keep || root) {
+      // diagnostics were not kept (keep_setup_data = 0) or l is the coarsest
+      if (!h->opt.keep_setup_data) return SA_ERR_INVALID_ARG;
+    }
+  }
+  SA_TRY(d2h(keep, L.keep.p, L.nnz));
+  SA_TRY(d2h(root, L.root.p, L.n));
+  if (dirichlet) {
+    if (L.dir.p) SA_TRY(d2h(dirichlet, L.dir.p, L.n));
+    else memset(dirichlet, 0, (size_t)L.n);
+  }
+  SA_TRY(d2h(coords, L.x.p, sizeof(double) * L.n * h->dim));
+  SA_TRY(d2h(sigma_inv, L.sinv.p, sizeof(double) * L.n * kp));
+  SA_CUDA(cudaStreamSynchronize(s));
+  if (scalars) {
+    scalars[0] = L.omega;
+    scalars[1] = L.lam_omega;
+    scalars[2] = L.lmax;
+    scalars[3] = L.lmin;
+  }
+  return SA_OK;
+}
+
+int sa_free(sa_handle h) {
+  if (!h) return SA_OK;
+  if (h->mixed) sa::mixed_free(h->mixed);
+  h->lev.clear();
+  h->W.release();
+  h->WT.release();
+  h->cy.release();
+  h->r.release(); h->p.release(); h->q.release(); h->rprev.release(); h->t.release();
+  h->part.release(); h->dots.release(); h->xb.release(); h->bb.release(); h->cg.release();
+  cudaStreamSynchronize(h->al.stream);
+  if (h->host_pin) cudaFreeHost(h->host_pin);
+  delete h;
+  return SA_OK;
+}
+
+const char* sa_status_string(int st) {
+  switch (st) {
+    case SA_OK: return "ok";
+    case SA_ERR_INVALID_ARG: return "invalid argument";
+    case SA_ERR_OOM: return "out of device memory";
+    case SA_ERR_CUDA: return "CUDA error";
+    case SA_ERR_NOT_SPD: return "coarse operator not SPD";
+    case SA_ERR_STAGNATION: return "coarsening stagnated";
+    case SA_ERR_NO_CONVERGENCE: return "no convergence within maxit";
+    case SA_ERR_BREAKDOWN: return "CG breakdown";
+    case SA_ERR_CAPACITY: return "internal capacity exceeded";
+    default: return "unknown status";
+  }
+}
+
+int sa_strength(sa_measure measure, int dim, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                const double* val, const double* coords, const double* sigma_inv, const uint8_t* dirichlet,
+                double theta, uint8_t* keep, void* stream) {
+  if (n < 0 || nnz < 0 || !row_ptr || !col || !keep || (dim != 2 && dim != 3)) return SA_ERR_INVALID_ARG;
+  if (measure == SA_MEASURE_CLASSICAL && !val) return SA_ERR_INVALID_ARG;
+  if (measure != SA_MEASURE_CLASSICAL && !coords) return SA_ERR_INVALID_ARG;
+  if (measure == SA_MEASURE_MATERIAL && !sigma_inv) return SA_ERR_INVALID_ARG;
+  if ((int)measure < 0 || (int)measure > 2) return SA_ERR_INVALID_ARG;
+  sa::Alloc al;
+  al.stream = (cudaStream_t)stream;
+  cudaStream_t s = al.stream;
+  sa::Buf<int64_t> cnt;
+  SA_TRY(cnt.alloc(&al, n + 1));
+  if (measure == SA_MEASURE_CLASSICAL) {
+    sa::Buf<double> diag;
+    sa::Buf<int> err;
+    SA_TRY(diag.alloc(&al, n));
+    SA_TRY(err.alloc(&al, 1));
+    SA_TRY(sa::memset_d(err.p, 0, sizeof(int), s));
+    SA_TRY(sa::launch_dirichlet_diag(s, n, row_ptr, col, val, nullptr, diag.p, err.p));
+    SA_TRY(sa::launch_strength_classical(s, n, row_ptr, col, val, diag.p, dirichlet, theta, keep, cnt.p));
+  } else {
+    sa::Buf<double> w, D, si, sg;
+    sa::Buf<int> err;
+    SA_TRY(w.alloc(&al, nnz));
+    SA_TRY(D.alloc(&al, n));
+    const double* sinv = sigma_inv;
+    if (measure == SA_MEASURE_DISTANCE) {
+      const int kp = dim == 3 ? 6 : 3;
+      SA_TRY(si.alloc(&al, n * kp));
+      SA_TRY(sg.alloc(&al, n * kp));
+      SA_TRY(err.alloc(&al, 1));
+      SA_TRY(sa::launch_nodal_tensors(al, dim, n, 0, nullptr, 0, 0, nullptr, nullptr, sg.p, si.p, err.p));
+      sinv = si.p;
+    }
+    SA_TRY(sa::launch_strength_material(s, dim, n, row_ptr, col, coords, sinv, dirichlet, theta, w.p, D.p, keep,
+                                        cnt.p));
+  }
+  return SA_OK;
+}
+
+}  // extern "C"

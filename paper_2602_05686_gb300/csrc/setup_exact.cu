@@ -1,0 +1,491 @@
+// Setup kernels whose floating-point results must be bitwise reproducible:
+// Dirichlet detection, nodal tensors and their inverses, the two strength
+// measures with pointwise dropping, the filtered matrix with lumping and the
+// 1-norm diagonal, coarse auxiliary data, and the smoothed prolongator
+// values.  This translation unit is compiled with -fmad=false: every
+// expression below is evaluated with separately rounded IEEE operations in
+// the order written, and every sum runs in ascending column / index order.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sa {
+
+// ---------------------------------------------------------------------------
+// a1. Dirichlet detection + diagonal (Sec. 3, Fig. 4 caption: Dirichlet
+// nodes are isolated in the filtered graph).  Warp per row.  A row is
+// Dirichlet iff every stored off-diagonal value is exactly zero.  err bit 1:
+// a row without a stored diagonal.
+// ---------------------------------------------------------------------------
+__global__ void k_dirichlet_diag(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const double* __restrict__ v, uint8_t* __restrict__ dir,
+                                 double* __restrict__ diag, int* __restrict__ err) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    bool offnz = false, has_d = false;
+    double d = 0.0;
+    for (int64_t p = b + lane; p < e; p += 32) {
+      int32_t j = ci[p];
+      double a = v[p];
+      if (j == (int32_t)i) { d = a; has_d = true; }
+      else if (a != 0.0) offnz = true;
+    }
+    unsigned anyoff = __ballot_sync(FULL, offnz);
+    unsigned hd = __ballot_sync(FULL, has_d);
+    // exactly one lane holds the diagonal
+    double dd = hd ? __shfl_sync(FULL, d, __ffs(hd) - 1) : 0.0;
+    if (lane == 0) {
+      if (dir) dir[i] = anyoff ? 0 : 1;
+      diag[i] = dd;
+      if (!hd) atomicOr(err, 1);
+    }
+  }
+}
+
+// input check of the level-0 CSR: row pointers monotone from 0 to nnz,
+// columns in [0, n) and strictly ascending in each row.  err bit 32.
+__global__ void k_validate_csr(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                               const int32_t* __restrict__ ci, int* __restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = rp[i], e = rp[i + 1];
+  if ((i == 0 && b != 0) || (i == n - 1 && e != nnz) || e < b || b < 0 || e > nnz) {
+    atomicOr(err, 32);
+    return;
+  }
+  int32_t prev = -1;
+  for (int64_t p = b; p < e; ++p) {
+    int32_t j = ci[p];
+    if (j <= prev || j < 0 || (int64_t)j >= n) { atomicOr(err, 32); return; }
+    prev = j;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a2. nodal tensors and inverses (Sec. 3: Clement interpolant of an
+// elementwise tensor; inverse by adjugate / determinant)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void invert_packed(int dim, const double* t, double* si) {
+  if (dim == 2) {
+    double det = t[0] * t[1] - t[2] * t[2];
+    si[0] = t[1] / det;
+    si[1] = t[0] / det;
+    si[2] = -t[2] / det;
+  } else {
+    double a = t[0], b = t[1], c = t[2], d = t[3], e = t[4], f = t[5];
+    double c00 = b * c - f * f;
+    double c11 = a * c - e * e;
+    double c22 = a * b - d * d;
+    double c01 = e * f - d * c;
+    double c02 = d * f - b * e;
+    double c12 = d * e - a * f;
+    double det = a * c00 + d * c01 + e * c02;
+    si[0] = c00 / det;
+    si[1] = c11 / det;
+    si[2] = c22 / det;
+    si[3] = c01 / det;
+    si[4] = c02 / det;
+    si[5] = c12 / det;
+  }
+}
+
+__global__ void k_node_elem_count(int64_t ne, int npe, const int32_t* __restrict__ en, int64_t n,
+                                  int64_t* __restrict__ cnt, int* __restrict__ err) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ne * npe) return;
+  int32_t node = en[t];
+  if (node < 0 || node >= n) { atomicOr(err, 2); return; }
+  atomicAdd((unsigned long long*)&cnt[node + 1], 1ull);
+}
+
+__global__ void k_node_elem_fill(int64_t ne, int npe, const int32_t* __restrict__ en, int64_t n,
+                                 const int64_t* __restrict__ off, int* __restrict__ cursor,
+                                 int32_t* __restrict__ list) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ne * npe) return;
+  int32_t node = en[t];
+  if (node < 0 || node >= n) return;
+  int pos = atomicAdd(&cursor[node], 1);
+  list[off[node] + pos] = (int32_t)(t / npe);
+}
+
+// thread per node: sort incident elements ascending, average, invert
+__global__ void k_node_tensor_from_elems(int64_t n, int dim, const int64_t* __restrict__ off,
+                                         int32_t* __restrict__ list, const double* __restrict__ meas,
+                                         const double* __restrict__ et, double* __restrict__ sigma,
+                                         double* __restrict__ sinv, int* __restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int kp = dim == 3 ? 6 : 3;
+  const int64_t b = off[i], e = off[i + 1];
+  for (int64_t p = b + 1; p < e; ++p) {  // insertion sort of the node's own segment
+    int32_t key = list[p];
+    int64_t q = p - 1;
+    while (q >= b && list[q] > key) { list[q + 1] = list[q]; --q; }
+    list[q + 1] = key;
+  }
+  double num[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double den = 0.0;
+  for (int64_t p = b; p < e; ++p) {
+    int64_t el = list[p];
+    double m = meas[el];
+    for (int c = 0; c < kp; ++c) num[c] += m * et[el * kp + c];
+    den += m;
+  }
+  if (den == 0.0) atomicOr(err, 4);
+  double s[6];
+  for (int c = 0; c < kp; ++c) {
+    s[c] = num[c] / den;
+    sigma[i * kp + c] = s[c];
+  }
+  double si[6];
+  invert_packed(dim, s, si);
+  for (int c = 0; c < kp; ++c) sinv[i * kp + c] = si[c];
+}
+
+// per-node tensors given (copy) or sigma = I (distance Laplacian); invert
+__global__ void k_node_tensor_direct(int64_t n, int dim, const double* __restrict__ given,
+                                     double* __restrict__ sigma, double* __restrict__ sinv) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int kp = dim == 3 ? 6 : 3;
+  double s[6];
+  for (int c = 0; c < kp; ++c) {
+    s[c] = given ? given[i * kp + c] : (c < dim ? 1.0 : 0.0);
+    sigma[i * kp + c] = s[c];
+  }
+  double si[6];
+  invert_packed(dim, s, si);
+  for (int c = 0; c < kp; ++c) sinv[i * kp + c] = si[c];
+}
+
+// ---------------------------------------------------------------------------
+// a3. classical measure + pointwise dropping (Sec. 2.1):
+//   keep_ij <=> a_ij*a_ij >= (theta*theta) * |a_ii*a_jj|, diagonal kept,
+//   Dirichlet nodes excluded.  Warp per row; also counts kept entries per
+//   row (diagonal included) into cnt[i+1].
+// ---------------------------------------------------------------------------
+__global__ void k_strength_classical(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const double* __restrict__ v, const double* __restrict__ diag,
+                                     const uint8_t* __restrict__ dir, double t2, uint8_t* __restrict__ keep,
+                                     int64_t* __restrict__ cnt) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    const double di = diag[i];
+    const bool diri = dir && dir[i];
+    int kept = 0;
+    for (int64_t p = b + lane; p < e; p += 32) {
+      int32_t j = ci[p];
+      uint8_t k;
+      if (j == (int32_t)i) k = 1;
+      else if (diri || (dir && dir[j])) k = 0;
+      else {
+        double a = v[p];
+        k = (a * a >= t2 * fabs(di * diag[j])) ? 1 : 0;
+      }
+      keep[p] = k;
+      kept += k;
+    }
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
+    if (lane == 0) cnt[i + 1] = kept;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a4. material-aware distance Laplacian (Sec. 2.1 distance Laplacian,
+// Sec. 3 material distance with max symmetrisation):
+//   w_ij = 1 / max(d^T sinv_i d, d^T sinv_j d), d = x_i - x_j,
+//   D_i = sum_{j != i} w_ij (ascending column order).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double quad_form(int dim, const double* __restrict__ si, const double* d) {
+  if (dim == 2)
+    return d[0] * (si[0] * d[0] + si[2] * d[1]) + d[1] * (si[2] * d[0] + si[1] * d[1]);
+  return d[0] * (si[0] * d[0] + si[3] * d[1] + si[4] * d[2]) +
+         d[1] * (si[3] * d[0] + si[1] * d[1] + si[5] * d[2]) +
+         d[2] * (si[4] * d[0] + si[5] * d[1] + si[2] * d[2]);
+}
+
+template <int DIM>
+__global__ void k_material_w(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ x, const double* __restrict__ sinv,
+                             double* __restrict__ w, double* __restrict__ D) {
+  constexpr int KP = DIM == 3 ? 6 : 3;
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    double xi[3], si_i[KP];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) xi[c] = x[i * DIM + c];
+#pragma unroll
+    for (int c = 0; c < KP; ++c) si_i[c] = sinv[i * KP + c];
+    double acc = 0.0;
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+      const int64_t p = p0 + lane;
+      double wv = 0.0;
+      bool off = false;
+      if (p < e) {
+        int32_t j = ci[p];
+        if (j != (int32_t)i) {
+          off = true;
+          double d[3], sj[KP];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) d[c] = xi[c] - x[(int64_t)j * DIM + c];
+#pragma unroll
+          for (int c = 0; c < KP; ++c) sj[c] = sinv[(int64_t)j * KP + c];
+          double qij = quad_form(DIM, si_i, d);
+          double qji = quad_form(DIM, sj, d);
+          double m = qij > qji ? qij : qji;
+          wv = 1.0 / m;
+        }
+        w[p] = wv;
+      }
+      // ordered sum over this chunk (ascending p)
+      unsigned offm = __ballot_sync(FULL, off);
+      for (int t = 0; t < 32; ++t) {
+        double u = __shfl_sync(FULL, wv, t);
+        if ((offm >> t) & 1u) acc += u;
+      }
+    }
+    if (lane == 0) D[i] = acc;
+  }
+}
+
+// keep_ij <=> w_ij*w_ij >= (theta*theta) * (D_i*D_j)
+__global__ void k_material_keep(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ w, const double* __restrict__ D,
+                                const uint8_t* __restrict__ dir, double t2, uint8_t* __restrict__ keep,
+                                int64_t* __restrict__ cnt) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    const double Di = D[i];
+    const bool diri = dir && dir[i];
+    int kept = 0;
+    for (int64_t p = b + lane; p < e; p += 32) {
+      int32_t j = ci[p];
+      uint8_t k;
+      if (j == (int32_t)i) k = 1;
+      else if (diri || (dir && dir[j])) k = 0;
+      else {
+        double wv = w[p];
+        k = (wv * wv >= t2 * (Di * D[j])) ? 1 : 0;
+      }
+      keep[p] = k;
+      kept += k;
+    }
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
+    if (lane == 0 && cnt) cnt[i + 1] = kept;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a10. filtered matrix A_F and 1-norm diagonal (Sec. 2.2, Eqs.
+// filtered_matrix and 1_norm_diagonal).  Warp per row.  rpF is the scan of
+// the kept counts.  A row whose filtered 1-norm is <= 1e-12 times the 1-norm
+// of its row of A (every off-diagonal dropped, lumped row sum ~ 0) gets
+// Dt = +inf: it is not smoothed.
+// ---------------------------------------------------------------------------
+__global__ void k_filter(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const double* __restrict__ v, const uint8_t* __restrict__ keep,
+                         const int64_t* __restrict__ rpF, int32_t* __restrict__ ciF, double* __restrict__ vF,
+                         double* __restrict__ Dt) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    // lumped diagonal: a_ii, then the dropped entries in ascending order
+    double dg = 0.0;
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+      int64_t p = p0 + lane;
+      bool isd = false;
+      double a = 0.0;
+      if (p < e) { isd = ci[p] == (int32_t)i; a = v[p]; }
+      unsigned m = __ballot_sync(FULL, isd);
+      if (m) dg = __shfl_sync(FULL, a, __ffs(m) - 1);
+    }
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+      int64_t p = p0 + lane;
+      bool drop = false;
+      double a = 0.0;
+      if (p < e) { drop = ci[p] != (int32_t)i && !keep[p]; a = v[p]; }
+      unsigned m = __ballot_sync(FULL, drop);
+      for (int t = 0; t < 32; ++t) {
+        double u = __shfl_sync(FULL, a, t);
+        if ((m >> t) & 1u) dg += u;
+      }
+    }
+    // write the filtered row and accumulate both 1-norms in ascending order
+    int64_t out = rpF[i];
+    double s = 0.0, a1 = 0.0;
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+      int64_t p = p0 + lane;
+      bool in = p < e;
+      int32_t j = in ? ci[p] : 0;
+      bool isd = in && j == (int32_t)i;
+      bool kp = in && (isd || keep[p]);
+      double a = in ? v[p] : 0.0;
+      double fv = isd ? dg : a;
+      unsigned km = __ballot_sync(FULL, kp);
+      unsigned im = __ballot_sync(FULL, in);
+      if (kp) {
+        int pos = __popc(km & ((1u << lane) - 1u));
+        ciF[out + pos] = j;
+        vF[out + pos] = fv;
+      }
+      for (int t = 0; t < 32; ++t) {
+        double uf = __shfl_sync(FULL, fabs(fv), t);
+        double ua = __shfl_sync(FULL, fabs(a), t);
+        if ((km >> t) & 1u) s += uf;
+        if ((im >> t) & 1u) a1 += ua;
+      }
+      out += __popc(km);
+    }
+    if (lane == 0) Dt[i] = (s <= 1e-12 * a1) ? INFINITY : s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a9. coarse coordinates and tensors (Sec. 3, Eq. auxiliary_transfer):
+// means over the aggregate members, summed in ascending fine index (mlist is
+// sorted per aggregate); the coarse inverse tensors follow by inversion.
+// ---------------------------------------------------------------------------
+__global__ void k_coarse_aux(int64_t nc, int dim, const int64_t* __restrict__ mrp, const int32_t* __restrict__ mlist,
+                             const double* __restrict__ x, const double* __restrict__ sigma,
+                             double* __restrict__ xc, double* __restrict__ sc, double* __restrict__ sic) {
+  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nc) return;
+  const int kp = dim == 3 ? 6 : 3;
+  double sx[3] = {0.0, 0.0, 0.0}, ss[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double cnt = 0.0;
+  for (int64_t p = mrp[a]; p < mrp[a + 1]; ++p) {
+    int64_t i = mlist[p];
+    for (int c = 0; c < dim; ++c) sx[c] += x[i * dim + c];
+    for (int c = 0; c < kp; ++c) ss[c] += sigma[i * kp + c];
+    cnt += 1.0;
+  }
+  for (int c = 0; c < dim; ++c) xc[a * dim + c] = sx[c] / cnt;
+  double s[6];
+  for (int c = 0; c < kp; ++c) {
+    s[c] = ss[c] / cnt;
+    sc[a * kp + c] = s[c];
+  }
+  double si[6];
+  invert_packed(dim, s, si);
+  for (int c = 0; c < kp; ++c) sic[a * kp + c] = si[c];
+}
+
+// ---------------------------------------------------------------------------
+// a12. smoothed prolongator values from T = A_F P^ (Sec. 2.2):
+//   c_i = omega / Dt_i,  P_ij = [j == agg(i)] - c_i * T_ij
+// P shares the pattern of T.  omega is read from device memory.
+// ---------------------------------------------------------------------------
+__global__ void k_smooth_p_values(int64_t n, const int64_t* __restrict__ rpT, const int32_t* __restrict__ ciT,
+                                  const double* __restrict__ vT, const int32_t* __restrict__ agg,
+                                  const double* __restrict__ Dt, const double* __restrict__ omega_p,
+                                  double* __restrict__ vP) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double omega = *omega_p;
+  const double c = omega / Dt[i];
+  const int32_t ai = agg[i];
+  for (int64_t p = rpT[i]; p < rpT[i + 1]; ++p) {
+    double t = vT[p];
+    vP[p] = (ciT[p] == ai) ? 1.0 - c * t : -(c * t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+int launch_dirichlet_diag(cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                          uint8_t* dir, double* diag, int* err) {
+  if (n <= 0) return SA_OK;
+  k_dirichlet_diag<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, v, dir, diag, err);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_validate_csr(cudaStream_t s, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, int* err) {
+  if (n <= 0) return SA_OK;
+  k_validate_csr<<<blocks_for(n, 256), 256, 0, s>>>(n, nnz, rp, ci, err);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_nodal_tensors(Alloc& al, int dim, int64_t n, int tloc, const double* tensors, int64_t ne, int npe,
+                         const int32_t* en, const double* meas, double* sigma, double* sinv, int* err) {
+  cudaStream_t s = al.stream;
+  if (tloc == 1) {
+    Buf<int64_t> off;
+    Buf<int> cursor;
+    Buf<int32_t> list;
+    SA_TRY(off.alloc(&al, n + 1));
+    SA_TRY(cursor.alloc(&al, n));
+    SA_TRY(list.alloc(&al, ne * npe));
+    SA_TRY(memset_d(off.p, 0, off.bytes(), s));
+    SA_TRY(memset_d(cursor.p, 0, cursor.bytes(), s));
+    k_node_elem_count<<<blocks_for(ne * npe, 256), 256, 0, s>>>(ne, npe, en, n, off.p, err);
+    SA_LAUNCHED();
+    SA_TRY(scan_inplace(al, off.p + 1, n));
+    k_node_elem_fill<<<blocks_for(ne * npe, 256), 256, 0, s>>>(ne, npe, en, n, off.p, cursor.p, list.p);
+    SA_LAUNCHED();
+    k_node_tensor_from_elems<<<blocks_for(n, 128), 128, 0, s>>>(n, dim, off.p, list.p, meas, tensors, sigma, sinv,
+                                                               err);
+    SA_LAUNCHED();
+  } else {
+    k_node_tensor_direct<<<blocks_for(n, 256), 256, 0, s>>>(n, dim, tensors, sigma, sinv);
+    SA_LAUNCHED();
+  }
+  return SA_OK;
+}
+
+int launch_strength_classical(cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                              const double* diag, const uint8_t* dir, double theta, uint8_t* keep,
+                              int64_t* cnt) {
+  if (n <= 0) return SA_OK;
+  const double t2 = theta * theta;
+  k_strength_classical<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, v, diag, dir, t2, keep, cnt);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_strength_material(cudaStream_t s, int dim, int64_t n, const int64_t* rp, const int32_t* ci,
+                             const double* x, const double* sinv, const uint8_t* dir, double theta,
+                             double* w, double* D, uint8_t* keep, int64_t* cnt) {
+  if (n <= 0) return SA_OK;
+  const double t2 = theta * theta;
+  if (dim == 3) k_material_w<3><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w, D);
+  else k_material_w<2><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w, D);
+  SA_LAUNCHED();
+  k_material_keep<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, w, D, dir, t2, keep, cnt);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_filter(cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                  const uint8_t* keep, const int64_t* rpF, int32_t* ciF, double* vF, double* Dt) {
+  if (n <= 0) return SA_OK;
+  k_filter<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, v, keep, rpF, ciF, vF, Dt);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_coarse_aux(cudaStream_t s, int64_t nc, int dim, const int64_t* mrp, const int32_t* mlist,
+                      const double* x, const double* sigma, double* xc, double* sc, double* sic) {
+  if (nc <= 0) return SA_OK;
+  k_coarse_aux<<<blocks_for(nc, 128), 128, 0, s>>>(nc, dim, mrp, mlist, x, sigma, xc, sc, sic);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_smooth_p_values(cudaStream_t s, int64_t n, const int64_t* rpT, const int32_t* ciT, const double* vT,
+                           const int32_t* agg, const double* Dt, const double* omega_dev, double* vP) {
+  if (n <= 0) return SA_OK;
+  k_smooth_p_values<<<blocks_for(n, 256), 256, 0, s>>>(n, rpT, ciT, vT, agg, Dt, omega_dev, vP);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+}  // namespace sa

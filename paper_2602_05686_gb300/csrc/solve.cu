@@ -1,0 +1,458 @@
+// Solve-phase and iteration kernels: CSR sparse matrix-vector products with
+// a sub-warp per row, the fused Chebyshev step, residual / restriction /
+// prolongation, fixed-order dot products, the power method, and the CG
+// vector updates with device-resident scalars.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "solve.cuh"
+
+namespace sa {
+
+// ---------------------------------------------------------------------------
+// row dot product with SW lanes per row; the result is valid in every lane
+// of the group
+// ---------------------------------------------------------------------------
+template <int SW, typename T, typename V>
+__device__ __forceinline__ T row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const V* __restrict__ v, const T* __restrict__ x, int64_t i, bool valid,
+                                     int sl) {
+  T acc = T(0);
+  if (valid) {
+    const int64_t e = rp[i + 1];
+    for (int64_t p = rp[i] + sl; p < e; p += SW) acc += (T)v[p] * x[ci[p]];
+  }
+#pragma unroll
+  for (int o = SW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SW);
+  return acc;
+}
+
+// scaled variant: sum_p v_p * (s_j * x_j)
+template <int SW>
+__device__ __forceinline__ double row_dot_scaled(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                 const double* __restrict__ v, const double* __restrict__ s,
+                                                 const double* __restrict__ x, int64_t i, bool valid, int sl) {
+  double acc = 0.0;
+  if (valid) {
+    const int64_t e = rp[i + 1];
+    for (int64_t p = rp[i] + sl; p < e; p += SW) {
+      int32_t j = ci[p];
+      acc += v[p] * (s[j] * x[j]);
+    }
+  }
+#pragma unroll
+  for (int o = SW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SW);
+  return acc;
+}
+
+#define ROW_SETUP(SW)                                                   \
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   \
+  const int64_t i = gt / SW;                                            \
+  const int sl = (int)(gt % SW);                                        \
+  const bool valid = i < n;
+
+// y = A x
+template <int SW>
+__global__ void k_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                       const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y) {
+  ROW_SETUP(SW)
+  double a = row_dot<SW>(rp, ci, v, x, i, valid, sl);
+  if (valid && sl == 0) y[i] = a;
+}
+
+// y += A x   (prolongation with correction: x_l += P x_{l+1})
+template <int SW>
+__global__ void k_spmv_add(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y) {
+  ROW_SETUP(SW)
+  double a = row_dot<SW>(rp, ci, v, x, i, valid, sl);
+  if (valid && sl == 0) y[i] += a;
+}
+
+// r = b - A x
+template <int SW>
+__global__ void k_residual(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, const double* __restrict__ b, const double* __restrict__ x,
+                           double* __restrict__ r) {
+  ROW_SETUP(SW)
+  double a = row_dot<SW>(rp, ci, v, x, i, valid, sl);
+  if (valid && sl == 0) r[i] = b[i] - a;
+}
+
+// one Chebyshev step (Sec. 4 smoother; three-term recurrence on D^-1 A):
+//   r = b - A x_in; d = first ? c2 * (dinv r) : c1 d + c2 (dinv r);
+//   x_out = x_in + d
+template <int SW>
+__global__ void k_cheb_step(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, const double* __restrict__ dinv,
+                            const double* __restrict__ b, const double* __restrict__ xin, double* __restrict__ xout,
+                            double* __restrict__ d, double c1, double c2, int first) {
+  ROW_SETUP(SW)
+  double a = row_dot<SW>(rp, ci, v, xin, i, valid, sl);
+  if (valid && sl == 0) {
+    double r = b[i] - a;
+    double z = dinv[i] * r;
+    double dn = first ? c2 * z : c1 * d[i] + c2 * z;
+    d[i] = dn;
+    xout[i] = xin[i] + dn;
+  }
+}
+
+// first Chebyshev step from x = 0: d = c2 dinv b, x = d
+__global__ void k_cheb_first(int64_t n, const double* __restrict__ dinv, const double* __restrict__ b, double c2,
+                             double* __restrict__ x, double* __restrict__ d) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double dn = c2 * (dinv[i] * b[i]);
+    d[i] = dn;
+    x[i] = dn;
+  }
+}
+
+// power method product: w_i = s_i * sum_p a_p (s_j v_j)
+template <int SW>
+__global__ void k_power_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ v, const double* __restrict__ s, const double* __restrict__ x,
+                             double* __restrict__ w) {
+  ROW_SETUP(SW)
+  double a = row_dot_scaled<SW>(rp, ci, v, s, x, i, valid, sl);
+  if (valid && sl == 0) w[i] = s[i] * a;
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order block reductions
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum_to(double (&val)[NV], double* __restrict__ out, int stride) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double t = warp_sum(val[k]);
+    if (lane == 0) sh[k][w] = t;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < nw ? sh[k][lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) out[(int64_t)k * stride + blockIdx.x] = t;
+    }
+  }
+}
+
+// partial sums of up to three dot products over a fixed grid
+__global__ void k_dots(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
+                       const double* __restrict__ a1, const double* __restrict__ b1, const double* __restrict__ a2,
+                       const double* __restrict__ b2, double* __restrict__ part) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    acc[0] += a0[i] * b0[i];
+    if (a1) acc[1] += a1[i] * b1[i];
+    if (a2) acc[2] += a2[i] * b2[i];
+  }
+  block_sum_to<3>(acc, part, RED_BLOCKS);
+}
+
+// sums `np` partials of each of 3 dots in index order -> out[0..2]
+__global__ void k_dots_finish(const double* __restrict__ part, int np, int stride, double* __restrict__ out) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < np; t += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] += part[(int64_t)k * stride + t];
+  __shared__ double sh[3][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = warp_sum(acc[k]);
+    if (lane == 0) sh[k][w] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) {
+      double s = 0.0;
+      for (int q = 0; q < nw; ++q) s += sh[k][q];
+      out[k] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// power method (Sec. 2.2): spectral-radius estimate of diag(s) A diag(s)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t fmix32_s(uint32_t h) {
+  // MurmurHash3 32-bit finaliser (Appleby, public domain)
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__global__ void k_start_vector(int64_t n, uint32_t tag, uint32_t seed, double* __restrict__ v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    uint32_t h = fmix32_s((uint32_t)i ^ (0x7F4A7C15u * tag) ^ (seed * 0x2545F491u));
+    double u = (double)h * (1.0 / 4294967296.0);
+    v[i] = 2.0 * u - 1.0;
+  }
+}
+
+// sc[0] = ||w||^2, sc[1] = ||v||^2 -> lam = ||w|| / ||v||, sc[2] = ||w||.
+// A zero product (every row unscaled) gives lam = 0 and leaves v as is.
+__global__ void k_power_scalars(double* __restrict__ sc, double* __restrict__ lam) {
+  double nw = sqrt(sc[0]);
+  if (nw == 0.0 || sc[3] != 0.0) {
+    sc[3] = 1.0;
+    *lam = 0.0;
+    return;
+  }
+  *lam = nw / sqrt(sc[1]);
+  sc[2] = nw;
+}
+
+__global__ void k_div_by(int64_t n, const double* __restrict__ w, const double* __restrict__ sc,
+                         double* __restrict__ v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && sc[3] == 0.0) v[i] = w[i] / sc[2];
+}
+
+__global__ void k_rsqrt_scale(int64_t n, const double* __restrict__ d, double* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = 1.0 / sqrt(d[i]);  // +inf -> 0
+}
+
+__global__ void k_reciprocal(int64_t n, const double* __restrict__ d, double* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = 1.0 / d[i];
+}
+
+__global__ void k_omega(const double* __restrict__ lam, double omega_sym, double* __restrict__ omega) {
+  *omega = *lam > 0.0 ? omega_sym / *lam : 0.0;
+}
+
+int pick_sw(int64_t n, int64_t nnz) {
+  double avg = n > 0 ? (double)nnz / (double)n : 1.0;
+  if (avg <= 6) return 4;
+  if (avg <= 40) return 8;
+  if (avg <= 96) return 16;
+  return 32;
+}
+
+#define DISPATCH_SW(sw, KERNEL, GRIDN, ...)                                                 \
+  do {                                                                                       \
+    const int _sw = (sw);                                                                    \
+    const unsigned _g = blocks_for((GRIDN) * (int64_t)_sw, 256);                             \
+    switch (_sw) {                                                                           \
+      case 4: KERNEL<4><<<_g, 256, 0, st>>>(__VA_ARGS__); break;                             \
+      case 8: KERNEL<8><<<_g, 256, 0, st>>>(__VA_ARGS__); break;                             \
+      case 16: KERNEL<16><<<_g, 256, 0, st>>>(__VA_ARGS__); break;                           \
+      default: KERNEL<32><<<_g, 256, 0, st>>>(__VA_ARGS__); break;                           \
+    }                                                                                        \
+  } while (0)
+
+int launch_dots(cudaStream_t st, int64_t n, const double* a0, const double* b0, const double* a1,
+                const double* b1, const double* a2, const double* b2, double* part, double* out) {
+  k_dots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, a0, b0, a1, b1, a2, b2, part);
+  SA_LAUNCHED();
+  k_dots_finish<<<1, 1024, 0, st>>>(part, RED_BLOCKS, RED_BLOCKS, out);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int run_power(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* s,
+              int steps, uint32_t tag, uint32_t seed, double* lam_dev) {
+  cudaStream_t st = al.stream;
+  if (n <= 0) return SA_OK;
+  Buf<double> x, w, part, sc;
+  SA_TRY(x.alloc(&al, n));
+  SA_TRY(w.alloc(&al, n));
+  SA_TRY(part.alloc(&al, 3 * RED_BLOCKS));
+  SA_TRY(sc.alloc(&al, 4));
+  SA_TRY(memset_d(sc.p, 0, 4 * sizeof(double), st));
+  int64_t nnz = 0;
+  SA_TRY(copy_d2h(&nnz, rp + n, sizeof(int64_t), st));
+  const int sw = pick_sw(n, nnz);
+  k_start_vector<<<blocks_for(n, 256), 256, 0, st>>>(n, tag, seed, x.p);
+  SA_LAUNCHED();
+  for (int it = 0; it < steps; ++it) {
+    DISPATCH_SW(sw, k_power_spmv, n, n, rp, ci, v, s, x.p, w.p);
+    SA_LAUNCHED();
+    SA_TRY(launch_dots(st, n, w.p, w.p, x.p, x.p, nullptr, nullptr, part.p, sc.p));
+    k_power_scalars<<<1, 1, 0, st>>>(sc.p, lam_dev);
+    SA_LAUNCHED();
+    k_div_by<<<blocks_for(n, 256), 256, 0, st>>>(n, w.p, sc.p, x.p);
+    SA_LAUNCHED();
+  }
+  return SA_OK;
+}
+
+int launch_rsqrt_scale(cudaStream_t s, int64_t n, const double* d, double* out) {
+  if (n <= 0) return SA_OK;
+  k_rsqrt_scale<<<blocks_for(n, 256), 256, 0, s>>>(n, d, out);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_reciprocal(cudaStream_t s, int64_t n, const double* d, double* out) {
+  if (n <= 0) return SA_OK;
+  k_reciprocal<<<blocks_for(n, 256), 256, 0, s>>>(n, d, out);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_omega(cudaStream_t s, const double* lam_dev, double omega_sym, double* omega_dev) {
+  k_omega<<<1, 1, 0, s>>>(lam_dev, omega_sym, omega_dev);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 V-cycle pieces
+// ---------------------------------------------------------------------------
+int launch_spmv(cudaStream_t st, const CsrView& A, const double* x, double* y) {
+  if (A.n <= 0) return SA_OK;
+  DISPATCH_SW(A.sw, k_spmv, A.n, A.n, A.rp, A.ci, A.v, x, y);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_spmv_add(cudaStream_t st, const CsrView& A, const double* x, double* y) {
+  if (A.n <= 0) return SA_OK;
+  DISPATCH_SW(A.sw, k_spmv_add, A.n, A.n, A.rp, A.ci, A.v, x, y);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_residual(cudaStream_t st, const CsrView& A, const double* b, const double* x, double* r) {
+  if (A.n <= 0) return SA_OK;
+  DISPATCH_SW(A.sw, k_residual, A.n, A.n, A.rp, A.ci, A.v, b, x, r);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_cheb_step(cudaStream_t st, const CsrView& A, const double* dinv, const double* b, const double* xin,
+                     double* xout, double* d, double c1, double c2, int first) {
+  if (A.n <= 0) return SA_OK;
+  DISPATCH_SW(A.sw, k_cheb_step, A.n, A.n, A.rp, A.ci, A.v, dinv, b, xin, xout, d, c1, c2, first);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_cheb_first(cudaStream_t st, int64_t n, const double* dinv, const double* b, double c2, double* x,
+                      double* d) {
+  if (n <= 0) return SA_OK;
+  k_cheb_first<<<blocks_for(n, 256), 256, 0, st>>>(n, dinv, b, c2, x, d);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CG with device-resident scalars (Sec. 4)
+// ---------------------------------------------------------------------------
+// q = A p, partial sums of p.q
+template <int SW>
+__global__ void k_spmv_dot(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, const double* __restrict__ p, double* __restrict__ q,
+                           double* __restrict__ part) {
+  ROW_SETUP(SW)
+  double a = row_dot<SW>(rp, ci, v, p, i, valid, sl);
+  double c[1] = {0.0};
+  if (valid && sl == 0) {
+    q[i] = a;
+    c[0] = a * p[i];
+  }
+  block_sum_to<1>(c, part, 0);
+}
+
+// alpha = rz / pq (pq = dots[0]); flags breakdown when pq <= 0 or NaN
+__global__ void k_cg_alpha(CgScalars* __restrict__ s, const double* __restrict__ dots) {
+  double pq = dots[0];
+  s->pq = pq;
+  if (!(pq > 0.0)) { s->breakdown = 1; s->alpha = 0.0; return; }
+  s->alpha = s->rz / pq;
+}
+
+// x += alpha p; r -= alpha q; (r_prev = r before the update, if given);
+// partial sums of r.r
+__global__ void k_cg_update(int64_t n, const CgScalars* __restrict__ s, const double* __restrict__ p,
+                            const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+                            double* __restrict__ rprev, double* __restrict__ part) {
+  const double alpha = s->alpha;
+  double acc[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double ri = r[i];
+    if (rprev) rprev[i] = ri;
+    x[i] += alpha * p[i];
+    ri -= alpha * q[i];
+    r[i] = ri;
+    acc[0] += ri * ri;
+  }
+  block_sum_to<1>(acc, part, 0);
+}
+
+// beta from the new r.z (and z.r_prev for flexible CG); flexible < 0
+// initialises rz from dots[0]
+__global__ void k_cg_beta(CgScalars* __restrict__ s, const double* __restrict__ dots, int flexible) {
+  double rz_new = dots[0];
+  if (flexible < 0) {
+    s->rz = rz_new;
+    s->beta = 0.0;
+    s->breakdown = 0;
+    return;
+  }
+  double num = flexible ? rz_new - dots[1] : rz_new;
+  s->beta = num / s->rz;
+  s->rz = rz_new;
+}
+
+__global__ void k_cg_pupdate(int64_t n, const CgScalars* __restrict__ s, const double* __restrict__ z,
+                             double* __restrict__ p, int first) {
+  const double beta = s->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = first ? z[i] : z[i] + beta * p[i];
+}
+
+int launch_spmv_dot(cudaStream_t st, const CsrView& A, const double* p, double* q, double* part, int* nparts) {
+  const int sw = A.sw;
+  *nparts = (int)blocks_for(A.n * (int64_t)sw, 256);
+  DISPATCH_SW(sw, k_spmv_dot, A.n, A.n, A.rp, A.ci, A.v, p, q, part);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_finish(cudaStream_t st, const double* part, int np, double* out) {
+  k_dots_finish<<<1, 1024, 0, st>>>(part, np, 0, out);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_cg_alpha(cudaStream_t st, CgScalars* s, const double* dots) {
+  k_cg_alpha<<<1, 1, 0, st>>>(s, dots);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_cg_update(cudaStream_t st, int64_t n, const CgScalars* s, const double* p, const double* q, double* x,
+                     double* r, double* rprev, double* part) {
+  k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, p, q, x, r, rprev, part);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_cg_beta(cudaStream_t st, CgScalars* s, const double* dots, int flexible) {
+  k_cg_beta<<<1, 1, 0, st>>>(s, dots, flexible);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_cg_pupdate(cudaStream_t st, int64_t n, const CgScalars* s, const double* z, double* p, int first) {
+  k_cg_pupdate<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, z, p, first);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+}  // namespace sa

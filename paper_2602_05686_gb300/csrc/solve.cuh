@@ -1,0 +1,46 @@
+// Solve-phase launchers and the device-resident CG scalars.
+#pragma once
+
+#include "common.cuh"
+
+namespace sa {
+
+struct CsrView {
+  int64_t n = 0, nnz = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* v = nullptr;
+  int sw = 8;  // lanes per row
+};
+
+struct CgScalars {
+  double rz, pq, alpha, beta;
+  int breakdown;
+  int pad;
+};
+
+int pick_sw(int64_t n, int64_t nnz);
+int launch_dots(cudaStream_t st, int64_t n, const double* a0, const double* b0, const double* a1, const double* b1,
+                const double* a2, const double* b2, double* part, double* out);
+int launch_spmv(cudaStream_t st, const CsrView& A, const double* x, double* y);
+int launch_spmv_add(cudaStream_t st, const CsrView& A, const double* x, double* y);
+int launch_residual(cudaStream_t st, const CsrView& A, const double* b, const double* x, double* r);
+int launch_cheb_step(cudaStream_t st, const CsrView& A, const double* dinv, const double* b, const double* xin,
+                     double* xout, double* d, double c1, double c2, int first);
+int launch_cheb_first(cudaStream_t st, int64_t n, const double* dinv, const double* b, double c2, double* x,
+                      double* d);
+int launch_spmv_dot(cudaStream_t st, const CsrView& A, const double* p, double* q, double* part, int* nparts);
+int launch_finish(cudaStream_t st, const double* part, int np, double* out);
+int launch_cg_alpha(cudaStream_t st, CgScalars* s, const double* dots);
+int launch_cg_update(cudaStream_t st, int64_t n, const CgScalars* s, const double* p, const double* q, double* x,
+                     double* r, double* rprev, double* part);
+int launch_cg_beta(cudaStream_t st, CgScalars* s, const double* dots, int flexible);
+int launch_cg_pupdate(cudaStream_t st, int64_t n, const CgScalars* s, const double* z, double* p, int first);
+
+// dense coarse level (dense.cu)
+int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                             Buf<double>& W, Buf<double>& WT);
+int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
+                        double* x);
+
+}  // namespace sa

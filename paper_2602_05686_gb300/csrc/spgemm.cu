@@ -1,0 +1,322 @@
+// Two-phase (count, then fill) sparse matrix product C = A B used for the
+// smoothed prolongator (A_F P^, Sec. 2.2) and the Galerkin product (R (A P),
+// Sec. 2).  One warp per row of A with an open-addressing hash table of
+// column indices in shared memory.  The fill phase sorts the row's columns
+// and accumulates each entry's products in ascending order of the A column
+// (the order of Gustavson's row algorithm), with separately rounded multiply
+// and add, so the values do not depend on scheduling.  Rows whose distinct
+// column count exceeds the table go to a block-per-row path with a dense
+// accumulator in global scratch memory.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sa {
+
+constexpr int HB = 512;             // hash slots per warp
+constexpr int HCAP = 384;           // max distinct columns on the warp path
+constexpr int SG_WARPS = 4;         // warps per CTA
+constexpr int BIG_THREADS = 512;
+
+__device__ __forceinline__ int hslot(int32_t j) { return (int)(((uint32_t)j * 0x9E3779B1u) >> 23); }  // 9 bits
+
+// insert j; returns 1 if newly inserted, 0 if present, -1 if the table is full
+__device__ __forceinline__ int hinsert(int32_t* keys, int32_t j) {
+  int h = hslot(j);
+  for (int probe = 0; probe < HB; ++probe) {
+    int32_t old = atomicCAS(&keys[h], -1, j);
+    if (old == -1) return 1;
+    if (old == j) return 0;
+    h = (h + 1) & (HB - 1);
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int hfind(const int32_t* keys, int32_t j) {
+  int h = hslot(j);
+  for (int probe = 0; probe < HB; ++probe) {
+    int32_t k = keys[h];
+    if (k == j) return h;
+    if (k == -1) return -1;
+    h = (h + 1) & (HB - 1);
+  }
+  return -1;
+}
+
+// inserts every column of row i of A*B; returns the distinct count, or -1 on
+// overflow (more than HCAP distinct columns)
+__device__ int warp_build_row(int64_t i, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+                              const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci, int32_t* keys,
+                              int* wcount) {
+  const int lane = lane_id();
+  for (int t = lane; t < HB; t += 32) keys[t] = -1;
+  if (lane == 0) *wcount = 0;
+  __syncwarp();
+  const int64_t b = Arp[i], e = Arp[i + 1];
+  bool over = false;
+  for (int64_t p = b; p < e && !over; ++p) {
+    const int32_t k = Aci[p];
+    const int64_t qb = Brp[k], qe = Brp[k + 1];
+    for (int64_t q = qb + lane; q < qe; q += 32) {
+      int r = hinsert(keys, Bci[q]);
+      if (r == 1) atomicAdd(wcount, 1);
+      if (r < 0) atomicAdd(wcount, HCAP + 1);
+    }
+    __syncwarp();
+    over = *((volatile int*)wcount) > HCAP;
+  }
+  __syncwarp();
+  int c = *((volatile int*)wcount);
+  return c > HCAP ? -1 : c;
+}
+
+__global__ void __launch_bounds__(SG_WARPS * 32)
+k_spgemm_count(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+               const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci, int64_t* __restrict__ cnt,
+               int32_t* __restrict__ big, unsigned long long* __restrict__ nbig) {
+  __shared__ int32_t keys_all[SG_WARPS][HB];
+  __shared__ int wcount_all[SG_WARPS];
+  const int w = threadIdx.x >> 5;
+  int32_t* keys = keys_all[w];
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    int c = warp_build_row(i, Arp, Aci, Brp, Bci, keys, &wcount_all[w]);
+    if (lane_id() == 0) {
+      if (c < 0) {
+        unsigned long long slot = atomicAdd(nbig, 1ull);
+        big[slot] = (int32_t)i;
+        cnt[i + 1] = 0;  // set by the big-row pass
+      } else {
+        cnt[i + 1] = c;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(SG_WARPS * 32)
+k_spgemm_fill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+              const double* __restrict__ Av, const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci,
+              const double* __restrict__ Bv, const int64_t* __restrict__ Crp, int32_t* __restrict__ Cci,
+              double* __restrict__ Cv, const uint8_t* __restrict__ isbig) {
+  __shared__ int32_t keys_all[SG_WARPS][HB];
+  __shared__ int32_t rank_all[SG_WARPS][HB];
+  __shared__ int32_t cols_all[SG_WARPS][HCAP];
+  __shared__ double acc_all[SG_WARPS][HCAP];
+  __shared__ int wcount_all[SG_WARPS];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  int32_t* keys = keys_all[w];
+  int32_t* rank_of = rank_all[w];
+  int32_t* cols = cols_all[w];
+  double* acc = acc_all[w];
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    if (isbig[i]) continue;  // warp-uniform
+    const int c = warp_build_row(i, Arp, Aci, Brp, Bci, keys, &wcount_all[w]);
+    if (c <= 0) continue;
+    // compact the keys (slot order), remember each key's slot
+    int out = 0;
+    for (int t0 = 0; t0 < HB; t0 += 32) {
+      int t = t0 + lane;
+      int32_t k = keys[t];
+      bool has = k != -1;
+      unsigned m = __ballot_sync(FULL, has);
+      if (has) {
+        int pos = out + __popc(m & ((1u << lane) - 1u));
+        cols[pos] = k;
+        rank_of[t] = pos;  // temporarily: compact position
+      }
+      out += __popc(m);
+    }
+    __syncwarp();
+    // rank sort (keys are distinct): slot -> rank in ascending column order
+    const int64_t cb = Crp[i];
+    for (int t0 = 0; t0 < HB; t0 += 32) {
+      int t = t0 + lane;
+      int32_t k = keys[t];
+      if (k != -1) {
+        int r = 0;
+        for (int u = 0; u < c; ++u) r += cols[u] < k;
+        rank_of[t] = r;
+        Cci[cb + r] = k;
+      }
+    }
+    for (int t = lane; t < c; t += 32) acc[t] = 0.0;
+    __syncwarp();
+    // ordered accumulation: A columns in ascending order, lanes over the B
+    // row (distinct columns, so no two lanes touch one accumulator per step)
+    const int64_t b = Arp[i], e = Arp[i + 1];
+    for (int64_t p = b; p < e; ++p) {
+      const int32_t k = Aci[p];
+      const double a = Av[p];
+      const int64_t qb = Brp[k], qe = Brp[k + 1];
+      for (int64_t q = qb + lane; q < qe; q += 32) {
+        int h = hfind(keys, Bci[q]);
+        if (h >= 0) {  // always found: the keys were inserted from the same rows
+          int r = rank_of[h];
+          acc[r] = __dadd_rn(acc[r], __dmul_rn(a, Bv[q]));
+        }
+      }
+      __syncwarp();
+    }
+    for (int t = lane; t < c; t += 32) Cv[cb + t] = acc[t];
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// big rows: one CTA per row with a dense accumulator of width m in global
+// scratch (stamp[m] holds the row currently using a column)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t block_excl_scan_count(int flag, int* sh, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned m = __ballot_sync(FULL, flag);
+  int before = __popc(m & ((1u << lane) - 1u));
+  if (lane == 0) sh[w] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < nw; ++k) { int t = sh[k]; sh[k] = run; run += t; }
+    sh[nw] = run;
+  }
+  __syncthreads();
+  int r = sh[w] + before;
+  *total = sh[nw];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(BIG_THREADS)
+k_spgemm_big(int phase, int64_t nbig, const int32_t* __restrict__ big, int64_t m,
+             const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci, const double* __restrict__ Av,
+             const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci, const double* __restrict__ Bv,
+             int64_t* __restrict__ cnt, const int64_t* __restrict__ Crp, int32_t* __restrict__ Cci,
+             double* __restrict__ Cv, int32_t* __restrict__ stamp_all, double* __restrict__ acc_all) {
+  __shared__ int sh[BIG_THREADS / 32 + 1];
+  int32_t* stamp = stamp_all + (int64_t)blockIdx.x * m;
+  double* acc = acc_all + (int64_t)blockIdx.x * m;
+  for (int64_t t = blockIdx.x; t < nbig; t += gridDim.x) {
+    const int32_t i = big[t];
+    const int64_t b = Arp[i], e = Arp[i + 1];
+    for (int64_t p = b; p < e; ++p) {
+      const int32_t k = Aci[p];
+      const double a = phase ? Av[p] : 0.0;
+      for (int64_t q = Brp[k] + threadIdx.x; q < Brp[k + 1]; q += blockDim.x) {
+        const int32_t j = Bci[q];
+        if (stamp[j] != i) {
+          stamp[j] = i;
+          acc[j] = 0.0;
+        }
+        if (phase) acc[j] = __dadd_rn(acc[j], __dmul_rn(a, Bv[q]));
+      }
+      __syncthreads();
+    }
+    // compact in ascending column order
+    int64_t run = 0;
+    for (int64_t j0 = 0; j0 < m; j0 += blockDim.x) {
+      int64_t j = j0 + threadIdx.x;
+      int f = (j < m && stamp[j] == i) ? 1 : 0;
+      int tot;
+      int r = (int)block_excl_scan_count(f, sh, &tot);
+      if (phase && f) {
+        Cci[Crp[i] + run + r] = (int32_t)j;
+        Cv[Crp[i] + run + r] = acc[j];
+      }
+      run += tot;
+    }
+    if (!phase && threadIdx.x == 0) cnt[i + 1] = run;
+    // release the stamps of this row
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x)
+      if (stamp[j] == i) stamp[j] = -1;
+    __syncthreads();
+  }
+}
+
+__global__ void k_mark_big(int64_t nbig, const int32_t* __restrict__ big, uint8_t* __restrict__ isbig) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nbig) isbig[big[t]] = 1;
+}
+
+int run_spgemm(Alloc& al, int64_t n, int64_t m, const int64_t* Arp, const int32_t* Aci, const double* Av,
+               const int64_t* Brp, const int32_t* Bci, const double* Bv, Buf<int64_t>& Crp, Buf<int32_t>& Cci,
+               Buf<double>& Cv, int64_t* nnzC) {
+  cudaStream_t s = al.stream;
+  SA_TRY(Crp.alloc(&al, n + 1));
+  SA_TRY(memset_d(Crp.p, 0, Crp.bytes(), s));
+  *nnzC = 0;
+  if (n <= 0) {
+    SA_TRY(Cci.alloc(&al, 0));
+    SA_TRY(Cv.alloc(&al, 0));
+    return SA_OK;
+  }
+  Buf<int32_t> big;
+  Buf<unsigned long long> nbig_d;
+  Buf<uint8_t> isbig;
+  SA_TRY(big.alloc(&al, n));
+  SA_TRY(nbig_d.alloc(&al, 1));
+  SA_TRY(isbig.alloc(&al, n));
+  SA_TRY(memset_d(nbig_d.p, 0, sizeof(unsigned long long), s));
+  SA_TRY(memset_d(isbig.p, 0, isbig.bytes(), s));
+  const unsigned grid = warp_rows_grid(n, SG_WARPS * 32);
+  k_spgemm_count<<<grid, SG_WARPS * 32, 0, s>>>(n, Arp, Aci, Brp, Bci, Crp.p, big.p, nbig_d.p);
+  SA_LAUNCHED();
+  unsigned long long nbig = 0;
+  SA_TRY(copy_d2h(&nbig, nbig_d.p, sizeof(nbig), s));
+  Buf<int32_t> stamp;
+  Buf<double> dacc;
+  unsigned gbig = 0;
+  if (nbig > 0) {
+    gbig = (unsigned)(nbig < 64 ? nbig : 64);
+    SA_TRY(stamp.alloc(&al, (int64_t)gbig * m));
+    SA_TRY(dacc.alloc(&al, (int64_t)gbig * m));
+    SA_TRY(memset_d(stamp.p, 0xff, stamp.bytes(), s));
+    k_mark_big<<<blocks_for((int64_t)nbig, 256), 256, 0, s>>>((int64_t)nbig, big.p, isbig.p);
+    SA_LAUNCHED();
+    k_spgemm_big<<<gbig, BIG_THREADS, 0, s>>>(0, (int64_t)nbig, big.p, m, Arp, Aci, Av, Brp, Bci, Bv, Crp.p,
+                                                nullptr, nullptr, nullptr, stamp.p, dacc.p);
+    SA_LAUNCHED();
+  }
+  SA_TRY(scan_inplace(al, Crp.p + 1, n));
+  SA_TRY(copy_d2h(nnzC, Crp.p + n, sizeof(int64_t), s));
+  SA_TRY(Cci.alloc(&al, *nnzC));
+  SA_TRY(Cv.alloc(&al, *nnzC));
+  k_spgemm_fill<<<grid, SG_WARPS * 32, 0, s>>>(n, Arp, Aci, Av, Brp, Bci, Bv, Crp.p, Cci.p, Cv.p, isbig.p);
+  SA_LAUNCHED();
+  if (nbig > 0) {
+    k_spgemm_big<<<gbig, BIG_THREADS, 0, s>>>(1, (int64_t)nbig, big.p, m, Arp, Aci, Av, Brp, Bci, Bv, nullptr,
+                                                Crp.p, Cci.p, Cv.p, stamp.p, dacc.p);
+    SA_LAUNCHED();
+  }
+  return SA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exact symmetry of the coarse operator: lower-triangle entries take the
+// value of the mirrored upper-triangle entry (found by binary search).
+// err bit 16: the pattern is not structurally symmetric.
+// ---------------------------------------------------------------------------
+__global__ void k_symmetrize(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             double* __restrict__ v, int* __restrict__ err) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+      int32_t j = ci[p];
+      if (j >= (int32_t)i) continue;
+      int64_t lo = rp[j], hi = rp[j + 1] - 1, f = -1;
+      while (lo <= hi) {
+        int64_t mid = (lo + hi) >> 1;
+        int32_t c = ci[mid];
+        if (c == (int32_t)i) { f = mid; break; }
+        if (c < (int32_t)i) lo = mid + 1; else hi = mid - 1;
+      }
+      if (f < 0) atomicOr(err, 16);
+      else v[p] = v[f];
+    }
+  }
+}
+
+int launch_symmetrize(cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* ci, double* v, int* err) {
+  if (n <= 0) return SA_OK;
+  k_symmetrize<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, v, err);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+}  // namespace sa

@@ -1,0 +1,250 @@
+"""CUDA path vs the CPU oracle, level by level and solve by solve.
+
+Bar: aggregates, roots, strength masks and sparsity patterns bit-exact;
+FP64 hierarchy values within 1e-12 of the row's largest magnitude; CG
+iteration counts within 1 and true relative residual <= 1e-8 (FP64 form);
+the FP32 V-cycle form reaches the same residual within a few extra
+iterations."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+VAL_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def sa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2602_05686_gb300 as m
+    m.build()
+    return m
+
+
+def row_rel_close(rp, a, b, tol=VAL_TOL):
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    scale = np.zeros(n)
+    np.maximum.at(scale, rows, np.abs(b))
+    err = np.abs(a - b)
+    bad = err > tol * np.maximum(scale[rows], 1e-300)
+    return not bad.any(), (float((err / np.maximum(scale[rows], 1e-300)).max()) if len(a) else 0.0)
+
+
+def compare(h, o, keep=True):
+    st = h.stats()
+    assert st["levels"] == o.nlev, (st["n"], [o.level(l)["n"] for l in range(o.nlev)])
+    worst = 0.0
+    for l in range(o.nlev):
+        g, r = h.export_level(l), o.level(l)
+        assert g["n"] == r["n"] and g["nnz"] == r["nnz"], (l, g["n"], r["n"], g["nnz"], r["nnz"])
+        assert np.array_equal(g["A_rp"], r["A_rp"]) and np.array_equal(g["A_ci"], r["A_ci"]), l
+        ok, e = row_rel_close(r["A_rp"], g["A_v"], r["A_v"])
+        worst = max(worst, e)
+        assert ok, (l, e)
+        if l < o.nlev - 1:
+            assert np.array_equal(g["agg"], r["agg"]), l
+            assert g["nnz_gc"] == r["nnz_gc"], l
+            assert np.array_equal(g["P_rp"], r["P_rp"]) and np.array_equal(g["P_ci"], r["P_ci"]), l
+            ok, e = row_rel_close(r["P_rp"], g["P_v"], r["P_v"])
+            worst = max(worst, e)
+            assert ok, (l, e)
+            if keep:
+                s = h.export_strength(l, keep=True, root=True, aux=False)
+                assert np.array_equal(s["keep"], r["keep"]), l
+                assert np.array_equal(s["root"], r["root"]), l
+                assert s["omega"] == pytest.approx(r["omega"], rel=1e-12)
+                assert s["cheb_lmax"] == pytest.approx(r["cheb_lmax"], rel=1e-12)
+    return worst
+
+
+CASES = [
+    ("c1-material", lambda g: g.layered_2d(32), 0.08, "material", 64),
+    ("c1-classical", lambda g: g.layered_2d(32), 0.08, "classical", 64),
+    ("c1-distance", lambda g: g.layered_2d(32), 0.08, "distance", 64),
+    ("twodomain-material", lambda g: g.two_domain(32, 1e4), 0.08, "material", 64),
+    ("twodomain-classical", lambda g: g.two_domain(32, 1e4), 0.08, "classical", 64),
+    ("battery-material", lambda g: g.battery_3d(16, 16, 32), 0.05, "material", 200),
+    ("battery-classical", lambda g: g.battery_3d(16, 16, 32), 0.04, "classical", 200),
+    ("voronoi-material", lambda g: g.voronoi_3d(14, seed=1), 0.05, "material", 150),
+    ("voronoi-classical", lambda g: g.voronoi_3d(14, seed=1), 0.04, "classical", 150),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_hierarchy_parity(sa, orc, gen_mod, case):
+    _, mk, theta, measure, mc = case
+    p = mk(gen_mod)
+    h = sa.Hierarchy(p, theta=theta, measure=measure, max_coarse=mc, keep_setup_data=True)
+    o = orc.Hierarchy(p, theta, measure, max_coarse=mc)
+    assert o.nlev >= 2
+    compare(h, o)
+    if measure != "classical":
+        for l in range(o.nlev):
+            s = h.export_strength(l, keep=False, root=False, aux=True)
+            r = o.level(l)
+            assert np.array_equal(s["x"], r["x"]) and np.array_equal(s["sinv"], r["sinv"]), l
+
+
+@pytest.mark.parametrize("case", CASES[:2] + CASES[5:8], ids=[c[0] for c in CASES[:2] + CASES[5:8]])
+def test_solve_parity_fp64(sa, orc, gen_mod, case):
+    import torch
+    _, mk, theta, measure, mc = case
+    p = mk(gen_mod)
+    h = sa.Hierarchy(p, theta=theta, measure=measure, max_coarse=mc)
+    o = orc.Hierarchy(p, theta, measure, max_coarse=mc)
+    x, info = h.solve(torch.from_numpy(p["b"]).cuda(), tol=1e-8)
+    xo, oinfo = o.solve(p["b"], tol=1e-8)
+    assert info["status"] == 0 and oinfo["status"] == 0
+    assert info["rel_res"] <= 1e-8
+    assert abs(info["iters"] - oinfo["iters"]) <= 1, (info, oinfo)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("case", CASES[:2] + CASES[5:8], ids=[c[0] for c in CASES[:2] + CASES[5:8]])
+def test_solve_mixed_precision(sa, orc, gen_mod, case):
+    import torch
+    _, mk, theta, measure, mc = case
+    p = mk(gen_mod)
+    h = sa.Hierarchy(p, theta=theta, measure=measure, max_coarse=mc, precision="fp32")
+    o = orc.Hierarchy(p, theta, measure, max_coarse=mc)
+    x, info = h.solve(torch.from_numpy(p["b"]).cuda(), tol=1e-8)
+    xo, oinfo = o.solve(p["b"], tol=1e-8, flexible=True)
+    assert info["status"] == 0, info
+    assert info["rel_res"] <= 1e-8
+    assert info["iters"] <= oinfo["iters"] + 3, (info, oinfo)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_vcycle_matches_oracle(sa, orc, gen_mod):
+    import torch
+    p = gen_mod.battery_3d(16, 16, 32)
+    h = sa.Hierarchy(p, theta=0.05, measure="material", max_coarse=200)
+    o = orc.Hierarchy(p, 0.05, "material", max_coarse=200)
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(p["n"])
+    zg = h.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+    zo = o.vcycle(r)
+    assert np.linalg.norm(zg - zo) <= 1e-10 * np.linalg.norm(zo)
+    hm = sa.Hierarchy(p, theta=0.05, measure="material", max_coarse=200, precision="fp32")
+    zm = hm.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert np.linalg.norm(zm - zo) <= 1e-3 * np.linalg.norm(zo)
+
+
+def test_standalone_strength_worked_example(sa, orc, gen_mod):
+    import torch
+    for kappa in (1.0, 100.0, 1e4):
+        p = gen_mod.worked_example(kappa=kappa)
+        sinv = orc.invert_tensors(2, p["tensors"])
+        for theta in (0.0, 0.05, 0.1, 0.2):
+            _, _, ko = orc.strength_material(2, p["n"], p["row_ptr"], p["col"], None, p["coords"], sinv, theta)
+            t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)  # noqa: E731
+            kg = sa.strength("material", 2, t(p["row_ptr"], torch.int64), t(p["col"], torch.int32), None,
+                             t(p["coords"], torch.float64), t(sinv, torch.float64), None, theta)
+            assert np.array_equal(kg.cpu().numpy(), ko)
+            kc = sa.strength("classical", 2, t(p["row_ptr"], torch.int64), t(p["col"], torch.int32),
+                             t(p["val"], torch.float64), None, None, None, theta)
+            assert np.array_equal(kc.cpu().numpy(),
+                                  orc.strength_classical(p["n"], p["row_ptr"], p["col"], p["val"], None, theta))
+
+
+def test_single_level_is_a_direct_solve(sa, gen_mod):
+    import torch
+    p = gen_mod.layered_2d(16)
+    h = sa.Hierarchy(p, theta=0.08, measure="material", max_coarse=5000)
+    assert h.stats()["levels"] == 1
+    x, info = h.solve(torch.from_numpy(p["b"]).cuda())
+    assert info["status"] == 0 and info["iters"] <= 2 and info["rel_res"] <= 1e-8
+
+
+def test_host_pointer_path_matches_device_path(sa, gen_mod):
+    import torch
+    p = gen_mod.battery_3d(12, 12, 24)
+    hd = sa.Hierarchy(p, theta=0.05, measure="material", max_coarse=100)
+    hh = sa.Hierarchy(p, theta=0.05, measure="material", max_coarse=100, host_inputs=True)
+    assert hd.stats() == {**hh.stats(), "device_bytes": hd.stats()["device_bytes"]}
+    xd, a = hd.solve(torch.from_numpy(p["b"]).cuda())
+    xh, b = hh.solve(p["b"])  # host buffers in, host buffers out
+    assert a["iters"] == b["iters"]
+    assert np.array_equal(xd.cpu().numpy(), xh)
+
+
+def test_error_statuses_without_faults(sa, gen_mod):
+    import torch
+    p = gen_mod.layered_2d(16)
+    # negative definite: the coarse Cholesky reports a non-positive pivot
+    q = dict(p)
+    q["val"] = -p["val"]
+    with pytest.raises(sa.SAError) as e:
+        sa.Hierarchy(q, theta=0.08, measure="classical", max_coarse=5000)
+    assert e.value.status == -4
+    # maxit reached: status NO_CONVERGENCE with the last iterate returned
+    h = sa.Hierarchy(p, theta=0.08, measure="material", max_coarse=30, maxit=1)
+    x, info = h.solve(torch.from_numpy(p["b"]).cuda(), tol=1e-14)
+    assert info["status"] == -6 and info["iters"] == 1 and torch.isfinite(x).all()
+    # material measure without coordinates is rejected before any copy
+    import ctypes
+    L = sa.lib()
+    o = sa.default_options()
+    t = {k: torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("row_ptr", "col", "val")}
+    pr = sa.Problem()
+    pr.dim, pr.n, pr.nnz = 2, p["n"], p["nnz"]
+    pr.row_ptr, pr.col, pr.val = t["row_ptr"].data_ptr(), t["col"].data_ptr(), t["val"].data_ptr()
+    hh = ctypes.c_void_p()
+    assert L.sa_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(hh)) == -1
+    assert not hh.value
+
+
+def test_allocator_failure_reports_oom(sa, gen_mod):
+    import ctypes
+    import torch
+    p = gen_mod.layered_2d(16)
+    L = sa.lib()
+    o = sa.default_options()
+    o.max_coarse = 30
+    o.stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    calls = {"n": 0}
+
+    @sa.api._ALLOC
+    def failing_alloc(nbytes, ctx):
+        calls["n"] += 1
+        return None
+
+    @sa.api._FREE
+    def no_free(ptr, ctx):
+        pass
+
+    o.alloc = failing_alloc
+    o.dealloc = no_free
+    t = {k: torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("row_ptr", "col", "val", "coords")}
+    pr = sa.Problem()
+    pr.dim, pr.n, pr.nnz = 2, p["n"], p["nnz"]
+    pr.row_ptr, pr.col, pr.val = t["row_ptr"].data_ptr(), t["col"].data_ptr(), t["val"].data_ptr()
+    pr.coords = t["coords"].data_ptr()
+    o.measure = 0
+    hh = ctypes.c_void_p()
+    assert L.sa_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(hh)) == -2
+    assert calls["n"] >= 1 and not hh.value
+
+
+def test_batch_solve_columns_independent(sa, gen_mod):
+    import torch
+    p = gen_mod.battery_3d(12, 12, 24)
+    h = sa.Hierarchy(p, theta=0.05, measure="material", max_coarse=100)
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((3, p["n"]))
+    B[:, p["dir_mask"] == 1] = 0.0
+    import ctypes
+    Bd = torch.from_numpy(B).cuda().contiguous()
+    Xd = torch.zeros_like(Bd)
+    infos = (sa.SolveInfo * 3)()
+    st = sa.lib().sa_solve_batch(h.h, 3, Bd.data_ptr(), Xd.data_ptr(), 1e-8, infos)
+    assert st == 0
+    for c in range(3):
+        x1, i1 = h.solve(Bd[c].clone())
+        assert infos[c].iters == i1["iters"]
+        assert torch.equal(Xd[c], x1)
+    del ctypes
