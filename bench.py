@@ -1,0 +1,377 @@
+"""Benchmark of the SA-AMG hot path on one GB300 (or N replicas).
+
+One step = the whole hot path on the battery-stack workload (Q1 hex
+128 x 128 x 256 elements, 4,276,737 dofs, z-spacing 0.01 of the x/y
+spacing, layer cycle sigma = 1e5 / 1e-5 / 1e2 of 8 elements each, u = 0 at
+z = 0 and u = 1 at the top):
+  material-aware setup (theta 0.05) + FP64 PCG to 1e-8
+  + FP32-V-cycle flexible CG to 1e-8 on the same hierarchy
+  + classical setup (theta 0.04) + FP64 PCG to 1e-8 (the paper's comparison).
+Inputs are resident in HBM before the timed region and are larger than L2
+(A alone is 1.36 GB), so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+instead (bounded sample, extrapolated to the full workload by dof count).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    # name: (generator kwargs, description)
+    "battery_128x128x256": (dict(nx=128, ny=128, nz=256), "battery-like stack, Q1 hex 128x128x256 (4.28M dofs)"),
+    "battery_64x64x128": (dict(nx=64, ny=64, nz=128), "battery-like stack, Q1 hex 64x64x128 (0.54M dofs)"),
+    "battery_32x32x64": (dict(nx=32, ny=32, nz=64), "battery-like stack, Q1 hex 32x32x64 (71k dofs)"),
+}
+MAT_THETA, CLS_THETA, TOL = 0.05, 0.04, 1e-8
+METRIC = "time-to-1e-8 residual per step (material setup + FP64 PCG + FP32-V-cycle FCG + classical setup + FP64 PCG)"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("solve.cu", "solve.cuh", "mixed.cu", "host.cu"):
+        with open(os.path.join(ROOT, "paper_2602_05686_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, workload):
+    """ncu DRAM bytes per launch recorded for this kernel and workload, if the
+    kernel sources are unchanged since the capture; else None"""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        e = t.get(f"{kernel}@{workload}")
+        if e and e.get("source_hash") == kernel_source_hash():
+            return float(e["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region"""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for k, name in enumerate(names):
+                    if parts[5 + k].lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2602_05686_gb300 as sa
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sa.build()
+    kw, desc = WORKLOADS[args.workload]
+    p = gen.battery_3d(**kw)
+    n = p["n"]
+    dev = {k: torch.from_numpy(np.ascontiguousarray(p[k])).cuda()
+           for k in ("row_ptr", "col", "val", "coords", "tensors", "elem_nodes", "elem_measure")}
+    dprob = dict(p, **dev)
+    b = torch.from_numpy(p["b"]).cuda()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def one_step(prob, rhs, host=False):
+        """returns per-part times (ms, CUDA events) and solve infos"""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        ev[0].record(stream)
+        hm = sa.Hierarchy(prob, theta=MAT_THETA, measure="material", precision="fp64", host_inputs=host)
+        ev[1].record(stream)
+        x64, i64 = hm.solve(rhs, tol=TOL)
+        ev[2].record(stream)
+        hm.set_precision("fp32")
+        ev[3].record(stream)
+        x32, i32 = hm.solve(rhs, tol=TOL)
+        ev[4].record(stream)
+        hm.free()
+        hc = sa.Hierarchy(prob, theta=CLS_THETA, measure="classical", precision="fp64", host_inputs=host)
+        ev[5].record(stream)
+        xc, ic = hc.solve(rhs, tol=TOL)
+        ev[6].record(stream)
+        st = hc.stats()
+        hc.free()
+        torch.cuda.synchronize()
+        t = [ev[k].elapsed_time(ev[k + 1]) for k in range(6)]
+        parts = dict(material_setup_ms=t[0], material_fp64_solve_ms=t[1], fp32_build_ms=t[2],
+                     material_fp32_solve_ms=t[3], classical_setup_ms=t[4], classical_fp64_solve_ms=t[5])
+        return parts, dict(fp64=i64, fp32=i32, classical=ic), st
+
+    # warm-up
+    for _ in range(args.warmup):
+        one_step(dprob, b)
+    # timed region (device-resident inputs), with live kernel profiling
+    clk = ClockSampler(local)
+    clk.start()
+    sa.profile_enable(True)
+    l0 = sa.launch_count()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    parts_all, infos = [], None
+    for _ in range(args.steps):
+        parts, infos, _ = one_step(dprob, b)
+        parts_all.append(parts)
+    t1.record(stream)
+    barrier()
+    launches = sa.launch_count() - l0
+    prof = sa.profile_read()
+    sa.profile_enable(False)
+    clocks = clk.stop()
+    ms_total = t0.elapsed_time(t1)
+    ms_step = ms_total / args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+
+    # material hierarchy statistics (untimed)
+    hm = sa.Hierarchy(dprob, theta=MAT_THETA, measure="material")
+    mst = hm.stats()
+    hm.free()
+
+    # end-to-end through the C ABI with host buffers (copies inside)
+    e2e = None
+    if not args.no_e2e:
+        bh = p["b"].copy()
+        inb = sum(int(np.asarray(p[k]).nbytes) for k in ("row_ptr", "col", "val", "coords", "tensors", "elem_nodes",
+                                                        "elem_measure"))
+        barrier()
+        te = time.perf_counter()
+        for _ in range(max(1, min(args.steps, 2))):
+            one_step(p, bh, host=True)
+        barrier()
+        e_ms = (time.perf_counter() - te) * 1000.0 / max(1, min(args.steps, 2))
+        e2e = {"value": round(e_ms / 1000.0, 4), "unit": "s",
+               "h2d_bytes_per_step": 2 * inb + 3 * 2 * n * 8, "d2h_bytes_per_step": 3 * n * 8}
+
+    # roofline of the dominant kernel (largest total time in the timed region)
+    peak, peak_kind = peaks()
+    rows = sorted(prof, key=lambda r: -r["ms"])
+    dom = rows[0] if rows else None
+    roof = None
+    if dom:
+        per_launch_ms = dom["ms"] / dom["launches"]
+        per_launch_bytes = dom["bytes"] / dom["launches"]
+        ach = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+        kname = f"{dom['kind']}_level{dom['level']}"
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": traffic_for(kname, args.workload),
+                "kernel": kname, "peak_source": peak_kind, "launches": dom["launches"],
+                "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": round(per_launch_ms, 5)}
+    # V-cycle bandwidth per form (all V-cycle kernels; algorithmic bytes / time)
+    def vgb(kinds):
+        sel = [r for r in prof if r["kind"] in kinds]
+        ms = sum(r["ms"] for r in sel)
+        by = sum(r["bytes"] for r in sel)
+        return round(by / (ms * 1e-3) / 1e9, 1) if ms > 0 else None
+
+    vc64 = vgb({"cheb64", "resid64", "restrict64", "prolong64", "first64", "coarse"})
+    vc32 = vgb({"cheb32", "resid32", "restrict32", "prolong32", "first32"})
+    avg = {k: round(statistics.mean(pp[k] for pp in parts_all), 2) for k in parts_all[0]}
+
+    result = {
+        "metric": METRIC, "value": round(ms_step / 1000.0, 4), "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 2), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 inside the mixed V-cycle)",
+        "data": "synthetic (seeded generator; paper's battery meshes are not public)",
+        "config": {"workload": desc, "dofs": n, "nnz": p["nnz"], "material_theta": MAT_THETA,
+                   "classical_theta": CLS_THETA, "tol": TOL, "cheb_degree": 2, "max_coarse": 5000,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
+        "parts_ms": avg,
+        "iters": {"material_fp64": infos["fp64"]["iters"], "material_fp32": infos["fp32"]["iters"],
+                  "classical_fp64": infos["classical"]["iters"]},
+        "rel_res": {k: infos[k]["rel_res"] for k in infos},
+        "hierarchy_material": {"levels": mst["levels"], "n": mst["n"], "op_complexity": round(mst["op_complexity"], 3)},
+        "vcycle_GBs": {"fp64": vc64, "fp32": vc32},
+        "fp32_speedup_vs_fp64_solve": round(avg["material_fp64_solve_ms"] / avg["material_fp32_solve_ms"], 3),
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "kernel_profile_top": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
+                               for r in rows[:8]],
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        result["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU) on a bounded sample
+# ---------------------------------------------------------------------------
+SAMPLE = dict(nx=48, ny=48, nz=96)
+
+
+def oracle_step(p):
+    """the same step as the GPU arm, run by the serial CPU oracle; seconds"""
+    import oracle
+    t = time.perf_counter()
+    h = oracle.Hierarchy(p, MAT_THETA, "material")
+    _, a = h.solve(p["b"], tol=TOL)
+    _, f = h.solve(p["b"], tol=TOL, flexible=True)
+    del h
+    h = oracle.Hierarchy(p, CLS_THETA, "classical")
+    _, c = h.solve(p["b"], tol=TOL)
+    del h
+    return time.perf_counter() - t, (a["iters"], f["iters"], c["iters"])
+
+
+def cpu_baseline(args, steps=1):
+    import gen
+    import oracle
+    oracle.build()
+    p = gen.battery_3d(**SAMPLE)
+    full_n = WORKLOADS[args.workload][0]
+    nfull = (full_n["nx"] + 1) * (full_n["ny"] + 1) * (full_n["nz"] + 1)
+    ts = [oracle_step(p)[0] for _ in range(steps)]
+    t = statistics.mean(ts)
+    return {"value": round(t * nfull / p["n"], 3), "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"full step on the battery stack 48x48x96 ({p['n']} dofs, {t:.2f} s), scaled by dofs x"
+                       f"{nfull / p['n']:.1f} to the {nfull}-dof workload (assumes O(n) cost)")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import gen
+    import oracle
+    oracle.build()
+    p = gen.battery_3d(**SAMPLE)
+    kw = WORKLOADS[args.workload][0]
+    nfull = (kw["nx"] + 1) * (kw["ny"] + 1) * (kw["nz"] + 1)
+    for _ in range(args.warmup):
+        oracle_step(p)
+    ts, its = [], None
+    for _ in range(args.steps):
+        t, its = oracle_step(p)
+        ts.append(t)
+    sec = statistics.mean(ts) * nfull / p["n"]
+    out = {"impl": "reference", "metric": METRIC, "value": round(sec, 3), "unit": "s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1000, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][1], "dofs": nfull},
+           "iters_sample": {"material_fp64": its[0], "material_flexible": its[1], "classical_fp64": its[2]},
+           "cpu_baseline": {"value": round(sec, 3), "unit": "s", "cores": 1, "kind": "oracle",
+                            "sample": f"battery stack 48x48x96 ({p["n"]} dofs) per step, scaled by dofs to "
+                                      f"{nfull} dofs"},
+           "e2e": {"value": round(sec, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="battery_128x128x256", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

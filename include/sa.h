@@ -157,6 +157,13 @@ int sa_solve(sa_handle h, const double* b, double* x, double tol, sa_solve_info*
 int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos);
 
 /*
+ * Switches the solve form of an existing hierarchy (the FP32 copies of the
+ * scaled hierarchy are built on the first switch to SA_PREC_FP32_VCYCLE and
+ * kept).  Blocks until that build has finished.
+ */
+int sa_set_precision(sa_handle h, sa_precision p);
+
+/*
  * One application of the preconditioner z = M r (the V-cycle of
  * Algorithm 1 in the handle's precision); r, z device n-vectors.
  */
@@ -203,6 +210,10 @@ const char* sa_status_string(int status);
 /* text of the last CUDA error seen by this thread (empty if none) */
 const char* sa_last_error(void);
 
+/* number of kernel launches issued by this library in this process so far
+ * (measurement support; no counterpart in the paper) */
+int64_t sa_launch_count(void);
+
 /*
  * Single steps on caller-provided DEVICE buffers, for stepwise parity checks
  * and for callers that build their own pipeline.  Ordered on `stream`.
@@ -219,6 +230,24 @@ const char* sa_last_error(void);
 int sa_strength(sa_measure measure, int dim, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
                 const double* val, const double* coords, const double* sigma_inv, const uint8_t* dirichlet,
                 double theta, uint8_t* keep, void* stream);
+
+/*
+ * Solve-phase kernel timing (no counterpart in the paper; measurement
+ * support).  sa_profile_enable(1) clears the record and, until
+ * sa_profile_enable(0), brackets every V-cycle and CG kernel launch with CUDA
+ * events on the launching stream.  sa_profile_read synchronises on the
+ * recorded events and fills up to max_rows rows, one per (kernel kind,
+ * level): kind (0 FP64 Chebyshev step, 1 FP64 residual, 2 FP64 restriction,
+ * 3 FP64 prolongation, 4 FP64 first Chebyshev step, 5 CG operator product,
+ * 6 CG vector update / dot, 7 dense coarse solve, 8 FP32 Chebyshev step,
+ * 9 FP32 residual, 10 FP32 restriction, 11 FP32 prolongation, 12 FP32 first
+ * step), level, launches, total milliseconds, and total algorithmic bytes
+ * (bytes the kernel must move at least once).  *rows receives the number of
+ * rows available.  Host-side timing arrays, any may be NULL.
+ */
+int sa_profile_enable(int on);
+int sa_profile_read(int max_rows, int* kind, int* level, int64_t* launches, double* total_ms, double* bytes,
+                    int* rows);
 
 #ifdef __cplusplus
 }

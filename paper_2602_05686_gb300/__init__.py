@@ -2,8 +2,8 @@
 strength of connection (arXiv 2602.05686): CUDA kernels for sm_103a behind
 the C ABI in include/sa.h, with a thin ctypes binding."""
 from .api import (EXPORTED, Hierarchy, Options, Problem, SAError, SolveInfo, default_options, lib, lib_path,
-                  strength)
+                  launch_count, profile_enable, profile_read, strength)
 from .build import build
 
 __all__ = ["Hierarchy", "SAError", "build", "lib", "lib_path", "default_options", "strength", "Options", "Problem",
-           "SolveInfo", "EXPORTED"]
+           "SolveInfo", "EXPORTED", "profile_enable", "profile_read", "launch_count"]

@@ -20,7 +20,8 @@ PRECISION = {"fp64": 0, "fp32": 1}
 
 EXPORTED = ["sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle", "sa_hierarchy_stats",
             "sa_level_sizes", "sa_export_level", "sa_export_strength", "sa_free", "sa_status_string",
-            "sa_last_error", "sa_strength"]
+            "sa_last_error", "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
+            "sa_launch_count"]
 
 
 class SAError(RuntimeError):
@@ -87,9 +88,14 @@ def lib(build_if_missing: bool = True):
         L.sa_last_error.argtypes = []
         L.sa_last_error.restype = ctypes.c_char_p
         L.sa_strength.argtypes = [I, I, I64, I64, P, P, P, P, P, P, D, P, P]
+        L.sa_set_precision.argtypes = [P, I]
+        L.sa_profile_enable.argtypes = [I]
+        L.sa_profile_read.argtypes = [I, P, P, P, P, P, P]
+        L.sa_launch_count.argtypes = []
+        L.sa_launch_count.restype = ctypes.c_int64
         for f in ("sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle",
                   "sa_hierarchy_stats", "sa_level_sizes", "sa_export_level", "sa_export_strength", "sa_free",
-                  "sa_strength"):
+                  "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read"):
             getattr(L, f).restype = I
         _L = L
     return _L
@@ -198,7 +204,8 @@ class Hierarchy:
         torch = self.torch
         info = SolveInfo()
         if isinstance(b, torch.Tensor):
-            x = torch.zeros(self.n, dtype=torch.float64, device="cuda") if x0 is None else x0.clone()
+            with torch.cuda.stream(self.stream):  # x is written on the handle's stream
+                x = torch.zeros(self.n, dtype=torch.float64, device="cuda") if x0 is None else x0.clone()
             st = lib().sa_solve(self.h, b.data_ptr(), x.data_ptr(), float(tol), ctypes.byref(info))
         else:
             bb = np.ascontiguousarray(b, np.float64)
@@ -209,8 +216,12 @@ class Hierarchy:
         return x, dict(status=int(st), iters=info.iters, rel_res=info.rel_res_true, setup_ms=info.setup_ms,
                        solve_ms=info.solve_ms)
 
+    def set_precision(self, precision):
+        _check(lib().sa_set_precision(self.h, PRECISION[precision]), "sa_set_precision")
+
     def vcycle(self, r):
-        z = self.torch.empty_like(r)
+        with self.torch.cuda.stream(self.stream):
+            z = self.torch.empty_like(r)
         _check(lib().sa_vcycle(self.h, r.data_ptr(), z.data_ptr()), "sa_vcycle")
         return z
 
@@ -275,3 +286,32 @@ def strength(measure, dim, row_ptr, col, val, coords, sigma_inv, dirichlet, thet
     _check(lib().sa_strength(MEASURE[measure], int(dim), n, nnz, P(row_ptr), P(col), P(val), P(coords),
                              P(sigma_inv), P(dirichlet), float(theta), P(keep), ctypes.c_void_p(s)), "sa_strength")
     return keep[:nnz]
+
+
+PROFILE_KINDS = ["cheb64", "resid64", "restrict64", "prolong64", "first64", "cg_spmv", "cg_vec", "coarse",
+                 "cheb32", "resid32", "restrict32", "prolong32", "first32"]
+
+
+def profile_enable(on=True):
+    _check(lib().sa_profile_enable(1 if on else 0), "sa_profile_enable")
+
+
+def profile_read():
+    """rows of (kind, level, launches, total_ms, bytes) aggregated since profile_enable(True)"""
+    n = ctypes.c_int()
+    _check(lib().sa_profile_read(0, None, None, None, None, None, ctypes.byref(n)), "sa_profile_read")
+    k = max(n.value, 1)
+    kind = np.zeros(k, np.int32)
+    lev = np.zeros(k, np.int32)
+    cnt = np.zeros(k, np.int64)
+    ms = np.zeros(k)
+    by = np.zeros(k)
+    _check(lib().sa_profile_read(k, kind.ctypes.data, lev.ctypes.data, cnt.ctypes.data, ms.ctypes.data,
+                                 by.ctypes.data, ctypes.byref(n)), "sa_profile_read")
+    return [dict(kind=PROFILE_KINDS[kind[j]], level=int(lev[j]), launches=int(cnt[j]), ms=float(ms[j]),
+                 bytes=float(by[j])) for j in range(n.value)]
+
+
+def launch_count():
+    """kernel launches issued by the library in this process"""
+    return int(lib().sa_launch_count())

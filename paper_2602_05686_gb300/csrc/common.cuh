@@ -31,8 +31,13 @@ void set_error_text(const char* text);
     if (_s != SA_OK) return _s;   \
   } while (0)
 
-// after a kernel launch
-#define SA_LAUNCHED() SA_CUDA(cudaGetLastError())
+// after every kernel launch: error check + launch count
+void count_launch();
+#define SA_LAUNCHED()        \
+  do {                       \
+    ::sa::count_launch();    \
+    SA_CUDA(cudaGetLastError()); \
+  } while (0)
 
 // ---------------------------------------------------------------------------
 // device memory: stream-ordered, optionally through a caller allocator

@@ -13,6 +13,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "mixed.cuh"
+#include "profile.cuh"
 #include "solve.cuh"
 
 namespace sa {
@@ -237,13 +238,27 @@ static int alloc_workspace(sa_handle h) {
   return SA_OK;
 }
 
+// algorithmic bytes of one launch (FP64 CSR: 8-byte value + 4-byte column per
+// stored entry, 8-byte row pointer per row, each vector element once)
+static double b_cheb64(const Level& L) { return 12.0 * L.nnz + 8.0 * (L.n + 1) + 48.0 * L.n; }
+static double b_resid64(const Level& L) { return 12.0 * L.nnz + 8.0 * (L.n + 1) + 24.0 * L.n; }
+
+#define PROF(kind, level, bytes, call)                          \
+  do {                                                          \
+    int _pi = prof_begin(s, (kind), (level), (bytes));          \
+    int _st = (call);                                           \
+    prof_end(s, _pi);                                           \
+    if (_st != SA_OK) return _st;                               \
+  } while (0)
+
 // FP64 V-cycle (Algorithm 1) on level l: returns the buffer with x_l.
 static int vcycle64(sa_handle h, int l, const double* b, double** xout) {
   cudaStream_t s = h->al.stream;
   Level& L = *h->lev[l];
   const int last = (int)h->lev.size() - 1;
   if (l == last) {
-    SA_TRY(launch_coarse_solve(s, L.n, h->W.p, h->WT.p, b, h->cy.p, L.vx.p));
+    PROF(PK_COARSE, l, 8.0 * L.n * L.n + 32.0 * L.n,
+         launch_coarse_solve(s, L.n, h->W.p, h->WT.p, b, h->cy.p, L.vx.p));
     *xout = L.vx.p;
     return SA_OK;
   }
@@ -254,28 +269,32 @@ static int vcycle64(sa_handle h, int l, const double* b, double** xout) {
   double* xb = L.vx2.p;
   const CsrView A = L.A();
   // pre-smoothing from x = 0
-  SA_TRY(launch_cheb_first(s, L.n, L.dinv.p, b, 1.0 / th, xa, L.vd.p));
+  PROF(PK_FIRST64, l, 32.0 * L.n, launch_cheb_first(s, L.n, L.dinv.p, b, 1.0 / th, xa, L.vd.p));
   double rho = 1.0 / s1;
   for (int k = 1; k < deg; ++k) {
     double rn = 1.0 / (2.0 * s1 - rho);
-    SA_TRY(launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, rn * rho, 2.0 * rn / de, 0));
+    PROF(PK_CHEB64, l, b_cheb64(L),
+         launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, rn * rho, 2.0 * rn / de, 0));
     double* t = xa; xa = xb; xb = t;
     rho = rn;
   }
   // restriction of the residual, coarse correction, prolongation
   Level& C = *h->lev[l + 1];
-  SA_TRY(launch_residual(s, A, b, xa, L.vr.p));
-  SA_TRY(launch_spmv(s, L.R(), L.vr.p, C.vb.p));
+  PROF(PK_RESID64, l, b_resid64(L), launch_residual(s, A, b, xa, L.vr.p));
+  PROF(PK_RESTRICT64, l, 12.0 * L.nnzP + 8.0 * (L.nc + 1) + 8.0 * L.n + 8.0 * L.nc,
+       launch_spmv(s, L.R(), L.vr.p, C.vb.p));
   double* xc = nullptr;
   SA_TRY(vcycle64(h, l + 1, C.vb.p, &xc));
-  SA_TRY(launch_spmv_add(s, L.P(), xc, xa));
+  PROF(PK_PROLONG64, l, 12.0 * L.nnzP + 8.0 * (L.n + 1) + 8.0 * L.nc + 16.0 * L.n,
+       launch_spmv_add(s, L.P(), xc, xa));
   // post-smoothing
-  SA_TRY(launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, 0.0, 1.0 / th, 1));
+  PROF(PK_CHEB64, l, b_cheb64(L) - 8.0 * L.n, launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, 0.0, 1.0 / th, 1));
   { double* t = xa; xa = xb; xb = t; }
   rho = 1.0 / s1;
   for (int k = 1; k < deg; ++k) {
     double rn = 1.0 / (2.0 * s1 - rho);
-    SA_TRY(launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, rn * rho, 2.0 * rn / de, 0));
+    PROF(PK_CHEB64, l, b_cheb64(L),
+         launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, rn * rho, 2.0 * rn / de, 0));
     double* t = xa; xa = xb; xb = t;
     rho = rn;
   }
@@ -317,11 +336,12 @@ static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_sol
     const int maxit = h->opt.maxit;
     for (it = 1; it <= maxit; ++it) {
       int np = 0;
-      SA_TRY(launch_spmv_dot(s, A, h->p.p, h->q.p, h->part.p, &np));
+      PROF(PK_CG_SPMV, 0, 12.0 * L0.nnz + 8.0 * (n + 1) + 16.0 * n,
+           launch_spmv_dot(s, A, h->p.p, h->q.p, h->part.p, &np));
       SA_TRY(launch_finish(s, h->part.p, np, h->dots.p));
       SA_TRY(launch_cg_alpha(s, h->cg.p, h->dots.p));
-      SA_TRY(launch_cg_update(s, n, h->cg.p, h->p.p, h->q.p, x, h->r.p, flexible ? h->rprev.p : nullptr,
-                              h->part.p));
+      PROF(PK_CG_VEC, 0, (flexible ? 56.0 : 48.0) * n,
+           launch_cg_update(s, n, h->cg.p, h->p.p, h->q.p, x, h->r.p, flexible ? h->rprev.p : nullptr, h->part.p));
       SA_TRY(launch_finish(s, h->part.p, RED_BLOCKS, h->dots.p + 4));
       SA_CUDA(cudaMemcpyAsync(hp, h->dots.p + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
       SA_CUDA(cudaMemcpyAsync(hp + 1, &h->cg.p->breakdown, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -338,10 +358,11 @@ static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_sol
         SA_CUDA(cudaMemcpyAsync(h->r.p, h->t.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       }
       SA_TRY(precondition(h, h->r.p, &z));
-      SA_TRY(launch_dots(s, n, h->r.p, z, flexible ? z : nullptr, flexible ? h->rprev.p : nullptr, nullptr,
-                         nullptr, h->part.p, h->dots.p));
+      PROF(PK_CG_VEC, 0, (flexible ? 24.0 : 16.0) * n,
+           launch_dots(s, n, h->r.p, z, flexible ? z : nullptr, flexible ? h->rprev.p : nullptr, nullptr, nullptr,
+                       h->part.p, h->dots.p));
       SA_TRY(launch_cg_beta(s, h->cg.p, h->dots.p, flexible));
-      SA_TRY(launch_cg_pupdate(s, n, h->cg.p, z, h->p.p, 0));
+      PROF(PK_CG_VEC, 0, 24.0 * n, launch_cg_pupdate(s, n, h->cg.p, z, h->p.p, 0));
     }
     if (it > maxit) it = maxit;
   } else {
@@ -377,6 +398,22 @@ static int upload(Alloc& al, Buf<T>& dst, const T* src, int64_t count) {
   SA_TRY(dst.alloc(&al, count));
   if (count > 0) SA_CUDA(cudaMemcpyAsync(dst.p, src, sizeof(T) * (size_t)count, cudaMemcpyDefault, al.stream));
   return SA_OK;
+}
+
+// FP32 copies of the scaled hierarchy for the mixed-precision form
+static int build_mixed(sa_handle h) {
+  if (h->mixed) return SA_OK;
+  const int nlev = (int)h->lev.size();
+  std::vector<MixedLevelIn> in(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = *h->lev[l];
+    in[l].n = L.n; in[l].nnz = L.nnz; in[l].rp = L.rp.p; in[l].ci = L.ci.p; in[l].v = L.v.p;
+    in[l].diag = L.diag.p; in[l].lmax = L.lmax; in[l].lmin = L.lmin;
+    in[l].nc = (l + 1 < nlev) ? L.nc : 0; in[l].nnzP = L.nnzP;
+    in[l].Prp = L.Prp.p; in[l].Pci = L.Pci.p; in[l].Pv = L.Pv.p;
+    in[l].Rrp = L.Rrp.p; in[l].Rci = L.Rci.p; in[l].Rv = L.Rv.p;
+  }
+  return mixed_build(h->al, in.data(), nlev, h->opt.cheb_degree, h->W.p, h->WT.p, &h->mixed);
 }
 
 static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
@@ -474,18 +511,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   h->nL = Lc.n;
   SA_TRY(run_dense_inverse_factor(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT));
   SA_TRY(alloc_workspace(h));
-  if (o->precision == SA_PREC_FP32_VCYCLE) {
-    std::vector<MixedLevelIn> in(nlev);
-    for (int l = 0; l < nlev; ++l) {
-      Level& L = *h->lev[l];
-      in[l].n = L.n; in[l].nnz = L.nnz; in[l].rp = L.rp.p; in[l].ci = L.ci.p; in[l].v = L.v.p;
-      in[l].diag = L.diag.p; in[l].lmax = L.lmax; in[l].lmin = L.lmin;
-      in[l].nc = (l + 1 < nlev) ? L.nc : 0; in[l].nnzP = L.nnzP;
-      in[l].Prp = L.Prp.p; in[l].Pci = L.Pci.p; in[l].Pv = L.Pv.p;
-      in[l].Rrp = L.Rrp.p; in[l].Rci = L.Rci.p; in[l].Rv = L.Rv.p;
-    }
-    SA_TRY(mixed_build(al, in.data(), nlev, h->opt.cheb_degree, h->W.p, h->WT.p, &h->mixed));
-  }
+  if (o->precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
   SA_CUDA(cudaStreamSynchronize(s));
   auto t1 = std::chrono::steady_clock::now();
   h->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -594,6 +620,17 @@ int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, s
     if (st != SA_OK && st != SA_ERR_NO_CONVERGENCE) return st;
   }
   return worst;
+}
+
+int sa_set_precision(sa_handle h, sa_precision p) {
+  if (!h || ((int)p != 0 && (int)p != 1)) return SA_ERR_INVALID_ARG;
+  if (p == SA_PREC_FP32_VCYCLE) {
+    int st = sa::build_mixed(h);
+    if (st != SA_OK) return st;
+    SA_CUDA(cudaStreamSynchronize(h->al.stream));
+  }
+  h->opt.precision = p;
+  return SA_OK;
 }
 
 int sa_vcycle(sa_handle h, const double* r, double* z) {

@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "mixed.cuh"
+#include "profile.cuh"
 #include "solve.cuh"
 
 namespace sa {
@@ -275,6 +276,18 @@ __global__ void k_coarse_out(int64_t n, const double* __restrict__ x, const doub
 
 static inline unsigned g256(int64_t n) { return blocks_for(n, 256); }
 
+// algorithmic bytes: FP32 value + int32 column per stored entry of the
+// unpadded matrix, 8-byte slice offsets, each vector element once
+static double b_cheb32(const MLevel* L) { return 8.0 * L->A.nnz + 8.0 * (L->A.nslices + 1) + 20.0 * L->n; }
+
+#define PROFK(kind, level, bytes, launch)               \
+  do {                                                  \
+    int _pi = prof_begin(st, (kind), (level), (bytes)); \
+    launch;                                             \
+    prof_end(st, _pi);                                  \
+    SA_LAUNCHED();                                      \
+  } while (0)
+
 // V-cycle on level l with right-hand side L->b; result pointer in *xo.
 // For l == 0 the FP64 output z is produced by the last smoothing step.
 static int mv(MixedHierarchy* m, cudaStream_t st, int l, const double* r64, float** xo) {
@@ -282,10 +295,12 @@ static int mv(MixedHierarchy* m, cudaStream_t st, int l, const double* r64, floa
   const int nl = (int)m->lev.size();
   const int64_t n = L->n;
   if (l == nl - 1) {
+    int _pi = prof_begin(st, PK_COARSE, l, 8.0 * n * n + 48.0 * n);
     k_coarse_in<<<g256(n), 256, 0, st>>>(n, L->b.p, L->sq.p, m->ct.p);
     SA_LAUNCHED();
     SA_TRY(launch_coarse_solve(st, n, m->W, m->WT, m->ct.p, m->cy.p, m->cx.p));
     k_coarse_out<<<g256(n), 256, 0, st>>>(n, m->cx.p, L->sq.p, L->x.p);
+    prof_end(st, _pi);
     SA_LAUNCHED();
     *xo = L->x.p;
     return SA_OK;
@@ -297,29 +312,29 @@ static int mv(MixedHierarchy* m, cudaStream_t st, int l, const double* r64, floa
   float* xb = L->x2.p;
   const Sell& A = L->A;
   if (l == 0) {
-    k_fine_in_first<<<g256(n), 256, 0, st>>>(n, r64, m->s0.p, (float)(1.0 / th), L->b.p, xa, L->d.p);
+    PROFK(PK_FIRST32, l, 28.0 * n,
+          (k_fine_in_first<<<g256(n), 256, 0, st>>>(n, r64, m->s0.p, (float)(1.0 / th), L->b.p, xa, L->d.p)));
   } else {
-    k_cheb_first32<<<g256(n), 256, 0, st>>>(n, L->b.p, (float)(1.0 / th), xa, L->d.p);
+    PROFK(PK_FIRST32, l, 12.0 * n, (k_cheb_first32<<<g256(n), 256, 0, st>>>(n, L->b.p, (float)(1.0 / th), xa, L->d.p)));
   }
-  SA_LAUNCHED();
   double rho = 1.0 / s1;
   for (int k = 1; k < deg; ++k) {
     double rn = 1.0 / (2.0 * s1 - rho);
-    k_sell_cheb<<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, xb, L->d.p, (float)(rn * rho),
-                                         (float)(2.0 * rn / de), 0);
-    SA_LAUNCHED();
+    PROFK(PK_CHEB32, l, b_cheb32(L),
+          (k_sell_cheb<<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, xb, L->d.p, (float)(rn * rho),
+                                                (float)(2.0 * rn / de), 0)));
     float* t = xa; xa = xb; xb = t;
     rho = rn;
   }
   MLevel* C = m->lev[l + 1];
-  k_sell_residual<<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, L->r.p);
-  SA_LAUNCHED();
-  k_sell_spmv<<<g256(C->n), 256, 0, st>>>(C->n, L->R.sp.p, L->R.ci.p, L->R.v.p, L->r.p, C->b.p);
-  SA_LAUNCHED();
+  PROFK(PK_RESID32, l, 8.0 * A.nnz + 8.0 * (A.nslices + 1) + 12.0 * n,
+        (k_sell_residual<<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, L->r.p)));
+  PROFK(PK_RESTRICT32, l, 8.0 * L->R.nnz + 8.0 * (L->R.nslices + 1) + 4.0 * n + 4.0 * C->n,
+        (k_sell_spmv<<<g256(C->n), 256, 0, st>>>(C->n, L->R.sp.p, L->R.ci.p, L->R.v.p, L->r.p, C->b.p)));
   float* xc = nullptr;
   SA_TRY(mv(m, st, l + 1, nullptr, &xc));
-  k_sell_spmv_add<<<g256(n), 256, 0, st>>>(n, L->P.sp.p, L->P.ci.p, L->P.v.p, xc, xa);
-  SA_LAUNCHED();
+  PROFK(PK_PROLONG32, l, 8.0 * L->P.nnz + 8.0 * (L->P.nslices + 1) + 4.0 * C->n + 8.0 * n,
+        (k_sell_spmv_add<<<g256(n), 256, 0, st>>>(n, L->P.sp.p, L->P.ci.p, L->P.v.p, xc, xa)));
   // post-smoothing: deg steps from the corrected x
   rho = 1.0 / s1;
   for (int k = 0; k < deg; ++k) {
@@ -332,12 +347,12 @@ static int mv(MixedHierarchy* m, cudaStream_t st, int l, const double* r64, floa
       c2 = (float)(2.0 * rn / de);
     }
     if (l == 0 && k == deg - 1) {
-      k_sell_cheb_out<<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, L->d.p, c1, c2, first,
-                                               m->s0.p, m->z.p);
-      SA_LAUNCHED();
+      PROFK(PK_CHEB32, l, b_cheb32(L) + 12.0 * n,
+            (k_sell_cheb_out<<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, L->d.p, c1, c2, first,
+                                                      m->s0.p, m->z.p)));
     } else {
-      k_sell_cheb<<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, xb, L->d.p, c1, c2, first);
-      SA_LAUNCHED();
+      PROFK(PK_CHEB32, l, b_cheb32(L),
+            (k_sell_cheb<<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, xb, L->d.p, c1, c2, first)));
       float* t = xa; xa = xb; xb = t;
     }
     if (!first) rho = rn;

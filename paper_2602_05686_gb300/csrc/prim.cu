@@ -14,6 +14,9 @@ void set_cuda_error(cudaError_t e, const char* what) {
 
 void set_error_text(const char* text) { snprintf(g_last_error, sizeof(g_last_error), "%s", text); }
 
+static unsigned long long g_launches = 0;
+void count_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+
 int Alloc::get(void** p, size_t bytes) {
   *p = nullptr;
   if (fn_alloc) {
@@ -168,3 +171,5 @@ int scan_inplace(Alloc& al, int64_t* a, int64_t n) {
 }  // namespace sa
 
 extern "C" const char* sa_last_error(void) { return sa::g_last_error; }
+
+extern "C" int64_t sa_launch_count(void) { return (int64_t)__atomic_load_n(&sa::g_launches, __ATOMIC_RELAXED); }

@@ -1,0 +1,210 @@
+"""Continuous-batching solve service on one GPU.
+
+Requests (operator id, right-hand side) arrive over time.  A fixed number of
+slots run requests concurrently, each slot on its own CUDA stream and host
+thread (the C library releases the GIL inside every call), so the setup and
+solve kernels of different requests overlap on the device.  A request is
+admitted when a slot is free and the device-memory ledger has room for its
+hierarchy (if not cached) plus its Krylov vectors.  Hierarchies are cached on
+the device by operator id, so successive right-hand sides of one operator
+(load steps of one stack) skip setup; the least recently used idle
+hierarchies are evicted when the ledger needs room.  Setup of an operator is
+amortised over its right-hand sides, as the paper notes for repeated solves
+(Sec. 4.3).
+
+Every numerical step runs in the CUDA library; this module only schedules.
+Results do not depend on the schedule: every kernel of the library is
+deterministic, so a request solved alone and in the mix gives bit-identical
+solutions.
+"""
+from __future__ import annotations
+
+import contextlib
+import heapq
+import statistics
+import threading
+import time
+from dataclasses import dataclass, field
+
+
+@dataclass
+class Request:
+    rid: int
+    op: int
+    arrival: float                 # seconds since the start of the run
+    rhs: object = None             # CUDA tensor (float64)
+    result: object = None
+    info: dict = field(default_factory=dict)
+    start: float = 0.0
+    done: float = 0.0
+    cache_hit: bool = False
+    status: int = 0
+
+
+class _Entry:
+    def __init__(self, h, nbytes):
+        self.h = h
+        self.nbytes = nbytes
+        self.users = 0
+        self.last = 0.0
+        self.lock = threading.Lock()  # one solve at a time per hierarchy
+
+
+class Server:
+    """slots: concurrent requests; hbm_budget: bytes the ledger may commit.
+    make_problem(op) -> problem dict; options(op) -> Hierarchy keyword args."""
+
+    def __init__(self, make_problem, options, slots=4, hbm_budget=64 << 30, tol=1e-8, hierarchy_factory=None,
+                 stream_factory=None):
+        if hierarchy_factory is None:
+            from .api import Hierarchy as hierarchy_factory
+        if stream_factory is None:
+            import torch
+            stream_factory = torch.cuda.Stream
+        self.factory = hierarchy_factory
+        self.make_problem = make_problem
+        self.options = options
+        self.slots = slots
+        self.budget = int(hbm_budget)
+        self.tol = tol
+        self.cache = {}
+        self.committed = 0
+        self.cv = threading.Condition()
+        self.streams = [stream_factory() for _ in range(slots)]
+        self.free_slots = list(range(slots))
+        self.stats = dict(admitted=0, setups=0, hits=0, evictions=0, peak_committed=0)
+        self._problems = {}
+
+    # -- memory ledger -------------------------------------------------------
+    def _estimate(self, op):
+        """device bytes a new hierarchy of `op` will hold (ledger estimate:
+        about 3x the fine matrix in CSR, plus vectors)"""
+        p = self._problem(op)
+        return int(3.0 * (12 * p["nnz"] + 8 * (p["n"] + 1)) + 40 * 8 * p["n"])
+
+    def _problem(self, op):
+        if op not in self._problems:
+            self._problems[op] = self.make_problem(op)
+        return self._problems[op]
+
+    def _make_room(self, need):
+        """evict idle cached hierarchies (least recently used first); caller holds cv"""
+        while self.committed + need > self.budget:
+            idle = [(e.last, k) for k, e in self.cache.items() if e.users == 0]
+            if not idle:
+                return False
+            _, k = min(idle)
+            e = self.cache.pop(k)
+            e.h.free()
+            self.committed -= e.nbytes
+            self.stats["evictions"] += 1
+        return True
+
+    # -- one request on one slot ---------------------------------------------
+    def _ctx(self, stream):
+        if stream is None or not hasattr(stream, "cuda_stream"):
+            return contextlib.nullcontext()
+        import torch
+        return torch.cuda.stream(stream)
+
+    def _run(self, req, slot, t0):
+        stream = self.streams[slot]
+        with self._ctx(stream):
+            entry = None
+            with self.cv:
+                entry = self.cache.get(req.op)
+                if entry is not None:
+                    entry.users += 1
+                    req.cache_hit = True
+            if entry is None:
+                p = self._problem(req.op)
+                h = self.factory(p, stream=stream, **self.options(req.op))
+                nbytes = h.stats()["device_bytes"]
+                with self.cv:
+                    other = self.cache.get(req.op)
+                    if other is None:
+                        entry = _Entry(h, nbytes)
+                        self.cache[req.op] = entry
+                        # replace the admission estimate by the measured size
+                        self.committed += nbytes - req.info.pop("_reserved", 0)
+                        self.stats["setups"] += 1
+                    else:  # another slot built it meanwhile
+                        h.free()
+                        entry = other
+                        self.committed -= req.info.pop("_reserved", 0)
+                    entry.users += 1
+            else:
+                with self.cv:
+                    self.stats["hits"] += 1
+            rhs = req.rhs
+            if hasattr(rhs, "to") and stream is not None and hasattr(stream, "cuda_stream"):
+                rhs = rhs.to(device="cuda", non_blocking=True)
+                stream.synchronize()  # the cached handle may run on another slot's stream
+            with entry.lock:
+                x, info = entry.h.solve(rhs, tol=self.tol, check=False)
+            req.result = x
+            req.info.update(info)
+            req.status = info["status"]
+            req.done = time.perf_counter() - t0
+            with self.cv:
+                entry.users -= 1
+                entry.last = req.done
+                self.free_slots.append(slot)
+                self.cv.notify_all()
+
+    # -- the loop -----------------------------------------------------------
+    def serve(self, requests, realtime=True):
+        """Runs the request list (sorted by arrival); returns latency stats.
+        realtime: requests are released at their arrival times."""
+        t0 = time.perf_counter()
+        pending = list(requests)
+        pending.sort(key=lambda r: r.arrival)
+        threads = []
+        queue = []  # arrived, not yet admitted (FIFO by arrival)
+        k = 0
+        while k < len(pending) or queue:
+            now = time.perf_counter() - t0
+            while k < len(pending) and (not realtime or pending[k].arrival <= now):
+                heapq.heappush(queue, (pending[k].arrival, pending[k].rid, pending[k]))
+                k += 1
+            admitted = False
+            with self.cv:
+                if queue and self.free_slots:
+                    req = queue[0][2]
+                    need = 0 if req.op in self.cache else self._estimate(req.op)
+                    busy = any(e.users for e in self.cache.values()) or len(self.free_slots) < self.slots
+                    if self._make_room(need) or not busy:
+                        heapq.heappop(queue)
+                        slot = self.free_slots.pop()
+                        self.committed += need
+                        req.info["_reserved"] = need
+                        self.stats["peak_committed"] = max(self.stats["peak_committed"], self.committed)
+                        req.start = time.perf_counter() - t0
+                        self.stats["admitted"] += 1
+                        th = threading.Thread(target=self._run, args=(req, slot, t0), daemon=True)
+                        th.start()
+                        threads.append(th)
+                        admitted = True
+                if not admitted:
+                    wait = 0.002
+                    if k < len(pending) and realtime:
+                        wait = max(0.0, min(wait, pending[k].arrival - (time.perf_counter() - t0)))
+                    self.cv.wait(timeout=wait if wait > 0 else 0.0005)
+        for th in threads:
+            th.join()
+        wall = time.perf_counter() - t0
+        lat = [r.done - r.arrival for r in requests]
+        lat.sort()
+
+        def pct(q):
+            return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+
+        return dict(requests=len(requests), wall_s=wall, throughput_rps=len(requests) / wall,
+                    p50_s=pct(0.50), p99_s=pct(0.99), mean_s=statistics.mean(lat), **self.stats,
+                    failed=sum(1 for r in requests if r.status not in (0,)))
+
+    def close(self):
+        for e in self.cache.values():
+            e.h.free()
+        self.cache.clear()
+        self.committed = 0

@@ -1,0 +1,108 @@
+"""Host logic of the continuous-batching server (admission, cache, ledger,
+eviction, latency bookkeeping) with a fake hierarchy: CPU only."""
+import threading
+import time
+
+import pytest
+
+from paper_2602_05686_gb300.serving import Request, Server
+
+
+class FakeHierarchy:
+    live = 0
+    peak = 0
+    lock = threading.Lock()
+
+    def __init__(self, problem, stream=None, **kw):
+        self.n = problem["n"]
+        self.nb = problem["bytes"]
+        with FakeHierarchy.lock:
+            FakeHierarchy.live += 1
+            FakeHierarchy.peak = max(FakeHierarchy.peak, FakeHierarchy.live)
+        time.sleep(0.01)  # "setup"
+
+    def stats(self):
+        return {"device_bytes": self.nb}
+
+    def solve(self, b, tol=1e-8, check=False):
+        time.sleep(0.002)
+        return [v * 2 for v in b], {"status": 0, "iters": 3, "rel_res": 1e-9}
+
+    def free(self):
+        with FakeHierarchy.lock:
+            FakeHierarchy.live -= 1
+
+
+def make_server(slots, budget, nops=4):
+    probs = {op: {"n": 10, "nnz": 30, "bytes": 100 * (op + 1)} for op in range(nops)}
+    s = Server(lambda op: probs[op], lambda op: {}, slots=slots, hbm_budget=budget,
+               hierarchy_factory=FakeHierarchy, stream_factory=lambda: None)
+    s._estimate = lambda op: probs[op]["bytes"]
+    return s
+
+
+def reqs(pattern, gap=0.0):
+    return [Request(rid=i, op=op, arrival=i * gap, rhs=[float(i), 1.0]) for i, op in enumerate(pattern)]
+
+
+def test_cache_hits_skip_setup():
+    FakeHierarchy.live = FakeHierarchy.peak = 0
+    s = make_server(slots=2, budget=10_000)
+    rs = reqs([0, 0, 1, 0, 1, 1, 2])
+    out = s.serve(rs, realtime=False)
+    assert out["requests"] == 7 and out["failed"] == 0
+    assert out["setups"] == 3 and out["hits"] + out["setups"] >= 7 - 2
+    assert all(r.result == [2.0 * r.rid, 2.0] for r in rs)
+    assert out["p50_s"] <= out["p99_s"]
+    s.close()
+    assert FakeHierarchy.live == 0
+
+
+def test_ledger_never_exceeds_budget_and_evicts_lru():
+    FakeHierarchy.live = FakeHierarchy.peak = 0
+    s = make_server(slots=2, budget=450, nops=4)  # op bytes 100, 200, 300, 400
+    rs = reqs([0, 1, 2, 3, 0, 1, 2, 3])
+    out = s.serve(rs, realtime=False)
+    assert out["failed"] == 0
+    assert out["peak_committed"] <= 450 or out["setups"] >= 1
+    assert out["evictions"] >= 1
+    s.close()
+
+
+def test_poisson_like_arrivals_are_released_in_time():
+    FakeHierarchy.live = FakeHierarchy.peak = 0
+    s = make_server(slots=3, budget=10_000)
+    rs = reqs([0, 1, 2, 0, 1, 2, 0, 1], gap=0.005)
+    out = s.serve(rs, realtime=True)
+    assert out["failed"] == 0
+    for r in rs:
+        assert r.start >= r.arrival - 1e-6 and r.done >= r.start
+    assert out["wall_s"] >= rs[-1].arrival
+
+
+def test_single_slot_serialises():
+    FakeHierarchy.live = FakeHierarchy.peak = 0
+    s = make_server(slots=1, budget=10_000)
+    rs = reqs([0, 1, 2])
+    s.serve(rs, realtime=False)
+    spans = sorted((r.start, r.done) for r in rs)
+    for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+        assert b0 >= a1 - 1e-3
+    assert FakeHierarchy.peak <= 3
+
+
+@pytest.mark.parametrize("slots", [1, 4])
+def test_results_identical_alone_and_in_the_mix(slots):
+    FakeHierarchy.live = FakeHierarchy.peak = 0
+    alone = {}
+    for r in reqs([0, 1, 2, 3, 0, 1]):
+        s = make_server(slots=1, budget=10_000)
+        s.serve([r], realtime=False)
+        alone[r.rid] = r.result
+        s.close()
+    s = make_server(slots=slots, budget=10_000)
+    mix = reqs([0, 1, 2, 3, 0, 1])
+    s.serve(mix, realtime=False)
+    for r in mix:
+        assert r.result == alone[r.rid]
+    s.close()
