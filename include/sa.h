@@ -15,7 +15,7 @@
  *     aborts, traps or spins without a bound;
  *   - "device pointer" means memory of the current CUDA device; "host
  *     pointer" means ordinary or pinned host memory; calls that accept
- *     either detect the kind with cudaPointerGetAttributes;
+ *     either copy with cudaMemcpyDefault (unified addressing);
  *   - all GPU work of a handle is ordered on options.stream (a
  *     cudaStream_t; NULL = the legacy default stream); a handle must not be
  *     used from two host threads at once;

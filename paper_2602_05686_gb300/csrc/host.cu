@@ -12,9 +12,9 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
-#include "mixed.cuh"
 #include "profile.cuh"
 #include "solve.cuh"
+#include "vcycle.cuh"
 
 namespace sa {
 
@@ -37,24 +37,7 @@ struct Level {
   // optional diagnostics
   Buf<uint8_t> keep, root, dir;
   double omega = 0, lam_omega = 0, lmax = 0, lmin = 0;
-  // FP64 V-cycle workspace
-  Buf<double> vb, vx, vx2, vr, vd;
 
-  CsrView A() const {
-    CsrView c;
-    c.n = n; c.nnz = nnz; c.rp = rp.p; c.ci = ci.p; c.v = v.p; c.sw = sw;
-    return c;
-  }
-  CsrView P() const {
-    CsrView c;
-    c.n = n; c.nnz = nnzP; c.rp = Prp.p; c.ci = Pci.p; c.v = Pv.p; c.sw = pick_sw(n, nnzP);
-    return c;
-  }
-  CsrView R() const {
-    CsrView c;
-    c.n = nc; c.nnz = nnzP; c.rp = Rrp.p; c.ci = Rci.p; c.v = Rv.p; c.sw = pick_sw(nc, nnzP);
-    return c;
-  }
 };
 
 }  // namespace sa
@@ -65,14 +48,23 @@ struct sa_handle_s {
   int dim = 0;
   int64_t n = 0;
   std::vector<std::unique_ptr<sa::Level>> lev;
-  sa::Buf<double> W, WT, cy;
+  sa::Buf<double> W, WT;
   int64_t nL = 0;
+  sa::Sell<double> A0s;  // fine operator (unscaled) for the outer CG
   // Krylov workspace (FP64, fine level)
   sa::Buf<double> r, p, q, rprev, t, part, dots, xb, bb;
   sa::Buf<sa::CgScalars> cg;
   double* host_pin = nullptr;  // pinned readback buffer
-  sa::MixedHierarchy* mixed = nullptr;
+  sa::VHier<double>* v64 = nullptr;  // FP64 V-cycle on the scaled hierarchy
+  sa::VHier<float>* v32 = nullptr;   // FP32 V-cycle on the scaled hierarchy
   double setup_ms = 0;
+  // device-driven CG loop: one captured graph per solve form
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int graph_failed = 0;
+  sa::Buf<int> it_dev;
+  sa::Buf<double> ctl;  // [0] tol * r0
 };
 
 namespace sa {
@@ -214,14 +206,6 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
 
 static int alloc_workspace(sa_handle h) {
   Alloc& al = h->al;
-  for (auto& Lp : h->lev) {
-    Level& L = *Lp;
-    SA_TRY(L.vb.alloc(&al, L.n));
-    SA_TRY(L.vx.alloc(&al, L.n));
-    SA_TRY(L.vx2.alloc(&al, L.n));
-    SA_TRY(L.vr.alloc(&al, L.n));
-    SA_TRY(L.vd.alloc(&al, L.n));
-  }
   const int64_t n = h->n;
   SA_TRY(h->r.alloc(&al, n));
   SA_TRY(h->p.alloc(&al, n));
@@ -234,14 +218,10 @@ static int alloc_workspace(sa_handle h) {
   SA_TRY(h->part.alloc(&al, 3 * np));
   SA_TRY(h->dots.alloc(&al, 8));
   SA_TRY(h->cg.alloc(&al, 1));
-  SA_TRY(h->cy.alloc(&al, h->nL > 0 ? h->nL : 1));
+  SA_TRY(h->it_dev.alloc(&al, 1));
+  SA_TRY(h->ctl.alloc(&al, 1));
   return SA_OK;
 }
-
-// algorithmic bytes of one launch (FP64 CSR: 8-byte value + 4-byte column per
-// stored entry, 8-byte row pointer per row, each vector element once)
-static double b_cheb64(const Level& L) { return 12.0 * L.nnz + 8.0 * (L.n + 1) + 48.0 * L.n; }
-static double b_resid64(const Level& L) { return 12.0 * L.nnz + 8.0 * (L.n + 1) + 24.0 * L.n; }
 
 #define PROF(kind, level, bytes, call)                          \
   do {                                                          \
@@ -251,78 +231,46 @@ static double b_resid64(const Level& L) { return 12.0 * L.nnz + 8.0 * (L.n + 1) 
     if (_st != SA_OK) return _st;                               \
   } while (0)
 
-// FP64 V-cycle (Algorithm 1) on level l: returns the buffer with x_l.
-static int vcycle64(sa_handle h, int l, const double* b, double** xout) {
-  cudaStream_t s = h->al.stream;
-  Level& L = *h->lev[l];
-  const int last = (int)h->lev.size() - 1;
-  if (l == last) {
-    PROF(PK_COARSE, l, 8.0 * L.n * L.n + 32.0 * L.n,
-         launch_coarse_solve(s, L.n, h->W.p, h->WT.p, b, h->cy.p, L.vx.p));
-    *xout = L.vx.p;
-    return SA_OK;
-  }
-  const int deg = h->opt.cheb_degree;
-  const double th = 0.5 * (L.lmax + L.lmin), de = 0.5 * (L.lmax - L.lmin);
-  const double s1 = th / de;
-  double* xa = L.vx.p;
-  double* xb = L.vx2.p;
-  const CsrView A = L.A();
-  // pre-smoothing from x = 0
-  PROF(PK_FIRST64, l, 32.0 * L.n, launch_cheb_first(s, L.n, L.dinv.p, b, 1.0 / th, xa, L.vd.p));
-  double rho = 1.0 / s1;
-  for (int k = 1; k < deg; ++k) {
-    double rn = 1.0 / (2.0 * s1 - rho);
-    PROF(PK_CHEB64, l, b_cheb64(L),
-         launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, rn * rho, 2.0 * rn / de, 0));
-    double* t = xa; xa = xb; xb = t;
-    rho = rn;
-  }
-  // restriction of the residual, coarse correction, prolongation
-  Level& C = *h->lev[l + 1];
-  PROF(PK_RESID64, l, b_resid64(L), launch_residual(s, A, b, xa, L.vr.p));
-  PROF(PK_RESTRICT64, l, 12.0 * L.nnzP + 8.0 * (L.nc + 1) + 8.0 * L.n + 8.0 * L.nc,
-       launch_spmv(s, L.R(), L.vr.p, C.vb.p));
-  double* xc = nullptr;
-  SA_TRY(vcycle64(h, l + 1, C.vb.p, &xc));
-  PROF(PK_PROLONG64, l, 12.0 * L.nnzP + 8.0 * (L.n + 1) + 8.0 * L.nc + 16.0 * L.n,
-       launch_spmv_add(s, L.P(), xc, xa));
-  // post-smoothing
-  PROF(PK_CHEB64, l, b_cheb64(L) - 8.0 * L.n, launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, 0.0, 1.0 / th, 1));
-  { double* t = xa; xa = xb; xb = t; }
-  rho = 1.0 / s1;
-  for (int k = 1; k < deg; ++k) {
-    double rn = 1.0 / (2.0 * s1 - rho);
-    PROF(PK_CHEB64, l, b_cheb64(L),
-         launch_cheb_step(s, A, L.dinv.p, b, xa, xb, L.vd.p, rn * rho, 2.0 * rn / de, 0));
-    double* t = xa; xa = xb; xb = t;
-    rho = rn;
-  }
-  *xout = xa;
-  return SA_OK;
+static int precondition(sa_handle h, const double* r, double** z) {
+  if (h->opt.precision == SA_PREC_FP32_VCYCLE) return vh_vcycle<float>(h->v32, h->al.stream, r, z);
+  return vh_vcycle<double>(h->v64, h->al.stream, r, z);
 }
 
-static int precondition(sa_handle h, const double* r, double** z) {
-  if (h->opt.precision == SA_PREC_FP32_VCYCLE) return mixed_vcycle(h->mixed, h->al.stream, r, z);
-  return vcycle64(h, 0, r, z);
+// outer-CG operator products on the FP64 SELL copy of the fine operator
+static int op_spmv_dot(sa_handle h, const double* p, double* q, double* part, int* np) {
+  return launch_sell_spmv_dot(h->al.stream, h->A0s, p, q, part, np);
+}
+static int op_residual(sa_handle h, const double* b, const double* x, double* r) {
+  return launch_sell_residual64(h->al.stream, h->A0s, b, x, r);
 }
 
 struct HostScal {
   double rr, pad0, pad1;
 };
 
-// CG / flexible CG on device buffers b, x (Sec. 4)
-static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
+// CG / flexible CG on device buffers b, x (Sec. 4), host-driven: one
+// readback per iteration.  Used when profiling (events bracket every launch).
+static int cg_eager_dev(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info);
+static int cg_eager(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
+  cudaStream_t s = h->al.stream;
+  SA_CUDA(cudaMemcpyAsync(h->bb.p, b, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  SA_CUDA(cudaMemcpyAsync(h->xb.p, x, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  int st = cg_eager_dev(h, h->bb.p, h->xb.p, tol, info);
+  SA_CUDA(cudaMemcpyAsync(x, h->xb.p, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  SA_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+static int cg_eager_dev(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
   cudaStream_t s = h->al.stream;
   Level& L0 = *h->lev[0];
-  const CsrView A = L0.A();
   const int64_t n = h->n;
   const int flexible = h->opt.precision == SA_PREC_FP32_VCYCLE;
   double* hp = h->host_pin;
   auto t0 = std::chrono::steady_clock::now();
   int status = SA_ERR_NO_CONVERGENCE, it = 0;
   double r0 = 0.0;
-  SA_TRY(launch_residual(s, A, b, x, h->r.p));
+  SA_TRY(op_residual(h, b, x, h->r.p));
   SA_TRY(launch_dots(s, n, h->r.p, h->r.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p));
   SA_CUDA(cudaMemcpyAsync(hp, h->dots.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   SA_CUDA(cudaStreamSynchronize(s));
@@ -336,8 +284,8 @@ static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_sol
     const int maxit = h->opt.maxit;
     for (it = 1; it <= maxit; ++it) {
       int np = 0;
-      PROF(PK_CG_SPMV, 0, 12.0 * L0.nnz + 8.0 * (n + 1) + 16.0 * n,
-           launch_spmv_dot(s, A, h->p.p, h->q.p, h->part.p, &np));
+      PROF(PK_CG_SPMV, 0, 12.0 * L0.nnz + 8.0 * (h->A0s.nslices + 1) + 16.0 * n,
+           op_spmv_dot(h, h->p.p, h->q.p, h->part.p, &np));
       SA_TRY(launch_finish(s, h->part.p, np, h->dots.p));
       SA_TRY(launch_cg_alpha(s, h->cg.p, h->dots.p));
       PROF(PK_CG_VEC, 0, (flexible ? 56.0 : 48.0) * n,
@@ -350,7 +298,7 @@ static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_sol
       memcpy(&brk, hp + 1, sizeof(int));
       if (brk) { status = SA_ERR_BREAKDOWN; break; }
       if (sqrt(hp[0]) <= tol * r0) {
-        SA_TRY(launch_residual(s, A, b, x, h->t.p));
+        SA_TRY(op_residual(h, b, x, h->t.p));
         SA_TRY(launch_dots(s, n, h->t.p, h->t.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p + 4));
         SA_CUDA(cudaMemcpyAsync(hp, h->dots.p + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
         SA_CUDA(cudaStreamSynchronize(s));
@@ -369,7 +317,7 @@ static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_sol
     status = SA_OK;
   }
   // true residual at exit
-  SA_TRY(launch_residual(s, A, b, x, h->t.p));
+  SA_TRY(op_residual(h, b, x, h->t.p));
   SA_TRY(launch_dots(s, n, h->t.p, h->t.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p + 4));
   SA_CUDA(cudaMemcpyAsync(hp, h->dots.p + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
   SA_CUDA(cudaStreamSynchronize(s));
@@ -384,13 +332,183 @@ static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_sol
   return status;
 }
 
-static bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+
+// loop control inside the captured CG body: count the iteration and decide
+// whether the WHILE node runs the body again
+__global__ void k_loop_ctrl(cudaGraphConditionalHandle ch, int* __restrict__ it, const CgScalars* __restrict__ s,
+                            const double* __restrict__ rr, const double* __restrict__ ctl, int maxit) {
+  int k = *it + 1;
+  *it = k;
+  int cont = !s->breakdown && !(sqrt(*rr) <= ctl[0]) && k < maxit;
+  cudaGraphSetConditional(ch, cont ? 1u : 0u);
+}
+
+// the second half of one CG iteration followed by the first half of the next:
+// z = M r, beta, p = z + beta p, q = A p, alpha, x/r update, ||r||^2, control
+static int cg_body(sa_handle h, cudaGraphConditionalHandle ch) {
+  cudaStream_t s = h->al.stream;
+  Level& L0 = *h->lev[0];
+  const int64_t n = h->n;
+  const int flexible = h->opt.precision == SA_PREC_FP32_VCYCLE;
+  double* z = nullptr;
+  SA_TRY(precondition(h, h->r.p, &z));
+  SA_TRY(launch_dots(s, n, h->r.p, z, flexible ? z : nullptr, flexible ? h->rprev.p : nullptr, nullptr, nullptr,
+                     h->part.p, h->dots.p));
+  SA_TRY(launch_cg_beta(s, h->cg.p, h->dots.p, flexible));
+  SA_TRY(launch_cg_pupdate(s, n, h->cg.p, z, h->p.p, 0));
+  int np = 0;
+  SA_TRY(op_spmv_dot(h, h->p.p, h->q.p, h->part.p, &np));
+  SA_TRY(launch_finish(s, h->part.p, np, h->dots.p));
+  SA_TRY(launch_cg_alpha(s, h->cg.p, h->dots.p));
+  SA_TRY(launch_cg_update(s, n, h->cg.p, h->p.p, h->q.p, h->xb.p, h->r.p, flexible ? h->rprev.p : nullptr,
+                          h->part.p));
+  SA_TRY(launch_finish(s, h->part.p, RED_BLOCKS, h->dots.p + 4));
+  k_loop_ctrl<<<1, 1, 0, s>>>(ch, h->it_dev.p, h->cg.p, h->dots.p + 4, h->ctl.p, h->opt.maxit);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+static void drop_graph(sa_handle h, int form) {
+  if (h->gexec[form]) cudaGraphExecDestroy(h->gexec[form]);
+  if (h->graph[form]) cudaGraphDestroy(h->graph[form]);
+  h->gexec[form] = nullptr;
+  h->graph[form] = nullptr;
+}
+
+// captures the body into a graph with a conditional WHILE node; on any
+// failure the handle falls back to host-driven iterations
+static int capture_loop(sa_handle h, int form) {
+  if (h->gexec[form]) return SA_OK;
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return SA_ERR_CUDA;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle ch;
+  cudaGraphNodeParams p = {};
+  cudaGraphNode_t node;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess ||
+      cudaGraphConditionalHandleCreate(&ch, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return SA_ERR_CUDA;
+  }
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = ch;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return SA_ERR_CUDA;
+  }
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  cudaStream_t user = h->al.stream;
+  h->al.stream = h->cap_stream;  // every launch of the body goes to the capture stream
+  int st = SA_OK;
+  if (cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess) {
+    st = SA_ERR_CUDA;
+  } else {
+    st = cg_body(h, ch);
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(h->cap_stream, &out) != cudaSuccess) st = SA_ERR_CUDA;
+  }
+  h->al.stream = user;
+  if (st == SA_OK && cudaGraphInstantiate(&h->gexec[form], g, 0) != cudaSuccess) st = SA_ERR_CUDA;
+  cudaGetLastError();
+  if (st != SA_OK) {
+    h->gexec[form] = nullptr;
+    cudaGraphDestroy(g);
+    return st;
+  }
+  h->graph[form] = g;
+  return SA_OK;
+}
+
+// CG with the iterations after the first run inside one graph launch; the
+// host reads back once per launch (convergence candidate, maxit or
+// breakdown) and confirms convergence with the true residual.
+static int cg_graph(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
+  cudaStream_t s = h->al.stream;
+  Level& L0 = *h->lev[0];
+  const int64_t n = h->n;
+  const int form = h->opt.precision == SA_PREC_FP32_VCYCLE ? 1 : 0;
+  const int flexible = form;
+  double* hp = h->host_pin;
+  auto t0 = std::chrono::steady_clock::now();
+  SA_CUDA(cudaMemcpyAsync(h->bb.p, b, sizeof(double) * n, cudaMemcpyDefault, s));
+  SA_CUDA(cudaMemcpyAsync(h->xb.p, x, sizeof(double) * n, cudaMemcpyDefault, s));
+  int status = SA_ERR_NO_CONVERGENCE, it = 0;
+  SA_TRY(op_residual(h, h->bb.p, h->xb.p, h->r.p));
+  SA_TRY(launch_dots(s, n, h->r.p, h->r.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p));
+  SA_CUDA(cudaMemcpyAsync(hp, h->dots.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SA_CUDA(cudaStreamSynchronize(s));
+  const double r0 = sqrt(hp[0]);
+  if (r0 > 0.0) {
+    hp[2] = tol * r0;
+    SA_CUDA(cudaMemcpyAsync(h->ctl.p, hp + 2, sizeof(double), cudaMemcpyHostToDevice, s));
+    // first iteration (host-driven)
+    double* z = nullptr;
+    SA_TRY(precondition(h, h->r.p, &z));
+    SA_TRY(launch_cg_pupdate(s, n, h->cg.p, z, h->p.p, 1));
+    SA_TRY(launch_dots(s, n, h->r.p, z, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p));
+    SA_TRY(launch_cg_beta(s, h->cg.p, h->dots.p, -1));
+    int np = 0;
+    SA_TRY(op_spmv_dot(h, h->p.p, h->q.p, h->part.p, &np));
+    SA_TRY(launch_finish(s, h->part.p, np, h->dots.p));
+    SA_TRY(launch_cg_alpha(s, h->cg.p, h->dots.p));
+    SA_TRY(launch_cg_update(s, n, h->cg.p, h->p.p, h->q.p, h->xb.p, h->r.p, flexible ? h->rprev.p : nullptr,
+                            h->part.p));
+    SA_TRY(launch_finish(s, h->part.p, RED_BLOCKS, h->dots.p + 4));
+    int one = 1;
+    SA_CUDA(cudaMemcpyAsync(h->it_dev.p, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    for (;;) {
+      SA_CUDA(cudaMemcpyAsync(hp, h->dots.p + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+      SA_CUDA(cudaMemcpyAsync(hp + 1, &h->cg.p->breakdown, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SA_CUDA(cudaMemcpyAsync((char*)(hp + 1) + sizeof(int), h->it_dev.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SA_CUDA(cudaStreamSynchronize(s));
+      int brk = 0;
+      memcpy(&brk, hp + 1, sizeof(int));
+      memcpy(&it, (char*)(hp + 1) + sizeof(int), sizeof(int));
+      if (brk) { status = SA_ERR_BREAKDOWN; break; }
+      if (sqrt(hp[0]) <= tol * r0) {
+        SA_TRY(op_residual(h, h->bb.p, h->xb.p, h->t.p));
+        SA_TRY(launch_dots(s, n, h->t.p, h->t.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p + 6));
+        SA_CUDA(cudaMemcpyAsync(hp + 3, h->dots.p + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SA_CUDA(cudaStreamSynchronize(s));
+        if (sqrt(hp[3]) <= tol * r0) { status = SA_OK; break; }
+        SA_CUDA(cudaMemcpyAsync(h->r.p, h->t.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      }
+      if (it >= h->opt.maxit) break;
+      SA_CUDA(cudaGraphLaunch(h->gexec[form], s));
+    }
+  } else {
+    status = SA_OK;
+  }
+  SA_TRY(op_residual(h, h->bb.p, h->xb.p, h->t.p));
+  SA_TRY(launch_dots(s, n, h->t.p, h->t.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p + 6));
+  SA_CUDA(cudaMemcpyAsync(hp + 3, h->dots.p + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SA_CUDA(cudaMemcpyAsync(x, h->xb.p, sizeof(double) * n, cudaMemcpyDefault, s));
+  SA_CUDA(cudaStreamSynchronize(s));
+  auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    info->iters = it;
+    info->rel_res_true = r0 > 0.0 ? sqrt(hp[3]) / r0 : 0.0;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->status = status;
+  }
+  return status;
+}
+
+static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
+  const int form = h->opt.precision == SA_PREC_FP32_VCYCLE ? 1 : 0;
+  if (!prof_on() && !h->graph_failed) {
+    if (!h->gexec[form] && capture_loop(h, form) != SA_OK) h->graph_failed = 1;
+    if (h->gexec[form]) return cg_graph(h, b, x, tol, info);
+  }
+  return cg_eager(h, b, x, tol, info);
 }
 
 template <typename T>
@@ -400,11 +518,9 @@ static int upload(Alloc& al, Buf<T>& dst, const T* src, int64_t count) {
   return SA_OK;
 }
 
-// FP32 copies of the scaled hierarchy for the mixed-precision form
-static int build_mixed(sa_handle h) {
-  if (h->mixed) return SA_OK;
+static std::vector<VLevelIn> vlevel_inputs(sa_handle h) {
   const int nlev = (int)h->lev.size();
-  std::vector<MixedLevelIn> in(nlev);
+  std::vector<VLevelIn> in(nlev);
   for (int l = 0; l < nlev; ++l) {
     Level& L = *h->lev[l];
     in[l].n = L.n; in[l].nnz = L.nnz; in[l].rp = L.rp.p; in[l].ci = L.ci.p; in[l].v = L.v.p;
@@ -413,7 +529,14 @@ static int build_mixed(sa_handle h) {
     in[l].Prp = L.Prp.p; in[l].Pci = L.Pci.p; in[l].Pv = L.Pv.p;
     in[l].Rrp = L.Rrp.p; in[l].Rci = L.Rci.p; in[l].Rv = L.Rv.p;
   }
-  return mixed_build(h->al, in.data(), nlev, h->opt.cheb_degree, h->W.p, h->WT.p, &h->mixed);
+  return in;
+}
+
+// FP32 copies of the scaled hierarchy for the mixed-precision form
+static int build_mixed(sa_handle h) {
+  if (h->v32) return SA_OK;
+  std::vector<VLevelIn> in = vlevel_inputs(h);
+  return vh_build<float>(h->al, in.data(), (int)in.size(), h->opt.cheb_degree, h->W.p, h->WT.p, &h->v32);
 }
 
 static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
@@ -511,6 +634,12 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   h->nL = Lc.n;
   SA_TRY(run_dense_inverse_factor(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT));
   SA_TRY(alloc_workspace(h));
+  {
+    Level& L0 = *h->lev[0];
+    SA_TRY(build_sell<double>(al, L0.n, L0.nnz, L0.rp.p, L0.ci.p, L0.v.p, nullptr, 0, nullptr, 0, h->A0s));
+    std::vector<VLevelIn> in = vlevel_inputs(h);
+    SA_TRY(vh_build<double>(al, in.data(), nlev, o->cheb_degree, h->W.p, h->WT.p, &h->v64));
+  }
   if (o->precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
   SA_CUDA(cudaStreamSynchronize(s));
   auto t1 = std::chrono::steady_clock::now();
@@ -592,23 +721,9 @@ int sa_setup(const sa_problem* prob, const sa_options* opt, sa_handle* out) {
 
 int sa_solve(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
   if (!h || !b || !x || !(tol > 0.0)) return SA_ERR_INVALID_ARG;
-  cudaStream_t s = h->al.stream;
-  const int64_t n = h->n;
-  const bool dev = sa::is_device_ptr(b) && sa::is_device_ptr(x);
-  const double* bd = b;
-  double* xd = x;
-  if (!dev) {
-    SA_CUDA(cudaMemcpyAsync(h->bb.p, b, sizeof(double) * n, cudaMemcpyDefault, s));
-    SA_CUDA(cudaMemcpyAsync(h->xb.p, x, sizeof(double) * n, cudaMemcpyDefault, s));
-    bd = h->bb.p;
-    xd = h->xb.p;
-  }
-  int st = sa::cg_device(h, bd, xd, tol, info);
-  if (!dev) {
-    SA_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDefault, s));
-    SA_CUDA(cudaStreamSynchronize(s));
-  }
-  return st;
+  // b and x are copied into handle-owned buffers (cudaMemcpyDefault: host or
+  // device), so the captured CG loop always sees the same addresses
+  return sa::cg_device(h, b, x, tol, info);
 }
 
 int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos) {
@@ -729,13 +844,20 @@ int sa_export_strength(sa_handle h, int l, uint8_t* keep, uint8_t* root, uint8_t
 
 int sa_free(sa_handle h) {
   if (!h) return SA_OK;
-  if (h->mixed) sa::mixed_free(h->mixed);
+  sa::drop_graph(h, 0);
+  sa::drop_graph(h, 1);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->v64) sa::vh_free<double>(h->v64);
+  if (h->v32) sa::vh_free<float>(h->v32);
+  h->A0s.sp.release();
+  h->A0s.ci.release();
+  h->A0s.v.release();
   h->lev.clear();
   h->W.release();
   h->WT.release();
-  h->cy.release();
   h->r.release(); h->p.release(); h->q.release(); h->rprev.release(); h->t.release();
   h->part.release(); h->dots.release(); h->xb.release(); h->bb.release(); h->cg.release();
+  h->it_dev.release(); h->ctl.release();
   cudaStreamSynchronize(h->al.stream);
   if (h->host_pin) cudaFreeHost(h->host_pin);
   delete h;

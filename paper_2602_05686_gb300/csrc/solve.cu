@@ -1,7 +1,6 @@
-// Solve-phase and iteration kernels: CSR sparse matrix-vector products with
-// a sub-warp per row, the fused Chebyshev step, residual / restriction /
-// prolongation, fixed-order dot products, the power method, and the CG
-// vector updates with device-resident scalars.
+// Iteration kernels: the power method on CSR matrices (sub-warp per row),
+// fixed-order dot products, and the CG vector updates with device-resident
+// scalars.  The V-cycle itself lives in vcycle.cu.
 #include <math.h>
 
 #include "common.cuh"
@@ -11,23 +10,9 @@
 namespace sa {
 
 // ---------------------------------------------------------------------------
-// row dot product with SW lanes per row; the result is valid in every lane
-// of the group
+// CSR row products with SW lanes per row (power method on the setup's CSR
+// matrices); the result is valid in every lane of the group
 // ---------------------------------------------------------------------------
-template <int SW, typename T, typename V>
-__device__ __forceinline__ T row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                     const V* __restrict__ v, const T* __restrict__ x, int64_t i, bool valid,
-                                     int sl) {
-  T acc = T(0);
-  if (valid) {
-    const int64_t e = rp[i + 1];
-    for (int64_t p = rp[i] + sl; p < e; p += SW) acc += (T)v[p] * x[ci[p]];
-  }
-#pragma unroll
-  for (int o = SW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SW);
-  return acc;
-}
-
 // scaled variant: sum_p v_p * (s_j * x_j)
 template <int SW>
 __device__ __forceinline__ double row_dot_scaled(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -51,64 +36,6 @@ __device__ __forceinline__ double row_dot_scaled(const int64_t* __restrict__ rp,
   const int64_t i = gt / SW;                                            \
   const int sl = (int)(gt % SW);                                        \
   const bool valid = i < n;
-
-// y = A x
-template <int SW>
-__global__ void k_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                       const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y) {
-  ROW_SETUP(SW)
-  double a = row_dot<SW>(rp, ci, v, x, i, valid, sl);
-  if (valid && sl == 0) y[i] = a;
-}
-
-// y += A x   (prolongation with correction: x_l += P x_{l+1})
-template <int SW>
-__global__ void k_spmv_add(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y) {
-  ROW_SETUP(SW)
-  double a = row_dot<SW>(rp, ci, v, x, i, valid, sl);
-  if (valid && sl == 0) y[i] += a;
-}
-
-// r = b - A x
-template <int SW>
-__global__ void k_residual(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const double* __restrict__ v, const double* __restrict__ b, const double* __restrict__ x,
-                           double* __restrict__ r) {
-  ROW_SETUP(SW)
-  double a = row_dot<SW>(rp, ci, v, x, i, valid, sl);
-  if (valid && sl == 0) r[i] = b[i] - a;
-}
-
-// one Chebyshev step (Sec. 4 smoother; three-term recurrence on D^-1 A):
-//   r = b - A x_in; d = first ? c2 * (dinv r) : c1 d + c2 (dinv r);
-//   x_out = x_in + d
-template <int SW>
-__global__ void k_cheb_step(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                            const double* __restrict__ v, const double* __restrict__ dinv,
-                            const double* __restrict__ b, const double* __restrict__ xin, double* __restrict__ xout,
-                            double* __restrict__ d, double c1, double c2, int first) {
-  ROW_SETUP(SW)
-  double a = row_dot<SW>(rp, ci, v, xin, i, valid, sl);
-  if (valid && sl == 0) {
-    double r = b[i] - a;
-    double z = dinv[i] * r;
-    double dn = first ? c2 * z : c1 * d[i] + c2 * z;
-    d[i] = dn;
-    xout[i] = xin[i] + dn;
-  }
-}
-
-// first Chebyshev step from x = 0: d = c2 dinv b, x = d
-__global__ void k_cheb_first(int64_t n, const double* __restrict__ dinv, const double* __restrict__ b, double c2,
-                             double* __restrict__ x, double* __restrict__ d) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    double dn = c2 * (dinv[i] * b[i]);
-    d[i] = dn;
-    x[i] = dn;
-  }
-}
 
 // power method product: w_i = s_i * sum_p a_p (s_j v_j)
 template <int SW>
@@ -311,63 +238,8 @@ int launch_omega(cudaStream_t s, const double* lam_dev, double omega_sym, double
 }
 
 // ---------------------------------------------------------------------------
-// FP64 V-cycle pieces
-// ---------------------------------------------------------------------------
-int launch_spmv(cudaStream_t st, const CsrView& A, const double* x, double* y) {
-  if (A.n <= 0) return SA_OK;
-  DISPATCH_SW(A.sw, k_spmv, A.n, A.n, A.rp, A.ci, A.v, x, y);
-  SA_LAUNCHED();
-  return SA_OK;
-}
-
-int launch_spmv_add(cudaStream_t st, const CsrView& A, const double* x, double* y) {
-  if (A.n <= 0) return SA_OK;
-  DISPATCH_SW(A.sw, k_spmv_add, A.n, A.n, A.rp, A.ci, A.v, x, y);
-  SA_LAUNCHED();
-  return SA_OK;
-}
-
-int launch_residual(cudaStream_t st, const CsrView& A, const double* b, const double* x, double* r) {
-  if (A.n <= 0) return SA_OK;
-  DISPATCH_SW(A.sw, k_residual, A.n, A.n, A.rp, A.ci, A.v, b, x, r);
-  SA_LAUNCHED();
-  return SA_OK;
-}
-
-int launch_cheb_step(cudaStream_t st, const CsrView& A, const double* dinv, const double* b, const double* xin,
-                     double* xout, double* d, double c1, double c2, int first) {
-  if (A.n <= 0) return SA_OK;
-  DISPATCH_SW(A.sw, k_cheb_step, A.n, A.n, A.rp, A.ci, A.v, dinv, b, xin, xout, d, c1, c2, first);
-  SA_LAUNCHED();
-  return SA_OK;
-}
-
-int launch_cheb_first(cudaStream_t st, int64_t n, const double* dinv, const double* b, double c2, double* x,
-                      double* d) {
-  if (n <= 0) return SA_OK;
-  k_cheb_first<<<blocks_for(n, 256), 256, 0, st>>>(n, dinv, b, c2, x, d);
-  SA_LAUNCHED();
-  return SA_OK;
-}
-
-// ---------------------------------------------------------------------------
 // CG with device-resident scalars (Sec. 4)
 // ---------------------------------------------------------------------------
-// q = A p, partial sums of p.q
-template <int SW>
-__global__ void k_spmv_dot(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const double* __restrict__ v, const double* __restrict__ p, double* __restrict__ q,
-                           double* __restrict__ part) {
-  ROW_SETUP(SW)
-  double a = row_dot<SW>(rp, ci, v, p, i, valid, sl);
-  double c[1] = {0.0};
-  if (valid && sl == 0) {
-    q[i] = a;
-    c[0] = a * p[i];
-  }
-  block_sum_to<1>(c, part, 0);
-}
-
 // alpha = rz / pq (pq = dots[0]); flags breakdown when pq <= 0 or NaN
 __global__ void k_cg_alpha(CgScalars* __restrict__ s, const double* __restrict__ dots) {
   double pq = dots[0];
@@ -414,14 +286,6 @@ __global__ void k_cg_pupdate(int64_t n, const CgScalars* __restrict__ s, const d
   const double beta = s->beta;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = first ? z[i] : z[i] + beta * p[i];
-}
-
-int launch_spmv_dot(cudaStream_t st, const CsrView& A, const double* p, double* q, double* part, int* nparts) {
-  const int sw = A.sw;
-  *nparts = (int)blocks_for(A.n * (int64_t)sw, 256);
-  DISPATCH_SW(sw, k_spmv_dot, A.n, A.n, A.rp, A.ci, A.v, p, q, part);
-  SA_LAUNCHED();
-  return SA_OK;
 }
 
 int launch_finish(cudaStream_t st, const double* part, int np, double* out) {

@@ -22,14 +22,6 @@ struct CgScalars {
 int pick_sw(int64_t n, int64_t nnz);
 int launch_dots(cudaStream_t st, int64_t n, const double* a0, const double* b0, const double* a1, const double* b1,
                 const double* a2, const double* b2, double* part, double* out);
-int launch_spmv(cudaStream_t st, const CsrView& A, const double* x, double* y);
-int launch_spmv_add(cudaStream_t st, const CsrView& A, const double* x, double* y);
-int launch_residual(cudaStream_t st, const CsrView& A, const double* b, const double* x, double* r);
-int launch_cheb_step(cudaStream_t st, const CsrView& A, const double* dinv, const double* b, const double* xin,
-                     double* xout, double* d, double c1, double c2, int first);
-int launch_cheb_first(cudaStream_t st, int64_t n, const double* dinv, const double* b, double c2, double* x,
-                      double* d);
-int launch_spmv_dot(cudaStream_t st, const CsrView& A, const double* p, double* q, double* part, int* nparts);
 int launch_finish(cudaStream_t st, const double* part, int np, double* out);
 int launch_cg_alpha(cudaStream_t st, CgScalars* s, const double* dots);
 int launch_cg_update(cudaStream_t st, int64_t n, const CgScalars* s, const double* p, const double* q, double* x,

@@ -1,0 +1,425 @@
+// The V-cycle of Algorithm 1 with Chebyshev smoothing (Sec. 4) on the
+// symmetrically diagonal-scaled hierarchy
+//   A~_l = D_l^-1/2 A_l D_l^-1/2,  P~_l = D_l^1/2 P_l D_{l+1}^-1/2,  R~_l = P~_l^T,
+// which satisfies A~_{l+1} = R~_l A~_l P~_l in real arithmetic; Chebyshev on A~
+// with a unit diagonal equals Chebyshev on D^-1 A in the original variables,
+// and z = D_0^-1/2 V~(D_0^-1/2 r).  One templated code path serves both solve
+// forms: T = double (FP64 PCG) and T = float (FP32 V-cycle inside FP64
+// flexible CG).  Matrices are SELL-32: slices of 32 consecutive rows stored
+// column-major with one thread per row, so every warp load of values and
+// column indices is one contiguous segment, and for finite-element stencils
+// (consecutive rows share their stencil shape) the gathers of x are
+// contiguous too.  The coarsest level is solved in FP64 with the dense
+// inverse factor.
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "profile.cuh"
+#include "solve.cuh"
+#include "vcycle.cuh"
+
+namespace sa {
+
+// ---------------------------------------------------------------------------
+// SELL-32 construction
+// ---------------------------------------------------------------------------
+__global__ void k_slice_width(int64_t n, const int64_t* __restrict__ rp, int64_t* __restrict__ sz) {
+  int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t ns = (n + 31) / 32;
+  if (sl >= ns) return;
+  int64_t w = 0;
+  for (int64_t r = sl * 32; r < sl * 32 + 32 && r < n; ++r) {
+    int64_t len = rp[r + 1] - rp[r];
+    w = len > w ? len : w;
+  }
+  sz[sl + 1] = w * 32;
+}
+
+// out = left_i * a_ij * right_j (left/right: sqrt(d) or 1/sqrt(d), NULL = 1);
+// padding entries point at column 0 with value 0
+template <typename T>
+__global__ void k_sell_fill(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, const double* __restrict__ left,
+                            const double* __restrict__ right, int left_sqrt, int right_sqrt,
+                            const int64_t* __restrict__ sp, int32_t* __restrict__ oci, T* __restrict__ ov) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t sl = i / 32, r = i % 32;
+  const int64_t base = sp[sl], width = (sp[sl + 1] - sp[sl]) / 32;
+  double li = 1.0;
+  if (left) li = left_sqrt ? sqrt(left[i]) : 1.0 / sqrt(left[i]);
+  int64_t k = 0;
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p, ++k) {
+    int32_t j = ci[p];
+    double rj = 1.0;
+    if (right) rj = right_sqrt ? sqrt(right[j]) : 1.0 / sqrt(right[j]);
+    oci[base + k * 32 + r] = j;
+    ov[base + k * 32 + r] = (T)(li * v[p] * rj);
+  }
+  for (; k < width; ++k) {
+    oci[base + k * 32 + r] = 0;
+    ov[base + k * 32 + r] = (T)0;
+  }
+}
+
+__global__ void k_sqrt_vec(int64_t n, const double* __restrict__ d, double* __restrict__ out, int inv) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = inv ? 1.0 / sqrt(d[i]) : sqrt(d[i]);
+}
+
+template <typename T>
+int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
+               const double* left, int left_sqrt, const double* right, int right_sqrt, Sell<T>& S) {
+  cudaStream_t s = al.stream;
+  S.n = n;
+  S.nnz = nnz;
+  S.nslices = (n + 31) / 32;
+  SA_TRY(S.sp.alloc(&al, S.nslices + 1));
+  SA_TRY(memset_d(S.sp.p, 0, S.sp.bytes(), s));
+  if (n <= 0) {
+    SA_TRY(S.ci.alloc(&al, 0));
+    SA_TRY(S.v.alloc(&al, 0));
+    return SA_OK;
+  }
+  k_slice_width<<<blocks_for(S.nslices, 256), 256, 0, s>>>(n, rp, S.sp.p);
+  SA_LAUNCHED();
+  SA_TRY(scan_inplace(al, S.sp.p + 1, S.nslices));
+  SA_TRY(copy_d2h(&S.stored, S.sp.p + S.nslices, sizeof(int64_t), s));
+  SA_TRY(S.ci.alloc(&al, S.stored));
+  SA_TRY(S.v.alloc(&al, S.stored));
+  k_sell_fill<T><<<blocks_for(n, 256), 256, 0, s>>>(n, rp, ci, v, left, right, left_sqrt, right_sqrt, S.sp.p,
+                                                    S.ci.p, S.v.p);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+template int build_sell<double>(Alloc&, int64_t, int64_t, const int64_t*, const int32_t*, const double*,
+                                const double*, int, const double*, int, Sell<double>&);
+template int build_sell<float>(Alloc&, int64_t, int64_t, const int64_t*, const int32_t*, const double*,
+                               const double*, int, const double*, int, Sell<float>&);
+
+template <typename T>
+int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const double* W, const double* WT,
+             VHier<T>** out) {
+  VHier<T>* m = new VHier<T>();
+  *out = m;
+  m->deg = cheb_degree;
+  m->W = W;
+  m->WT = WT;
+  cudaStream_t s = al.stream;
+  for (int l = 0; l < nlev; ++l) {
+    VLevel<T>* L = new VLevel<T>();
+    m->lev.push_back(L);
+    const VLevelIn& I = in[l];
+    L->n = I.n;
+    L->nc = I.nc;
+    L->lmax = I.lmax;
+    L->lmin = I.lmin;
+    SA_TRY(L->b.alloc(&al, I.n));
+    SA_TRY(L->x.alloc(&al, I.n));
+    SA_TRY(L->x2.alloc(&al, I.n));
+    SA_TRY(L->r.alloc(&al, I.n));
+    SA_TRY(L->d.alloc(&al, I.n));
+    if (l + 1 < nlev) {
+      SA_TRY(build_sell<T>(al, I.n, I.nnz, I.rp, I.ci, I.v, I.diag, 0, I.diag, 0, L->A));
+      const double* dc = in[l + 1].diag;
+      SA_TRY(build_sell<T>(al, I.n, I.nnzP, I.Prp, I.Pci, I.Pv, I.diag, 1, dc, 0, L->P));
+      SA_TRY(build_sell<T>(al, I.nc, I.nnzP, I.Rrp, I.Rci, I.Rv, dc, 0, I.diag, 1, L->R));
+    } else {
+      SA_TRY(L->sq.alloc(&al, I.n));
+      k_sqrt_vec<<<blocks_for(I.n, 256), 256, 0, s>>>(I.n, I.diag, L->sq.p, 0);
+      SA_LAUNCHED();
+      SA_TRY(m->ct.alloc(&al, I.n));
+      SA_TRY(m->cy.alloc(&al, I.n));
+      SA_TRY(m->cx.alloc(&al, I.n));
+    }
+  }
+  const int64_t n0 = in[0].n;
+  SA_TRY(m->s0.alloc(&al, n0));
+  SA_TRY(m->z.alloc(&al, n0));
+  k_sqrt_vec<<<blocks_for(n0, 256), 256, 0, s>>>(n0, in[0].diag, m->s0.p, 1);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+template int vh_build<double>(Alloc&, const VLevelIn*, int, int, const double*, const double*, VHier<double>**);
+template int vh_build<float>(Alloc&, const VLevelIn*, int, int, const double*, const double*, VHier<float>**);
+
+// ---------------------------------------------------------------------------
+// kernels (one thread per row)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T sell_row(const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                                      const T* __restrict__ v, const T* __restrict__ x, int64_t i) {
+  const int64_t sl = i >> 5, r = i & 31;
+  const int64_t b = sp[sl], e = sp[sl + 1];
+  T acc = (T)0;
+  for (int64_t p = b + r; p < e; p += 32) acc += v[p] * __ldg(&x[ci[p]]);
+  return acc;
+}
+
+// x_out = x_in + d,  d = first ? c2 r : c1 d + c2 r,  r = b - A~ x_in
+template <typename T>
+__global__ void k_vc_cheb(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                          const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ xin,
+                          T* __restrict__ xout, T* __restrict__ d, T c1, T c2, int first) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T r = b[i] - sell_row<T>(sp, ci, v, xin, i);
+  T dn = first ? c2 * r : c1 * d[i] + c2 * r;
+  d[i] = dn;
+  xout[i] = xin[i] + dn;
+}
+
+template <typename T>
+__global__ void k_vc_first(int64_t n, const T* __restrict__ b, T c2, T* __restrict__ x, T* __restrict__ d) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    T dn = c2 * b[i];
+    d[i] = dn;
+    x[i] = dn;
+  }
+}
+
+// fine entry b~ = D^-1/2 r (FP64 r), fused with the first Chebyshev step
+template <typename T>
+__global__ void k_vc_fine_in(int64_t n, const double* __restrict__ r, const double* __restrict__ s, T c2,
+                             T* __restrict__ b, T* __restrict__ x, T* __restrict__ d) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    T bi = (T)(s[i] * r[i]);
+    b[i] = bi;
+    T dn = c2 * bi;
+    d[i] = dn;
+    x[i] = dn;
+  }
+}
+
+template <typename T>
+__global__ void k_vc_residual(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                              const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ x,
+                              T* __restrict__ r) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = b[i] - sell_row<T>(sp, ci, v, x, i);
+}
+
+template <typename T>
+__global__ void k_vc_spmv(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                          const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = sell_row<T>(sp, ci, v, x, i);
+}
+
+template <typename T>
+__global__ void k_vc_spmv_add(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                              const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += sell_row<T>(sp, ci, v, x, i);
+}
+
+// fine exit: the last post-smoothing step writes z = D^-1/2 x~ in FP64
+template <typename T>
+__global__ void k_vc_cheb_out(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                              const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ xin,
+                              const T* __restrict__ d, T c1, T c2, int first, const double* __restrict__ s,
+                              double* __restrict__ z) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T r = b[i] - sell_row<T>(sp, ci, v, xin, i);
+  T dn = first ? c2 * r : c1 * d[i] + c2 * r;
+  z[i] = s[i] * (double)(xin[i] + dn);
+}
+
+template <typename T>
+__global__ void k_coarse_in(int64_t n, const T* __restrict__ b, const double* __restrict__ sq,
+                            double* __restrict__ t) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) t[i] = sq[i] * (double)b[i];
+}
+
+template <typename T>
+__global__ void k_coarse_out(int64_t n, const double* __restrict__ x, const double* __restrict__ sq,
+                             T* __restrict__ xo) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xo[i] = (T)(sq[i] * x[i]);
+}
+
+// ---------------------------------------------------------------------------
+// the cycle
+// ---------------------------------------------------------------------------
+static inline unsigned g256(int64_t n) { return blocks_for(n, 256); }
+
+// algorithmic bytes: S-byte value + int32 column per stored entry of the
+// unpadded matrix, 8-byte slice offsets, each vector element once
+template <typename T>
+static double b_cheb(const VLevel<T>* L) {
+  const double S = sizeof(T);
+  return (S + 4.0) * L->A.nnz + 8.0 * (L->A.nslices + 1) + 5.0 * S * L->n;
+}
+
+#define PROFK(kind, level, bytes, launch)               \
+  do {                                                  \
+    int _pi = prof_begin(st, (kind), (level), (bytes)); \
+    launch;                                             \
+    prof_end(st, _pi);                                  \
+    SA_LAUNCHED();                                      \
+  } while (0)
+
+template <typename T>
+static int mv(VHier<T>* m, cudaStream_t st, int l, const double* r64, T** xo) {
+  constexpr bool F64 = sizeof(T) == 8;
+  const int K_CHEB = F64 ? PK_CHEB64 : PK_CHEB32, K_RES = F64 ? PK_RESID64 : PK_RESID32;
+  const int K_RST = F64 ? PK_RESTRICT64 : PK_RESTRICT32, K_PRL = F64 ? PK_PROLONG64 : PK_PROLONG32;
+  const int K_FST = F64 ? PK_FIRST64 : PK_FIRST32;
+  const double S = sizeof(T);
+  VLevel<T>* L = m->lev[l];
+  const int nl = (int)m->lev.size();
+  const int64_t n = L->n;
+  if (l == nl - 1) {
+    int pi = prof_begin(st, PK_COARSE, l, 8.0 * n * n + 48.0 * n);
+    k_coarse_in<T><<<g256(n), 256, 0, st>>>(n, L->b.p, L->sq.p, m->ct.p);
+    SA_LAUNCHED();
+    SA_TRY(launch_coarse_solve(st, n, m->W, m->WT, m->ct.p, m->cy.p, m->cx.p));
+    k_coarse_out<T><<<g256(n), 256, 0, st>>>(n, m->cx.p, L->sq.p, L->x.p);
+    prof_end(st, pi);
+    SA_LAUNCHED();
+    *xo = L->x.p;
+    return SA_OK;
+  }
+  const int deg = m->deg;
+  const double th = 0.5 * (L->lmax + L->lmin), de = 0.5 * (L->lmax - L->lmin);
+  const double s1 = th / de;
+  T* xa = L->x.p;
+  T* xb = L->x2.p;
+  const Sell<T>& A = L->A;
+  if (l == 0) {
+    PROFK(K_FST, l, 16.0 * n + 3.0 * S * n,
+          (k_vc_fine_in<T><<<g256(n), 256, 0, st>>>(n, r64, m->s0.p, (T)(1.0 / th), L->b.p, xa, L->d.p)));
+  } else {
+    PROFK(K_FST, l, 3.0 * S * n, (k_vc_first<T><<<g256(n), 256, 0, st>>>(n, L->b.p, (T)(1.0 / th), xa, L->d.p)));
+  }
+  double rho = 1.0 / s1;
+  for (int k = 1; k < deg; ++k) {
+    double rn = 1.0 / (2.0 * s1 - rho);
+    PROFK(K_CHEB, l, b_cheb(L),
+          (k_vc_cheb<T><<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, xb, L->d.p, (T)(rn * rho),
+                                                 (T)(2.0 * rn / de), 0)));
+    T* t = xa; xa = xb; xb = t;
+    rho = rn;
+  }
+  VLevel<T>* C = m->lev[l + 1];
+  PROFK(K_RES, l, (S + 4.0) * A.nnz + 8.0 * (A.nslices + 1) + 3.0 * S * n,
+        (k_vc_residual<T><<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, L->r.p)));
+  PROFK(K_RST, l, (S + 4.0) * L->R.nnz + 8.0 * (L->R.nslices + 1) + S * n + S * C->n,
+        (k_vc_spmv<T><<<g256(C->n), 256, 0, st>>>(C->n, L->R.sp.p, L->R.ci.p, L->R.v.p, L->r.p, C->b.p)));
+  T* xc = nullptr;
+  SA_TRY(mv(m, st, l + 1, nullptr, &xc));
+  PROFK(K_PRL, l, (S + 4.0) * L->P.nnz + 8.0 * (L->P.nslices + 1) + S * C->n + 2.0 * S * n,
+        (k_vc_spmv_add<T><<<g256(n), 256, 0, st>>>(n, L->P.sp.p, L->P.ci.p, L->P.v.p, xc, xa)));
+  rho = 1.0 / s1;
+  for (int k = 0; k < deg; ++k) {
+    int first = (k == 0);
+    T c1 = (T)0, c2 = (T)(1.0 / th);
+    double rn = rho;
+    if (!first) {
+      rn = 1.0 / (2.0 * s1 - rho);
+      c1 = (T)(rn * rho);
+      c2 = (T)(2.0 * rn / de);
+    }
+    if (l == 0 && k == deg - 1) {
+      PROFK(K_CHEB, l, b_cheb(L) + 16.0 * n - S * n,
+            (k_vc_cheb_out<T><<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, L->d.p, c1, c2, first,
+                                                       m->s0.p, m->z.p)));
+    } else {
+      PROFK(K_CHEB, l, b_cheb(L),
+            (k_vc_cheb<T><<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, xb, L->d.p, c1, c2,
+                                                   first)));
+      T* t = xa; xa = xb; xb = t;
+    }
+    if (!first) rho = rn;
+  }
+  *xo = xa;
+  return SA_OK;
+}
+
+template <typename T>
+int vh_vcycle(VHier<T>* m, cudaStream_t st, const double* r, double** z) {
+  if (m->lev.size() == 1) {
+    // one level: the dense solve on r directly
+    const int64_t n = m->lev[0]->n;
+    int pi = prof_begin(st, PK_COARSE, 0, 8.0 * n * n + 32.0 * n);
+    int s = launch_coarse_solve(st, n, m->W, m->WT, r, m->cy.p, m->z.p);
+    prof_end(st, pi);
+    SA_TRY(s);
+    *z = m->z.p;
+    return SA_OK;
+  }
+  T* xo = nullptr;
+  SA_TRY(mv<T>(m, st, 0, r, &xo));
+  *z = m->z.p;
+  return SA_OK;
+}
+
+template int vh_vcycle<double>(VHier<double>*, cudaStream_t, const double*, double**);
+template int vh_vcycle<float>(VHier<float>*, cudaStream_t, const double*, double**);
+
+template <typename T>
+void vh_free(VHier<T>* m) {
+  if (!m) return;
+  for (VLevel<T>* L : m->lev) delete L;
+  delete m;
+}
+
+template void vh_free<double>(VHier<double>*);
+template void vh_free<float>(VHier<float>*);
+
+// ---------------------------------------------------------------------------
+// FP64 SELL kernels for the outer CG (unscaled fine operator)
+// ---------------------------------------------------------------------------
+// q = A p, partial sums of p.q per CTA (fixed order)
+__global__ void k_sell_spmv_dot(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ v, const double* __restrict__ p, double* __restrict__ q,
+                                double* __restrict__ part) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double c = 0.0;
+  if (i < n) {
+    double a = sell_row<double>(sp, ci, v, p, i);
+    q[i] = a;
+    c = a * p[i];
+  }
+  c = warp_sum(c);
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = c;
+  __syncthreads();
+  if (w == 0) {
+    double t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sell_res64(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ v, const double* __restrict__ b,
+                             const double* __restrict__ x, double* __restrict__ r) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = b[i] - sell_row<double>(sp, ci, v, x, i);
+}
+
+int launch_sell_spmv_dot(cudaStream_t st, const Sell<double>& A, const double* p, double* q, double* part,
+                         int* nparts) {
+  *nparts = (int)g256(A.n);
+  k_sell_spmv_dot<<<g256(A.n), 256, 0, st>>>(A.n, A.sp.p, A.ci.p, A.v.p, p, q, part);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_sell_residual64(cudaStream_t st, const Sell<double>& A, const double* b, const double* x, double* r) {
+  k_sell_res64<<<g256(A.n), 256, 0, st>>>(A.n, A.sp.p, A.ci.p, A.v.p, b, x, r);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+}  // namespace sa

@@ -1,0 +1,73 @@
+// SELL-32 storage and the templated V-cycle on the scaled hierarchy.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace sa {
+
+template <typename T>
+struct Sell {
+  int64_t n = 0, nslices = 0, stored = 0, nnz = 0;
+  Buf<int64_t> sp;  // slice offsets (nslices + 1), in entries
+  Buf<int32_t> ci;
+  Buf<T> v;
+};
+
+// per-level input of the scaled hierarchy (device pointers of the FP64 CSR
+// hierarchy)
+struct VLevelIn {
+  int64_t n = 0, nnz = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* v = nullptr;
+  const double* diag = nullptr;
+  double lmax = 0, lmin = 0;
+  int64_t nc = 0, nnzP = 0;
+  const int64_t* Prp = nullptr;
+  const int32_t* Pci = nullptr;
+  const double* Pv = nullptr;
+  const int64_t* Rrp = nullptr;
+  const int32_t* Rci = nullptr;
+  const double* Rv = nullptr;
+};
+
+template <typename T>
+struct VLevel {
+  int64_t n = 0, nc = 0;
+  double lmax = 0, lmin = 0;
+  Sell<T> A, P, R;
+  Buf<T> b, x, x2, r, d;
+  Buf<double> sq;  // sqrt(diag) on the coarsest level
+};
+
+template <typename T>
+struct VHier {
+  int deg = 2;
+  std::vector<VLevel<T>*> lev;
+  Buf<double> s0;  // fine-level D^-1/2
+  Buf<double> z;   // FP64 output of the cycle
+  Buf<double> ct, cy, cx;
+  const double* W = nullptr;
+  const double* WT = nullptr;
+};
+
+template <typename T>
+int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
+               const double* left, int left_sqrt, const double* right, int right_sqrt, Sell<T>& S);
+template <typename T>
+int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const double* W, const double* WT,
+             VHier<T>** out);
+// z = D^-1/2 V~(D^-1/2 r); *z points to hierarchy-owned FP64 memory
+template <typename T>
+int vh_vcycle(VHier<T>* m, cudaStream_t s, const double* r, double** z);
+template <typename T>
+void vh_free(VHier<T>* m);
+
+// outer CG on the unscaled fine operator in FP64 SELL
+int launch_sell_spmv_dot(cudaStream_t st, const Sell<double>& A, const double* p, double* q, double* part,
+                         int* nparts);
+int launch_sell_residual64(cudaStream_t st, const Sell<double>& A, const double* b, const double* x, double* r);
+
+}  // namespace sa

@@ -248,3 +248,36 @@ def test_batch_solve_columns_independent(sa, gen_mod):
         assert infos[c].iters == i1["iters"]
         assert torch.equal(Xd[c], x1)
     del ctypes
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_loop_equals_host_loop(sa, gen_mod, precision):
+    """the captured CG loop (conditional WHILE graph) and the host-driven loop
+    (used while profiling) launch the same kernels in the same order"""
+    import torch
+    p = gen_mod.battery_3d(16, 16, 32)
+    h = sa.Hierarchy(p, theta=0.05, measure="material", max_coarse=200, precision=precision)
+    b = torch.from_numpy(p["b"]).cuda()
+    xg, ig = h.solve(b)
+    sa.profile_enable(True)
+    try:
+        xe, ie = h.solve(b)
+        rows = sa.profile_read()
+    finally:
+        sa.profile_enable(False)
+    assert ig["iters"] == ie["iters"] and ig["status"] == ie["status"] == 0
+    assert torch.equal(xg, xe)
+    kinds = {r["kind"] for r in rows}
+    assert ("cheb64" if precision == "fp64" else "cheb32") in kinds and "cg_spmv" in kinds
+    assert all(r["ms"] > 0 and r["bytes"] > 0 for r in rows)
+
+
+def test_theta_sweep_runs(sa, gen_mod):
+    from paper_2602_05686_gb300.sweep import theta_sweep
+    p = gen_mod.two_domain(16, 1e4)
+    rows = theta_sweep(p, thetas=(0.02, 0.08), measures=("classical", "material"), max_coarse=30)
+    assert len(rows) == 4
+    for r in rows:
+        assert r["status"] in (0, -5, -6)
+        if r["status"] == 0:
+            assert r["cost"] == pytest.approx(r["op_complexity"] * r["iters"])
