@@ -133,6 +133,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def setup_phases(prof, steps):
+    """stream time per setup phase, summed over levels, per step"""
+    out = {}
+    for r in prof:
+        if r["kind"].startswith("setup_"):
+            out[r["kind"][6:]] = out.get(r["kind"][6:], 0.0) + r["ms"] / steps
+    return {k: round(v, 2) for k, v in sorted(out.items(), key=lambda kv: -kv[1])}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -240,7 +249,8 @@ def run_ours(args):
     # roofline of the dominant kernel (largest total time in the timed region)
     peak, peak_kind = peaks()
     rows = sorted(prof, key=lambda r: -r["ms"])
-    dom = rows[0] if rows else None
+    krows = [r for r in rows if r["bytes"] > 0]   # kernels with an algorithmic-bytes model
+    dom = krows[0] if krows else None
     roof = None
     if dom:
         per_launch_ms = dom["ms"] / dom["launches"]
@@ -282,7 +292,8 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "kernel_profile_top": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
-                               for r in rows[:8]],
+                               for r in krows[:8]],
+        "setup_phases_ms": setup_phases(prof, args.steps),
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         result["cpu_baseline"] = cpu_baseline(args)

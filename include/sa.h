@@ -241,8 +241,13 @@ int sa_strength(sa_measure measure, int dim, int64_t n, int64_t nnz, const int64
  * 3 FP64 prolongation, 4 FP64 first Chebyshev step, 5 CG operator product,
  * 6 CG vector update / dot, 7 dense coarse solve, 8 FP32 Chebyshev step,
  * 9 FP32 residual, 10 FP32 restriction, 11 FP32 prolongation, 12 FP32 first
- * step), level, launches, total milliseconds, and total algorithmic bytes
- * (bytes the kernel must move at least once).  *rows receives the number of
+ * step; setup phases, stream time from the phase's first to last launch:
+ * 13 nodal tensors, 14 strength, 15 filtered graph, 16 MIS-2, 17
+ * aggregation, 18 filtered matrix, 19 omega, 20 smoothed P, 21 transpose,
+ * 22 Galerkin product, 23 coarse aux data, 24 Chebyshev bounds, 25 dense
+ * coarse factor, 26 SELL packing), level, launches, total milliseconds, and
+ * total algorithmic bytes (bytes the kernel must move at least once; 0 for
+ * the setup phases).  *rows receives the number of
  * rows available.  Host-side timing arrays, any may be NULL.
  */
 int sa_profile_enable(int on);

@@ -289,7 +289,10 @@ def strength(measure, dim, row_ptr, col, val, coords, sigma_inv, dirichlet, thet
 
 
 PROFILE_KINDS = ["cheb64", "resid64", "restrict64", "prolong64", "first64", "cg_spmv", "cg_vec", "coarse",
-                 "cheb32", "resid32", "restrict32", "prolong32", "first32"]
+                 "cheb32", "resid32", "restrict32", "prolong32", "first32",
+                 "setup_nodal", "setup_strength", "setup_graph", "setup_mis2", "setup_aggregate", "setup_filter",
+                 "setup_omega", "setup_smooth_p", "setup_transpose", "setup_galerkin", "setup_aux",
+                 "setup_cheb_bounds", "setup_dense", "setup_sell"]
 
 
 def profile_enable(on=True):
@@ -315,3 +318,4 @@ def profile_read():
 def launch_count():
     """kernel launches issued by the library in this process"""
     return int(lib().sa_launch_count())
+

@@ -80,6 +80,9 @@ static int read_i64(cudaStream_t s, const int64_t* d, int64_t* h) { return copy_
 
 // one coarsening step: level l -> level l+1.  *stop = 1 when level l is the
 // coarsest (stagnation or nothing to coarsen).
+#define PHASE_BEGIN(kind, level) int _ph_##kind = prof_begin(s, (kind), (level), 0.0)
+#define PHASE_END(kind) prof_end(s, _ph_##kind)
+
 static int coarsen(sa_handle h, int l, int* err, int* stop) {
   Alloc& al = h->al;
   cudaStream_t s = al.stream;
@@ -91,6 +94,7 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
   *stop = 0;
 
   // a3/a4: strength + pointwise dropping; kept counts per row -> rpF
+  PHASE_BEGIN(PK_S_STRENGTH, l);
   Buf<uint8_t> keep;
   Buf<int64_t> rpF;
   SA_TRY(keep.alloc(&al, nnz));
@@ -108,8 +112,10 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
   SA_TRY(scan_inplace(al, rpF.p + 1, n));
   int64_t nnzF = 0;
   SA_TRY(read_i64(s, rpF.p + n, &nnzF));
+  PHASE_END(PK_S_STRENGTH);
 
   // a5: filtered graph
+  PHASE_BEGIN(PK_S_GRAPH, l);
   Buf<int64_t> gcrp;
   Buf<int32_t> gcci;
   L.nnz_gc = nnzF - n;
@@ -117,11 +123,15 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
   SA_TRY(gcci.alloc(&al, L.nnz_gc));
   SA_TRY(launch_graph_rowptr(s, n, rpF.p, gcrp.p));
   SA_TRY(launch_graph_compact(s, n, L.rp.p, L.ci.p, keep.p, gcrp.p, gcci.p));
+  PHASE_END(PK_S_GRAPH);
 
   // a6/a7: MIS-2 and aggregates
+  PHASE_BEGIN(PK_S_MIS, l);
   Buf<uint64_t> tag;
   SA_TRY(tag.alloc(&al, n));
   SA_TRY(run_mis2(al, n, gcrp.p, gcci.p, dir, l, o.seed, tag.p, &L.mis_rounds, 100000));
+  PHASE_END(PK_S_MIS);
+  PHASE_BEGIN(PK_S_AGG, l);
   SA_TRY(L.agg.alloc(&al, n));
   Buf<uint8_t> root;
   if (o.keep_setup_data) SA_TRY(root.alloc(&al, n));
@@ -151,8 +161,10 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
   SA_TRY(Tci.alloc(&al, nnzT));
   SA_TRY(Tv.alloc(&al, nnzT));
   SA_TRY(launch_tentative(s, n, L.agg.p, Trp.p, Tci.p, Tv.p));
+  PHASE_END(PK_S_AGG);
 
   // a10: filtered matrix and 1-norm diagonal
+  PHASE_BEGIN(PK_S_FILTER, l);
   Buf<int32_t> ciF;
   Buf<double> vF, Dt, sc, scal;
   SA_TRY(ciF.alloc(&al, nnzF));
@@ -160,24 +172,32 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
   SA_TRY(Dt.alloc(&al, n));
   const uint8_t* keep_p = o.keep_setup_data ? L.keep.p : keep.p;
   SA_TRY(launch_filter(s, n, L.rp.p, L.ci.p, L.v.p, keep_p, rpF.p, ciF.p, vF.p, Dt.p));
+  PHASE_END(PK_S_FILTER);
 
   // a11: omega = omega_sym / rho(D~^-1 A_F)
+  PHASE_BEGIN(PK_S_OMEGA, l);
   SA_TRY(sc.alloc(&al, n));
   SA_TRY(scal.alloc(&al, 2));
   SA_TRY(launch_rsqrt_scale(s, n, Dt.p, sc.p));
   SA_TRY(run_power(al, n, rpF.p, ciF.p, vF.p, sc.p, o.power_iters, (uint32_t)(2 * l + 1), o.seed, scal.p));
   SA_TRY(launch_omega(s, scal.p, o.omega_sym, scal.p + 1));
+  PHASE_END(PK_S_OMEGA);
 
   // a12: P = P^ - omega D~^-1 A_F P^
+  PHASE_BEGIN(PK_S_SMOOTHP, l);
   SA_TRY(run_spgemm(al, n, nc, rpF.p, ciF.p, vF.p, Trp.p, Tci.p, Tv.p, L.Prp, L.Pci, L.Pv, &L.nnzP));
   SA_TRY(launch_smooth_p_values(s, n, L.Prp.p, L.Pci.p, L.Pv.p, L.agg.p, Dt.p, scal.p + 1, L.Pv.p));
+  PHASE_END(PK_S_SMOOTHP);
   double hs[2];
   SA_TRY(copy_d2h(hs, scal.p, sizeof(hs), s));
   L.lam_omega = hs[0];
   L.omega = hs[1];
 
   // a13: R = P^T, A_{l+1} = R (A P), exactly symmetric
+  PHASE_BEGIN(PK_S_TRANSPOSE, l);
   SA_TRY(run_transpose(al, n, nc, L.Prp.p, L.Pci.p, L.Pv.p, L.Rrp, L.Rci, &L.Rv));
+  PHASE_END(PK_S_TRANSPOSE);
+  PHASE_BEGIN(PK_S_RAP, l);
   Buf<int64_t> APrp;
   Buf<int32_t> APci;
   Buf<double> APv;
@@ -188,9 +208,11 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
   SA_TRY(run_spgemm(al, nc, nc, L.Rrp.p, L.Rci.p, L.Rv.p, APrp.p, APci.p, APv.p, N->rp, N->ci, N->v, &N->nnz));
   SA_TRY(launch_symmetrize(s, nc, N->rp.p, N->ci.p, N->v.p, err));
   SA_TRY(level_diag(h, *N, nullptr, err));
+  PHASE_END(PK_S_RAP);
 
   // a9: coarse coordinates and tensors
   if (aux) {
+    PHASE_BEGIN(PK_S_AUX, l);
     Buf<int64_t> Mrp;
     Buf<int32_t> Mci;
     SA_TRY(run_transpose(al, n, nc, Trp.p, Tci.p, nullptr, Mrp, Mci, nullptr));
@@ -199,6 +221,7 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
     SA_TRY(N->sigma.alloc(&al, nc * kp));
     SA_TRY(N->sinv.alloc(&al, nc * kp));
     SA_TRY(launch_coarse_aux(s, nc, h->dim, Mrp.p, Mci.p, L.x.p, L.sigma.p, N->x.p, N->sigma.p, N->sinv.p));
+    PHASE_END(PK_S_AUX);
   }
   h->lev.push_back(std::move(N));
   return SA_OK;
@@ -574,6 +597,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
     }
   }
   const int kp = P->dim == 3 ? 6 : 3;
+  PHASE_BEGIN(PK_S_NODAL, 0);
   if (o->measure != SA_MEASURE_CLASSICAL) {
     SA_TRY(upload(al, L0->x, P->coords, P->n * P->dim));
     SA_TRY(L0->sigma.alloc(&al, P->n * kp));
@@ -595,6 +619,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
                                   L0->sinv.p, err.p));
     }
   }
+  PHASE_END(PK_S_NODAL);
   h->lev.push_back(std::move(L0));
   for (int l = 0;; ++l) {
     Level& L = *h->lev[l];
@@ -615,6 +640,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   Level& Lc = *h->lev[nlev - 1];
   if (Lc.n > 16384) return SA_ERR_STAGNATION;
   // a15: smoother data (Chebyshev bounds from 10 power steps on D^-1/2 A D^-1/2)
+  PHASE_BEGIN(PK_S_CHEB, 0);
   for (int l = 0; l < nlev; ++l) {
     Level& L = *h->lev[l];
     SA_TRY(L.dinv.alloc(&al, L.n));
@@ -631,15 +657,20 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
       L.lmin = L.lmax / o->cheb_ratio;
     }
   }
+  PHASE_END(PK_S_CHEB);
   h->nL = Lc.n;
+  PHASE_BEGIN(PK_S_DENSE, nlev - 1);
   SA_TRY(run_dense_inverse_factor(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT));
+  PHASE_END(PK_S_DENSE);
   SA_TRY(alloc_workspace(h));
+  PHASE_BEGIN(PK_S_SELL, 0);
   {
     Level& L0 = *h->lev[0];
     SA_TRY(build_sell<double>(al, L0.n, L0.nnz, L0.rp.p, L0.ci.p, L0.v.p, nullptr, 0, nullptr, 0, h->A0s));
     std::vector<VLevelIn> in = vlevel_inputs(h);
     SA_TRY(vh_build<double>(al, in.data(), nlev, o->cheb_degree, h->W.p, h->WT.p, &h->v64));
   }
+  PHASE_END(PK_S_SELL);
   if (o->precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
   SA_CUDA(cudaStreamSynchronize(s));
   auto t1 = std::chrono::steady_clock::now();

@@ -20,7 +20,22 @@ enum ProfKind {
   PK_RESTRICT32 = 10,
   PK_PROLONG32 = 11,
   PK_FIRST32 = 12,
-  PK_NKINDS = 13
+  // setup phases (stream time between the phase's first and last launch)
+  PK_S_NODAL = 13,     // a2 nodal tensors
+  PK_S_STRENGTH = 14,  // a3/a4 strength + dropping (+ row counts)
+  PK_S_GRAPH = 15,     // a5 filtered graph
+  PK_S_MIS = 16,       // a6 MIS-2 rounds
+  PK_S_AGG = 17,       // a7 aggregation, a8 tentative P
+  PK_S_FILTER = 18,    // a10 filtered matrix, 1-norm diagonal
+  PK_S_OMEGA = 19,     // a11 power method for omega
+  PK_S_SMOOTHP = 20,   // a12 smoothed prolongator (SpGEMM + values)
+  PK_S_TRANSPOSE = 21, // R = P^T
+  PK_S_RAP = 22,       // a13 Galerkin product (two SpGEMMs + symmetrise)
+  PK_S_AUX = 23,       // a9 coarse coordinates / tensors
+  PK_S_CHEB = 24,      // a15 Chebyshev bounds
+  PK_S_DENSE = 25,     // a15 coarse Cholesky + inverse factor
+  PK_S_SELL = 26,      // a15 SELL packing of the scaled hierarchy
+  PK_NKINDS = 27
 };
 
 bool prof_on();

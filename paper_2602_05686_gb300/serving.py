@@ -74,6 +74,7 @@ class Server:
         self.free_slots = list(range(slots))
         self.stats = dict(admitted=0, setups=0, hits=0, evictions=0, peak_committed=0)
         self._problems = {}
+        self.building = {}  # op -> threading.Event of an in-flight setup
 
     # -- memory ledger -------------------------------------------------------
     def _estimate(self, op):
@@ -107,48 +108,69 @@ class Server:
         import torch
         return torch.cuda.stream(stream)
 
-    def _run(self, req, slot, t0):
-        stream = self.streams[slot]
-        with self._ctx(stream):
-            entry = None
+    def _acquire(self, req, stream):
+        """the cached hierarchy of req.op, building it if nobody else is; a
+        request whose operator is being built by another slot waits for it"""
+        while True:
+            builder = False
             with self.cv:
                 entry = self.cache.get(req.op)
                 if entry is not None:
                     entry.users += 1
                     req.cache_hit = True
-            if entry is None:
+                    self.stats["hits"] += 1
+                    self.committed -= req.info.pop("_reserved", 0)
+                    return entry
+                ev = self.building.get(req.op)
+                if ev is None:
+                    ev = threading.Event()
+                    self.building[req.op] = ev
+                    builder = True
+            if not builder:
+                ev.wait()
+                continue  # cached now (or evicted again: retry)
+            try:
                 p = self._problem(req.op)
                 h = self.factory(p, stream=stream, **self.options(req.op))
                 nbytes = h.stats()["device_bytes"]
                 with self.cv:
-                    other = self.cache.get(req.op)
-                    if other is None:
-                        entry = _Entry(h, nbytes)
-                        self.cache[req.op] = entry
-                        # replace the admission estimate by the measured size
-                        self.committed += nbytes - req.info.pop("_reserved", 0)
-                        self.stats["setups"] += 1
-                    else:  # another slot built it meanwhile
-                        h.free()
-                        entry = other
-                        self.committed -= req.info.pop("_reserved", 0)
+                    entry = _Entry(h, nbytes)
                     entry.users += 1
-            else:
+                    self.cache[req.op] = entry
+                    # the measured size replaces the admission estimate
+                    self.committed += nbytes - req.info.pop("_reserved", 0)
+                    self.stats["setups"] += 1
+                return entry
+            finally:
                 with self.cv:
-                    self.stats["hits"] += 1
-            rhs = req.rhs
-            if hasattr(rhs, "to") and stream is not None and hasattr(stream, "cuda_stream"):
-                rhs = rhs.to(device="cuda", non_blocking=True)
-                stream.synchronize()  # the cached handle may run on another slot's stream
-            with entry.lock:
-                x, info = entry.h.solve(rhs, tol=self.tol, check=False)
-            req.result = x
-            req.info.update(info)
-            req.status = info["status"]
+                    self.building.pop(req.op, None)
+                    self.cv.notify_all()
+                ev.set()
+
+    def _run(self, req, slot, t0):
+        stream = self.streams[slot]
+        with self._ctx(stream):
+            entry = None
+            try:
+                entry = self._acquire(req, stream)
+                rhs = req.rhs
+                if hasattr(rhs, "to") and stream is not None and hasattr(stream, "cuda_stream"):
+                    rhs = rhs.to(device="cuda", non_blocking=True)
+                    stream.synchronize()  # the cached handle may run on another slot's stream
+                with entry.lock:
+                    x, info = entry.h.solve(rhs, tol=self.tol, check=False)
+                req.result = x
+                req.info.update(info)
+                req.status = info["status"]
+            except Exception as e:  # a failed request is retired with its status
+                req.status = getattr(e, "status", -1)
+                req.info["error"] = str(e)
             req.done = time.perf_counter() - t0
             with self.cv:
-                entry.users -= 1
-                entry.last = req.done
+                if entry is not None:
+                    entry.users -= 1
+                    entry.last = req.done
+                self.committed -= req.info.pop("_reserved", 0)
                 self.free_slots.append(slot)
                 self.cv.notify_all()
 
@@ -171,7 +193,7 @@ class Server:
             with self.cv:
                 if queue and self.free_slots:
                     req = queue[0][2]
-                    need = 0 if req.op in self.cache else self._estimate(req.op)
+                    need = 0 if (req.op in self.cache or req.op in self.building) else self._estimate(req.op)
                     busy = any(e.users for e in self.cache.values()) or len(self.free_slots) < self.slots
                     if self._make_room(need) or not busy:
                         heapq.heappop(queue)
