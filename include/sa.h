@@ -232,6 +232,34 @@ int sa_strength(sa_measure measure, int dim, int64_t n, int64_t nnz, const int64
                 double theta, uint8_t* keep, void* stream);
 
 /*
+ * sa_strength_material_noalloc: the material-aware strength filter of
+ * sa_strength (SA_MEASURE_MATERIAL, same kernels, same bit-exact keep mask)
+ * for callers that must not allocate device memory during the call: code
+ * under an allocator or memory-pool policy that forbids new allocations, a
+ * real-time or callback context where an allocation could block or fail, or
+ * an application that owns all device memory and passes only inputs and
+ * outputs.  (The paper has no counterpart; this is a deployment variant.)
+ *   - Allocates nothing: its scratch (w and D, nnz + n doubles) is a fixed
+ *     16 MiB static device array that every GPU loading this library holds
+ *     until the process exits.  Sizes with nnz + n > 2,097,152 return
+ *     SA_ERR_CAPACITY (see sa_last_error) without launching anything.
+ *   - Inputs and outputs are caller-owned DEVICE buffers as for sa_strength:
+ *     row_ptr[n+1], col[nnz], coords[n*dim], sigma_inv[n*kp] (inverse nodal
+ *     tensors; identity tensors give the plain distance Laplacian),
+ *     dirichlet[n] (may be NULL), keep[nnz] (output).  Ordered on `stream`.
+ *   - The first call on a device looks up the device address of the array
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     outside any stream capture.
+ *   - All calls share the one array and every call overwrites it completely
+ *     before reading it, so nothing carries over between calls; calls whose
+ *     GPU work overlaps (different streams, host threads) race on it and
+ *     must be serialised by the caller.
+ */
+int sa_strength_material_noalloc(int dim, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                                 const double* coords, const double* sigma_inv, const uint8_t* dirichlet,
+                                 double theta, uint8_t* keep, void* stream);
+
+/*
  * Solve-phase kernel timing (no counterpart in the paper; measurement
  * support).  sa_profile_enable(1) clears the record and, until
  * sa_profile_enable(0), brackets every V-cycle and CG kernel launch with CUDA

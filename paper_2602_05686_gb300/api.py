@@ -21,7 +21,7 @@ PRECISION = {"fp64": 0, "fp32": 1}
 EXPORTED = ["sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle", "sa_hierarchy_stats",
             "sa_level_sizes", "sa_export_level", "sa_export_strength", "sa_free", "sa_status_string",
             "sa_last_error", "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
-            "sa_launch_count"]
+            "sa_launch_count", "sa_strength_material_noalloc"]
 
 
 class SAError(RuntimeError):
@@ -91,6 +91,8 @@ def lib(build_if_missing: bool = True):
         L.sa_set_precision.argtypes = [P, I]
         L.sa_profile_enable.argtypes = [I]
         L.sa_profile_read.argtypes = [I, P, P, P, P, P, P]
+        L.sa_strength_material_noalloc.argtypes = [I, I64, I64, P, P, P, P, P, D, P, P]
+        L.sa_strength_material_noalloc.restype = I
         L.sa_launch_count.argtypes = []
         L.sa_launch_count.restype = ctypes.c_int64
         for f in ("sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle",
@@ -319,3 +321,18 @@ def launch_count():
     """kernel launches issued by the library in this process"""
     return int(lib().sa_launch_count())
 
+
+def strength_material_noalloc(dim, row_ptr, col, coords, sigma_inv, dirichlet, theta, keep, stream=None):
+    """sa_strength_material_noalloc on CUDA tensors; writes the keep mask into
+    the caller's `keep` (uint8, nnz) and returns the status (no allocation
+    inside the call)"""
+    torch = _torch()
+    n = row_ptr.numel() - 1
+    nnz = col.numel()
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+
+    def P(t):
+        return None if t is None else t.data_ptr()
+
+    return int(lib().sa_strength_material_noalloc(int(dim), n, nnz, P(row_ptr), P(col), P(coords), P(sigma_inv),
+                                                  P(dirichlet), float(theta), P(keep), ctypes.c_void_p(s)))
