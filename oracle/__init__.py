@@ -69,6 +69,7 @@ def lib():
             "or_level_sizes": (None, [P, I32, P]),
             "or_level_export": (None, [P, I32] + [P] * 13),
             "or_operator_complexity": (D, [P]),
+            "or_set_cheb": (None, [P, I32, D, D]),
             "or_pcg": (I32, [P, P, P, D, I32, I32, P, P]),
             "or_vcycle": (None, [P, P, P]),
             "or_coarsest_solve": (None, [P, P, P]),
@@ -325,6 +326,10 @@ class Hierarchy:
             d[k] = d[k][:pnnz]
         d["omega"], d["lam_omega"], d["cheb_lmax"], d["cheb_lmin"] = (float(x) for x in d["scalars"])
         return d
+
+    def set_cheb(self, l, lmax, lmin):
+        """override the Chebyshev interval of level l (experiments only)"""
+        lib().or_set_cheb(self.h, int(l), float(lmax), float(lmin))
 
     def operator_complexity(self):
         return float(lib().or_operator_complexity(self.h))

@@ -994,6 +994,13 @@ void or_level_export(const or_hier_t* h, int l, int64_t* A_rp, int32_t* A_ci, do
   }
 }
 
+/* overrides the Chebyshev interval of level l (for experiments on the
+ * eigenvalue estimate; not part of the method) */
+void or_set_cheb(or_hier_t* h, int l, double lmax, double lmin) {
+  h->lev[l].cheb_lmax = lmax;
+  h->lev[l].cheb_lmin = lmin;
+}
+
 double or_operator_complexity(const or_hier_t* h) {
   double s = 0.0;
   for (int l = 0; l < h->nlev; ++l) s += (double)csr_nnz(&h->lev[l].A);

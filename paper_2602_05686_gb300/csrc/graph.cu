@@ -133,16 +133,21 @@ int run_mis2(Alloc& al, int64_t n, const int64_t* gcrp, const int32_t* gcci, con
   const uint32_t salt = 0x9E3779B9u * (uint32_t)(level + 1);
   k_mis_init<<<blocks_for(n, 256), 256, 0, s>>>(n, dir, salt, seed, tag);
   SA_LAUNCHED();
+  // rounds are launched in groups between read-backs of the undecided count;
+  // a round after convergence changes nothing (every node is decided)
   unsigned long long h_cnt = 1;
+  const int group = 4;
   while (h_cnt > 0) {
     if (*rounds >= max_rounds) return SA_ERR_CAPACITY;
-    SA_TRY(memset_d(cnt.p, 0, sizeof(unsigned long long), s));
-    k_mis_max1<<<warp_rows_grid(n), 256, 0, s>>>(n, gcrp, gcci, tag, m1.p);
-    SA_LAUNCHED();
-    k_mis_max2<<<warp_rows_grid(n), 256, 0, s>>>(n, gcrp, gcci, m1.p, tag, cnt.p);
-    SA_LAUNCHED();
+    for (int g = 0; g < group; ++g) {
+      SA_TRY(memset_d(cnt.p, 0, sizeof(unsigned long long), s));
+      k_mis_max1<<<warp_rows_grid(n), 256, 0, s>>>(n, gcrp, gcci, tag, m1.p);
+      SA_LAUNCHED();
+      k_mis_max2<<<warp_rows_grid(n), 256, 0, s>>>(n, gcrp, gcci, m1.p, tag, cnt.p);
+      SA_LAUNCHED();
+      ++*rounds;
+    }
     SA_TRY(copy_d2h(&h_cnt, cnt.p, sizeof(h_cnt), s));
-    ++*rounds;
   }
   return SA_OK;
 }

@@ -210,8 +210,7 @@ __device__ __forceinline__ double quad_form(int dim, const double* __restrict__ 
 
 template <int DIM>
 __global__ void k_material_w(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const double* __restrict__ x, const double* __restrict__ sinv,
-                             double* __restrict__ w, double* __restrict__ D) {
+                             const double* __restrict__ x, const double* __restrict__ sinv, double* __restrict__ w) {
   constexpr int KP = DIM == 3 ? 6 : 3;
   const int lane = lane_id();
   for (int64_t i = global_warp(); i < n; i += warp_stride()) {
@@ -221,36 +220,36 @@ __global__ void k_material_w(int64_t n, const int64_t* __restrict__ rp, const in
     for (int c = 0; c < DIM; ++c) xi[c] = x[i * DIM + c];
 #pragma unroll
     for (int c = 0; c < KP; ++c) si_i[c] = sinv[i * KP + c];
-    double acc = 0.0;
-    for (int64_t p0 = b; p0 < e; p0 += 32) {
-      const int64_t p = p0 + lane;
+    for (int64_t p = b + lane; p < e; p += 32) {
+      int32_t j = ci[p];
       double wv = 0.0;
-      bool off = false;
-      if (p < e) {
-        int32_t j = ci[p];
-        if (j != (int32_t)i) {
-          off = true;
-          double d[3], sj[KP];
+      if (j != (int32_t)i) {
+        double d[3], sj[KP];
 #pragma unroll
-          for (int c = 0; c < DIM; ++c) d[c] = xi[c] - x[(int64_t)j * DIM + c];
+        for (int c = 0; c < DIM; ++c) d[c] = xi[c] - x[(int64_t)j * DIM + c];
 #pragma unroll
-          for (int c = 0; c < KP; ++c) sj[c] = sinv[(int64_t)j * KP + c];
-          double qij = quad_form(DIM, si_i, d);
-          double qji = quad_form(DIM, sj, d);
-          double m = qij > qji ? qij : qji;
-          wv = 1.0 / m;
-        }
-        w[p] = wv;
+        for (int c = 0; c < KP; ++c) sj[c] = sinv[(int64_t)j * KP + c];
+        double qij = quad_form(DIM, si_i, d);
+        double qji = quad_form(DIM, sj, d);
+        double m = qij > qji ? qij : qji;
+        wv = 1.0 / m;
       }
-      // ordered sum over this chunk (ascending p)
-      unsigned offm = __ballot_sync(FULL, off);
-      for (int t = 0; t < 32; ++t) {
-        double u = __shfl_sync(FULL, wv, t);
-        if ((offm >> t) & 1u) acc += u;
-      }
+      w[p] = wv;
     }
-    if (lane == 0) D[i] = acc;
   }
+}
+
+// D_i = sum of the row's w in ascending column order (thread per row, so the
+// sequential FP64 additions of 32 rows share one warp instruction).  The
+// diagonal's w is +0, and adding +0 to a non-negative sum leaves it unchanged,
+// so this equals the sum over the off-diagonal entries only.
+__global__ void k_row_sum_ordered(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ w,
+                                  double* __restrict__ D) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc += w[p];
+  D[i] = acc;
 }
 
 // keep_ij <=> w_ij*w_ij >= (theta*theta) * (D_i*D_j)
@@ -283,7 +282,7 @@ __global__ void k_material_keep(int64_t n, const int64_t* __restrict__ rp, const
 
 // ---------------------------------------------------------------------------
 // a10. filtered matrix A_F and 1-norm diagonal (Sec. 2.2, Eqs.
-// filtered_matrix and 1_norm_diagonal).  Warp per row.  rpF is the scan of
+// filtered_matrix and 1_norm_diagonal).  rpF is the scan of
 // the kept counts.  A row whose filtered 1-norm is <= 1e-12 times the 1-norm
 // of its row of A (every off-diagonal dropped, lumped row sum ~ 0) gets
 // Dt = +inf: it is not smoothed.
@@ -292,58 +291,33 @@ __global__ void k_filter(int64_t n, const int64_t* __restrict__ rp, const int32_
                          const double* __restrict__ v, const uint8_t* __restrict__ keep,
                          const int64_t* __restrict__ rpF, int32_t* __restrict__ ciF, double* __restrict__ vF,
                          double* __restrict__ Dt) {
-  const int lane = lane_id();
-  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
-    const int64_t b = rp[i], e = rp[i + 1];
-    // lumped diagonal: a_ii, then the dropped entries in ascending order
-    double dg = 0.0;
-    for (int64_t p0 = b; p0 < e; p0 += 32) {
-      int64_t p = p0 + lane;
-      bool isd = false;
-      double a = 0.0;
-      if (p < e) { isd = ci[p] == (int32_t)i; a = v[p]; }
-      unsigned m = __ballot_sync(FULL, isd);
-      if (m) dg = __shfl_sync(FULL, a, __ffs(m) - 1);
+  // thread per row: the three ordered sums are sequential FP64 chains, so
+  // one warp instruction advances 32 rows
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = rp[i], e = rp[i + 1];
+  // lumped diagonal: a_ii, then the dropped entries in ascending order
+  double dg = 0.0;
+  for (int64_t p = b; p < e; ++p)
+    if (ci[p] == (int32_t)i) dg = v[p];
+  for (int64_t p = b; p < e; ++p)
+    if (ci[p] != (int32_t)i && !keep[p]) dg += v[p];
+  // the filtered row and both 1-norms in ascending order
+  int64_t out = rpF[i];
+  double s = 0.0, a1 = 0.0;
+  for (int64_t p = b; p < e; ++p) {
+    const int32_t j = ci[p];
+    const double a = v[p];
+    a1 += fabs(a);
+    if (j == (int32_t)i || keep[p]) {
+      const double fv = (j == (int32_t)i) ? dg : a;
+      ciF[out] = j;
+      vF[out] = fv;
+      ++out;
+      s += fabs(fv);
     }
-    for (int64_t p0 = b; p0 < e; p0 += 32) {
-      int64_t p = p0 + lane;
-      bool drop = false;
-      double a = 0.0;
-      if (p < e) { drop = ci[p] != (int32_t)i && !keep[p]; a = v[p]; }
-      unsigned m = __ballot_sync(FULL, drop);
-      for (int t = 0; t < 32; ++t) {
-        double u = __shfl_sync(FULL, a, t);
-        if ((m >> t) & 1u) dg += u;
-      }
-    }
-    // write the filtered row and accumulate both 1-norms in ascending order
-    int64_t out = rpF[i];
-    double s = 0.0, a1 = 0.0;
-    for (int64_t p0 = b; p0 < e; p0 += 32) {
-      int64_t p = p0 + lane;
-      bool in = p < e;
-      int32_t j = in ? ci[p] : 0;
-      bool isd = in && j == (int32_t)i;
-      bool kp = in && (isd || keep[p]);
-      double a = in ? v[p] : 0.0;
-      double fv = isd ? dg : a;
-      unsigned km = __ballot_sync(FULL, kp);
-      unsigned im = __ballot_sync(FULL, in);
-      if (kp) {
-        int pos = __popc(km & ((1u << lane) - 1u));
-        ciF[out + pos] = j;
-        vF[out + pos] = fv;
-      }
-      for (int t = 0; t < 32; ++t) {
-        double uf = __shfl_sync(FULL, fabs(fv), t);
-        double ua = __shfl_sync(FULL, fabs(a), t);
-        if ((km >> t) & 1u) s += uf;
-        if ((im >> t) & 1u) a1 += ua;
-      }
-      out += __popc(km);
-    }
-    if (lane == 0) Dt[i] = (s <= 1e-12 * a1) ? INFINITY : s;
   }
+  Dt[i] = (s <= 1e-12 * a1) ? INFINITY : s;
 }
 
 // ---------------------------------------------------------------------------
@@ -456,8 +430,10 @@ int launch_strength_material(cudaStream_t s, int dim, int64_t n, const int64_t* 
                              double* w, double* D, uint8_t* keep, int64_t* cnt) {
   if (n <= 0) return SA_OK;
   const double t2 = theta * theta;
-  if (dim == 3) k_material_w<3><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w, D);
-  else k_material_w<2><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w, D);
+  if (dim == 3) k_material_w<3><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
+  else k_material_w<2><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
+  SA_LAUNCHED();
+  k_row_sum_ordered<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, w, D);
   SA_LAUNCHED();
   k_material_keep<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, w, D, dir, t2, keep, cnt);
   SA_LAUNCHED();
@@ -467,7 +443,7 @@ int launch_strength_material(cudaStream_t s, int dim, int64_t n, const int64_t* 
 int launch_filter(cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                   const uint8_t* keep, const int64_t* rpF, int32_t* ciF, double* vF, double* Dt) {
   if (n <= 0) return SA_OK;
-  k_filter<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, v, keep, rpF, ciF, vF, Dt);
+  k_filter<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, v, keep, rpF, ciF, vF, Dt);
   SA_LAUNCHED();
   return SA_OK;
 }

@@ -13,38 +13,31 @@ namespace sa {
 // CSR row products with SW lanes per row (power method on the setup's CSR
 // matrices); the result is valid in every lane of the group
 // ---------------------------------------------------------------------------
-// scaled variant: sum_p v_p * (s_j * x_j)
-template <int SW>
-__device__ __forceinline__ double row_dot_scaled(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                 const double* __restrict__ v, const double* __restrict__ s,
-                                                 const double* __restrict__ x, int64_t i, bool valid, int sl) {
-  double acc = 0.0;
-  if (valid) {
-    const int64_t e = rp[i + 1];
-    for (int64_t p = rp[i] + sl; p < e; p += SW) {
-      int32_t j = ci[p];
-      acc += v[p] * (s[j] * x[j]);
-    }
-  }
-#pragma unroll
-  for (int o = SW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SW);
-  return acc;
-}
-
 #define ROW_SETUP(SW)                                                   \
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   \
   const int64_t i = gt / SW;                                            \
   const int sl = (int)(gt % SW);                                        \
   const bool valid = i < n;
 
-// power method product: w_i = s_i * sum_p a_p (s_j v_j)
+// power method product: w_i = s_i * sum_p a_p (s_j v_j), v_j = X_j / sc[2]
+// (the previous product divided by its norm; sc[2] = 1 for the start vector)
 template <int SW>
 __global__ void k_power_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const double* __restrict__ v, const double* __restrict__ s, const double* __restrict__ x,
-                             double* __restrict__ w) {
+                             const double* __restrict__ v, const double* __restrict__ s, const double* __restrict__ X,
+                             const double* __restrict__ sc, double* __restrict__ w) {
   ROW_SETUP(SW)
-  double a = row_dot_scaled<SW>(rp, ci, v, s, x, i, valid, sl);
-  if (valid && sl == 0) w[i] = s[i] * a;
+  const double nrm = sc[2];
+  double acc = 0.0;
+  if (valid) {
+    const int64_t e = rp[i + 1];
+    for (int64_t p = rp[i] + sl; p < e; p += SW) {
+      int32_t j = ci[p];
+      acc += v[p] * (s[j] * (X[j] / nrm));
+    }
+  }
+#pragma unroll
+  for (int o = SW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SW);
+  if (valid && sl == 0) w[i] = s[i] * acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -128,23 +121,47 @@ __global__ void k_start_vector(int64_t n, uint32_t tag, uint32_t seed, double* _
   }
 }
 
-// sc[0] = ||w||^2, sc[1] = ||v||^2 -> lam = ||w|| / ||v||, sc[2] = ||w||.
-// A zero product (every row unscaled) gives lam = 0 and leaves v as is.
-__global__ void k_power_scalars(double* __restrict__ sc, double* __restrict__ lam) {
-  double nw = sqrt(sc[0]);
-  if (nw == 0.0 || sc[3] != 0.0) {
-    sc[3] = 1.0;
-    *lam = 0.0;
-    return;
+// partial sums of w.w and v.v with v_j = X_j / sc[2]
+__global__ void k_power_dots(int64_t n, const double* __restrict__ w, const double* __restrict__ X,
+                             const double* __restrict__ sc, double* __restrict__ part) {
+  const double nrm = sc[2];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double vi = X[i] / nrm;
+    acc[0] += w[i] * w[i];
+    acc[1] += vi * vi;
   }
-  *lam = nw / sqrt(sc[1]);
-  sc[2] = nw;
+  block_sum_to<3>(acc, part, RED_BLOCKS);
 }
 
-__global__ void k_div_by(int64_t n, const double* __restrict__ w, const double* __restrict__ sc,
-                         double* __restrict__ v) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && sc[3] == 0.0) v[i] = w[i] / sc[2];
+// one CTA: sums the partials in index order, then lam = ||w|| / ||v|| and
+// sc[2] = ||w|| (the divisor of the next iterate).  A zero product (every
+// row unscaled) gives lam = 0 and stops the iteration (sc[3] = 1).
+__global__ void k_power_finish(const double* __restrict__ part, double* __restrict__ sc, double* __restrict__ lam) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < RED_BLOCKS; t += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) acc[k] += part[(int64_t)k * RED_BLOCKS + t];
+  __shared__ double sh[2][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    double t = warp_sum(acc[k]);
+    if (lane == 0) sh[k][w] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ww = 0.0, vv = 0.0;
+    for (int q = 0; q < nw; ++q) { ww += sh[0][q]; vv += sh[1][q]; }
+    double nw2 = sqrt(ww);
+    if (nw2 == 0.0 || sc[3] != 0.0) {
+      sc[3] = 1.0;
+      *lam = 0.0;
+      return;
+    }
+    *lam = nw2 / sqrt(vv);
+    sc[2] = nw2;
+  }
 }
 
 __global__ void k_rsqrt_scale(int64_t n, const double* __restrict__ d, double* __restrict__ out) {
@@ -199,20 +216,24 @@ int run_power(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const 
   SA_TRY(w.alloc(&al, n));
   SA_TRY(part.alloc(&al, 3 * RED_BLOCKS));
   SA_TRY(sc.alloc(&al, 4));
-  SA_TRY(memset_d(sc.p, 0, 4 * sizeof(double), st));
+  const double init[4] = {0.0, 0.0, 1.0, 0.0};
+  SA_CUDA(cudaMemcpyAsync(sc.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
   int64_t nnz = 0;
   SA_TRY(copy_d2h(&nnz, rp + n, sizeof(int64_t), st));
-  const int sw = pick_sw(n, nnz);
+  const double avg = (double)nnz / (double)n;
+  const int sw = avg <= 40.0 ? 4 : (avg <= 96.0 ? 8 : 16);
   k_start_vector<<<blocks_for(n, 256), 256, 0, st>>>(n, tag, seed, x.p);
   SA_LAUNCHED();
+  double* X = x.p;  // previous product (the start vector at first)
+  double* W = w.p;
   for (int it = 0; it < steps; ++it) {
-    DISPATCH_SW(sw, k_power_spmv, n, n, rp, ci, v, s, x.p, w.p);
+    DISPATCH_SW(sw, k_power_spmv, n, n, rp, ci, v, s, X, sc.p, W);
     SA_LAUNCHED();
-    SA_TRY(launch_dots(st, n, w.p, w.p, x.p, x.p, nullptr, nullptr, part.p, sc.p));
-    k_power_scalars<<<1, 1, 0, st>>>(sc.p, lam_dev);
+    k_power_dots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, W, X, sc.p, part.p);
     SA_LAUNCHED();
-    k_div_by<<<blocks_for(n, 256), 256, 0, st>>>(n, w.p, sc.p, x.p);
+    k_power_finish<<<1, 1024, 0, st>>>(part.p, sc.p, lam_dev);
     SA_LAUNCHED();
+    double* t = X; X = W; W = t;
   }
   return SA_OK;
 }

@@ -100,6 +100,57 @@ template int build_sell<double>(Alloc&, int64_t, int64_t, const int64_t*, const 
 template int build_sell<float>(Alloc&, int64_t, int64_t, const int64_t*, const int32_t*, const double*,
                                const double*, int, const double*, int, Sell<float>&);
 
+// CSR copy with scaled values
+template <typename T>
+__global__ void k_csr_scale(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, const double* __restrict__ left,
+                            const double* __restrict__ right, int left_sqrt, int right_sqrt, T* __restrict__ ov) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double li = 1.0;
+  if (left) li = left_sqrt ? sqrt(left[i]) : 1.0 / sqrt(left[i]);
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    double rj = 1.0;
+    if (right) rj = right_sqrt ? sqrt(right[ci[p]]) : 1.0 / sqrt(right[ci[p]]);
+    ov[p] = (T)(li * v[p] * rj);
+  }
+}
+
+// SELL-32 if it stores at most 25 % padding and rows average <= 40 entries,
+// else CSR with 4..32 lanes per row by average row length
+template <typename T>
+int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
+              const double* left, int left_sqrt, const double* right, int right_sqrt, Mat<T>& M) {
+  cudaStream_t s = al.stream;
+  M.n = n;
+  M.nnz = nnz;
+  M.nslices = (n + 31) / 32;
+  const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+  int64_t stored = 0;
+  if (n > 0) {
+    Buf<int64_t> sz;
+    SA_TRY(sz.alloc(&al, M.nslices + 1));
+    SA_TRY(memset_d(sz.p, 0, sz.bytes(), s));
+    k_slice_width<<<blocks_for(M.nslices, 256), 256, 0, s>>>(n, rp, sz.p);
+    SA_LAUNCHED();
+    SA_TRY(scan_inplace(al, sz.p + 1, M.nslices));
+    SA_TRY(copy_d2h(&stored, sz.p + M.nslices, sizeof(int64_t), s));
+  }
+  if (n == 0 || ((double)stored <= 1.25 * (double)nnz && avg <= 40.0)) {
+    M.sw = 0;
+    return build_sell<T>(al, n, nnz, rp, ci, v, left, left_sqrt, right, right_sqrt, M.sell);
+  }
+  M.sw = avg <= 12.0 ? 4 : (avg <= 40.0 ? 8 : (avg <= 96.0 ? 16 : 32));
+  SA_TRY(M.rp.alloc(&al, n + 1));
+  SA_TRY(M.ci.alloc(&al, nnz));
+  SA_TRY(M.v.alloc(&al, nnz));
+  SA_CUDA(cudaMemcpyAsync(M.rp.p, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+  if (nnz > 0) SA_CUDA(cudaMemcpyAsync(M.ci.p, ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s));
+  k_csr_scale<T><<<blocks_for(n, 256), 256, 0, s>>>(n, rp, ci, v, left, right, left_sqrt, right_sqrt, M.v.p);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
 template <typename T>
 int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const double* W, const double* WT,
              VHier<T>** out) {
@@ -123,10 +174,10 @@ int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const dou
     SA_TRY(L->r.alloc(&al, I.n));
     SA_TRY(L->d.alloc(&al, I.n));
     if (l + 1 < nlev) {
-      SA_TRY(build_sell<T>(al, I.n, I.nnz, I.rp, I.ci, I.v, I.diag, 0, I.diag, 0, L->A));
+      SA_TRY(build_mat<T>(al, I.n, I.nnz, I.rp, I.ci, I.v, I.diag, 0, I.diag, 0, L->A));
       const double* dc = in[l + 1].diag;
-      SA_TRY(build_sell<T>(al, I.n, I.nnzP, I.Prp, I.Pci, I.Pv, I.diag, 1, dc, 0, L->P));
-      SA_TRY(build_sell<T>(al, I.nc, I.nnzP, I.Rrp, I.Rci, I.Rv, dc, 0, I.diag, 1, L->R));
+      SA_TRY(build_mat<T>(al, I.n, I.nnzP, I.Prp, I.Pci, I.Pv, I.diag, 1, dc, 0, L->P));
+      SA_TRY(build_mat<T>(al, I.nc, I.nnzP, I.Rrp, I.Rci, I.Rv, dc, 0, I.diag, 1, L->R));
     } else {
       SA_TRY(L->sq.alloc(&al, I.n));
       k_sqrt_vec<<<blocks_for(I.n, 256), 256, 0, s>>>(I.n, I.diag, L->sq.p, 0);
@@ -160,17 +211,95 @@ __device__ __forceinline__ T sell_row(const int64_t* __restrict__ sp, const int3
   return acc;
 }
 
-// x_out = x_in + d,  d = first ? c2 r : c1 d + c2 r,  r = b - A~ x_in
 template <typename T>
-__global__ void k_vc_cheb(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
-                          const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ xin,
-                          T* __restrict__ xout, T* __restrict__ d, T c1, T c2, int first) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  T r = b[i] - sell_row<T>(sp, ci, v, xin, i);
+struct MatView {
+  int64_t n;
+  const int64_t* p;  // SELL slice offsets or CSR row pointers
+  const int32_t* ci;
+  const T* v;
+};
+
+template <typename T>
+static MatView<T> view(const Mat<T>& M) {
+  MatView<T> m;
+  m.n = M.n;
+  if (M.sw == 0) { m.p = M.sell.sp.p; m.ci = M.sell.ci.p; m.v = M.sell.v.p; }
+  else { m.p = M.rp.p; m.ci = M.ci.p; m.v = M.v.p; }
+  return m;
+}
+
+// the row product of this thread's row; SW = 0: SELL-32, one thread per row;
+// SW > 0: CSR, SW lanes per row, reduced by shuffles (every lane of the warp
+// reaches the shuffles).  Returns true for the thread that owns the row.
+template <typename T, int SW>
+__device__ __forceinline__ bool row_apply(const MatView<T>& M, const T* __restrict__ x, T& out, int64_t& row) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (SW == 0) {
+    row = gt;
+    if (gt >= M.n) return false;
+    out = sell_row<T>(M.p, M.ci, M.v, x, gt);
+    return true;
+  } else {
+    const int64_t i = gt / SW;
+    const int sl = (int)(gt % SW);
+    row = i;
+    T acc = (T)0;
+    if (i < M.n) {
+      const int64_t e = M.p[i + 1];
+      for (int64_t q = M.p[i] + sl; q < e; q += SW) acc += M.v[q] * __ldg(&x[M.ci[q]]);
+    }
+#pragma unroll
+    for (int o = SW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SW);
+    out = acc;
+    return i < M.n && sl == 0;
+  }
+}
+
+// x_out = x_in + d,  d = first ? c2 r : c1 d + c2 r,  r = b - A~ x_in
+template <typename T, int SW>
+__global__ void k_vc_cheb(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+                          T* __restrict__ d, T c1, T c2, int first) {
+  T y;
+  int64_t i;
+  if (!row_apply<T, SW>(A, xin, y, i)) return;
+  T r = b[i] - y;
   T dn = first ? c2 * r : c1 * d[i] + c2 * r;
   d[i] = dn;
   xout[i] = xin[i] + dn;
+}
+
+template <typename T, int SW>
+__global__ void k_vc_residual(MatView<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
+  T y;
+  int64_t i;
+  if (row_apply<T, SW>(A, x, y, i)) r[i] = b[i] - y;
+}
+
+template <typename T, int SW>
+__global__ void k_vc_spmv(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
+  T y;
+  int64_t i;
+  if (row_apply<T, SW>(A, x, y, i)) out[i] = y;
+}
+
+template <typename T, int SW>
+__global__ void k_vc_spmv_add(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
+  T y;
+  int64_t i;
+  if (row_apply<T, SW>(A, x, y, i)) out[i] += y;
+}
+
+// fine exit: the last post-smoothing step writes z = D^-1/2 x~ in FP64
+template <typename T, int SW>
+__global__ void k_vc_cheb_out(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin,
+                              const T* __restrict__ d, T c1, T c2, int first, const double* __restrict__ s,
+                              double* __restrict__ z) {
+  T y;
+  int64_t i;
+  if (!row_apply<T, SW>(A, xin, y, i)) return;
+  T r = b[i] - y;
+  T dn = first ? c2 * r : c1 * d[i] + c2 * r;
+  z[i] = s[i] * (double)(xin[i] + dn);
 }
 
 template <typename T>
@@ -197,40 +326,20 @@ __global__ void k_vc_fine_in(int64_t n, const double* __restrict__ r, const doub
   }
 }
 
-template <typename T>
-__global__ void k_vc_residual(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
-                              const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ x,
-                              T* __restrict__ r) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) r[i] = b[i] - sell_row<T>(sp, ci, v, x, i);
-}
-
-template <typename T>
-__global__ void k_vc_spmv(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
-                          const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = sell_row<T>(sp, ci, v, x, i);
-}
-
-template <typename T>
-__global__ void k_vc_spmv_add(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
-                              const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] += sell_row<T>(sp, ci, v, x, i);
-}
-
-// fine exit: the last post-smoothing step writes z = D^-1/2 x~ in FP64
-template <typename T>
-__global__ void k_vc_cheb_out(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
-                              const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ xin,
-                              const T* __restrict__ d, T c1, T c2, int first, const double* __restrict__ s,
-                              double* __restrict__ z) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  T r = b[i] - sell_row<T>(sp, ci, v, xin, i);
-  T dn = first ? c2 * r : c1 * d[i] + c2 * r;
-  z[i] = s[i] * (double)(xin[i] + dn);
-}
+// launch `K<T, sw>` over the rows of M (SELL: one thread per row; CSR: sw lanes)
+#define LAUNCH_MAT(K, M, st, ...)                                                        \
+  do {                                                                                   \
+    const MatView<T> _mv = view(M);                                                      \
+    const int64_t _thr = (M).sw == 0 ? (M).n : (M).n * (int64_t)(M).sw;                  \
+    const unsigned _g = blocks_for(_thr, 256);                                           \
+    switch ((M).sw) {                                                                    \
+      case 0: K<T, 0><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
+      case 4: K<T, 4><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
+      case 8: K<T, 8><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
+      case 16: K<T, 16><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                    \
+      default: K<T, 32><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                    \
+    }                                                                                    \
+  } while (0)
 
 template <typename T>
 __global__ void k_coarse_in(int64_t n, const T* __restrict__ b, const double* __restrict__ sq,
@@ -254,9 +363,13 @@ static inline unsigned g256(int64_t n) { return blocks_for(n, 256); }
 // algorithmic bytes: S-byte value + int32 column per stored entry of the
 // unpadded matrix, 8-byte slice offsets, each vector element once
 template <typename T>
+static double b_ptr(const Mat<T>& M) {  // row-pointer or slice-offset bytes
+  return M.sw == 0 ? 8.0 * (M.nslices + 1) : 8.0 * (M.n + 1);
+}
+template <typename T>
 static double b_cheb(const VLevel<T>* L) {
   const double S = sizeof(T);
-  return (S + 4.0) * L->A.nnz + 8.0 * (L->A.nslices + 1) + 5.0 * S * L->n;
+  return (S + 4.0) * L->A.nnz + b_ptr(L->A) + 5.0 * S * L->n;
 }
 
 #define PROFK(kind, level, bytes, launch)               \
@@ -293,7 +406,7 @@ static int mv(VHier<T>* m, cudaStream_t st, int l, const double* r64, T** xo) {
   const double s1 = th / de;
   T* xa = L->x.p;
   T* xb = L->x2.p;
-  const Sell<T>& A = L->A;
+  const Mat<T>& A = L->A;
   if (l == 0) {
     PROFK(K_FST, l, 16.0 * n + 3.0 * S * n,
           (k_vc_fine_in<T><<<g256(n), 256, 0, st>>>(n, r64, m->s0.p, (T)(1.0 / th), L->b.p, xa, L->d.p)));
@@ -304,20 +417,18 @@ static int mv(VHier<T>* m, cudaStream_t st, int l, const double* r64, T** xo) {
   for (int k = 1; k < deg; ++k) {
     double rn = 1.0 / (2.0 * s1 - rho);
     PROFK(K_CHEB, l, b_cheb(L),
-          (k_vc_cheb<T><<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, xb, L->d.p, (T)(rn * rho),
-                                                 (T)(2.0 * rn / de), 0)));
+          LAUNCH_MAT(k_vc_cheb, A, st, L->b.p, xa, xb, L->d.p, (T)(rn * rho), (T)(2.0 * rn / de), 0));
     T* t = xa; xa = xb; xb = t;
     rho = rn;
   }
   VLevel<T>* C = m->lev[l + 1];
-  PROFK(K_RES, l, (S + 4.0) * A.nnz + 8.0 * (A.nslices + 1) + 3.0 * S * n,
-        (k_vc_residual<T><<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, L->r.p)));
-  PROFK(K_RST, l, (S + 4.0) * L->R.nnz + 8.0 * (L->R.nslices + 1) + S * n + S * C->n,
-        (k_vc_spmv<T><<<g256(C->n), 256, 0, st>>>(C->n, L->R.sp.p, L->R.ci.p, L->R.v.p, L->r.p, C->b.p)));
+  PROFK(K_RES, l, (S + 4.0) * A.nnz + b_ptr(A) + 3.0 * S * n, LAUNCH_MAT(k_vc_residual, A, st, L->b.p, xa, L->r.p));
+  PROFK(K_RST, l, (S + 4.0) * L->R.nnz + b_ptr(L->R) + S * n + S * C->n,
+        LAUNCH_MAT(k_vc_spmv, L->R, st, L->r.p, C->b.p));
   T* xc = nullptr;
   SA_TRY(mv(m, st, l + 1, nullptr, &xc));
-  PROFK(K_PRL, l, (S + 4.0) * L->P.nnz + 8.0 * (L->P.nslices + 1) + S * C->n + 2.0 * S * n,
-        (k_vc_spmv_add<T><<<g256(n), 256, 0, st>>>(n, L->P.sp.p, L->P.ci.p, L->P.v.p, xc, xa)));
+  PROFK(K_PRL, l, (S + 4.0) * L->P.nnz + b_ptr(L->P) + S * C->n + 2.0 * S * n,
+        LAUNCH_MAT(k_vc_spmv_add, L->P, st, xc, xa));
   rho = 1.0 / s1;
   for (int k = 0; k < deg; ++k) {
     int first = (k == 0);
@@ -330,12 +441,9 @@ static int mv(VHier<T>* m, cudaStream_t st, int l, const double* r64, T** xo) {
     }
     if (l == 0 && k == deg - 1) {
       PROFK(K_CHEB, l, b_cheb(L) + 16.0 * n - S * n,
-            (k_vc_cheb_out<T><<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, L->d.p, c1, c2, first,
-                                                       m->s0.p, m->z.p)));
+            LAUNCH_MAT(k_vc_cheb_out, A, st, L->b.p, xa, L->d.p, c1, c2, first, m->s0.p, m->z.p));
     } else {
-      PROFK(K_CHEB, l, b_cheb(L),
-            (k_vc_cheb<T><<<g256(n), 256, 0, st>>>(n, A.sp.p, A.ci.p, A.v.p, L->b.p, xa, xb, L->d.p, c1, c2,
-                                                   first)));
+      PROFK(K_CHEB, l, b_cheb(L), LAUNCH_MAT(k_vc_cheb, A, st, L->b.p, xa, xb, L->d.p, c1, c2, first));
       T* t = xa; xa = xb; xb = t;
     }
     if (!first) rho = rn;

@@ -33,11 +33,23 @@ struct VLevelIn {
   const double* Rv = nullptr;
 };
 
+// a V-cycle matrix: SELL-32 (thread per row) when rows are short and padding
+// small, else CSR with sw lanes per row; values scaled and stored in T
+template <typename T>
+struct Mat {
+  int sw = 0;  // 0: SELL-32; 4/8/16/32: CSR lanes per row
+  int64_t n = 0, nnz = 0, nslices = 0;
+  Sell<T> sell;
+  Buf<int64_t> rp;
+  Buf<int32_t> ci;
+  Buf<T> v;
+};
+
 template <typename T>
 struct VLevel {
   int64_t n = 0, nc = 0;
   double lmax = 0, lmin = 0;
-  Sell<T> A, P, R;
+  Mat<T> A, P, R;
   Buf<T> b, x, x2, r, d;
   Buf<double> sq;  // sqrt(diag) on the coarsest level
 };
