@@ -25,6 +25,7 @@ _L = None
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_SPD, ERR_STAGNATION, ERR_NO_CONVERGENCE, ERR_BREAKDOWN = (
     0, -1, -2, -4, -5, -6, -7)
 MEASURES = {"classical": 0, "material": 1, "distance": 2}
+DROPS = {"pointwise": 0, "cut": 1}
 
 
 def build(force: bool = False) -> str:
@@ -39,7 +40,8 @@ def build(force: bool = False) -> str:
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("theta", ctypes.c_double), ("measure", ctypes.c_int), ("max_coarse", ctypes.c_int),
+    _fields_ = [("theta", ctypes.c_double), ("measure", ctypes.c_int), ("drop", ctypes.c_int),
+                ("max_coarse", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("power_iters", ctypes.c_int),
                 ("omega_sym", ctypes.c_double), ("cheb_boost", ctypes.c_double),
                 ("cheb_ratio", ctypes.c_double), ("seed", ctypes.c_uint32)]
@@ -59,6 +61,9 @@ def lib():
             "or_invert_tensors": (None, [I32, I64, P, P]),
             "or_strength_classical": (None, [I64, P, P, P, P, D, P]),
             "or_strength_material": (None, [I32, I64, P, P, P, P, P, D, P, P, P]),
+            "or_cut_drop": (None, [I64, P, P, P, P, D, P]),
+            "or_strength2_classical": (None, [I64, P, P, P, P]),
+            "or_strength2_material": (None, [I64, P, P, P, P, P]),
             "or_filtered_graph": (I64, [I64, P, P, P, P, P, P]),
             "or_mis2": (None, [I64, P, P, P, I32, U32, P]),
             "or_aggregate": (I64, [I64, P, P, P, P, P]),
@@ -172,6 +177,26 @@ def strength_material(dim, n, rp, ci, dirm, coords, sinv, theta):
     return w, D, keep
 
 
+def strength2_classical(n, rp, ci, v):
+    s2 = np.zeros(len(ci))
+    lib().or_strength2_classical(n, _p(_c(rp, np.int64)), _p(_c(ci, np.int32)), _p(_c(v, np.float64)), _p(s2))
+    return s2
+
+
+def strength2_material(n, rp, ci, w, D):
+    s2 = np.zeros(len(ci))
+    lib().or_strength2_material(n, _p(_c(rp, np.int64)), _p(_c(ci, np.int32)), _p(_c(w, np.float64)),
+                                _p(_c(D, np.float64)), _p(s2))
+    return s2
+
+
+def cut_drop(n, rp, ci, dirm, s2, theta):
+    keep = np.zeros(len(ci), np.uint8)
+    lib().or_cut_drop(n, _p(_c(rp, np.int64)), _p(_c(ci, np.int32)), _p(None if dirm is None else _c(dirm, np.uint8)),
+                      _p(_c(s2, np.float64)), float(theta), _p(keep))
+    return keep
+
+
 def filtered_graph(n, rp, ci, keep, dirm):
     grp = np.zeros(n + 1, np.int64)
     gci = np.zeros(max(len(ci), 1), np.int32)
@@ -275,11 +300,11 @@ class Hierarchy:
     """Oracle hierarchy built by or_setup; levels exported as numpy dicts."""
 
     def __init__(self, problem, theta, measure="material", max_coarse=5000, max_levels=10, seed=0,
-                 power_iters=10, omega_sym=4.0 / 3.0, cheb_boost=1.1, cheb_ratio=30.0):
+                 power_iters=10, omega_sym=4.0 / 3.0, cheb_boost=1.1, cheb_ratio=30.0, drop="pointwise"):
         L = lib()
         self.dim = int(problem["dim"])
         self.n = int(problem["n"])
-        o = _Opts(theta=float(theta), measure=MEASURES[measure], max_coarse=int(max_coarse),
+        o = _Opts(theta=float(theta), measure=MEASURES[measure], drop=DROPS[drop], max_coarse=int(max_coarse),
                   max_levels=int(max_levels), power_iters=int(power_iters), omega_sym=float(omega_sym),
                   cheb_boost=float(cheb_boost), cheb_ratio=float(cheb_ratio), seed=int(seed))
         self._keep = [_c(problem["row_ptr"], np.int64), _c(problem["col"], np.int32),

@@ -32,6 +32,8 @@
  *   - d_sigma(x,y) = max(d~(x,y), d~(y,x)): the printed max has two identical
  *     arguments; the low/high argument of Sec. 3 needs both nodes' tensors.
  *   - "A_ij != 0" in L_d means a stored entry of the structural pattern.
+ *   - cut-drop: no gap in a row keeps the whole row; row decisions are
+ *     symmetrised by keeping an edge only when both rows keep it.
  *   - pointwise dropping keeps |S_ij| >= theta; the diagonal is always kept
  *     and never enters the filtered graph; Dirichlet nodes never enter it.
  *   - the squared forms a_ij^2 >= theta^2 |a_ii a_jj| and
@@ -256,6 +258,80 @@ void or_strength_material(int dim, int64_t n, const int64_t* rp, const int32_t* 
       if (j == i) { keep[p] = 1; continue; }
       if (dir && (dir[i] || dir[j])) { keep[p] = 0; continue; }
       keep[p] = (uint8_t)(w[p] * w[p] >= t2 * (D[i] * D[j]));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cut-drop criterion (Sec. 2.1, Eq. C^cut-drop) on squared strengths s2[p]
+ * (off-diagonal entries; the diagonal and Dirichlet-incident entries are
+ * ignored and never kept).  Per row: order the values descending,
+ * s_1 >= s_2 >= ... >= s_m; k is the smallest index with
+ * theta * s_k >= s_{k+1} (in squares: theta^2 s2_k >= s2_{k+1}); keep the
+ * entries with s >= s_k.  Readings: if no such k exists every entry is kept;
+ * the row-wise decisions are symmetrised by keeping an edge only when both
+ * of its rows keep it (the filtered graph must be symmetric). */
+/* ------------------------------------------------------------------------ */
+static int cmp_dbl_desc(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x < y) - (x > y);
+}
+
+void or_cut_drop(int64_t n, const int64_t* rp, const int32_t* ci, const uint8_t* dir, const double* s2,
+                 double theta, uint8_t* keep) {
+  const double t2 = theta * theta;
+  int64_t maxrow = 0;
+  for (int64_t i = 0; i < n; ++i) if (rp[i + 1] - rp[i] > maxrow) maxrow = rp[i + 1] - rp[i];
+  double* vals = (double*)malloc(sizeof(double) * (size_t)(maxrow > 0 ? maxrow : 1));
+  uint8_t* rowkeep = (uint8_t*)calloc((size_t)(rp[n] > 0 ? rp[n] : 1), 1);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t m = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t j = ci[p];
+      if (j == i || (dir && (dir[i] || dir[j]))) continue;
+      vals[m++] = s2[p];
+    }
+    if (m == 0) continue;
+    qsort(vals, (size_t)m, sizeof(double), cmp_dbl_desc);
+    double thr = vals[m - 1];
+    for (int64_t k = 0; k + 1 < m; ++k)
+      if (t2 * vals[k] >= vals[k + 1]) { thr = vals[k]; break; }
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t j = ci[p];
+      if (j == i || (dir && (dir[i] || dir[j]))) continue;
+      rowkeep[p] = (uint8_t)(s2[p] >= thr);
+    }
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t j = ci[p];
+      if (j == i) { keep[p] = 1; continue; }
+      int64_t q = -1;
+      for (int64_t r = rp[j]; r < rp[j + 1]; ++r) if (ci[r] == i) { q = r; break; }
+      keep[p] = (uint8_t)(rowkeep[p] && q >= 0 && rowkeep[q]);
+    }
+  free(vals);
+  free(rowkeep);
+}
+
+/* squared strengths for cut-drop: classical a_ij^2 / |a_ii a_jj|, material
+ * (or distance) w_ij^2 / (D_i D_j) */
+void or_strength2_classical(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, double* s2) {
+  double* dg = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) dg[i] = diag_of(rp, ci, v, i);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t j = ci[p];
+      s2[p] = (j == i) ? 0.0 : (v[p] * v[p]) / fabs(dg[i] * dg[j]);
+    }
+  free(dg);
+}
+
+void or_strength2_material(int64_t n, const int64_t* rp, const int32_t* ci, const double* w, const double* D,
+                           double* s2) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t j = ci[p];
+      s2[p] = (j == i) ? 0.0 : (w[p] * w[p]) / (D[i] * D[j]);
     }
 }
 
@@ -639,6 +715,7 @@ typedef struct {
 typedef struct {
   double theta;
   int measure;      /* 0 classical, 1 material, 2 distance Laplacian (sigma = I) */
+  int drop;         /* 0 pointwise, 1 cut-drop */
   int max_coarse, max_levels;
   int power_iters;
   double omega_sym;
@@ -749,14 +826,21 @@ or_hier_t* or_setup(int dim, int64_t n, const int64_t* rp, const int32_t* ci, co
     if (nl <= o->max_coarse || l + 1 >= o->max_levels) break;
     int64_t nnz = csr_nnz(&Lc->A);
     Lc->keep = (uint8_t*)malloc((size_t)(nnz > 0 ? nnz : 1));
+    double* s2 = o->drop ? (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1)) : NULL;
     if (o->measure == 0) {
       or_strength_classical(nl, Lc->A.rp, Lc->A.ci, Lc->A.v, Lc->dir, o->theta, Lc->keep);
+      if (o->drop) or_strength2_classical(nl, Lc->A.rp, Lc->A.ci, Lc->A.v, s2);
     } else {
       double* w = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
       double* D = (double*)malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1));
       or_strength_material(dim, nl, Lc->A.rp, Lc->A.ci, Lc->dir, Lc->x, Lc->sinv, o->theta, w, D,
                            Lc->keep);
+      if (o->drop) or_strength2_material(nl, Lc->A.rp, Lc->A.ci, w, D, s2);
       free(w); free(D);
+    }
+    if (o->drop) {
+      or_cut_drop(nl, Lc->A.rp, Lc->A.ci, Lc->dir, s2, o->theta, Lc->keep);
+      free(s2);
     }
     int64_t* gc_rp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nl + 1));
     int32_t* gc_ci = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));

@@ -494,3 +494,137 @@ def test_two_domain_material_robust_in_kappa(orc, gen_mod):
     assert it[("material", 1e4)] <= 1.5 * it[("material", 1.0)]
     assert it[("classical", 1e4)] >= 2 * it[("classical", 1.0)]
     assert it[("material", 1e4)] < it[("classical", 1e4)]
+
+
+# ---------------------------------------------------------------------------
+# cut-drop criterion (Sec. 2.1, Eq. C^cut-drop)
+# ---------------------------------------------------------------------------
+def _row_csr(vals_per_row):
+    """a symmetric pattern is not needed for the row-wise part: build a
+    'star' graph where row 0 holds the given values and every other row
+    mirrors its single edge with the same value"""
+    m = len(vals_per_row)
+    n = m + 1
+    rp = [0]
+    ci, s2 = [], []
+    ci += list(range(n)); s2 += [0.0] + [v * v for v in vals_per_row]
+    rp.append(len(ci))
+    for j in range(1, n):
+        ci += [0, j]; s2 += [vals_per_row[j - 1] ** 2, 0.0]
+        rp.append(len(ci))
+    return n, np.array(rp, np.int64), np.array(ci, np.int32), np.array(s2)
+
+
+@pytest.mark.parametrize("vals,theta,kept", [
+    ([1.0, 0.9, 0.05, 0.04], 0.1, [1, 1, 0, 0]),      # first gap after 0.9 (0.09 >= 0.05)
+    ([1.0, 0.05, 0.04, 0.039], 0.1, [1, 0, 0, 0]),    # gap right after the largest
+    ([1.0, 0.5, 0.25, 0.125], 0.1, [1, 1, 1, 1]),     # no gap: every entry kept
+    ([0.3, 1.0, 0.3, 0.001], 0.1, [1, 1, 1, 0]),      # ties kept together, order-independent
+])
+def test_cut_drop_definition_examples(orc, vals, theta, kept):
+    n, rp, ci, s2 = _row_csr(vals)
+    keep = orc.cut_drop(n, rp, ci, None, s2, theta)
+    row0 = keep[rp[0]:rp[1]]
+    assert row0[0] == 1 and list(row0[1:]) == kept
+
+
+def test_cut_drop_worked_example(orc, gen_mod):
+    # nodes 12 and 13 keep their in-region edges and cut the interface edges
+    # at kappa = 1e4, theta = 0.08 (first gap: 0.08 * 0.102 >= 0.00204)
+    p = gen_mod.worked_example(kappa=1e4)
+    sinv = orc.invert_tensors(2, p["tensors"])
+    w, D, _ = orc.strength_material(2, p["n"], p["row_ptr"], p["col"], None, p["coords"], sinv, 0.0)
+    s2 = orc.strength2_material(p["n"], p["row_ptr"], p["col"], w, D)
+    keep = orc.cut_drop(p["n"], p["row_ptr"], p["col"], None, s2, 0.08)
+    for node, low in ((12, True), (13, False)):
+        i = node - 1
+        for q in range(p["row_ptr"][i], p["row_ptr"][i + 1]):
+            j = p["col"][q]
+            if j == i:
+                continue
+            same_side = (p["coords"][2 * j] <= 1.0) == low
+            assert keep[q] == (1 if same_side else 0), (node, j)
+
+
+def _cut_drop_brute(n, rp, ci, s2, theta):
+    rowkeep = np.zeros(len(ci), bool)
+    for i in range(n):
+        idx = [q for q in range(rp[i], rp[i + 1]) if ci[q] != i]
+        if not idx:
+            continue
+        s = np.sqrt(np.array([s2[q] for q in idx]))
+        order = np.argsort(-s, kind="stable")
+        srt = s[order]
+        khat = len(srt) - 1
+        for k in range(len(srt) - 1):
+            if theta * srt[k] >= srt[k + 1] * (1 + 1e-12):
+                khat = k
+                break
+        for q, v in zip(idx, s):
+            rowkeep[q] = v >= srt[khat] * (1 - 1e-12)
+    keep = np.zeros(len(ci), np.uint8)
+    for i in range(n):
+        for q in range(rp[i], rp[i + 1]):
+            j = ci[q]
+            if j == i:
+                keep[q] = 1
+                continue
+            back = [r for r in range(rp[j], rp[j + 1]) if ci[r] == i]
+            keep[q] = int(rowkeep[q] and back and rowkeep[back[0]])
+    return keep
+
+
+@pytest.mark.parametrize("measure", ["classical", "material"])
+def test_cut_drop_brute_force_and_symmetry(orc, gen_mod, measure):
+    p = gen_mod.voronoi_3d(5, nseeds=4, seed=8)
+    n, rp, ci, v = p["n"], p["row_ptr"], p["col"], p["val"]
+    if measure == "classical":
+        s2 = orc.strength2_classical(n, rp, ci, v)
+    else:
+        sig = orc.nodal_from_elements(3, n, p["elem_nodes"], p["elem_measure"], p["tensors"])
+        w, D, _ = orc.strength_material(3, n, rp, ci, None, p["coords"], orc.invert_tensors(3, sig), 0.0)
+        s2 = orc.strength2_material(n, rp, ci, w, D)
+    for theta in (0.02, 0.08, 0.3):
+        keep = orc.cut_drop(n, rp, ci, None, s2, theta)
+        assert np.array_equal(keep, _cut_drop_brute(n, rp, ci, s2, theta))
+        K = sp.csr_matrix((keep.astype(float), ci, rp), shape=(n, n))
+        assert (K != K.T).nnz == 0
+
+
+def test_cut_drop_hierarchy_converges(orc, gen_mod):
+    p = gen_mod.two_domain(32, 1e4)
+    h = orc.Hierarchy(p, 0.08, "material", max_coarse=64, drop="cut")
+    _, info = h.solve(p["b"])
+    assert info["status"] == 0 and info["iters"] < 40
+
+
+# ---------------------------------------------------------------------------
+# conditioning of the level chain: a one-ulp symmetric perturbation of the
+# fine matrix moves the oracle's deeper levels by far more than one ulp; the
+# chained GPU-vs-oracle bar (1e-12 * 4^l) must cover this inherent spread
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("drop,theta", [("cut", 0.08), ("pointwise", 0.05)])
+def test_chain_sensitivity(orc, gen_mod, drop, theta):
+    from _tol import chain_tol
+    p = gen_mod.battery_3d(16, 16, 32)
+    A = csr(p)
+    U = sp.triu(A, 1).tocoo()
+    sgn = np.where(np.arange(U.nnz) % 3 == 0, 1.0, -1.0)
+    U = sp.coo_matrix((U.data * (1 + sgn * 2.0 ** -52), (U.row, U.col)), shape=A.shape)
+    A2 = (sp.triu(U, 1) + sp.triu(U, 1).T + sp.diags(A.diagonal())).tocsr()
+    A2.sort_indices()
+    assert np.array_equal(A2.indices, p["col"])
+    o = orc.Hierarchy(p, theta, "material", max_coarse=200, drop=drop)
+    o2 = orc.Hierarchy(dict(p, val=A2.data.copy()), theta, "material", max_coarse=200, drop=drop)
+    assert o.nlev == o2.nlev
+    spread = 0.0
+    for l in range(o.nlev - 1):
+        r, r2 = o.level(l), o2.level(l)
+        assert np.array_equal(r["agg"], r2["agg"]) and np.array_equal(r["P_ci"], r2["P_ci"])
+        rows = np.repeat(np.arange(r["n"]), np.diff(r["P_rp"]))
+        sc = np.zeros(r["n"])
+        np.maximum.at(sc, rows, np.abs(r["P_v"]))
+        e = float((np.abs(r["P_v"] - r2["P_v"]) / np.maximum(sc[rows], 1e-300)).max())
+        spread = max(spread, e)
+        assert e <= chain_tol(l) / 10, (l, e)   # a tenth of the bar: GPU sums differ in more than one ulp
+    assert spread > 1e-14   # the chain does amplify last-bit differences
