@@ -53,6 +53,11 @@ def _lib():
         L.q1_voronoi_regions.argtypes = [ctypes.c_int] * 4 + [P, P]
         L.q1_mark_sphere.restype = ctypes.c_int64
         L.q1_mark_sphere.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 4 + [P]
+        L.q1_annulus_nnz.restype = ctypes.c_int64
+        L.q1_annulus_nnz.argtypes = [ctypes.c_int] * 3
+        L.q1_assemble_annulus.restype = ctypes.c_int64
+        L.q1_assemble_annulus.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [P, P] +
+                                          [ctypes.c_double] * 2 + [P] * 8)
         _lib_handle = L
     return _lib_handle
 
@@ -333,11 +338,77 @@ def serving_requests(n_requests=512, seed=0, max2d=512, max3d=96, min_el=16):
     return ops, reqs
 
 
+def annulus_tensors(coords, elem_nodes, kappa):
+    """Per element K = Q^T diag(kappa, 1, 1) Q at the element centroid, with
+    Q's rows the circumferential unit vector (-y, x, 0)/r, the radial unit
+    vector (x, y, 0)/r and e_z: conductivity kappa along the circle, 1 across
+    it.  Packed (xx, yy, zz, xy, xz, yz)."""
+    X = coords.reshape(-1, 3)[elem_nodes.reshape(-1, 8)].mean(axis=1)
+    r = np.hypot(X[:, 0], X[:, 1])
+    tx, ty = -X[:, 1] / r, X[:, 0] / r
+    rx, ry = X[:, 0] / r, X[:, 1] / r
+    K = np.zeros((X.shape[0], 6))
+    K[:, 0] = kappa * tx * tx + rx * rx
+    K[:, 1] = kappa * ty * ty + ry * ry
+    K[:, 2] = 1.0
+    K[:, 3] = kappa * tx * ty + rx * ry
+    return K
+
+
+def annulus_3d(refine=0, kappa=100.0, ri=0.5, ro=1.0, t=0.1, base=(20, 150, 1), g_in=0.0, g_out=1.0,
+               load=True, seed=0):
+    """Thick annulus r_i <= r <= r_o, 0 <= z <= t, meshed with
+    base * 2^refine trilinear hexahedra (radial, circumferential, thickness),
+    conductivity kappa along the circumference and 1 radially and through
+    the thickness; Dirichlet u = g_in on the inner and u = g_out on the outer
+    cylinder, natural conditions on the two flat faces.  With `load`, a
+    seeded element load f ~ U(0,1) (so that the right-hand side is not
+    rotation invariant); without it f = 0 and the exact solution of the
+    continuous problem is ln(r/r_i)/ln(r_o/r_i) scaled to g_in..g_out."""
+    L = _lib()
+    m = 1 << int(refine)
+    nr, nt, nz = base[0] * m, base[1] * m, base[2] * m
+    n = (nr + 1) * nt * (nz + 1)
+    ne = nr * nt * nz
+    nnz_max = L.q1_annulus_nnz(nr, nt, nz)
+    row_ptr = np.empty(n + 1, np.int64)
+    col = np.empty(nnz_max, np.int32)
+    val = np.empty(nnz_max, np.float64)
+    b = np.empty(n, np.float64)
+    coords = np.empty(3 * n, np.float64)
+    elem_nodes = np.empty(8 * ne, np.int32)
+    elem_measure = np.empty(ne, np.float64)
+    dmask = np.empty(n, np.uint8)
+    # the element tensors depend only on the (closed-form) node coordinates
+    a = np.arange(nr + 1)
+    bq = np.arange(nt)
+    c = np.arange(nz + 1)
+    C, B, A = np.meshgrid(c, bq, a, indexing="ij")
+    rad = ri + (ro - ri) * A.ravel() / nr
+    phi = 2.0 * math.pi * B.ravel() / nt
+    xyz = np.stack([rad * np.cos(phi), rad * np.sin(phi), t * C.ravel() / nz], axis=1).ravel()
+    ec, eb, ea = np.meshgrid(np.arange(nz), np.arange(nt), np.arange(nr), indexing="ij")
+    ea, eb, ec = ea.ravel(), eb.ravel(), ec.ravel()
+    en = np.stack([(ea + (l & 1)) + (nr + 1) * (((eb + ((l >> 1) & 1)) % nt) + nt * (ec + ((l >> 2) & 1)))
+                   for l in range(8)], axis=1)
+    K = np.ascontiguousarray(annulus_tensors(xyz, en, kappa))
+    f = Stream(seed, 6).uniform(ne) if load else None
+    nnz = L.q1_assemble_annulus(nr, nt, nz, ri, ro, t, _p(K), _p(f), g_in, g_out, _p(row_ptr), _p(col), _p(val),
+                                _p(b), _p(coords), _p(elem_nodes), _p(elem_measure), _p(dmask))
+    if nnz < 0:
+        raise ValueError("q1_assemble_annulus failed")
+    p = dict(dim=3, n=n, nnz=int(nnz), row_ptr=row_ptr, col=col[:nnz].copy(), val=val[:nnz].copy(), b=b,
+             coords=coords, elem_nodes=elem_nodes, elem_measure=elem_measure, dir_mask=dmask, n_elem=ne,
+             grid=(nr, nt, nz))
+    return _finish(p, K, "annulus_3d", refine=refine, kappa=kappa, nr=nr, nt=nt, nz=nz, load=load)
+
+
 CONFIGS = {
     "c1": lambda **kw: layered_2d(**kw),
     "c2": lambda **kw: battery_3d(**kw),
     "c3": lambda **kw: voronoi_3d(**kw),
     "c5": lambda **kw: inclusions_3d(**kw),
+    "annulus": lambda **kw: annulus_3d(**kw),
 }
 
 

@@ -101,6 +101,36 @@ static void elem_matrix(int dim, const double h[3], const double* K, double* Ke)
     for (int b = 0; b < a; ++b) Ke[a * nl + b] = Ke[b * nl + a];
 }
 
+/* symmetric Dirichlet elimination in place: a Dirichlet row keeps only its
+ * diagonal (value 1, rhs = g), the column of a Dirichlet node is removed from
+ * every other row and that row's rhs is lifted by -a_ij * g_j */
+static void eliminate_dirichlet(int64_t n, int64_t* row_ptr, int32_t* col, double* val, double* b,
+                                const uint8_t* dir_mask, const double* dir_val) {
+  for (int64_t r = 0; r < n; ++r) {
+    if (dir_mask[r]) continue;
+    for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
+      int32_t c = col[p];
+      if (dir_mask[c]) b[r] -= val[p] * (dir_val ? dir_val[c] : 0.0);
+    }
+  }
+  int64_t w = 0, start = 0;
+  for (int64_t r = 0; r < n; ++r) {
+    int64_t end = row_ptr[r + 1];
+    for (int64_t p = start; p < end; ++p) {
+      int32_t c = col[p];
+      int keepit = dir_mask[r] ? (c == r) : !dir_mask[c];
+      if (keepit) {
+        col[w] = c;
+        val[w] = dir_mask[r] ? 1.0 : val[p];
+        ++w;
+      }
+    }
+    start = end;
+    row_ptr[r + 1] = w;
+    if (dir_mask[r]) b[r] = dir_val ? dir_val[r] : 0.0;
+  }
+}
+
 /*
  * Assemble the Q1 system on the tensor-product mesh with node coordinates
  * xc[0..nx], yc[0..ny], zc[0..nz] (zc ignored in 2D).
@@ -180,32 +210,7 @@ int64_t q1_assemble(int dim, int nx, int ny, int nz,
           }
         }
       }
-  /* symmetric Dirichlet elimination */
-  if (dir_mask) {
-    for (int64_t r = 0; r < n; ++r) {
-      if (dir_mask[r]) continue;
-      for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
-        int32_t c = col[p];
-        if (dir_mask[c]) b[r] -= val[p] * (dir_val ? dir_val[c] : 0.0);
-      }
-    }
-    int64_t w = 0, start = 0;
-    for (int64_t r = 0; r < n; ++r) {
-      int64_t end = row_ptr[r + 1];
-      for (int64_t p = start; p < end; ++p) {
-        int32_t c = col[p];
-        int keepit = dir_mask[r] ? (c == r) : !dir_mask[c];
-        if (keepit) {
-          col[w] = c;
-          val[w] = dir_mask[r] ? 1.0 : val[p];
-          ++w;
-        }
-      }
-      start = end;
-      row_ptr[r + 1] = w;
-      if (dir_mask[r]) b[r] = dir_val ? dir_val[r] : 0.0;
-    }
-  }
+  if (dir_mask) eliminate_dirichlet(n, row_ptr, col, val, b, dir_mask, dir_val);
   return row_ptr[n];
 }
 
@@ -261,4 +266,188 @@ int64_t q1_mark_sphere(int nx, int ny, int nz, double cx, double cy, double cz, 
         }
       }
   return added;
+}
+
+/* ------------------------------------------------------------------------
+ * Annulus: trilinear hexahedra on r_i <= r <= r_o, 0 <= z <= t with nr x nt x
+ * nz elements in the radial, circumferential and thickness directions,
+ * periodic in the angle (nt >= 3).
+ * Node (a, b, c) -> a + Nr*(b + nt*c), Nr = nr+1, Nz = nz+1, with coordinates
+ * (r_a cos phi_b, r_a sin phi_b, z_c), r_a = r_i + a (r_o - r_i)/nr,
+ * phi_b = 2 pi b / nt, z_c = c t / nz.  Local element node bits: bit0 = +r,
+ * bit1 = +angle, bit2 = +z.  Element matrices use the isoparametric map with
+ * 2x2x2 Gauss points (exact for the element volume, whose Jacobian is
+ * polynomial of low degree on these straight-edged hexahedra).
+ * Rows hold the full 27-point pattern with columns sorted ascending;
+ * Dirichlet on a = 0 (value g_in) and a = nr (value g_out), natural
+ * boundaries on z = 0 and z = t; elem_f (NULL -> 0) is a load density
+ * constant per element, integrated against each shape function.
+ * ------------------------------------------------------------------------ */
+static void hex_matrix(const double X[8][3], const double* K, double* Ke, double* meas, double* Nint) {
+  const double g = 1.0 / sqrt(3.0);
+  const double Kf[3][3] = {{K[0], K[3], K[4]}, {K[3], K[1], K[5]}, {K[4], K[5], K[2]}};
+  for (int a = 0; a < 64; ++a) Ke[a] = 0.0;
+  for (int a = 0; a < 8; ++a) Nint[a] = 0.0;
+  *meas = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    const double xi[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
+    double dN[8][3], N[8];
+    for (int a = 0; a < 8; ++a) {
+      double s[3], sg[3];
+      for (int d = 0; d < 3; ++d) {
+        sg[d] = ((a >> d) & 1) ? 1.0 : -1.0;
+        s[d] = 0.5 * (1.0 + sg[d] * xi[d]);
+      }
+      N[a] = s[0] * s[1] * s[2];
+      dN[a][0] = 0.5 * sg[0] * s[1] * s[2];
+      dN[a][1] = 0.5 * sg[1] * s[0] * s[2];
+      dN[a][2] = 0.5 * sg[2] * s[0] * s[1];
+    }
+    double J[3][3] = {{0}};  /* J[d][e] = d x_d / d xi_e */
+    for (int a = 0; a < 8; ++a)
+      for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e) J[d][e] += X[a][d] * dN[a][e];
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    /* inverse by the adjugate: Ji[e][d] = d xi_e / d x_d */
+    double Ji[3][3];
+    Ji[0][0] = c00 / det;
+    Ji[1][0] = c01 / det;
+    Ji[2][0] = c02 / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    double gr[8][3];
+    for (int a = 0; a < 8; ++a)
+      for (int d = 0; d < 3; ++d) gr[a][d] = dN[a][0] * Ji[0][d] + dN[a][1] * Ji[1][d] + dN[a][2] * Ji[2][d];
+    for (int a = 0; a < 8; ++a)
+      for (int bb = a; bb < 8; ++bb) {
+        double acc = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          double kg = 0.0;
+          for (int e = 0; e < 3; ++e) kg += Kf[d][e] * gr[bb][e];
+          acc += gr[a][d] * kg;
+        }
+        Ke[a * 8 + bb] += acc * det;
+      }
+    *meas += det;
+    for (int a = 0; a < 8; ++a) Nint[a] += N[a] * det;
+  }
+  for (int a = 0; a < 8; ++a)
+    for (int bb = 0; bb < a; ++bb) Ke[a * 8 + bb] = Ke[bb * 8 + a];
+}
+
+static int64_t ann_id(int a, int b, int c, int Nr, int nt) {
+  return (int64_t)a + (int64_t)Nr * ((int64_t)b + (int64_t)nt * (int64_t)c);
+}
+
+int64_t q1_annulus_nnz(int nr, int nt, int nz) {
+  return (int64_t)(3 * (nr + 1) - 2) * (3 * (int64_t)nt) * (3 * (nz + 1) - 2);
+}
+
+int64_t q1_assemble_annulus(int nr, int nt, int nz, double ri, double ro, double t, const double* elem_K,
+                            const double* elem_f, double g_in, double g_out, int64_t* row_ptr, int32_t* col, double* val, double* b,
+                            double* coords, int32_t* elem_nodes, double* elem_measure, uint8_t* dir_mask) {
+  if (nr < 1 || nt < 3 || nz < 1 || !(ro > ri) || !(ri > 0.0) || !(t > 0.0)) return -1;
+  const double two_pi = 6.283185307179586476925286766559;
+  const int Nr = nr + 1, Nz = nz + 1;
+  const int64_t n = (int64_t)Nr * nt * Nz;
+  /* pattern: 3 angle neighbours (periodic) x up to 3 radial x up to 3 thickness */
+  row_ptr[0] = 0;
+  for (int c = 0; c < Nz; ++c)
+    for (int bq = 0; bq < nt; ++bq)
+      for (int a = 0; a < Nr; ++a) {
+        const int64_t r = ann_id(a, bq, c, Nr, nt);
+        const int64_t p0 = row_ptr[r];
+        int64_t p = p0;
+        for (int dc = -1; dc <= 1; ++dc) {
+          if (c + dc < 0 || c + dc > nz) continue;
+          for (int db = -1; db <= 1; ++db) {
+            const int bb = (bq + db + nt) % nt;
+            for (int da = -1; da <= 1; ++da) {
+              if (a + da < 0 || a + da > nr) continue;
+              col[p++] = (int32_t)ann_id(a + da, bb, c + dc, Nr, nt);
+            }
+          }
+        }
+        for (int64_t x = p0 + 1; x < p; ++x) { /* insertion sort, <= 27 entries */
+          int32_t v = col[x];
+          int64_t y = x - 1;
+          while (y >= p0 && col[y] > v) { col[y + 1] = col[y]; --y; }
+          col[y + 1] = v;
+        }
+        row_ptr[r + 1] = p;
+      }
+  const int64_t nnz_full = row_ptr[n];
+  memset(val, 0, sizeof(double) * (size_t)nnz_full);
+  memset(b, 0, sizeof(double) * (size_t)n);
+  for (int c = 0; c < Nz; ++c)
+    for (int bq = 0; bq < nt; ++bq)
+      for (int a = 0; a < Nr; ++a) {
+        const int64_t r = ann_id(a, bq, c, Nr, nt);
+        const double rad = ri + (ro - ri) * (double)a / (double)nr;
+        const double phi = two_pi * (double)bq / (double)nt;
+        coords[3 * r + 0] = rad * cos(phi);
+        coords[3 * r + 1] = rad * sin(phi);
+        coords[3 * r + 2] = t * (double)c / (double)nz;
+        dir_mask[r] = (uint8_t)(a == 0 || a == nr);
+      }
+  /* The mesh and the tensor field are invariant under a rotation by
+   * 2 pi / nt, so all elements of a ring (fixed ea, ec) share one element
+   * matrix: it is computed once, from the element at angle index 0 and its
+   * tensor, and reused around the ring. */
+  const int64_t nring = (int64_t)nr * nz;
+  double* Kr = (double*)malloc(sizeof(double) * (size_t)(nring * 64));
+  double* Nr8 = (double*)malloc(sizeof(double) * (size_t)(nring * 8));
+  double* Mr = (double*)malloc(sizeof(double) * (size_t)nring);
+  if (!Kr || !Nr8 || !Mr) { free(Kr); free(Nr8); free(Mr); return -1; }
+  double X[8][3];
+  int64_t gid[8];
+  for (int ec = 0; ec < nz; ++ec)
+    for (int ea = 0; ea < nr; ++ea) {
+      const int64_t e0 = (int64_t)ea + (int64_t)nr * ((int64_t)nt * ec);
+      const int64_t q = (int64_t)ec * nr + ea;
+      for (int l = 0; l < 8; ++l) {
+        const int64_t gl = ann_id(ea + (l & 1), ((l >> 1) & 1) % nt, ec + ((l >> 2) & 1), Nr, nt);
+        for (int d = 0; d < 3; ++d) X[l][d] = coords[3 * gl + d];
+      }
+      hex_matrix(X, elem_K + e0 * 6, Kr + q * 64, &Mr[q], Nr8 + q * 8);
+    }
+  for (int ec = 0; ec < nz; ++ec)
+    for (int eb = 0; eb < nt; ++eb)
+      for (int ea = 0; ea < nr; ++ea) {
+        const int64_t e = (int64_t)ea + (int64_t)nr * ((int64_t)eb + (int64_t)nt * ec);
+        const int64_t q = (int64_t)ec * nr + ea;
+        const double* Ke = Kr + q * 64;
+        const double* Nint = Nr8 + q * 8;
+        elem_measure[e] = Mr[q];
+        for (int l = 0; l < 8; ++l) {
+          const int a = ea + (l & 1), bq = (eb + ((l >> 1) & 1)) % nt, c = ec + ((l >> 2) & 1);
+          gid[l] = ann_id(a, bq, c, Nr, nt);
+          elem_nodes[e * 8 + l] = (int32_t)gid[l];
+        }
+        for (int l = 0; l < 8; ++l) {
+          if (elem_f) b[gid[l]] += elem_f[e] * Nint[l];  /* consistent load of a constant f */
+          for (int m = 0; m < 8; ++m) {
+            int64_t p = row_ptr[gid[l]];
+            while (col[p] != (int32_t)gid[m]) ++p;  /* present by construction */
+            val[p] += Ke[l * 8 + m];
+          }
+        }
+      }
+  free(Kr);
+  free(Nr8);
+  free(Mr);
+  /* Dirichlet values: g_in on the inner ring, g_out on the outer ring */
+  double* g = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!g) return -1;
+  for (int64_t r = 0; r < n; ++r) g[r] = (r % Nr == 0) ? g_in : g_out;
+  eliminate_dirichlet(n, row_ptr, col, val, b, dir_mask, g);
+  free(g);
+  return row_ptr[n];
 }
