@@ -30,10 +30,14 @@ sys.path.insert(0, ROOT)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM_GBS = 6800.0
+# FP64 FMA lanes: 2 per SM per cycle (one warp instruction per 16 cycles; the
+# nominal 1.25 TFLOP/s at 152 SMs x 2070 MHz x 4 FLOP)
+N_SM, FP64_FLOP_PER_SM_CYCLE, SM_MAX_MHZ = 152, 4.0, 2070.0
 
 WORKLOADS = {
     # name: (generator kwargs, description)
     "battery_128x128x256": (dict(nx=128, ny=128, nz=256), "battery-like stack, Q1 hex 128x128x256 (4.28M dofs)"),
+    "battery_96x96x192": (dict(nx=96, ny=96, nz=192), "battery-like stack, Q1 hex 96x96x192 (1.8M dofs)"),
     "battery_64x64x128": (dict(nx=64, ny=64, nz=128), "battery-like stack, Q1 hex 64x64x128 (0.54M dofs)"),
     "battery_32x32x64": (dict(nx=32, ny=32, nz=64), "battery-like stack, Q1 hex 32x32x64 (71k dofs)"),
 }
@@ -59,7 +63,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("solve.cu", "solve.cuh", "mixed.cu", "host.cu"):
+    for f in ("vcycle.cu", "vcycle.cuh", "solve.cu", "solve.cuh", "host.cu"):
         with open(os.path.join(ROOT, "paper_2602_05686_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -234,20 +238,37 @@ def run_ours(args):
     # end-to-end through the C ABI with host buffers (copies inside)
     e2e = None
     if not args.no_e2e:
-        bh = p["b"].copy()
-        inb = sum(int(np.asarray(p[k]).nbytes) for k in ("row_ptr", "col", "val", "coords", "tensors", "elem_nodes",
-                                                        "elem_measure"))
+        # the step's inputs in pinned host memory (numpy views of pinned torch
+        # tensors), copied to the device inside the timed region
+        hkeys = ("row_ptr", "col", "val", "coords", "tensors", "elem_nodes", "elem_measure")
+        ph = dict(p, **{k: torch.from_numpy(np.ascontiguousarray(p[k])).pin_memory().numpy() for k in hkeys})
+        bh = torch.from_numpy(p["b"].copy()).pin_memory().numpy()
+        inb = sum(int(np.asarray(p[k]).nbytes) for k in hkeys)
         barrier()
         te = time.perf_counter()
         for _ in range(max(1, min(args.steps, 2))):
-            one_step(p, bh, host=True)
+            one_step(ph, bh, host=True)
         barrier()
         e_ms = (time.perf_counter() - te) * 1000.0 / max(1, min(args.steps, 2))
         e2e = {"value": round(e_ms / 1000.0, 4), "unit": "s",
                "h2d_bytes_per_step": 2 * inb + 3 * 2 * n * 8, "d2h_bytes_per_step": 3 * n * 8}
 
-    # roofline of the dominant kernel (largest total time in the timed region)
+    # roofline of the dominant kernel (largest total time in the timed region):
+    # the HBM floor (algorithmic bytes / measured copy bandwidth) and, for the
+    # FP64 fine-level kernels, the FP64-pipe floor (algorithmic FLOPs / the FP64
+    # peak at the sampled SM clock); the larger floor names the bound
     peak, peak_kind = peaks()
+    mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
+    fp64_peak = N_SM * FP64_FLOP_PER_SM_CYCLE * mhz * 1e6 / 1e12   # TFLOP/s
+    nnz0 = int(p["nnz"])
+
+    def fp64_flops(kind, level):
+        """FP64 FLOPs per launch: one FMA per stored entry plus the row updates"""
+        if level != 0:
+            return None
+        per_row = {"cheb64": 5, "resid64": 1, "cg_spmv": 2}.get(kind)
+        return None if per_row is None else 2.0 * nnz0 + per_row * n
+
     rows = sorted(prof, key=lambda r: -r["ms"])
     krows = [r for r in rows if r["bytes"] > 0]   # kernels with an algorithmic-bytes model
     dom = krows[0] if krows else None
@@ -261,6 +282,19 @@ def run_ours(args):
                 "frac": round(ach / peak, 4), "traffic": traffic_for(kname, args.workload),
                 "kernel": kname, "peak_source": peak_kind, "launches": dom["launches"],
                 "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": round(per_launch_ms, 5)}
+        fl = fp64_flops(dom["kind"], dom["level"])
+        if fl:
+            t_hbm = per_launch_bytes / (peak * 1e9)
+            t_fp64 = fl / (fp64_peak * 1e12)
+            a64 = fl / (per_launch_ms * 1e-3) / 1e12
+            roof["fp64_pipe"] = {"achieved": round(a64, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                                 "frac": round(a64 / fp64_peak, 4), "flops_per_launch": fl,
+                                 "peak_source": f"derived: {N_SM} SMs x 4 FLOP/cycle x {mhz:.0f} MHz"}
+            if t_fp64 > t_hbm:   # the FP64 pipe is the tighter floor
+                hb = {k: roof.pop(k) for k in ("achieved", "peak", "unit", "frac", "peak_source")}
+                roof.update(bound="alu", achieved=roof["fp64_pipe"]["achieved"], peak=roof["fp64_pipe"]["peak"],
+                            unit="TFLOP/s", frac=roof["fp64_pipe"]["frac"],
+                            peak_source=roof["fp64_pipe"]["peak_source"], hbm=hb)
     # V-cycle bandwidth per form (all V-cycle kernels; algorithmic bytes / time)
     def vgb(kinds):
         sel = [r for r in prof if r["kind"] in kinds]
@@ -424,6 +458,31 @@ def run_serving(args):
     print(json.dumps(res), flush=True)
 
 
+def run_annulus(args):
+    """The annulus study of Sec. 4.2 (Table 1 analogue): refinements h ..
+    h/2^max, contrast 1 .. 1e4, material measure, theta 0.05 and 0.1, FP64
+    PCG to 1e-8; one JSON line per configuration."""
+    import torch
+
+    import gen
+    import paper_2602_05686_gb300 as sa
+    from paper_2602_05686_gb300.sweep import annulus_study
+
+    torch.cuda.set_device(0)
+    sa.build()
+    cache = {}
+
+    def make(rf, k):
+        if (rf, k) not in cache:
+            cache.clear()
+            cache[(rf, k)] = gen.annulus_3d(rf, kappa=k)
+        return cache[(rf, k)]
+
+    annulus_study(make, refines=(0,), kappas=(1.0,))   # warm-up (module loads)
+    for row in annulus_study(make, refines=tuple(range(args.annulus_refine + 1))):
+        print(json.dumps(dict(row, workload="annulus (Sec. 4.2)")), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,9 +498,13 @@ def main():
     ap.add_argument("--hbm-gb", type=int, default=64)
     ap.add_argument("--max2d", type=int, default=512)
     ap.add_argument("--max3d", type=int, default=96)
+    ap.add_argument("--annulus", action="store_true", help="run the annulus study (Sec. 4.2) instead")
+    ap.add_argument("--annulus-refine", type=int, default=4)
     args = ap.parse_args()
     if args.serving:
         run_serving(args)
+    elif args.annulus:
+        run_annulus(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -52,6 +52,13 @@ typedef enum {
 } sa_measure;
 
 typedef enum {
+  SA_DROP_POINTWISE = 0,  /* keep |S_ij| >= theta (Sec. 2.1, Eq. C^pw) */
+  SA_DROP_CUT = 1         /* cut-drop (Sec. 2.1, Eq. C^cut-drop): per row, keep the entries above the
+                             first gap where theta |S_(k)| >= |S_(k+1)| in descending order (no gap:
+                             keep the row); an edge is kept only when both of its rows keep it */
+} sa_drop;
+
+typedef enum {
   SA_PREC_FP64 = 0,        /* FP64 PCG with an FP64 V-cycle */
   SA_PREC_FP32_VCYCLE = 1  /* FP64 flexible CG with an FP32 V-cycle on the
                               symmetrically diagonal-scaled hierarchy */
@@ -96,7 +103,7 @@ typedef struct {
 
 /*
  * Options.  sa_default_options fills the paper's settings (Sec. 4):
- *   theta = 0.08, measure MATERIAL, precision FP64, max_coarse = 5000,
+ *   theta = 0.08, measure MATERIAL, pointwise dropping, precision FP64, max_coarse = 5000,
  *   max_levels = 10, Chebyshev degree 2 with lambda_max boost 1.1 and ratio
  *   30, 10 power steps, omega_sym = 4/3, maxit = 500.
  * alloc/dealloc: optional device allocator (e.g. a caching allocator);
@@ -118,6 +125,7 @@ typedef struct {
   void (*dealloc)(void* ptr, void* ctx);
   void* alloc_ctx;
   int keep_setup_data;     /* 1: keep strength masks and roots for sa_export_strength */
+  sa_drop drop;            /* dropping criterion (default pointwise) */
 } sa_options;
 
 typedef struct {
@@ -203,6 +211,47 @@ int sa_export_strength(sa_handle h, int l, uint8_t* keep, uint8_t* root, uint8_t
 
 /* releases every device buffer of the handle (stream-ordered) */
 int sa_free(sa_handle h);
+
+/*
+ * Hierarchy store (no counterpart in the paper, which rebuilds the hierarchy
+ * in every run; Sec. 4.3 notes that the setup cost is amortised over
+ * right-hand sides, and a stored hierarchy carries that over to another
+ * process or a later run).  The store holds the FP64 hierarchy: per level
+ * A_l (CSR), its diagonal, P_l and R_l = P_l^T (CSR), the aggregate map and
+ * the smoother scalars (omega, lambda_omega, Chebyshev bounds), plus the
+ * options that built it.  Loading re-derives the rest deterministically
+ * (reciprocal diagonals, the coarse Cholesky factor, the SELL copies of the
+ * scaled hierarchy), so a loaded handle solves bit-identically to the one
+ * that was stored.
+ *
+ * Format: a 112-byte header (magic "SAAMGH1", version 1, byte-order mark
+ * 0x01020304, dim, levels, n, the setup options, payload bytes, FNV-1a-64
+ * checksum over the payload's 64-bit words) followed by the levels, each a
+ * 72-byte record {n, nnz, nc, nnzP, nnz_gc, omega, lambda_omega, lmax, lmin}
+ * and its arrays in the order rp, col, val, diag [, P rp, P col, P val,
+ * R rp, R col, R val, agg], every array zero-padded to 8 bytes.  Host byte
+ * order; a store written on a machine of the other order is rejected.
+ */
+
+/* *bytes = size of the store of h (the buffer sa_serialize needs) */
+int sa_serialized_size(sa_handle h, uint64_t* bytes);
+
+/* writes the store of h into the caller-owned HOST buffer buf of `bytes`
+ * bytes (>= sa_serialized_size, else SA_ERR_INVALID_ARG); synchronises the
+ * handle's stream */
+int sa_serialize(sa_handle h, void* buf, uint64_t bytes);
+
+/*
+ * Builds a handle from a store in the HOST buffer buf (`bytes` = its exact
+ * size).  opt supplies the stream, the allocator callbacks, maxit and the
+ * solve precision; every setup option is taken from the store.  Returns
+ * SA_ERR_INVALID_ARG (with sa_last_error text) for a wrong magic, version,
+ * byte order or size, a checksum mismatch, inconsistent level sizes or CSR
+ * arrays whose row pointers or columns are out of range (checked on the
+ * device before any use); SA_ERR_OOM when memory runs out.  The buffer is
+ * only read and may be freed on return.
+ */
+int sa_deserialize(const void* buf, uint64_t bytes, const sa_options* opt, sa_handle* out);
 
 /* static description of a status code */
 const char* sa_status_string(int status);

@@ -17,11 +17,13 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_SPD, ERR_STAGNATION, ERR_NO_CONV
     ERR_CAPACITY = 0, -1, -2, -3, -4, -5, -6, -7, -8
 MEASURE = {"classical": 0, "material": 1, "distance": 2}
 PRECISION = {"fp64": 0, "fp32": 1}
+DROP = {"pointwise": 0, "cut": 1}
 
 EXPORTED = ["sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle", "sa_hierarchy_stats",
             "sa_level_sizes", "sa_export_level", "sa_export_strength", "sa_free", "sa_status_string",
             "sa_last_error", "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
-            "sa_launch_count", "sa_strength_material_noalloc"]
+            "sa_launch_count", "sa_strength_material_noalloc", "sa_serialized_size", "sa_serialize",
+            "sa_deserialize"]
 
 
 class SAError(RuntimeError):
@@ -48,7 +50,7 @@ class Options(ctypes.Structure):
                 ("cheb_ratio", ctypes.c_double), ("cheb_boost", ctypes.c_double), ("power_iters", ctypes.c_int),
                 ("omega_sym", ctypes.c_double), ("seed", ctypes.c_uint32), ("maxit", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("alloc", _ALLOC), ("dealloc", _FREE),
-                ("alloc_ctx", ctypes.c_void_p), ("keep_setup_data", ctypes.c_int)]
+                ("alloc_ctx", ctypes.c_void_p), ("keep_setup_data", ctypes.c_int), ("drop", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -95,9 +97,13 @@ def lib(build_if_missing: bool = True):
         L.sa_strength_material_noalloc.restype = I
         L.sa_launch_count.argtypes = []
         L.sa_launch_count.restype = ctypes.c_int64
+        L.sa_serialized_size.argtypes = [P, P]
+        L.sa_serialize.argtypes = [P, P, ctypes.c_uint64]
+        L.sa_deserialize.argtypes = [P, ctypes.c_uint64, P, P]
         for f in ("sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle",
                   "sa_hierarchy_stats", "sa_level_sizes", "sa_export_level", "sa_export_strength", "sa_free",
-                  "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read"):
+                  "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
+                  "sa_serialized_size", "sa_serialize", "sa_deserialize"):
             getattr(L, f).restype = I
         _L = L
     return _L
@@ -136,7 +142,7 @@ class Hierarchy:
 
     def __init__(self, problem, theta=0.08, measure="material", precision="fp64", max_coarse=5000,
                  max_levels=10, seed=0, maxit=500, keep_setup_data=False, host_inputs=False, stream=None,
-                 cheb_degree=2, power_iters=10):
+                 cheb_degree=2, power_iters=10, drop="pointwise"):
         torch = _torch()
         L = lib()
         self.torch = torch
@@ -154,6 +160,7 @@ class Hierarchy:
         o.keep_setup_data = int(keep_setup_data)
         o.cheb_degree = int(cheb_degree)
         o.power_iters = int(power_iters)
+        o.drop = DROP[drop]
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         self.opts = o
         pr = Problem()
@@ -187,6 +194,45 @@ class Hierarchy:
         del keep
         _check(st, "sa_setup")
         self.h = h
+
+    # -- store ---------------------------------------------------------------
+    def to_bytes(self):
+        """The stored FP64 hierarchy (sa_serialize) as a numpy uint8 array."""
+        nb = ctypes.c_uint64()
+        _check(lib().sa_serialized_size(self.h, ctypes.byref(nb)), "sa_serialized_size")
+        buf = np.empty(nb.value, np.uint8)
+        _check(lib().sa_serialize(self.h, buf.ctypes.data, nb.value), "sa_serialize")
+        return buf
+
+    def save(self, path):
+        self.to_bytes().tofile(path)
+
+    @classmethod
+    def from_bytes(cls, buf, precision="fp64", maxit=500, stream=None):
+        """A handle rebuilt from a store (sa_deserialize) without re-running the
+        setup; the setup options come from the store."""
+        torch = _torch()
+        buf = np.ascontiguousarray(np.frombuffer(buf, np.uint8) if isinstance(buf, (bytes, bytearray)) else buf,
+                                   np.uint8)
+        self = cls.__new__(cls)
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        o = default_options()
+        o.precision = PRECISION[precision]
+        o.maxit = int(maxit)
+        o.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        h = ctypes.c_void_p()
+        _check(lib().sa_deserialize(buf.ctypes.data, buf.size, ctypes.byref(o), ctypes.byref(h)), "sa_deserialize")
+        self.h = h
+        self.opts = o
+        st = self.stats()
+        self.n = int(st["n"][0])
+        self.dim = int(np.frombuffer(buf[16:20].tobytes(), np.int32)[0])  # header field after magic, version, order
+        return self
+
+    @classmethod
+    def load(cls, path, **kw):
+        return cls.from_bytes(np.fromfile(path, np.uint8), **kw)
 
     # -- lifetime ------------------------------------------------------------
     def free(self):
@@ -294,7 +340,7 @@ PROFILE_KINDS = ["cheb64", "resid64", "restrict64", "prolong64", "first64", "cg_
                  "cheb32", "resid32", "restrict32", "prolong32", "first32",
                  "setup_nodal", "setup_strength", "setup_graph", "setup_mis2", "setup_aggregate", "setup_filter",
                  "setup_omega", "setup_smooth_p", "setup_transpose", "setup_galerkin", "setup_aux",
-                 "setup_cheb_bounds", "setup_dense", "setup_sell"]
+                 "setup_cheb_bounds", "setup_dense", "setup_sell", "setup_galerkin_ap", "setup_galerkin_rap"]
 
 
 def profile_enable(on=True):

@@ -80,44 +80,53 @@ __global__ void k_mis_init(int64_t n, const uint8_t* __restrict__ dir, uint32_t 
   tag[i] = key + 1;
 }
 
+// neighbour maxima with MIS_SW lanes per G_C row (rows hold 0..26 entries)
+constexpr int MIS_SW = 8;
+
 __global__ void k_mis_max1(int64_t n, const int64_t* __restrict__ gcrp, const int32_t* __restrict__ gcci,
                            const uint64_t* __restrict__ tag, uint64_t* __restrict__ m1) {
-  const int lane = lane_id();
-  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
-    uint64_t m = lane == 0 ? tag[i] : 0;
-    for (int64_t p = gcrp[i] + lane; p < gcrp[i + 1]; p += 32) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = gt / MIS_SW;
+  const int sl = (int)(gt % MIS_SW);
+  uint64_t m = 0;
+  if (i < n) {
+    if (sl == 0) m = tag[i];
+    for (int64_t p = gcrp[i] + sl; p < gcrp[i + 1]; p += MIS_SW) {
       uint64_t t = tag[gcci[p]];
       m = t > m ? t : m;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      uint64_t t = __shfl_xor_sync(FULL, m, o);
-      m = t > m ? t : m;
-    }
-    if (lane == 0) m1[i] = m;
   }
+  for (int o = MIS_SW / 2; o > 0; o >>= 1) {
+    uint64_t t = __shfl_xor_sync(FULL, m, o, MIS_SW);
+    m = t > m ? t : m;
+  }
+  if (i < n && sl == 0) m1[i] = m;
 }
 
 __global__ void k_mis_max2(int64_t n, const int64_t* __restrict__ gcrp, const int32_t* __restrict__ gcci,
                            const uint64_t* __restrict__ m1, uint64_t* __restrict__ tag,
                            unsigned long long* __restrict__ undecided) {
-  const int lane = lane_id();
-  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
-    const uint64_t ti = tag[i];
-    if (ti == 0 || ti == TAG_SEL) continue;  // warp-uniform
-    uint64_t m = lane == 0 ? m1[i] : 0;
-    for (int64_t p = gcrp[i] + lane; p < gcrp[i + 1]; p += 32) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = gt / MIS_SW;
+  const int sl = (int)(gt % MIS_SW);
+  const uint64_t ti = i < n ? tag[i] : 0;
+  const bool active = i < n && ti != 0 && ti != TAG_SEL;
+  uint64_t m = 0;
+  if (active) {
+    if (sl == 0) m = m1[i];
+    for (int64_t p = gcrp[i] + sl; p < gcrp[i + 1]; p += MIS_SW) {
       uint64_t t = m1[gcci[p]];
       m = t > m ? t : m;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      uint64_t t = __shfl_xor_sync(FULL, m, o);
-      m = t > m ? t : m;
-    }
-    if (lane == 0) {
-      uint64_t nt = (m == TAG_SEL) ? 0 : (m == ti ? TAG_SEL : ti);
-      tag[i] = nt;
-      if (nt != 0 && nt != TAG_SEL) atomicAdd(undecided, 1ull);
-    }
+  }
+  for (int o = MIS_SW / 2; o > 0; o >>= 1) {
+    uint64_t t = __shfl_xor_sync(FULL, m, o, MIS_SW);
+    m = t > m ? t : m;
+  }
+  if (active && sl == 0) {
+    uint64_t nt = (m == TAG_SEL) ? 0 : (m == ti ? TAG_SEL : ti);
+    tag[i] = nt;
+    if (nt != 0 && nt != TAG_SEL) atomicAdd(undecided, 1ull);
   }
 }
 
@@ -141,9 +150,9 @@ int run_mis2(Alloc& al, int64_t n, const int64_t* gcrp, const int32_t* gcci, con
     if (*rounds >= max_rounds) return SA_ERR_CAPACITY;
     for (int g = 0; g < group; ++g) {
       SA_TRY(memset_d(cnt.p, 0, sizeof(unsigned long long), s));
-      k_mis_max1<<<warp_rows_grid(n), 256, 0, s>>>(n, gcrp, gcci, tag, m1.p);
+      k_mis_max1<<<blocks_for(n * MIS_SW, 256), 256, 0, s>>>(n, gcrp, gcci, tag, m1.p);
       SA_LAUNCHED();
-      k_mis_max2<<<warp_rows_grid(n), 256, 0, s>>>(n, gcrp, gcci, m1.p, tag, cnt.p);
+      k_mis_max2<<<blocks_for(n * MIS_SW, 256), 256, 0, s>>>(n, gcrp, gcci, m1.p, tag, cnt.p);
       SA_LAUNCHED();
       ++*rounds;
     }

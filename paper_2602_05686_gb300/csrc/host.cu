@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <type_traits>
 #include <memory>
 #include <vector>
 
@@ -102,12 +103,17 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
   SA_TRY(memset_d(rpF.p, 0, sizeof(int64_t), s));
   if (!aux) {
     SA_TRY(launch_strength_classical(s, n, L.rp.p, L.ci.p, L.v.p, L.diag.p, dir, o.theta, keep.p, rpF.p));
+    if (o.drop == SA_DROP_CUT)
+      SA_TRY(launch_cut_drop(al, 1, n, nnz, L.rp.p, L.ci.p, L.v.p, L.diag.p, nullptr, nullptr, dir, o.theta, keep.p,
+                             rpF.p));
   } else {
     Buf<double> w, D;
     SA_TRY(w.alloc(&al, nnz));
     SA_TRY(D.alloc(&al, n));
     SA_TRY(launch_strength_material(s, h->dim, n, L.rp.p, L.ci.p, L.x.p, L.sinv.p, dir, o.theta, w.p, D.p, keep.p,
                                     rpF.p));
+    if (o.drop == SA_DROP_CUT)
+      SA_TRY(launch_cut_drop(al, 0, n, nnz, L.rp.p, L.ci.p, nullptr, nullptr, w.p, D.p, dir, o.theta, keep.p, rpF.p));
   }
   SA_TRY(scan_inplace(al, rpF.p + 1, n));
   int64_t nnzF = 0;
@@ -185,7 +191,7 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
 
   // a12: P = P^ - omega D~^-1 A_F P^
   PHASE_BEGIN(PK_S_SMOOTHP, l);
-  SA_TRY(run_spgemm(al, n, nc, rpF.p, ciF.p, vF.p, Trp.p, Tci.p, Tv.p, L.Prp, L.Pci, L.Pv, &L.nnzP));
+  SA_TRY(run_spgemm(al, n, nc, n, rpF.p, ciF.p, vF.p, Trp.p, Tci.p, Tv.p, L.Prp, L.Pci, L.Pv, &L.nnzP));
   SA_TRY(launch_smooth_p_values(s, n, L.Prp.p, L.Pci.p, L.Pv.p, L.agg.p, Dt.p, scal.p + 1, L.Pv.p));
   PHASE_END(PK_S_SMOOTHP);
   double hs[2];
@@ -202,11 +208,18 @@ static int coarsen(sa_handle h, int l, int* err, int* stop) {
   Buf<int32_t> APci;
   Buf<double> APv;
   int64_t nnzAP = 0;
-  SA_TRY(run_spgemm(al, n, nc, L.rp.p, L.ci.p, L.v.p, L.Prp.p, L.Pci.p, L.Pv.p, APrp, APci, APv, &nnzAP));
+  PHASE_BEGIN(PK_S_RAP_AP, l);
+  SA_TRY(run_spgemm(al, n, nc, n, L.rp.p, L.ci.p, L.v.p, L.Prp.p, L.Pci.p, L.Pv.p, APrp, APci, APv, &nnzAP));
+  PHASE_END(PK_S_RAP_AP);
   std::unique_ptr<Level> N(new Level());
   N->n = nc;
-  SA_TRY(run_spgemm(al, nc, nc, L.Rrp.p, L.Rci.p, L.Rv.p, APrp.p, APci.p, APv.p, N->rp, N->ci, N->v, &N->nnz));
+  // R (A P) is symmetric: only its upper triangle is accumulated, the lower
+  // one is mirrored from it
+  PHASE_BEGIN(PK_S_RAP_RAP, l);
+  SA_TRY(run_spgemm(al, nc, nc, n, L.Rrp.p, L.Rci.p, L.Rv.p, APrp.p, APci.p, APv.p, N->rp, N->ci, N->v, &N->nnz,
+                    1));
   SA_TRY(launch_symmetrize(s, nc, N->rp.p, N->ci.p, N->v.p, err));
+  PHASE_END(PK_S_RAP_RAP);
   SA_TRY(level_diag(h, *N, nullptr, err));
   PHASE_END(PK_S_RAP);
 
@@ -307,7 +320,7 @@ static int cg_eager_dev(sa_handle h, const double* b, double* x, double tol, sa_
     const int maxit = h->opt.maxit;
     for (it = 1; it <= maxit; ++it) {
       int np = 0;
-      PROF(PK_CG_SPMV, 0, 12.0 * L0.nnz + 8.0 * (h->A0s.nslices + 1) + 16.0 * n,
+      PROF(PK_CG_SPMV, 0, (8.0 + h->A0s.idx_bytes()) * L0.nnz + 8.0 * (h->A0s.nslices + 1) + 16.0 * n,
            op_spmv_dot(h, h->p.p, h->q.p, h->part.p, &np));
       SA_TRY(launch_finish(s, h->part.p, np, h->dots.p));
       SA_TRY(launch_cg_alpha(s, h->cg.p, h->dots.p));
@@ -577,7 +590,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   SA_TRY(upload(al, L0->rp, P->row_ptr, P->n + 1));
   SA_TRY(upload(al, L0->ci, P->col, P->nnz));
   SA_TRY(upload(al, L0->v, P->val, P->nnz));
-  SA_TRY(launch_validate_csr(s, P->n, P->nnz, L0->rp.p, L0->ci.p, err.p));
+  SA_TRY(launch_validate_csr(s, P->n, P->n, P->nnz, L0->rp.p, L0->ci.p, err.p));
   {
     int e0 = 0;
     SA_TRY(copy_d2h(&e0, err.p, sizeof(int), s));
@@ -666,7 +679,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   PHASE_BEGIN(PK_S_SELL, 0);
   {
     Level& L0 = *h->lev[0];
-    SA_TRY(build_sell<double>(al, L0.n, L0.nnz, L0.rp.p, L0.ci.p, L0.v.p, nullptr, 0, nullptr, 0, h->A0s));
+    SA_TRY(build_sell<double>(al, L0.n, L0.nnz, L0.rp.p, L0.ci.p, L0.v.p, nullptr, nullptr, h->A0s));
     std::vector<VLevelIn> in = vlevel_inputs(h);
     SA_TRY(vh_build<double>(al, in.data(), nlev, o->cheb_degree, h->W.p, h->WT.p, &h->v64));
   }
@@ -709,6 +722,7 @@ static int validate(const sa_problem* P, const sa_options* o) {
   if (P->n <= 0 || P->nnz < P->n || P->n >= (int64_t)0x7fffffff) return SA_ERR_INVALID_ARG;
   if (!P->row_ptr || !P->col || !P->val) return SA_ERR_INVALID_ARG;
   if ((int)o->measure < 0 || (int)o->measure > 2) return SA_ERR_INVALID_ARG;
+  if ((int)o->drop < 0 || (int)o->drop > 1) return SA_ERR_INVALID_ARG;
   if ((int)o->precision < 0 || (int)o->precision > 1) return SA_ERR_INVALID_ARG;
   if (o->measure != SA_MEASURE_CLASSICAL && !P->coords) return SA_ERR_INVALID_ARG;
   if (o->measure == SA_MEASURE_MATERIAL) {
@@ -872,6 +886,296 @@ int sa_export_strength(sa_handle h, int l, uint8_t* keep, uint8_t* root, uint8_t
   }
   return SA_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// hierarchy store: the FP64 hierarchy (A_l, D_l, P_l, R_l, aggregates and the
+// smoother scalars) in one host buffer, reloaded without re-running the setup
+// ---------------------------------------------------------------------------
+namespace {
+
+const char kStoreMagic[8] = {'S', 'A', 'A', 'M', 'G', 'H', '1', '\0'};
+const uint32_t kStoreVersion = 1;
+const uint32_t kStoreOrder = 0x01020304u;
+
+struct StoreHeader {
+  char magic[8];
+  uint32_t version, order;
+  int32_t dim, nlev;
+  int64_t n;
+  double theta, cheb_ratio, cheb_boost, omega_sym;
+  int32_t measure, drop, max_coarse, max_levels, cheb_degree, power_iters;
+  uint32_t seed, reserved;
+  uint64_t payload, checksum;
+};
+
+struct StoreLevel {
+  int64_t n, nnz, nc, nnzP, nnz_gc;
+  double omega, lam_omega, lmax, lmin;
+};
+
+static_assert(sizeof(StoreHeader) == 112, "store header layout");
+static_assert(sizeof(StoreLevel) == 72, "store level record layout");
+
+uint64_t pad8(uint64_t b) { return (b + 7) & ~(uint64_t)7; }
+
+// payload bytes of one level (arrays padded to 8 bytes)
+uint64_t level_bytes(const StoreLevel& L, bool last) {
+  uint64_t b = sizeof(StoreLevel);
+  b += pad8(8ull * (uint64_t)(L.n + 1)) + pad8(4ull * (uint64_t)L.nnz) + pad8(8ull * (uint64_t)L.nnz) +
+       pad8(8ull * (uint64_t)L.n);
+  if (!last)
+    b += pad8(8ull * (uint64_t)(L.n + 1)) + pad8(4ull * (uint64_t)L.nnzP) + pad8(8ull * (uint64_t)L.nnzP) +
+         pad8(8ull * (uint64_t)(L.nc + 1)) + pad8(4ull * (uint64_t)L.nnzP) + pad8(8ull * (uint64_t)L.nnzP) +
+         pad8(4ull * (uint64_t)L.n);
+  return b;
+}
+
+// FNV-1a over 64-bit words (the payload is a whole number of words)
+uint64_t store_checksum(const unsigned char* p, uint64_t bytes) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (uint64_t o = 0; o + 8 <= bytes; o += 8) {
+    uint64_t w;
+    memcpy(&w, p + o, 8);
+    h ^= w;
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+StoreLevel store_level_of(const sa::Level& L, bool last) {
+  StoreLevel d;
+  memset(&d, 0, sizeof(d));
+  d.n = L.n; d.nnz = L.nnz; d.nnz_gc = L.nnz_gc;
+  d.nc = last ? 0 : L.nc;
+  d.nnzP = last ? 0 : L.nnzP;
+  d.omega = L.omega; d.lam_omega = L.lam_omega; d.lmax = L.lmax; d.lmin = L.lmin;
+  return d;
+}
+
+}  // namespace
+
+namespace sa {
+
+static uint64_t store_size(sa_handle h) {
+  const int nlev = (int)h->lev.size();
+  uint64_t b = sizeof(StoreHeader);
+  for (int l = 0; l < nlev; ++l) b += level_bytes(store_level_of(*h->lev[l], l + 1 == nlev), l + 1 == nlev);
+  return b;
+}
+
+// rebuild what the solve needs from a loaded FP64 hierarchy: reciprocal
+// diagonals, the coarse factor, the Krylov workspace and the SELL copies
+static int finish_loaded(sa_handle h) {
+  Alloc& al = h->al;
+  cudaStream_t s = al.stream;
+  const int nlev = (int)h->lev.size();
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = *h->lev[l];
+    SA_TRY(L.dinv.alloc(&al, L.n));
+    SA_TRY(launch_reciprocal(s, L.n, L.diag.p, L.dinv.p));
+    L.sw = pick_sw(L.n, L.nnz);
+  }
+  Level& Lc = *h->lev[nlev - 1];
+  h->nL = Lc.n;
+  SA_TRY(run_dense_inverse_factor(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT));
+  SA_TRY(alloc_workspace(h));
+  Level& L0 = *h->lev[0];
+  SA_TRY(build_sell<double>(al, L0.n, L0.nnz, L0.rp.p, L0.ci.p, L0.v.p, nullptr, nullptr, h->A0s));
+  std::vector<VLevelIn> in = vlevel_inputs(h);
+  SA_TRY(vh_build<double>(al, in.data(), nlev, h->opt.cheb_degree, h->W.p, h->WT.p, &h->v64));
+  if (h->opt.precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
+  return SA_OK;
+}
+
+static int load_impl(const unsigned char* buf, uint64_t bytes, sa_handle h) {
+  Alloc& al = h->al;
+  cudaStream_t s = al.stream;
+  auto t0 = std::chrono::steady_clock::now();
+  StoreHeader H;
+  memcpy(&H, buf, sizeof(H));
+  const unsigned char* p = buf + sizeof(H);
+  const unsigned char* end = buf + bytes;
+  h->dim = H.dim;
+  h->n = H.n;
+  Buf<int> err;
+  SA_TRY(err.alloc(&al, 1));
+  SA_TRY(memset_d(err.p, 0, sizeof(int), s));
+  auto take = [&](void* dst, uint64_t nb) -> bool {
+    if ((uint64_t)(end - p) < pad8(nb)) return false;
+    if (dst) memcpy(dst, p, nb);
+    p += pad8(nb);
+    return true;
+  };
+  auto up = [&](auto& B, int64_t count) -> int {
+    using T = typename std::remove_reference<decltype(*B.p)>::type;
+    const uint64_t nb = sizeof(T) * (uint64_t)count;
+    if ((uint64_t)(end - p) < pad8(nb)) return SA_ERR_INVALID_ARG;
+    SA_TRY(upload(al, B, reinterpret_cast<const T*>(p), count));
+    p += pad8(nb);
+    return SA_OK;
+  };
+  int64_t expect_n = H.n;
+  for (int l = 0; l < H.nlev; ++l) {
+    const bool last = l + 1 == H.nlev;
+    StoreLevel d;
+    if (!take(&d, sizeof(d))) return SA_ERR_INVALID_ARG;
+    if (d.n != expect_n || d.n <= 0 || d.n >= (int64_t)0x7fffffff || d.nnz < d.n || d.nnz_gc < 0 ||
+        (!last && (d.nc <= 0 || d.nc >= d.n || d.nnzP < 0)) || (last && (d.nc != 0 || d.nnzP != 0)))
+      return SA_ERR_INVALID_ARG;
+    std::unique_ptr<Level> L(new Level());
+    L->n = d.n; L->nnz = d.nnz; L->nnz_gc = d.nnz_gc;
+    L->omega = d.omega; L->lam_omega = d.lam_omega; L->lmax = d.lmax; L->lmin = d.lmin;
+    SA_TRY(up(L->rp, d.n + 1));
+    SA_TRY(up(L->ci, d.nnz));
+    SA_TRY(up(L->v, d.nnz));
+    SA_TRY(up(L->diag, d.n));
+    SA_TRY(launch_validate_csr(s, d.n, d.n, d.nnz, L->rp.p, L->ci.p, err.p));
+    if (!last) {
+      L->nc = d.nc; L->nnzP = d.nnzP;
+      SA_TRY(up(L->Prp, d.n + 1));
+      SA_TRY(up(L->Pci, d.nnzP));
+      SA_TRY(up(L->Pv, d.nnzP));
+      SA_TRY(up(L->Rrp, d.nc + 1));
+      SA_TRY(up(L->Rci, d.nnzP));
+      SA_TRY(up(L->Rv, d.nnzP));
+      SA_TRY(up(L->agg, d.n));
+      SA_TRY(launch_validate_csr(s, d.n, d.nc, d.nnzP, L->Prp.p, L->Pci.p, err.p));
+      SA_TRY(launch_validate_csr(s, d.nc, d.n, d.nnzP, L->Rrp.p, L->Rci.p, err.p));
+      expect_n = d.nc;
+    }
+    h->lev.push_back(std::move(L));
+  }
+  if (p != end) return SA_ERR_INVALID_ARG;
+  int e0 = 0;
+  SA_TRY(copy_d2h(&e0, err.p, sizeof(int), s));
+  if (e0) {
+    set_error_text("stored hierarchy has invalid row pointers or column indices");
+    return SA_ERR_INVALID_ARG;
+  }
+  if (h->lev.back()->n > 16384) return SA_ERR_INVALID_ARG;
+  SA_TRY(finish_loaded(h));
+  SA_CUDA(cudaStreamSynchronize(s));
+  h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return SA_OK;
+}
+
+}  // namespace sa
+
+extern "C" {
+
+int sa_serialized_size(sa_handle h, uint64_t* bytes) {
+  if (!h || !bytes) return SA_ERR_INVALID_ARG;
+  *bytes = sa::store_size(h);
+  return SA_OK;
+}
+
+int sa_serialize(sa_handle h, void* buf, uint64_t bytes) {
+  if (!h || !buf) return SA_ERR_INVALID_ARG;
+  const uint64_t need = sa::store_size(h);
+  if (bytes < need) {
+    sa::set_error_text("buffer smaller than sa_serialized_size");
+    return SA_ERR_INVALID_ARG;
+  }
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  cudaStream_t s = h->al.stream;
+  StoreHeader H;
+  memset(&H, 0, sizeof(H));
+  memcpy(H.magic, kStoreMagic, 8);
+  H.version = kStoreVersion;
+  H.order = kStoreOrder;
+  H.dim = h->dim;
+  H.nlev = (int32_t)h->lev.size();
+  H.n = h->n;
+  H.theta = h->opt.theta; H.cheb_ratio = h->opt.cheb_ratio; H.cheb_boost = h->opt.cheb_boost;
+  H.omega_sym = h->opt.omega_sym;
+  H.measure = (int32_t)h->opt.measure; H.drop = (int32_t)h->opt.drop; H.max_coarse = h->opt.max_coarse;
+  H.max_levels = h->opt.max_levels; H.cheb_degree = h->opt.cheb_degree; H.power_iters = h->opt.power_iters;
+  H.seed = h->opt.seed;
+  H.payload = need - sizeof(H);
+  uint64_t o = sizeof(H);
+  memset(out + o, 0, (size_t)H.payload);  // padding bytes are part of the checksum
+  auto put = [&](const void* src, uint64_t nb, bool dev) -> int {
+    if (nb) {
+      if (dev) SA_CUDA(cudaMemcpyAsync(out + o, src, (size_t)nb, cudaMemcpyDeviceToHost, s));
+      else memcpy(out + o, src, (size_t)nb);
+    }
+    o += pad8(nb);
+    return SA_OK;
+  };
+  for (int l = 0; l < H.nlev; ++l) {
+    const bool last = l + 1 == H.nlev;
+    const sa::Level& L = *h->lev[l];
+    const StoreLevel d = store_level_of(L, last);
+    SA_TRY(put(&d, sizeof(d), false));
+    SA_TRY(put(L.rp.p, 8ull * (uint64_t)(L.n + 1), true));
+    SA_TRY(put(L.ci.p, 4ull * (uint64_t)L.nnz, true));
+    SA_TRY(put(L.v.p, 8ull * (uint64_t)L.nnz, true));
+    SA_TRY(put(L.diag.p, 8ull * (uint64_t)L.n, true));
+    if (!last) {
+      SA_TRY(put(L.Prp.p, 8ull * (uint64_t)(L.n + 1), true));
+      SA_TRY(put(L.Pci.p, 4ull * (uint64_t)L.nnzP, true));
+      SA_TRY(put(L.Pv.p, 8ull * (uint64_t)L.nnzP, true));
+      SA_TRY(put(L.Rrp.p, 8ull * (uint64_t)(L.nc + 1), true));
+      SA_TRY(put(L.Rci.p, 4ull * (uint64_t)L.nnzP, true));
+      SA_TRY(put(L.Rv.p, 8ull * (uint64_t)L.nnzP, true));
+      SA_TRY(put(L.agg.p, 4ull * (uint64_t)L.n, true));
+    }
+  }
+  SA_CUDA(cudaStreamSynchronize(s));
+  H.checksum = store_checksum(out + sizeof(H), H.payload);
+  memcpy(out, &H, sizeof(H));
+  return SA_OK;
+}
+
+int sa_deserialize(const void* buf, uint64_t bytes, const sa_options* opt, sa_handle* out) {
+  if (!out) return SA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!buf || !opt || bytes < sizeof(StoreHeader)) return SA_ERR_INVALID_ARG;
+  if ((int)opt->precision < 0 || (int)opt->precision > 1 || opt->maxit < 1) return SA_ERR_INVALID_ARG;
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  StoreHeader H;
+  memcpy(&H, in, sizeof(H));
+  if (memcmp(H.magic, kStoreMagic, 8) != 0 || H.version != kStoreVersion || H.order != kStoreOrder ||
+      (H.dim != 2 && H.dim != 3) || H.nlev < 1 || H.nlev > 32 || H.payload != bytes - sizeof(H) ||
+      H.cheb_degree < 1 || H.payload % 8 != 0) {
+    sa::set_error_text("not a stored hierarchy of this version");
+    return SA_ERR_INVALID_ARG;
+  }
+  if (store_checksum(in + sizeof(H), H.payload) != H.checksum) {
+    sa::set_error_text("stored hierarchy checksum mismatch");
+    return SA_ERR_INVALID_ARG;
+  }
+  sa_handle h = new (std::nothrow) sa_handle_s();
+  if (!h) return SA_ERR_OOM;
+  h->opt = *opt;
+  h->opt.theta = H.theta; h->opt.cheb_ratio = H.cheb_ratio; h->opt.cheb_boost = H.cheb_boost;
+  h->opt.omega_sym = H.omega_sym; h->opt.measure = (sa_measure)H.measure; h->opt.drop = (sa_drop)H.drop;
+  h->opt.max_coarse = H.max_coarse; h->opt.max_levels = H.max_levels; h->opt.cheb_degree = H.cheb_degree;
+  h->opt.power_iters = H.power_iters; h->opt.seed = H.seed; h->opt.keep_setup_data = 0;
+  h->al.stream = (cudaStream_t)opt->stream;
+  h->al.fn_alloc = opt->alloc;
+  h->al.fn_free = opt->dealloc;
+  h->al.ctx = opt->alloc_ctx;
+  if (cudaMallocHost(&h->host_pin, 64) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return SA_ERR_OOM;
+  }
+  int st = sa::load_impl(in, bytes, h);
+  if (st != SA_OK) {
+    cudaStreamSynchronize(h->al.stream);
+    sa_free(h);
+    return st;
+  }
+  *out = h;
+  return SA_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 int sa_free(sa_handle h) {
   if (!h) return SA_OK;

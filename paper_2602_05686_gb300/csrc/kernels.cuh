@@ -6,7 +6,10 @@
 namespace sa {
 
 // ---- setup_exact.cu --------------------------------------------------------
-int launch_validate_csr(cudaStream_t s, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, int* err);
+// rows sorted, strictly ascending columns in [0, ncols), row pointers from 0
+// to nnz; any violation ORs 32 into *err
+int launch_validate_csr(cudaStream_t s, int64_t n, int64_t ncols, int64_t nnz, const int64_t* rp, const int32_t* ci,
+                        int* err);
 int launch_dirichlet_diag(cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                           uint8_t* dir, double* diag, int* err);
 int launch_nodal_tensors(Alloc& al, int dim, int64_t n, int tloc, const double* tensors, int64_t ne, int npe,
@@ -16,6 +19,11 @@ int launch_strength_classical(cudaStream_t s, int64_t n, const int64_t* rp, cons
 int launch_strength_material(cudaStream_t s, int dim, int64_t n, const int64_t* rp, const int32_t* ci,
                              const double* x, const double* sinv, const uint8_t* dir, double theta, double* w,
                              double* D, uint8_t* keep, int64_t* cnt);
+// cut-drop (replaces the pointwise mask in keep and the counts in cnt[i+1]);
+// classical reads v/diag, material reads w/D
+int launch_cut_drop(Alloc& al, int measure_classical, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci,
+                    const double* v, const double* diag, const double* w, const double* D, const uint8_t* dir,
+                    double theta, uint8_t* keep, int64_t* cnt);
 int launch_filter(cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                   const uint8_t* keep, const int64_t* rpF, int32_t* ciF, double* vF, double* Dt);
 int launch_coarse_aux(cudaStream_t s, int64_t nc, int dim, const int64_t* mrp, const int32_t* mlist,
@@ -45,10 +53,13 @@ int run_transpose(Alloc& al, int64_t n, int64_t m, const int64_t* rp, const int3
 // ---- spgemm.cu -------------------------------------------------------------
 // C = A * B (n x k times k x m) by count / fill with per-warp shared hash
 // tables; rows of C have ascending columns and each entry accumulates its
-// products in ascending A-column order (Gustavson order).
-int run_spgemm(Alloc& al, int64_t n, int64_t m, const int64_t* Arp, const int32_t* Aci, const double* Av,
-               const int64_t* Brp, const int32_t* Bci, const double* Bv, Buf<int64_t>& Crp, Buf<int32_t>& Cci,
-               Buf<double>& Cv, int64_t* nnzC);
+// products in ascending A-column order (Gustavson order).  upper_only: the
+// warp path leaves entries left of the diagonal at 0 (for a symmetric result
+// whose lower triangle is mirrored from the upper one afterwards).  A is
+// n x kdim, B is kdim x m.
+int run_spgemm(Alloc& al, int64_t n, int64_t m, int64_t kdim, const int64_t* Arp, const int32_t* Aci,
+               const double* Av, const int64_t* Brp, const int32_t* Bci, const double* Bv, Buf<int64_t>& Crp,
+               Buf<int32_t>& Cci, Buf<double>& Cv, int64_t* nnzC, int upper_only = 0);
 // lower triangle takes the value of the mirrored upper-triangle entry
 int launch_symmetrize(cudaStream_t s, int64_t n, const int64_t* rp, const int32_t* ci, double* v, int* err);
 

@@ -35,7 +35,9 @@ enum ProfKind {
   PK_S_CHEB = 24,      // a15 Chebyshev bounds
   PK_S_DENSE = 25,     // a15 coarse Cholesky + inverse factor
   PK_S_SELL = 26,      // a15 SELL packing of the scaled hierarchy
-  PK_NKINDS = 27
+  PK_S_RAP_AP = 27,    // part of PK_S_RAP: the product A P
+  PK_S_RAP_RAP = 28,   // part of PK_S_RAP: R (A P) and the mirror of its upper triangle
+  PK_NKINDS = 29
 };
 
 bool prof_on();

@@ -46,7 +46,7 @@ __global__ void k_dirichlet_diag(int64_t n, const int64_t* __restrict__ rp, cons
 
 // input check of the level-0 CSR: row pointers monotone from 0 to nnz,
 // columns in [0, n) and strictly ascending in each row.  err bit 32.
-__global__ void k_validate_csr(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+__global__ void k_validate_csr(int64_t n, int64_t ncols, int64_t nnz, const int64_t* __restrict__ rp,
                                const int32_t* __restrict__ ci, int* __restrict__ err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -58,7 +58,7 @@ __global__ void k_validate_csr(int64_t n, int64_t nnz, const int64_t* __restrict
   int32_t prev = -1;
   for (int64_t p = b; p < e; ++p) {
     int32_t j = ci[p];
-    if (j <= prev || j < 0 || (int64_t)j >= n) { atomicOr(err, 32); return; }
+    if (j <= prev || j < 0 || (int64_t)j >= ncols) { atomicOr(err, 32); return; }
     prev = j;
   }
 }
@@ -281,6 +281,159 @@ __global__ void k_material_keep(int64_t n, const int64_t* __restrict__ rp, const
 }
 
 // ---------------------------------------------------------------------------
+// Cut-drop criterion (Sec. 2.1, Eq. C^cut-drop) on squared strengths:
+// classical s2 = a_ij^2 / |a_ii a_jj|, material s2 = w_ij^2 / (D_i D_j).
+// Per row the off-diagonal strengths are ordered descending; the first k with
+// theta^2 s2_k >= s2_{k+1} gives the threshold s2_k (no such k: keep all);
+// an edge survives when both of its rows keep it.
+// ---------------------------------------------------------------------------
+__global__ void k_s2_classical(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ v, const double* __restrict__ diag,
+                               double* __restrict__ s2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double di = diag[i];
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    int32_t j = ci[p];
+    s2[p] = (j == (int32_t)i) ? 0.0 : (v[p] * v[p]) / fabs(di * diag[j]);
+  }
+}
+
+__global__ void k_s2_material(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const double* __restrict__ w, const double* __restrict__ D, double* __restrict__ s2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double Di = D[i];
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    int32_t j = ci[p];
+    s2[p] = (j == (int32_t)i) ? 0.0 : (w[p] * w[p]) / (Di * D[j]);
+  }
+}
+
+constexpr int CUT_CAP = 256;   // row entries sorted in shared memory
+constexpr int CUT_WARPS = 4;
+
+// serial threshold for rows longer than CUT_CAP: walk the distinct values in
+// descending order (ties form pairs of equal neighbours in the ordering)
+__device__ double cut_threshold_serial(const int64_t b, const int64_t e, const int32_t* __restrict__ ci, int64_t i,
+                                       const uint8_t* __restrict__ dir, const double* __restrict__ s2, double t2) {
+  const bool diri = dir && dir[i];
+  double cur = INFINITY, last = 0.0;
+  bool any = false;
+  for (;;) {
+    double nxt = -1.0;
+    int mult = 0;
+    for (int64_t p = b; p < e; ++p) {
+      int32_t j = ci[p];
+      if (j == (int32_t)i || diri || (dir && dir[j])) continue;
+      double x = s2[p];
+      if (x < cur) {
+        if (x > nxt) { nxt = x; mult = 1; }
+        else if (x == nxt) ++mult;
+      }
+    }
+    if (nxt < 0.0) return any ? last : 0.0;  // values exhausted: no gap, keep all
+    if (any && t2 * last >= nxt) return last;
+    if (mult >= 2 && t2 * nxt >= nxt) return nxt;
+    any = true;
+    last = nxt;
+    cur = nxt;
+  }
+}
+
+__global__ void __launch_bounds__(CUT_WARPS * 32)
+k_cut_rows(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+           const uint8_t* __restrict__ dir, const double* __restrict__ s2, double t2,
+           uint8_t* __restrict__ rowkeep) {
+  __shared__ double vals_all[CUT_WARPS][CUT_CAP];
+  __shared__ double srt_all[CUT_WARPS][CUT_CAP];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  double* vals = vals_all[w];
+  double* srt = srt_all[w];
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    const bool diri = dir && dir[i];
+    // collect the row's valid strengths in column order
+    int m = 0;
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+      int64_t p = p0 + lane;
+      bool ok = false;
+      double x = 0.0;
+      if (p < e) {
+        int32_t j = ci[p];
+        ok = j != (int32_t)i && !diri && !(dir && dir[j]);
+        x = s2[p];
+      }
+      unsigned bm = __ballot_sync(FULL, ok);
+      if (ok && m + __popc(bm & lt) < CUT_CAP) vals[m + __popc(bm & lt)] = x;
+      m += __popc(bm);
+    }
+    __syncwarp();
+    double thr = 0.0;
+    if (m > CUT_CAP) {
+      if (lane == 0) thr = cut_threshold_serial(b, e, ci, i, dir, s2, t2);
+      thr = __shfl_sync(FULL, thr, 0);
+    } else if (m > 0) {
+      // rank sort, descending (ties by position)
+      for (int t = lane; t < m; t += 32) {
+        const double x = vals[t];
+        int r = 0;
+        for (int u = 0; u < m; ++u) r += (vals[u] > x) || (vals[u] == x && u < t);
+        srt[r] = x;
+      }
+      __syncwarp();
+      thr = srt[m - 1];
+      for (int k0 = 0; k0 < m - 1; k0 += 32) {
+        const int k = k0 + lane;
+        const bool gap = k < m - 1 && t2 * srt[k] >= srt[k + 1];
+        const unsigned gm = __ballot_sync(FULL, gap);
+        if (gm) {
+          thr = srt[k0 + __ffs(gm) - 1];
+          break;
+        }
+      }
+    }
+    for (int64_t p = b + lane; p < e; p += 32) {
+      int32_t j = ci[p];
+      bool ok = j != (int32_t)i && !diri && !(dir && dir[j]);
+      rowkeep[p] = (ok && m > 0 && s2[p] >= thr) ? 1 : 0;
+    }
+    __syncwarp();
+  }
+}
+
+// keep = diagonal, or kept by both rows; counts kept entries into cnt[i+1]
+__global__ void k_cut_symmetrize(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const uint8_t* __restrict__ rowkeep, uint8_t* __restrict__ keep,
+                                 int64_t* __restrict__ cnt) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    int kept = 0;
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+      int32_t j = ci[p];
+      uint8_t k;
+      if (j == (int32_t)i) k = 1;
+      else if (!rowkeep[p]) k = 0;
+      else {
+        int64_t lo = rp[j], hi = rp[j + 1] - 1, f = -1;
+        while (lo <= hi) {
+          int64_t mid = (lo + hi) >> 1;
+          int32_t c = ci[mid];
+          if (c == (int32_t)i) { f = mid; break; }
+          if (c < (int32_t)i) lo = mid + 1; else hi = mid - 1;
+        }
+        k = (f >= 0 && rowkeep[f]) ? 1 : 0;
+      }
+      keep[p] = k;
+      kept += k;
+    }
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
+    if (lane == 0) cnt[i + 1] = kept;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // a10. filtered matrix A_F and 1-norm diagonal (Sec. 2.2, Eqs.
 // filtered_matrix and 1_norm_diagonal).  rpF is the scan of
 // the kept counts.  A row whose filtered 1-norm is <= 1e-12 times the 1-norm
@@ -381,9 +534,10 @@ int launch_dirichlet_diag(cudaStream_t s, int64_t n, const int64_t* rp, const in
   return SA_OK;
 }
 
-int launch_validate_csr(cudaStream_t s, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, int* err) {
+int launch_validate_csr(cudaStream_t s, int64_t n, int64_t ncols, int64_t nnz, const int64_t* rp, const int32_t* ci,
+                        int* err) {
   if (n <= 0) return SA_OK;
-  k_validate_csr<<<blocks_for(n, 256), 256, 0, s>>>(n, nnz, rp, ci, err);
+  k_validate_csr<<<blocks_for(n, 256), 256, 0, s>>>(n, ncols, nnz, rp, ci, err);
   SA_LAUNCHED();
   return SA_OK;
 }
@@ -436,6 +590,26 @@ int launch_strength_material(cudaStream_t s, int dim, int64_t n, const int64_t* 
   k_row_sum_ordered<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, w, D);
   SA_LAUNCHED();
   k_material_keep<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, w, D, dir, t2, keep, cnt);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_cut_drop(Alloc& al, int measure_classical, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci,
+                    const double* v, const double* diag, const double* w, const double* D, const uint8_t* dir,
+                    double theta, uint8_t* keep, int64_t* cnt) {
+  cudaStream_t s = al.stream;
+  if (n <= 0) return SA_OK;
+  Buf<double> s2;
+  Buf<uint8_t> rowkeep;
+  SA_TRY(s2.alloc(&al, nnz));
+  SA_TRY(rowkeep.alloc(&al, nnz));
+  if (measure_classical) k_s2_classical<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, v, diag, s2.p);
+  else k_s2_material<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, w, D, s2.p);
+  SA_LAUNCHED();
+  const double t2 = theta * theta;
+  k_cut_rows<<<warp_rows_grid(n, CUT_WARPS * 32), CUT_WARPS * 32, 0, s>>>(n, rp, ci, dir, s2.p, t2, rowkeep.p);
+  SA_LAUNCHED();
+  k_cut_symmetrize<<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, rowkeep.p, keep, cnt);
   SA_LAUNCHED();
   return SA_OK;
 }

@@ -19,20 +19,21 @@ namespace sa {
   const int sl = (int)(gt % SW);                                        \
   const bool valid = i < n;
 
-// power method product: w_i = s_i * sum_p a_p (s_j v_j), v_j = X_j / sc[2]
-// (the previous product divided by its norm; sc[2] = 1 for the start vector)
+// power method product: w_i = s_i * sum_p a_p (s_j v_j), v_j = X_j * sc[4]
+// (the previous product times the reciprocal of its norm; 1 for the start
+// vector) -- one reciprocal per step instead of a division per entry
 template <int SW>
 __global__ void k_power_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                              const double* __restrict__ v, const double* __restrict__ s, const double* __restrict__ X,
                              const double* __restrict__ sc, double* __restrict__ w) {
   ROW_SETUP(SW)
-  const double nrm = sc[2];
+  const double inv = sc[4];
   double acc = 0.0;
   if (valid) {
     const int64_t e = rp[i + 1];
     for (int64_t p = rp[i] + sl; p < e; p += SW) {
       int32_t j = ci[p];
-      acc += v[p] * (s[j] * (X[j] / nrm));
+      acc += v[p] * (s[j] * (X[j] * inv));
     }
   }
 #pragma unroll
@@ -121,21 +122,21 @@ __global__ void k_start_vector(int64_t n, uint32_t tag, uint32_t seed, double* _
   }
 }
 
-// partial sums of w.w and v.v with v_j = X_j / sc[2]
+// partial sums of w.w and v.v with v_j = X_j * sc[4]
 __global__ void k_power_dots(int64_t n, const double* __restrict__ w, const double* __restrict__ X,
                              const double* __restrict__ sc, double* __restrict__ part) {
-  const double nrm = sc[2];
+  const double inv = sc[4];
   double acc[3] = {0.0, 0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double vi = X[i] / nrm;
+    const double vi = X[i] * inv;
     acc[0] += w[i] * w[i];
     acc[1] += vi * vi;
   }
   block_sum_to<3>(acc, part, RED_BLOCKS);
 }
 
-// one CTA: sums the partials in index order, then lam = ||w|| / ||v|| and
-// sc[2] = ||w|| (the divisor of the next iterate).  A zero product (every
+// one CTA: sums the partials in index order, then lam = ||w|| / ||v||,
+// sc[2] = ||w|| and sc[4] = 1 / ||w|| (the scale of the next iterate).  A zero product (every
 // row unscaled) gives lam = 0 and stops the iteration (sc[3] = 1).
 __global__ void k_power_finish(const double* __restrict__ part, double* __restrict__ sc, double* __restrict__ lam) {
   double acc[3] = {0.0, 0.0, 0.0};
@@ -161,6 +162,7 @@ __global__ void k_power_finish(const double* __restrict__ part, double* __restri
     }
     *lam = nw2 / sqrt(vv);
     sc[2] = nw2;
+    sc[4] = 1.0 / nw2;
   }
 }
 
@@ -215,8 +217,8 @@ int run_power(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const 
   SA_TRY(x.alloc(&al, n));
   SA_TRY(w.alloc(&al, n));
   SA_TRY(part.alloc(&al, 3 * RED_BLOCKS));
-  SA_TRY(sc.alloc(&al, 4));
-  const double init[4] = {0.0, 0.0, 1.0, 0.0};
+  SA_TRY(sc.alloc(&al, 5));
+  const double init[5] = {0.0, 0.0, 1.0, 0.0, 1.0};
   SA_CUDA(cudaMemcpyAsync(sc.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
   int64_t nnz = 0;
   SA_TRY(copy_d2h(&nnz, rp + n, sizeof(int64_t), st));

@@ -1,7 +1,10 @@
 // Two-phase (count, then fill) sparse matrix product C = A B used for the
 // smoothed prolongator (A_F P^, Sec. 2.2) and the Galerkin product (R (A P),
-// Sec. 2).  One warp per row of A with an open-addressing hash table of
-// column indices in shared memory.  The fill phase sorts the row's columns
+// Sec. 2).  Three tiers by the row's distinct column count: one thread per
+// row with a sorted column list in shared memory (narrow products, e.g. the
+// aggregation prolongators with one to a few entries per row), then one warp
+// per row with an open-addressing hash table of column indices in shared
+// memory.  The fill phase sorts the row's columns
 // and accumulates each entry's products in ascending order of the A column
 // (the order of Gustavson's row algorithm), with separately rounded multiply
 // and add, so the values do not depend on scheduling.  Rows whose distinct
@@ -70,14 +73,15 @@ __device__ int warp_build_row(int64_t i, const int64_t* __restrict__ Arp, const 
 }
 
 __global__ void __launch_bounds__(SG_WARPS * 32)
-k_spgemm_count(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
-               const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci, int64_t* __restrict__ cnt,
-               int32_t* __restrict__ big, unsigned long long* __restrict__ nbig) {
+k_spgemm_count(int64_t n, const int32_t* __restrict__ rows, const int64_t* __restrict__ Arp,
+               const int32_t* __restrict__ Aci, const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci,
+               int64_t* __restrict__ cnt, int32_t* __restrict__ big, unsigned long long* __restrict__ nbig) {
   __shared__ int32_t keys_all[SG_WARPS][HB];
   __shared__ int wcount_all[SG_WARPS];
   const int w = threadIdx.x >> 5;
   int32_t* keys = keys_all[w];
-  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+  for (int64_t t = global_warp(); t < n; t += warp_stride()) {
+    const int64_t i = rows ? rows[t] : t;  // rows: the rows the thread tier could not hold
     int c = warp_build_row(i, Arp, Aci, Brp, Bci, keys, &wcount_all[w]);
     if (lane_id() == 0) {
       if (c < 0) {
@@ -93,10 +97,10 @@ k_spgemm_count(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __rest
 }
 
 __global__ void __launch_bounds__(SG_WARPS * 32)
-k_spgemm_fill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
-              const double* __restrict__ Av, const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci,
-              const double* __restrict__ Bv, const int64_t* __restrict__ Crp, int32_t* __restrict__ Cci,
-              double* __restrict__ Cv, const uint8_t* __restrict__ isbig) {
+k_spgemm_fill(int64_t n, const int32_t* __restrict__ rows, const int64_t* __restrict__ Arp,
+              const int32_t* __restrict__ Aci, const double* __restrict__ Av, const int64_t* __restrict__ Brp,
+              const int32_t* __restrict__ Bci, const double* __restrict__ Bv, const int64_t* __restrict__ Crp,
+              int32_t* __restrict__ Cci, double* __restrict__ Cv, const uint8_t* __restrict__ isbig, int upper_only) {
   __shared__ int32_t keys_all[SG_WARPS][HB];
   __shared__ int32_t rank_all[SG_WARPS][HB];
   __shared__ int32_t cols_all[SG_WARPS][HCAP];
@@ -107,7 +111,8 @@ k_spgemm_fill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restr
   int32_t* rank_of = rank_all[w];
   int32_t* cols = cols_all[w];
   double* acc = acc_all[w];
-  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+  for (int64_t t = global_warp(); t < n; t += warp_stride()) {
+    const int64_t i = rows ? rows[t] : t;
     if (isbig[i]) continue;  // warp-uniform
     const int c = warp_build_row(i, Arp, Aci, Brp, Bci, keys, &wcount_all[w]);
     if (c <= 0) continue;
@@ -141,14 +146,19 @@ k_spgemm_fill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restr
     for (int t = lane; t < c; t += 32) acc[t] = 0.0;
     __syncwarp();
     // ordered accumulation: A columns in ascending order, lanes over the B
-    // row (distinct columns, so no two lanes touch one accumulator per step)
+    // row (distinct columns, so no two lanes touch one accumulator per step).
+    // upper_only: entries left of the diagonal stay 0 (the caller mirrors
+    // the upper triangle into them)
     const int64_t b = Arp[i], e = Arp[i + 1];
+    const int32_t jmin = upper_only ? (int32_t)i : INT32_MIN;
     for (int64_t p = b; p < e; ++p) {
       const int32_t k = Aci[p];
       const double a = Av[p];
       const int64_t qb = Brp[k], qe = Brp[k + 1];
       for (int64_t q = qb + lane; q < qe; q += 32) {
-        int h = hfind(keys, Bci[q]);
+        const int32_t j = Bci[q];
+        if (j < jmin) continue;
+        int h = hfind(keys, j);
         if (h >= 0) {  // always found: the keys were inserted from the same rows
           int r = rank_of[h];
           acc[r] = __dadd_rn(acc[r], __dmul_rn(a, Bv[q]));
@@ -158,6 +168,100 @@ k_spgemm_fill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restr
     }
     for (int t = lane; t < c; t += 32) Cv[cb + t] = acc[t];
     __syncwarp();
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// thread tier: one thread per row, its distinct columns kept sorted in a
+// private column of shared memory (element k of thread t at [k * TB + t]);
+// rows with more than TCAP distinct columns go to the warp tier
+// ---------------------------------------------------------------------------
+constexpr int TB = 128;
+constexpr int TCAP = 32;
+
+__device__ __forceinline__ int tlower(const int32_t* cols, int c, int32_t j) {
+  int lo = 0, hi = c;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cols[mid * TB] < j) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(TB)
+k_spgemm_tcount(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+                const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci, int64_t* __restrict__ cnt,
+                int32_t* __restrict__ mid, unsigned long long* __restrict__ nmid) {
+  __shared__ int32_t cols_all[TCAP * TB];
+  int32_t* cols = cols_all + threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  bool over = false;
+  const int64_t e = Arp[i + 1];
+  for (int64_t p = Arp[i]; p < e && !over; ++p) {
+    const int32_t k = Aci[p];
+    const int64_t qe = Brp[k + 1];
+    for (int64_t q = Brp[k]; q < qe; ++q) {
+      const int32_t j = Bci[q];
+      const int pos = tlower(cols, c, j);
+      if (pos < c && cols[pos * TB] == j) continue;
+      if (c == TCAP) { over = true; break; }
+      for (int t = c; t > pos; --t) cols[t * TB] = cols[(t - 1) * TB];
+      cols[pos * TB] = j;
+      ++c;
+    }
+  }
+  if (over) {
+    const unsigned long long slot = atomicAdd(nmid, 1ull);
+    mid[slot] = (int32_t)i;
+    cnt[i + 1] = 0;  // set by the warp tier
+  } else {
+    cnt[i + 1] = c;
+  }
+}
+
+// same insertion order as the count; each entry starts at 0 and adds its
+// products in ascending A-column order (Gustavson order), like the warp tier
+__global__ void __launch_bounds__(TB)
+k_spgemm_tfill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+               const double* __restrict__ Av, const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci,
+               const double* __restrict__ Bv, const int64_t* __restrict__ Crp, int32_t* __restrict__ Cci,
+               double* __restrict__ Cv, const uint8_t* __restrict__ ismid, int upper_only) {
+  __shared__ int32_t cols_all[TCAP * TB];
+  __shared__ double vals_all[TCAP * TB];
+  int32_t* cols = cols_all + threadIdx.x;
+  double* vals = vals_all + threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+  if (i >= n || ismid[i]) return;
+  const int32_t jmin = upper_only ? (int32_t)i : INT32_MIN;
+  int c = 0;
+  const int64_t e = Arp[i + 1];
+  for (int64_t p = Arp[i]; p < e; ++p) {
+    const int32_t k = Aci[p];
+    const double a = Av[p];
+    const int64_t qe = Brp[k + 1];
+    for (int64_t q = Brp[k]; q < qe; ++q) {
+      const int32_t j = Bci[q];
+      const int pos = tlower(cols, c, j);
+      if (!(pos < c && cols[pos * TB] == j)) {
+        if (c == TCAP) return;  // cannot happen: the count held this row
+        for (int t = c; t > pos; --t) {
+          cols[t * TB] = cols[(t - 1) * TB];
+          vals[t * TB] = vals[(t - 1) * TB];
+        }
+        cols[pos * TB] = j;
+        vals[pos * TB] = 0.0;
+        ++c;
+      }
+      if (j >= jmin) vals[pos * TB] = __dadd_rn(vals[pos * TB], __dmul_rn(a, Bv[q]));
+    }
+  }
+  const int64_t cb = Crp[i];
+  for (int t = 0; t < c; ++t) {
+    Cci[cb + t] = cols[t * TB];
+    Cv[cb + t] = vals[t * TB];
   }
 }
 
@@ -234,9 +338,9 @@ __global__ void k_mark_big(int64_t nbig, const int32_t* __restrict__ big, uint8_
   if (t < nbig) isbig[big[t]] = 1;
 }
 
-int run_spgemm(Alloc& al, int64_t n, int64_t m, const int64_t* Arp, const int32_t* Aci, const double* Av,
-               const int64_t* Brp, const int32_t* Bci, const double* Bv, Buf<int64_t>& Crp, Buf<int32_t>& Cci,
-               Buf<double>& Cv, int64_t* nnzC) {
+int run_spgemm(Alloc& al, int64_t n, int64_t m, int64_t kdim, const int64_t* Arp, const int32_t* Aci,
+               const double* Av, const int64_t* Brp, const int32_t* Bci, const double* Bv, Buf<int64_t>& Crp,
+               Buf<int32_t>& Cci, Buf<double>& Cv, int64_t* nnzC, int upper_only) {
   cudaStream_t s = al.stream;
   SA_TRY(Crp.alloc(&al, n + 1));
   SA_TRY(memset_d(Crp.p, 0, Crp.bytes(), s));
@@ -246,19 +350,46 @@ int run_spgemm(Alloc& al, int64_t n, int64_t m, const int64_t* Arp, const int32_
     SA_TRY(Cv.alloc(&al, 0));
     return SA_OK;
   }
-  Buf<int32_t> big;
-  Buf<unsigned long long> nbig_d;
-  Buf<uint8_t> isbig;
+  // tier choice by the expected products per row, (nnz(A)/n) (nnz(B)/kdim):
+  // narrow products start on the thread tier
+  int64_t nnzA = 0, nnzB = 0;
+  SA_TRY(copy_d2h(&nnzA, Arp + n, sizeof(int64_t), s));
+  if (kdim > 0) SA_TRY(copy_d2h(&nnzB, Brp + kdim, sizeof(int64_t), s));
+  const bool thread_tier = kdim > 0 && ((double)nnzA / (double)n) * ((double)nnzB / (double)kdim) <= 96.0;
+  Buf<int32_t> big, midl;
+  Buf<unsigned long long> nbig_d, nmid_d;
+  Buf<uint8_t> isbig, ismid;
   SA_TRY(big.alloc(&al, n));
   SA_TRY(nbig_d.alloc(&al, 1));
   SA_TRY(isbig.alloc(&al, n));
   SA_TRY(memset_d(nbig_d.p, 0, sizeof(unsigned long long), s));
   SA_TRY(memset_d(isbig.p, 0, isbig.bytes(), s));
-  const unsigned grid = warp_rows_grid(n, SG_WARPS * 32);
-  k_spgemm_count<<<grid, SG_WARPS * 32, 0, s>>>(n, Arp, Aci, Brp, Bci, Crp.p, big.p, nbig_d.p);
-  SA_LAUNCHED();
+  int64_t nwarp = n;             // rows on the warp tier
+  const int32_t* wrows = nullptr;  // NULL: every row
+  if (thread_tier) {
+    SA_TRY(midl.alloc(&al, n));
+    SA_TRY(nmid_d.alloc(&al, 1));
+    SA_TRY(ismid.alloc(&al, n));
+    SA_TRY(memset_d(nmid_d.p, 0, sizeof(unsigned long long), s));
+    SA_TRY(memset_d(ismid.p, 0, ismid.bytes(), s));
+    k_spgemm_tcount<<<blocks_for(n, TB), TB, 0, s>>>(n, Arp, Aci, Brp, Bci, Crp.p, midl.p, nmid_d.p);
+    SA_LAUNCHED();
+    unsigned long long nmid = 0;
+    SA_TRY(copy_d2h(&nmid, nmid_d.p, sizeof(nmid), s));
+    nwarp = (int64_t)nmid;
+    wrows = midl.p;
+    if (nmid > 0) {
+      k_mark_big<<<blocks_for(nwarp, 256), 256, 0, s>>>(nwarp, midl.p, ismid.p);
+      SA_LAUNCHED();
+    }
+  }
+  if (nwarp > 0) {
+    k_spgemm_count<<<warp_rows_grid(nwarp, SG_WARPS * 32), SG_WARPS * 32, 0, s>>>(nwarp, wrows, Arp, Aci, Brp, Bci,
+                                                                                 Crp.p, big.p, nbig_d.p);
+    SA_LAUNCHED();
+  }
   unsigned long long nbig = 0;
-  SA_TRY(copy_d2h(&nbig, nbig_d.p, sizeof(nbig), s));
+  if (nwarp > 0) SA_TRY(copy_d2h(&nbig, nbig_d.p, sizeof(nbig), s));
   Buf<int32_t> stamp;
   Buf<double> dacc;
   unsigned gbig = 0;
@@ -277,8 +408,16 @@ int run_spgemm(Alloc& al, int64_t n, int64_t m, const int64_t* Arp, const int32_
   SA_TRY(copy_d2h(nnzC, Crp.p + n, sizeof(int64_t), s));
   SA_TRY(Cci.alloc(&al, *nnzC));
   SA_TRY(Cv.alloc(&al, *nnzC));
-  k_spgemm_fill<<<grid, SG_WARPS * 32, 0, s>>>(n, Arp, Aci, Av, Brp, Bci, Bv, Crp.p, Cci.p, Cv.p, isbig.p);
-  SA_LAUNCHED();
+  if (thread_tier) {
+    k_spgemm_tfill<<<blocks_for(n, TB), TB, 0, s>>>(n, Arp, Aci, Av, Brp, Bci, Bv, Crp.p, Cci.p, Cv.p, ismid.p,
+                                                    upper_only);
+    SA_LAUNCHED();
+  }
+  if (nwarp > 0) {
+    k_spgemm_fill<<<warp_rows_grid(nwarp, SG_WARPS * 32), SG_WARPS * 32, 0, s>>>(
+        nwarp, wrows, Arp, Aci, Av, Brp, Bci, Bv, Crp.p, Cci.p, Cv.p, isbig.p, upper_only);
+    SA_LAUNCHED();
+  }
   if (nbig > 0) {
     k_spgemm_big<<<gbig, BIG_THREADS, 0, s>>>(1, (int64_t)nbig, big.p, m, Arp, Aci, Av, Brp, Bci, Bv, nullptr,
                                                 Crp.p, Cci.p, Cv.p, stamp.p, dacc.p);

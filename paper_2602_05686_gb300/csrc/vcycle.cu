@@ -37,30 +37,65 @@ __global__ void k_slice_width(int64_t n, const int64_t* __restrict__ rp, int64_t
   sz[sl + 1] = w * 32;
 }
 
-// out = left_i * a_ij * right_j (left/right: sqrt(d) or 1/sqrt(d), NULL = 1);
+// out = left_i * a_ij * right_j with precomputed scale vectors (NULL = 1);
 // padding entries point at column 0 with value 0
 template <typename T>
 __global__ void k_sell_fill(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                             const double* __restrict__ v, const double* __restrict__ left,
-                            const double* __restrict__ right, int left_sqrt, int right_sqrt,
-                            const int64_t* __restrict__ sp, int32_t* __restrict__ oci, T* __restrict__ ov) {
+                            const double* __restrict__ right, const int64_t* __restrict__ sp,
+                            int32_t* __restrict__ oci, T* __restrict__ ov) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t sl = i / 32, r = i % 32;
   const int64_t base = sp[sl], width = (sp[sl + 1] - sp[sl]) / 32;
-  double li = 1.0;
-  if (left) li = left_sqrt ? sqrt(left[i]) : 1.0 / sqrt(left[i]);
+  const double li = left ? left[i] : 1.0;
   int64_t k = 0;
   for (int64_t p = rp[i]; p < rp[i + 1]; ++p, ++k) {
     int32_t j = ci[p];
-    double rj = 1.0;
-    if (right) rj = right_sqrt ? sqrt(right[j]) : 1.0 / sqrt(right[j]);
+    const double rj = right ? right[j] : 1.0;
     oci[base + k * 32 + r] = j;
     ov[base + k * 32 + r] = (T)(li * v[p] * rj);
   }
   for (; k < width; ++k) {
     oci[base + k * 32 + r] = 0;
     ov[base + k * 32 + r] = (T)0;
+  }
+}
+
+// per slice: smallest column and the span of the real (unpadded) entries;
+// one thread per row, the 32 rows of a slice form one warp
+__global__ void k_slice_span(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             int32_t* __restrict__ base, unsigned int* __restrict__ maxspan) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lo = 0x7fffffff, hi = -1;
+  if (r < n) {
+    const int64_t b = rp[r], e = rp[r + 1];
+    if (e > b) {  // columns ascend: first and last entry
+      lo = ci[b];
+      hi = ci[e - 1];
+    }
+  }
+  lo = __reduce_min_sync(FULL, lo);
+  hi = __reduce_max_sync(FULL, hi);
+  if ((threadIdx.x & 31) == 0 && r < n) {
+    if (hi < 0) lo = hi = 0;
+    base[r >> 5] = lo;
+    atomicMax(maxspan, (unsigned int)(hi - lo));
+  }
+}
+
+// 16-bit offsets from the slice base (padding: offset 0, value 0)
+__global__ void k_sell_compress(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                                const int32_t* __restrict__ base, uint16_t* __restrict__ c16) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t sl = i / 32, r = i % 32;
+  const int64_t b = sp[sl], width = (sp[sl + 1] - sp[sl]) / 32;
+  const int32_t bs = base[sl];
+  for (int64_t k = 0; k < width; ++k) {
+    const int64_t q = b + k * 32 + r;
+    int32_t c = ci[q] - bs;
+    c16[q] = (uint16_t)(c < 0 ? 0 : c);  // padding held column 0
   }
 }
 
@@ -71,7 +106,7 @@ __global__ void k_sqrt_vec(int64_t n, const double* __restrict__ d, double* __re
 
 template <typename T>
 int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
-               const double* left, int left_sqrt, const double* right, int right_sqrt, Sell<T>& S) {
+               const double* left, const double* right, Sell<T>& S) {
   cudaStream_t s = al.stream;
   S.n = n;
   S.nnz = nnz;
@@ -89,38 +124,50 @@ int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32
   SA_TRY(copy_d2h(&S.stored, S.sp.p + S.nslices, sizeof(int64_t), s));
   SA_TRY(S.ci.alloc(&al, S.stored));
   SA_TRY(S.v.alloc(&al, S.stored));
-  k_sell_fill<T><<<blocks_for(n, 256), 256, 0, s>>>(n, rp, ci, v, left, right, left_sqrt, right_sqrt, S.sp.p,
-                                                    S.ci.p, S.v.p);
+  k_sell_fill<T><<<blocks_for(n, 256), 256, 0, s>>>(n, rp, ci, v, left, right, S.sp.p, S.ci.p, S.v.p);
   SA_LAUNCHED();
+  // compress the columns when every slice spans less than 2^16 columns
+  Buf<unsigned int> span;
+  SA_TRY(span.alloc(&al, 1));
+  SA_TRY(memset_d(span.p, 0, sizeof(unsigned int), s));
+  SA_TRY(S.base.alloc(&al, S.nslices));
+  k_slice_span<<<blocks_for(n, 256), 256, 0, s>>>(n, rp, ci, S.base.p, span.p);
+  SA_LAUNCHED();
+  unsigned int h_span = 0;
+  SA_TRY(copy_d2h(&h_span, span.p, sizeof(h_span), s));
+  if (h_span < 65536u) {
+    SA_TRY(S.c16.alloc(&al, S.stored));
+    k_sell_compress<<<blocks_for(n, 256), 256, 0, s>>>(n, S.sp.p, S.ci.p, S.base.p, S.c16.p);
+    SA_LAUNCHED();
+    S.idx16 = 1;
+    S.ci.release();
+  } else {
+    S.base.release();
+  }
   return SA_OK;
 }
 
 template int build_sell<double>(Alloc&, int64_t, int64_t, const int64_t*, const int32_t*, const double*,
-                                const double*, int, const double*, int, Sell<double>&);
+                                const double*, const double*, Sell<double>&);
 template int build_sell<float>(Alloc&, int64_t, int64_t, const int64_t*, const int32_t*, const double*,
-                               const double*, int, const double*, int, Sell<float>&);
+                               const double*, const double*, Sell<float>&);
 
-// CSR copy with scaled values
+// CSR copy with scaled values (precomputed scale vectors, NULL = 1)
 template <typename T>
 __global__ void k_csr_scale(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                             const double* __restrict__ v, const double* __restrict__ left,
-                            const double* __restrict__ right, int left_sqrt, int right_sqrt, T* __restrict__ ov) {
+                            const double* __restrict__ right, T* __restrict__ ov) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double li = 1.0;
-  if (left) li = left_sqrt ? sqrt(left[i]) : 1.0 / sqrt(left[i]);
-  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-    double rj = 1.0;
-    if (right) rj = right_sqrt ? sqrt(right[ci[p]]) : 1.0 / sqrt(right[ci[p]]);
-    ov[p] = (T)(li * v[p] * rj);
-  }
+  const double li = left ? left[i] : 1.0;
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) ov[p] = (T)(li * v[p] * (right ? right[ci[p]] : 1.0));
 }
 
 // SELL-32 if it stores at most 25 % padding and rows average <= 40 entries,
 // else CSR with 4..32 lanes per row by average row length
 template <typename T>
 int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
-              const double* left, int left_sqrt, const double* right, int right_sqrt, Mat<T>& M) {
+              const double* left, const double* right, Mat<T>& M) {
   cudaStream_t s = al.stream;
   M.n = n;
   M.nnz = nnz;
@@ -138,7 +185,7 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
   }
   if (n == 0 || ((double)stored <= 1.25 * (double)nnz && avg <= 40.0)) {
     M.sw = 0;
-    return build_sell<T>(al, n, nnz, rp, ci, v, left, left_sqrt, right, right_sqrt, M.sell);
+    return build_sell<T>(al, n, nnz, rp, ci, v, left, right, M.sell);
   }
   M.sw = avg <= 12.0 ? 4 : (avg <= 40.0 ? 8 : (avg <= 96.0 ? 16 : 32));
   SA_TRY(M.rp.alloc(&al, n + 1));
@@ -146,7 +193,7 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
   SA_TRY(M.v.alloc(&al, nnz));
   SA_CUDA(cudaMemcpyAsync(M.rp.p, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
   if (nnz > 0) SA_CUDA(cudaMemcpyAsync(M.ci.p, ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s));
-  k_csr_scale<T><<<blocks_for(n, 256), 256, 0, s>>>(n, rp, ci, v, left, right, left_sqrt, right_sqrt, M.v.p);
+  k_csr_scale<T><<<blocks_for(n, 256), 256, 0, s>>>(n, rp, ci, v, left, right, M.v.p);
   SA_LAUNCHED();
   return SA_OK;
 }
@@ -160,6 +207,16 @@ int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const dou
   m->W = W;
   m->WT = WT;
   cudaStream_t s = al.stream;
+  // D_l^-1/2 and D_l^1/2 of every level, once (FP64 square roots are costly)
+  std::vector<Buf<double>> isq(nlev), sq(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    SA_TRY(isq[l].alloc(&al, in[l].n));
+    SA_TRY(sq[l].alloc(&al, in[l].n));
+    k_sqrt_vec<<<blocks_for(in[l].n, 256), 256, 0, s>>>(in[l].n, in[l].diag, isq[l].p, 1);
+    SA_LAUNCHED();
+    k_sqrt_vec<<<blocks_for(in[l].n, 256), 256, 0, s>>>(in[l].n, in[l].diag, sq[l].p, 0);
+    SA_LAUNCHED();
+  }
   for (int l = 0; l < nlev; ++l) {
     VLevel<T>* L = new VLevel<T>();
     m->lev.push_back(L);
@@ -174,14 +231,12 @@ int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const dou
     SA_TRY(L->r.alloc(&al, I.n));
     SA_TRY(L->d.alloc(&al, I.n));
     if (l + 1 < nlev) {
-      SA_TRY(build_mat<T>(al, I.n, I.nnz, I.rp, I.ci, I.v, I.diag, 0, I.diag, 0, L->A));
-      const double* dc = in[l + 1].diag;
-      SA_TRY(build_mat<T>(al, I.n, I.nnzP, I.Prp, I.Pci, I.Pv, I.diag, 1, dc, 0, L->P));
-      SA_TRY(build_mat<T>(al, I.nc, I.nnzP, I.Rrp, I.Rci, I.Rv, dc, 0, I.diag, 1, L->R));
+      // A~ = D^-1/2 A D^-1/2, P~ = D_l^1/2 P D_{l+1}^-1/2, R~ = D_{l+1}^-1/2 R D_l^1/2
+      SA_TRY(build_mat<T>(al, I.n, I.nnz, I.rp, I.ci, I.v, isq[l].p, isq[l].p, L->A));
+      SA_TRY(build_mat<T>(al, I.n, I.nnzP, I.Prp, I.Pci, I.Pv, sq[l].p, isq[l + 1].p, L->P));
+      SA_TRY(build_mat<T>(al, I.nc, I.nnzP, I.Rrp, I.Rci, I.Rv, isq[l + 1].p, sq[l].p, L->R));
     } else {
-      SA_TRY(L->sq.alloc(&al, I.n));
-      k_sqrt_vec<<<blocks_for(I.n, 256), 256, 0, s>>>(I.n, I.diag, L->sq.p, 0);
-      SA_LAUNCHED();
+      L->sq = std::move(sq[l]);
       SA_TRY(m->ct.alloc(&al, I.n));
       SA_TRY(m->cy.alloc(&al, I.n));
       SA_TRY(m->cx.alloc(&al, I.n));
@@ -211,20 +266,41 @@ __device__ __forceinline__ T sell_row(const int64_t* __restrict__ sp, const int3
   return acc;
 }
 
+// compressed columns: x[base[slice] + offset]
+template <typename T>
+__device__ __forceinline__ T sell_row16(const int64_t* __restrict__ sp, const int32_t* __restrict__ base,
+                                        const uint16_t* __restrict__ c16, const T* __restrict__ v,
+                                        const T* __restrict__ x, int64_t i) {
+  const int64_t sl = i >> 5, r = i & 31;
+  const int64_t b = sp[sl], e = sp[sl + 1];
+  const T* __restrict__ xs = x + base[sl];
+  T acc = (T)0;
+  for (int64_t p = b + r; p < e; p += 32) acc += v[p] * __ldg(&xs[c16[p]]);
+  return acc;
+}
+
 template <typename T>
 struct MatView {
   int64_t n;
   const int64_t* p;  // SELL slice offsets or CSR row pointers
   const int32_t* ci;
   const T* v;
+  const int32_t* base;   // compressed SELL columns (else NULL)
+  const uint16_t* c16;
 };
 
 template <typename T>
 static MatView<T> view(const Mat<T>& M) {
   MatView<T> m;
   m.n = M.n;
-  if (M.sw == 0) { m.p = M.sell.sp.p; m.ci = M.sell.ci.p; m.v = M.sell.v.p; }
-  else { m.p = M.rp.p; m.ci = M.ci.p; m.v = M.v.p; }
+  m.base = nullptr;
+  m.c16 = nullptr;
+  if (M.sw == 0) {
+    m.p = M.sell.sp.p; m.ci = M.sell.ci.p; m.v = M.sell.v.p;
+    if (M.sell.idx16) { m.base = M.sell.base.p; m.c16 = M.sell.c16.p; }
+  } else {
+    m.p = M.rp.p; m.ci = M.ci.p; m.v = M.v.p;
+  }
   return m;
 }
 
@@ -237,7 +313,7 @@ __device__ __forceinline__ bool row_apply(const MatView<T>& M, const T* __restri
   if constexpr (SW == 0) {
     row = gt;
     if (gt >= M.n) return false;
-    out = sell_row<T>(M.p, M.ci, M.v, x, gt);
+    out = M.c16 ? sell_row16<T>(M.p, M.base, M.c16, M.v, x, gt) : sell_row<T>(M.p, M.ci, M.v, x, gt);
     return true;
   } else {
     const int64_t i = gt / SW;
@@ -363,13 +439,16 @@ static inline unsigned g256(int64_t n) { return blocks_for(n, 256); }
 // algorithmic bytes: S-byte value + int32 column per stored entry of the
 // unpadded matrix, 8-byte slice offsets, each vector element once
 template <typename T>
-static double b_ptr(const Mat<T>& M) {  // row-pointer or slice-offset bytes
-  return M.sw == 0 ? 8.0 * (M.nslices + 1) : 8.0 * (M.n + 1);
+static double b_ptr(const Mat<T>& M) {  // row-pointer or slice-offset (+ slice base) bytes
+  if (M.sw != 0) return 8.0 * (M.n + 1);
+  return 8.0 * (M.nslices + 1) + (M.sell.idx16 ? 4.0 * M.nslices : 0.0);
 }
+template <typename T>
+static double b_idx(const Mat<T>& M) { return M.sw == 0 ? M.sell.idx_bytes() : 4.0; }
 template <typename T>
 static double b_cheb(const VLevel<T>* L) {
   const double S = sizeof(T);
-  return (S + 4.0) * L->A.nnz + b_ptr(L->A) + 5.0 * S * L->n;
+  return (S + b_idx(L->A)) * L->A.nnz + b_ptr(L->A) + 5.0 * S * L->n;
 }
 
 #define PROFK(kind, level, bytes, launch)               \
@@ -422,12 +501,13 @@ static int mv(VHier<T>* m, cudaStream_t st, int l, const double* r64, T** xo) {
     rho = rn;
   }
   VLevel<T>* C = m->lev[l + 1];
-  PROFK(K_RES, l, (S + 4.0) * A.nnz + b_ptr(A) + 3.0 * S * n, LAUNCH_MAT(k_vc_residual, A, st, L->b.p, xa, L->r.p));
-  PROFK(K_RST, l, (S + 4.0) * L->R.nnz + b_ptr(L->R) + S * n + S * C->n,
+  PROFK(K_RES, l, (S + b_idx(A)) * A.nnz + b_ptr(A) + 3.0 * S * n,
+        LAUNCH_MAT(k_vc_residual, A, st, L->b.p, xa, L->r.p));
+  PROFK(K_RST, l, (S + b_idx(L->R)) * L->R.nnz + b_ptr(L->R) + S * n + S * C->n,
         LAUNCH_MAT(k_vc_spmv, L->R, st, L->r.p, C->b.p));
   T* xc = nullptr;
   SA_TRY(mv(m, st, l + 1, nullptr, &xc));
-  PROFK(K_PRL, l, (S + 4.0) * L->P.nnz + b_ptr(L->P) + S * C->n + 2.0 * S * n,
+  PROFK(K_PRL, l, (S + b_idx(L->P)) * L->P.nnz + b_ptr(L->P) + S * C->n + 2.0 * S * n,
         LAUNCH_MAT(k_vc_spmv_add, L->P, st, xc, xa));
   rho = 1.0 / s1;
   for (int k = 0; k < deg; ++k) {
@@ -488,12 +568,13 @@ template void vh_free<float>(VHier<float>*);
 // ---------------------------------------------------------------------------
 // q = A p, partial sums of p.q per CTA (fixed order)
 __global__ void k_sell_spmv_dot(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                                const int32_t* __restrict__ base, const uint16_t* __restrict__ c16,
                                 const double* __restrict__ v, const double* __restrict__ p, double* __restrict__ q,
                                 double* __restrict__ part) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double c = 0.0;
   if (i < n) {
-    double a = sell_row<double>(sp, ci, v, p, i);
+    double a = c16 ? sell_row16<double>(sp, base, c16, v, p, i) : sell_row<double>(sp, ci, v, p, i);
     q[i] = a;
     c = a * p[i];
   }
@@ -510,22 +591,26 @@ __global__ void k_sell_spmv_dot(int64_t n, const int64_t* __restrict__ sp, const
 }
 
 __global__ void k_sell_res64(int64_t n, const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
+                             const int32_t* __restrict__ base, const uint16_t* __restrict__ c16,
                              const double* __restrict__ v, const double* __restrict__ b,
                              const double* __restrict__ x, double* __restrict__ r) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) r[i] = b[i] - sell_row<double>(sp, ci, v, x, i);
+  if (i < n)
+    r[i] = b[i] - (c16 ? sell_row16<double>(sp, base, c16, v, x, i) : sell_row<double>(sp, ci, v, x, i));
 }
 
 int launch_sell_spmv_dot(cudaStream_t st, const Sell<double>& A, const double* p, double* q, double* part,
                          int* nparts) {
   *nparts = (int)g256(A.n);
-  k_sell_spmv_dot<<<g256(A.n), 256, 0, st>>>(A.n, A.sp.p, A.ci.p, A.v.p, p, q, part);
+  k_sell_spmv_dot<<<g256(A.n), 256, 0, st>>>(A.n, A.sp.p, A.ci.p, A.idx16 ? A.base.p : nullptr,
+                                              A.idx16 ? A.c16.p : nullptr, A.v.p, p, q, part);
   SA_LAUNCHED();
   return SA_OK;
 }
 
 int launch_sell_residual64(cudaStream_t st, const Sell<double>& A, const double* b, const double* x, double* r) {
-  k_sell_res64<<<g256(A.n), 256, 0, st>>>(A.n, A.sp.p, A.ci.p, A.v.p, b, x, r);
+  k_sell_res64<<<g256(A.n), 256, 0, st>>>(A.n, A.sp.p, A.ci.p, A.idx16 ? A.base.p : nullptr,
+                                           A.idx16 ? A.c16.p : nullptr, A.v.p, b, x, r);
   SA_LAUNCHED();
   return SA_OK;
 }

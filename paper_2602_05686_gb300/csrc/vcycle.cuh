@@ -11,8 +11,14 @@ template <typename T>
 struct Sell {
   int64_t n = 0, nslices = 0, stored = 0, nnz = 0;
   Buf<int64_t> sp;  // slice offsets (nslices + 1), in entries
-  Buf<int32_t> ci;
+  Buf<int32_t> ci;  // column indices (empty when compressed)
   Buf<T> v;
+  // compressed columns: slice base + 16-bit offset, used when every slice's
+  // column span fits in 16 bits
+  int idx16 = 0;
+  Buf<int32_t> base;
+  Buf<uint16_t> c16;
+  double idx_bytes() const { return idx16 ? 2.0 : 4.0; }
 };
 
 // per-level input of the scaled hierarchy (device pointers of the FP64 CSR
@@ -65,9 +71,10 @@ struct VHier {
   const double* WT = nullptr;
 };
 
+// SELL-32 copy with values left_i * a_ij * right_j (scale vectors may be NULL = 1)
 template <typename T>
 int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
-               const double* left, int left_sqrt, const double* right, int right_sqrt, Sell<T>& S);
+               const double* left, const double* right, Sell<T>& S);
 template <typename T>
 int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const double* W, const double* WT,
              VHier<T>** out);

@@ -10,7 +10,10 @@ the device by operator id, so successive right-hand sides of one operator
 (load steps of one stack) skip setup; the least recently used idle
 hierarchies are evicted when the ledger needs room.  Setup of an operator is
 amortised over its right-hand sides, as the paper notes for repeated solves
-(Sec. 4.3).
+(Sec. 4.3).  With a store directory the amortisation reaches across
+processes and restarts: a built hierarchy is written there (sa_serialize)
+and a later miss on the same operator and options loads it (sa_deserialize)
+instead of running the setup.
 
 Every numerical step runs in the CUDA library; this module only schedules.
 Results do not depend on the schedule: every kernel of the library is
@@ -20,7 +23,9 @@ solutions.
 from __future__ import annotations
 
 import contextlib
+import hashlib
 import heapq
+import os
 import statistics
 import threading
 import time
@@ -55,9 +60,16 @@ class Server:
     make_problem(op) -> problem dict; options(op) -> Hierarchy keyword args."""
 
     def __init__(self, make_problem, options, slots=4, hbm_budget=64 << 30, tol=1e-8, hierarchy_factory=None,
-                 stream_factory=None):
+                 stream_factory=None, store_dir=None, store_key=None, hierarchy_loader=None):
         if hierarchy_factory is None:
             from .api import Hierarchy as hierarchy_factory
+        if hierarchy_loader is None and store_dir is not None:
+            from .api import Hierarchy
+            hierarchy_loader = Hierarchy.load
+        self.loader = hierarchy_loader
+        self.store_dir = store_dir
+        # store_key(op) names an operator across processes (default: its id)
+        self.store_key = store_key or (lambda op: f"op{op}")
         if stream_factory is None:
             import torch
             stream_factory = torch.cuda.Stream
@@ -72,7 +84,7 @@ class Server:
         self.cv = threading.Condition()
         self.streams = [stream_factory() for _ in range(slots)]
         self.free_slots = list(range(slots))
-        self.stats = dict(admitted=0, setups=0, hits=0, evictions=0, peak_committed=0)
+        self.stats = dict(admitted=0, setups=0, hits=0, evictions=0, peak_committed=0, loads=0, stores=0)
         self._problems = {}
         self.building = {}  # op -> threading.Event of an in-flight setup
 
@@ -100,6 +112,40 @@ class Server:
             self.committed -= e.nbytes
             self.stats["evictions"] += 1
         return True
+
+    # -- hierarchy store ---------------------------------------------------------
+    def _store_path(self, op):
+        if self.store_dir is None:
+            return None
+        opts = self.options(op)
+        tag = hashlib.sha256(repr(sorted((k, repr(v)) for k, v in opts.items() if k != "stream")).encode())
+        return os.path.join(self.store_dir, f"{self.store_key(op)}-{tag.hexdigest()[:16]}.saamg")
+
+    def _load_or_build(self, op, stream):
+        """the stored hierarchy of op when one exists (a damaged store is
+        rebuilt), else a new setup, which is then stored"""
+        opts = self.options(op)
+        path = self._store_path(op)
+        if path is not None and os.path.exists(path):
+            try:
+                h = self.loader(path, stream=stream, precision=opts.get("precision", "fp64"),
+                                maxit=opts.get("maxit", 500))
+                with self.cv:
+                    self.stats["loads"] += 1
+                return h
+            except Exception:
+                pass
+        h = self.factory(self._problem(op), stream=stream, **opts)
+        with self.cv:
+            self.stats["setups"] += 1
+        if path is not None:
+            os.makedirs(self.store_dir, exist_ok=True)
+            tmp = f"{path}.{os.getpid()}.{threading.get_ident()}.tmp"
+            h.save(tmp)
+            os.replace(tmp, path)  # readers never see a partial store
+            with self.cv:
+                self.stats["stores"] += 1
+        return h
 
     # -- one request on one slot ---------------------------------------------
     def _ctx(self, stream):
@@ -130,8 +176,7 @@ class Server:
                 ev.wait()
                 continue  # cached now (or evicted again: retry)
             try:
-                p = self._problem(req.op)
-                h = self.factory(p, stream=stream, **self.options(req.op))
+                h = self._load_or_build(req.op, stream)
                 nbytes = h.stats()["device_bytes"]
                 with self.cv:
                     entry = _Entry(h, nbytes)
@@ -139,7 +184,6 @@ class Server:
                     self.cache[req.op] = entry
                     # the measured size replaces the admission estimate
                     self.committed += nbytes - req.info.pop("_reserved", 0)
-                    self.stats["setups"] += 1
                 return entry
             finally:
                 with self.cv:

@@ -34,3 +34,48 @@ def theta_sweep(problem, thetas=THETAS, measures=MEASURES, max_coarse=64, precis
                        cost=st["op_complexity"] * info["iters"] if ok else None)
             rows.append(row)
     return rows
+
+
+# the annulus study of Sec. 4.2 (Table 1): refinements h .. h/16 of the
+# 20 x 150 x 1 base mesh, contrast kappa in {1, ..., 1e4}, material measure
+# with pointwise dropping at theta in {0.05, 0.1}, coarsening to <= 5000
+ANNULUS_KAPPAS = (1.0, 10.0, 100.0, 1e3, 1e4)
+ANNULUS_THETAS = (0.05, 0.1)
+
+
+def annulus_study(make_problem, refines=(0, 1, 2, 3, 4), kappas=ANNULUS_KAPPAS, thetas=ANNULUS_THETAS,
+                  precision="fp64", max_coarse=5000, maxit=500, tol=1e-8):
+    """make_problem(refine, kappa) -> problem dict (the annulus generator).
+    Returns one row per (refine, kappa, theta): iterations, levels, operator
+    complexity, setup and solve times (CUDA events on the handle's stream)."""
+    import torch
+
+    from .api import Hierarchy, SAError
+    rows = []
+    for rf in refines:
+        for k in kappas:
+            p = make_problem(rf, k)
+            b = torch.from_numpy(p["b"]).cuda()
+            for th in thetas:
+                row = dict(refine=rf, n=int(p["n"]), kappa=k, theta=th)
+                s = torch.cuda.current_stream()
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(s)
+                try:
+                    h = Hierarchy(p, theta=th, measure="material", max_coarse=max_coarse, precision=precision,
+                                  maxit=maxit)
+                except SAError as e:
+                    row.update(status=e.status)
+                    rows.append(row)
+                    continue
+                e1.record(s)
+                _, info = h.solve(b, tol=tol)
+                e2.record(s)
+                st = h.stats()
+                h.free()
+                torch.cuda.synchronize()
+                row.update(status=info["status"], iters=info["iters"], rel_res=info["rel_res"],
+                           levels=st["levels"], op_complexity=round(st["op_complexity"], 3),
+                           setup_ms=round(e0.elapsed_time(e1), 2), solve_ms=round(e1.elapsed_time(e2), 2))
+                rows.append(row)
+    return rows

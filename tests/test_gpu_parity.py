@@ -7,10 +7,9 @@ the FP32 V-cycle form reaches the same residual within a few extra
 iterations."""
 import numpy as np
 import pytest
+from _tol import VAL_TOL, chain_tol
 
 pytestmark = pytest.mark.gpu
-
-VAL_TOL = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -33,30 +32,56 @@ def row_rel_close(rp, a, b, tol=VAL_TOL):
     return not bad.any(), (float((err / np.maximum(scale[rows], 1e-300)).max()) if len(a) else 0.0)
 
 
-def compare(h, o, keep=True):
+def stepwise(orc, g, s, l, omega_gpu):
+    """This level's steps in the oracle on the CUDA path's own A_l, strength
+    mask and aggregates: the filtered matrix and 1-norm diagonal (Sec. 2.3),
+    omega from 10 power steps (tag 2l+1), P = P^ - omega D~^-1 A_F P^, then
+    the Galerkin product with the CUDA path's own P_l.  Identical inputs, so
+    the bar is the plain 1e-12 of the row's largest magnitude."""
+    n = g["n"]
+    F, Dt = orc.filter_matrix(n, g["A_rp"], g["A_ci"], g["A_v"], s["keep"])
+    lam = orc.power_estimate(F, np.where(np.isfinite(Dt), 1.0 / np.sqrt(Dt), 0.0), 10, 2 * l + 1, 0)
+    om = 4.0 / 3.0 / lam if lam > 0 else 0.0
+    assert omega_gpu == pytest.approx(om, rel=1e-12), l
+    P = orc.smooth_prolongator(F, Dt, om, g["agg"], g["nc"])
+    assert np.array_equal(P["row_ptr"], g["P_rp"]) and np.array_equal(P["col"], g["P_ci"]), l
+    ok, e = row_rel_close(P["row_ptr"], g["P_v"], P["val"])
+    assert ok, ("stepwise P", l, e)
+    Pg = dict(nrows=n, ncols=g["nc"], row_ptr=g["P_rp"], col=g["P_ci"], val=g["P_v"])
+    return orc.galerkin(dict(nrows=n, ncols=n, row_ptr=g["A_rp"], col=g["A_ci"], val=g["A_v"]), Pg)
+
+
+def compare(h, o, keep=True, orc=None):
     st = h.stats()
     assert st["levels"] == o.nlev, (st["n"], [o.level(l)["n"] for l in range(o.nlev)])
     worst = 0.0
+    A_next = None
     for l in range(o.nlev):
         g, r = h.export_level(l), o.level(l)
         assert g["n"] == r["n"] and g["nnz"] == r["nnz"], (l, g["n"], r["n"], g["nnz"], r["nnz"])
         assert np.array_equal(g["A_rp"], r["A_rp"]) and np.array_equal(g["A_ci"], r["A_ci"]), l
-        ok, e = row_rel_close(r["A_rp"], g["A_v"], r["A_v"])
+        ok, e = row_rel_close(r["A_rp"], g["A_v"], r["A_v"], chain_tol(l))
         worst = max(worst, e)
-        assert ok, (l, e)
+        assert ok, ("chained A", l, e)
+        if A_next is not None:
+            assert np.array_equal(A_next["row_ptr"], g["A_rp"]) and np.array_equal(A_next["col"], g["A_ci"]), l
+            ok, e = row_rel_close(g["A_rp"], g["A_v"], A_next["val"])
+            assert ok, ("stepwise A", l, e)
         if l < o.nlev - 1:
             assert np.array_equal(g["agg"], r["agg"]), l
             assert g["nnz_gc"] == r["nnz_gc"], l
             assert np.array_equal(g["P_rp"], r["P_rp"]) and np.array_equal(g["P_ci"], r["P_ci"]), l
-            ok, e = row_rel_close(r["P_rp"], g["P_v"], r["P_v"])
+            ok, e = row_rel_close(r["P_rp"], g["P_v"], r["P_v"], chain_tol(l))
             worst = max(worst, e)
-            assert ok, (l, e)
+            assert ok, ("chained P", l, e)
             if keep:
                 s = h.export_strength(l, keep=True, root=True, aux=False)
                 assert np.array_equal(s["keep"], r["keep"]), l
                 assert np.array_equal(s["root"], r["root"]), l
-                assert s["omega"] == pytest.approx(r["omega"], rel=1e-12)
-                assert s["cheb_lmax"] == pytest.approx(r["cheb_lmax"], rel=1e-12)
+                assert s["omega"] == pytest.approx(r["omega"], rel=chain_tol(l)), l
+                assert s["cheb_lmax"] == pytest.approx(r["cheb_lmax"], rel=chain_tol(l)), l
+                if orc is not None:
+                    A_next = stepwise(orc, g, s, l, s["omega"])
     return worst
 
 
@@ -70,6 +95,8 @@ CASES = [
     ("battery-classical", lambda g: g.battery_3d(16, 16, 32), 0.04, "classical", 200),
     ("voronoi-material", lambda g: g.voronoi_3d(14, seed=1), 0.05, "material", 150),
     ("voronoi-classical", lambda g: g.voronoi_3d(14, seed=1), 0.04, "classical", 150),
+    ("annulus-material-0.05", lambda g: g.annulus_3d(0, kappa=1e4), 0.05, "material", 500),
+    ("annulus-material-0.1", lambda g: g.annulus_3d(0, kappa=1e4), 0.1, "material", 500),
 ]
 
 
@@ -80,12 +107,36 @@ def test_hierarchy_parity(sa, orc, gen_mod, case):
     h = sa.Hierarchy(p, theta=theta, measure=measure, max_coarse=mc, keep_setup_data=True)
     o = orc.Hierarchy(p, theta, measure, max_coarse=mc)
     assert o.nlev >= 2
-    compare(h, o)
+    compare(h, o, orc=orc)
     if measure != "classical":
         for l in range(o.nlev):
             s = h.export_strength(l, keep=False, root=False, aux=True)
             r = o.level(l)
             assert np.array_equal(s["x"], r["x"]) and np.array_equal(s["sinv"], r["sinv"]), l
+
+
+CUT_CASES = [
+    ("c1-material-cut", lambda g: g.layered_2d(32), 0.08, "material", 64),
+    ("twodomain-classical-cut", lambda g: g.two_domain(32, 1e4), 0.08, "classical", 64),
+    ("twodomain-material-cut", lambda g: g.two_domain(32, 1e4), 0.08, "material", 64),
+    ("battery-material-cut", lambda g: g.battery_3d(16, 16, 32), 0.08, "material", 200),
+    ("voronoi-classical-cut", lambda g: g.voronoi_3d(14, seed=1), 0.08, "classical", 150),
+    ("voronoi-material-cut", lambda g: g.voronoi_3d(14, seed=1), 0.08, "material", 150),
+]
+
+
+@pytest.mark.parametrize("case", CUT_CASES, ids=[c[0] for c in CUT_CASES])
+def test_hierarchy_parity_cut_drop(sa, orc, gen_mod, case):
+    import torch
+    _, mk, theta, measure, mc = case
+    p = mk(gen_mod)
+    h = sa.Hierarchy(p, theta=theta, measure=measure, max_coarse=mc, keep_setup_data=True, drop="cut")
+    o = orc.Hierarchy(p, theta, measure, max_coarse=mc, drop="cut")
+    assert o.nlev >= 2
+    compare(h, o, orc=orc)
+    x, info = h.solve(torch.from_numpy(p["b"]).cuda())
+    _, oinfo = o.solve(p["b"])
+    assert info["status"] == 0 and abs(info["iters"] - oinfo["iters"]) <= 1
 
 
 @pytest.mark.parametrize("case", CASES[:2] + CASES[5:8], ids=[c[0] for c in CASES[:2] + CASES[5:8]])
@@ -281,3 +332,19 @@ def test_theta_sweep_runs(sa, gen_mod):
         assert r["status"] in (0, -5, -6)
         if r["status"] == 0:
             assert r["cost"] == pytest.approx(r["op_complexity"] * r["iters"])
+
+
+def test_annulus_study_matches_oracle(sa, orc, gen_mod):
+    """Sec. 4.2 study driver on h and h/2 at the extreme contrasts: every
+    configuration converges with the oracle's iteration count (within 1),
+    level count and operator complexity."""
+    from paper_2602_05686_gb300.sweep import annulus_study
+    rows = annulus_study(lambda rf, k: gen_mod.annulus_3d(rf, kappa=k), refines=(0, 1), kappas=(1.0, 1e4))
+    assert len(rows) == 8
+    for r in rows:
+        p = gen_mod.annulus_3d(r["refine"], kappa=r["kappa"])
+        o = orc.Hierarchy(p, r["theta"], "material")
+        _, oi = o.solve(p["b"])
+        assert r["status"] == 0 and r["rel_res"] <= 1e-8, r
+        assert abs(r["iters"] - oi["iters"]) <= 1 and r["levels"] == o.nlev, (r, oi)
+        assert r["op_complexity"] == pytest.approx(o.operator_complexity(), abs=1e-3)

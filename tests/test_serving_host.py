@@ -134,3 +134,56 @@ def test_failed_request_is_retired_with_status():
     assert [r.status != 0 for r in rs] == [False, False, True, False]
     assert s.committed == 10  # only the cached hierarchy stays committed
     s.close()
+
+
+class StoredFake(FakeHierarchy):
+    """a fake whose store is a small text file"""
+    loads = 0
+
+    def save(self, path):
+        with open(path, "w") as f:
+            f.write(f"{self.n} {self.nb}")
+
+    @classmethod
+    def load(cls, path, stream=None, **kw):
+        with open(path) as f:
+            n, nb = (int(x) for x in f.read().split())
+        StoredFake.loads += 1
+        return cls({"n": n, "bytes": nb})
+
+
+def test_store_carries_setups_across_servers(tmp_path):
+    """a second server (a restarted process) loads the stored hierarchies
+    instead of running setups; a damaged store is rebuilt"""
+    probs = {op: {"n": 10, "nnz": 30, "bytes": 100 * (op + 1)} for op in range(3)}
+
+    def server():
+        s = Server(lambda op: probs[op], lambda op: {"theta": 0.05}, slots=2, hbm_budget=10_000,
+                   hierarchy_factory=StoredFake, stream_factory=lambda: None, store_dir=str(tmp_path),
+                   hierarchy_loader=StoredFake.load)
+        s._estimate = lambda op: probs[op]["bytes"]
+        return s
+
+    s1 = server()
+    out1 = s1.serve(reqs([0, 1, 0, 2]), realtime=False)
+    s1.close()
+    assert out1["setups"] == 3 and out1["stores"] == 3 and out1["loads"] == 0
+    assert len(list(tmp_path.glob("*.saamg"))) == 3 and not list(tmp_path.glob("*.tmp"))
+    s2 = server()
+    out2 = s2.serve(reqs([2, 1, 0, 0]), realtime=False)
+    s2.close()
+    assert out2["setups"] == 0 and out2["loads"] == 3 and out2["failed"] == 0
+    # options are part of the store name: other options miss the store
+    s3 = Server(lambda op: probs[op], lambda op: {"theta": 0.1}, slots=1, hbm_budget=10_000,
+                hierarchy_factory=StoredFake, stream_factory=lambda: None, store_dir=str(tmp_path),
+                hierarchy_loader=StoredFake.load)
+    out3 = s3.serve(reqs([0]), realtime=False)
+    s3.close()
+    assert out3["setups"] == 1 and out3["loads"] == 0
+    # a damaged store falls back to a setup
+    for f in tmp_path.glob("op1-*.saamg"):
+        f.write_text("garbage")
+    s4 = server()
+    out4 = s4.serve(reqs([1]), realtime=False)
+    s4.close()
+    assert out4["setups"] == 1 and out4["failed"] == 0
