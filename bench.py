@@ -233,6 +233,31 @@ def run_ours(args):
     # material hierarchy statistics (untimed)
     hm = sa.Hierarchy(dprob, theta=MAT_THETA, measure="material")
     mst = hm.stats()
+
+    # several right-hand sides on the cached hierarchy: K one-vector solves
+    # against one K-column solve (every launch shared), both forms, CUDA events
+    multi = None
+    if not args.no_multi_rhs:
+        K = 8
+        Bk = torch.from_numpy(np.stack([gen.Stream(500 + c, 9).normal(n) * (1 - p["dir_mask"])
+                                        for c in range(K)])).cuda()
+        multi = {"rhs": K}
+        for form in ("fp64", "fp32"):
+            hm.set_precision(form)
+            hm.solve(Bk[0].clone())    # warm (graph capture, buffers)
+            hm.solve_batch(Bk[:2])
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            its1 = [hm.solve(Bk[c].clone())[1]["iters"] for c in range(K)]
+            e[1].record(stream)
+            _, inf = hm.solve_batch(Bk)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            t1, tk = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+            multi[form] = {"one_by_one_ms": round(t1, 2), "block_ms": round(tk, 2),
+                           "speedup": round(t1 / tk, 3), "iters": [i["iters"] for i in inf],
+                           "iters_equal": its1 == [i["iters"] for i in inf],
+                           "max_rel_res": max(i["rel_res"] for i in inf)}
     hm.free()
 
     # end-to-end through the C ABI with host buffers (copies inside)
@@ -328,6 +353,7 @@ def run_ours(args):
         "kernel_profile_top": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
                                for r in krows[:8]],
         "setup_phases_ms": setup_phases(prof, args.steps),
+        "multi_rhs": multi,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         result["cpu_baseline"] = cpu_baseline(args)
@@ -483,6 +509,27 @@ def run_annulus(args):
         print(json.dumps(dict(row, workload="annulus (Sec. 4.2)")), flush=True)
 
 
+def run_sweep(args):
+    """The two-domain drop-tolerance study of Sec. 4.1: (-1,1)^2 with
+    32, 128 and 512 elements per side, kappa in {1, 1e2, 1e4}, every theta of
+    the paper's list, the three strength measures and both dropping criteria,
+    FP64 PCG to 1e-8; one JSON line per configuration."""
+    import torch
+
+    import gen
+    import paper_2602_05686_gb300 as sa
+    from paper_2602_05686_gb300.sweep import theta_sweep
+
+    torch.cuda.set_device(0)
+    sa.build()
+    theta_sweep(gen.two_domain(32, 1.0), thetas=(0.08,), measures=("material",))   # warm-up (module loads)
+    for n_el in (32, 128, 512):
+        for kappa in (1.0, 1e2, 1e4):
+            p = gen.two_domain(n_el, kappa)
+            for row in theta_sweep(p, drops=("pointwise", "cut")):
+                print(json.dumps(dict(row, n_el=n_el, kappa=kappa, workload="two-domain (Sec. 4.1)")), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -492,6 +539,7 @@ def main():
     ap.add_argument("--workload", default="battery_128x128x256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-multi-rhs", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--slots", type=int, default=4)
@@ -500,9 +548,12 @@ def main():
     ap.add_argument("--max3d", type=int, default=96)
     ap.add_argument("--annulus", action="store_true", help="run the annulus study (Sec. 4.2) instead")
     ap.add_argument("--annulus-refine", type=int, default=4)
+    ap.add_argument("--sweep", action="store_true", help="run the two-domain theta sweep (Sec. 4.1) instead")
     args = ap.parse_args()
     if args.serving:
         run_serving(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.annulus:
         run_annulus(args)
     elif args.impl == "reference":

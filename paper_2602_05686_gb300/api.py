@@ -264,6 +264,30 @@ class Hierarchy:
         return x, dict(status=int(st), iters=info.iters, rel_res=info.rel_res_true, setup_ms=info.setup_ms,
                        solve_ms=info.solve_ms)
 
+    def solve_batch(self, B, X0=None, tol=1e-8, check=True):
+        """k right-hand sides at once (sa_solve_batch: up to 8 columns share every
+        launch; each column ends bitwise where solve() on it ends).  B: (k, n)
+        CUDA tensor (float64) or numpy array; returns (X of the same kind,
+        list of per-column info dicts)."""
+        torch = self.torch
+        if isinstance(B, torch.Tensor):
+            B = B.to(device="cuda", dtype=torch.float64).contiguous()
+            k = int(B.shape[0])
+            with torch.cuda.stream(self.stream):
+                X = torch.zeros_like(B) if X0 is None else X0.to(device="cuda", dtype=torch.float64).clone()
+            bp, xp = B.data_ptr(), X.data_ptr()
+        else:
+            B = np.ascontiguousarray(B, np.float64)
+            k = int(B.shape[0])
+            X = np.zeros_like(B) if X0 is None else np.array(X0, np.float64)
+            bp, xp = B.ctypes.data, X.ctypes.data
+        infos = (SolveInfo * max(k, 1))()
+        st = lib().sa_solve_batch(self.h, k, bp, xp, float(tol), infos)
+        if check and st not in (OK, ERR_NO_CONVERGENCE):
+            _check(st, "sa_solve_batch")
+        return X, [dict(status=int(infos[c].status), iters=infos[c].iters, rel_res=infos[c].rel_res_true,
+                        setup_ms=infos[c].setup_ms, solve_ms=infos[c].solve_ms) for c in range(k)]
+
     def set_precision(self, precision):
         _check(lib().sa_set_precision(self.h, PRECISION[precision]), "sa_set_precision")
 

@@ -26,9 +26,13 @@ __global__ void k_set_identity(int64_t n, double* __restrict__ W) {
   if (t < n * n) W[t] = (t / n == t % n) ? 1.0 : 0.0;
 }
 
-// factor the diagonal tile (k,k) in place; err = 1 on a non-positive pivot
-__global__ void k_potrf_diag(int64_t n, double* __restrict__ M, int k, int* __restrict__ err) {
+// factor the diagonal tile (k,k) in place (err = 1 on a non-positive pivot)
+// and write the inverse of the factored tile, L_kk^-1 (lower triangular), to
+// Dinv + k NB^2: the panel and inverse solves then become tile products
+__global__ void k_potrf_diag(int64_t n, double* __restrict__ M, int k, int* __restrict__ err,
+                             double* __restrict__ Dinv) {
   __shared__ double T[NB][NB + 1];
+  __shared__ double rinv[NB];
   const int64_t o = (int64_t)k * NB;
   const int bs = (int)((n - o) < NB ? (n - o) : NB);
   for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
@@ -40,10 +44,13 @@ __global__ void k_potrf_diag(int64_t n, double* __restrict__ M, int k, int* __re
     if (threadIdx.x == 0) {
       double d = T[j][j];
       if (!(d > 0.0)) { atomicOr(err, 1); d = 1.0; }
-      T[j][j] = sqrt(d);
+      d = sqrt(d);
+      T[j][j] = d;
+      rinv[j] = 1.0 / d;
     }
     __syncthreads();
-    for (int r = j + 1 + threadIdx.x; r < bs; r += blockDim.x) T[r][j] /= T[j][j];
+    const double ri = rinv[j];
+    for (int r = j + 1 + threadIdx.x; r < bs; r += blockDim.x) T[r][j] *= ri;
     __syncthreads();
     const int m = bs - j - 1;
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
@@ -56,34 +63,54 @@ __global__ void k_potrf_diag(int64_t n, double* __restrict__ M, int k, int* __re
     int r = t / bs, c = t % bs;
     M[(o + r) * n + o + c] = (c <= r) ? T[r][c] : 0.0;
   }
+  // inverse by forward substitution, one column per thread: L y = e_c
+  __shared__ double Y[NB][NB + 1];
+  const int c = threadIdx.x;
+  if (c < NB) {
+    for (int r = 0; r < NB; ++r) {
+      double y = 0.0;
+      if (r < bs && c < bs && r >= c) {
+        y = (r == c) ? 1.0 : 0.0;
+        for (int q = c; q < r; ++q) y -= T[r][q] * Y[q][c];
+        y *= rinv[r];
+      }
+      Y[r][c] = y;
+    }
+  }
+  __syncthreads();
+  double* D = Dinv + (int64_t)k * NB * NB;
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) D[t] = Y[t / NB][t % NB];
 }
 
-// L_ik = A_ik L_kk^-T for block rows i > k (one CTA of NB threads per block row)
-__global__ void k_trsm_panel(int64_t n, double* __restrict__ M, int k) {
-  __shared__ double L[NB][NB + 1];
+// L_ik = A_ik L_kk^-T for block rows i > k: a tile product with the stored
+// L_kk^-1 (one CTA of 256 threads per block row, 4 outputs per thread)
+__global__ void k_trsm_panel(int64_t n, double* __restrict__ M, int k, const double* __restrict__ Dinv) {
+  __shared__ double Li[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
   const int64_t ok = (int64_t)k * NB;
   const int bk = (int)((n - ok) < NB ? (n - ok) : NB);
   const int64_t oi = (int64_t)(k + 1 + blockIdx.x) * NB;
   const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
+  const double* D = Dinv + (int64_t)k * NB * NB;
   for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
     int r = t / NB, c = t % NB;
-    L[r][c] = (r < bk && c < bk) ? M[(ok + r) * n + ok + c] : 0.0;
+    Li[r][c] = D[t];
     X[r][c] = (r < bi && c < bk) ? M[(oi + r) * n + ok + c] : 0.0;
   }
   __syncthreads();
-  const int r = threadIdx.x;
-  if (r < bi) {
-    for (int c = 0; c < bk; ++c) {
-      double x = X[r][c];
-      for (int m = 0; m < c; ++m) x -= X[r][m] * L[c][m];
-      X[r][c] = x / L[c][c];
-    }
+  double out[NB * NB / 256];
+#pragma unroll
+  for (int u = 0; u < NB * NB / 256; ++u) {
+    const int t = threadIdx.x + u * 256, r = t / NB, c = t % NB;
+    double acc = 0.0;  // (L^-T)_qc = (L^-1)_cq, nonzero for q <= c
+    for (int q = 0; q <= c; ++q) acc += X[r][q] * Li[c][q];
+    out[u] = acc;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < bi * bk; t += blockDim.x) {
-    int rr = t / bk, c = t % bk;
-    M[(oi + rr) * n + ok + c] = X[rr][c];
+#pragma unroll
+  for (int u = 0; u < NB * NB / 256; ++u) {
+    const int t = threadIdx.x + u * 256, r = t / NB, c = t % NB;
+    if (r < bi && c < bk) M[(oi + r) * n + ok + c] = out[u];
   }
 }
 
@@ -132,32 +159,35 @@ __global__ void k_syrk_update(int64_t n, double* __restrict__ M, int k) {
   tile_gemm_nt_sub(n, M, oi, oj, bi, bj, M, oi, ok, M, oj, ok, bk, n, n);
 }
 
-// W_ij <- L_ii^-1 W_ij for block columns j <= i (CTA of NB threads per j)
-__global__ void k_trsm_lower_left(int64_t n, const double* __restrict__ L, double* __restrict__ W, int i) {
-  __shared__ double Ls[NB][NB + 1];
+// W_ij <- L_ii^-1 W_ij for block columns j <= i, a tile product with the
+// stored L_ii^-1 (one CTA of 256 threads per j, 4 outputs per thread)
+__global__ void k_trsm_lower_left(int64_t n, const double* __restrict__ Dinv, double* __restrict__ W, int i) {
+  __shared__ double Li[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
   const int j = blockIdx.x;
   const int64_t oi = (int64_t)i * NB, oj = (int64_t)j * NB;
   const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
   const int bj = (int)((n - oj) < NB ? (n - oj) : NB);
+  const double* D = Dinv + (int64_t)i * NB * NB;
   for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
     int r = t / NB, c = t % NB;
-    Ls[r][c] = (r < bi && c < bi) ? L[(oi + r) * n + oi + c] : 0.0;
+    Li[r][c] = D[t];
     X[r][c] = (r < bi && c < bj) ? W[(oi + r) * n + oj + c] : 0.0;
   }
   __syncthreads();
-  const int c = threadIdx.x;
-  if (c < bj) {
-    for (int r = 0; r < bi; ++r) {
-      double x = X[r][c];
-      for (int m = 0; m < r; ++m) x -= Ls[r][m] * X[m][c];
-      X[r][c] = x / Ls[r][r];
-    }
+  double out[NB * NB / 256];
+#pragma unroll
+  for (int u = 0; u < NB * NB / 256; ++u) {
+    const int t = threadIdx.x + u * 256, r = t / NB, c = t % NB;
+    double acc = 0.0;
+    for (int q = 0; q <= r; ++q) acc += Li[r][q] * X[q][c];
+    out[u] = acc;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < bi * bj; t += blockDim.x) {
-    int r = t / bj, cc = t % bj;
-    W[(oi + r) * n + oj + cc] = X[r][cc];
+#pragma unroll
+  for (int u = 0; u < NB * NB / 256; ++u) {
+    const int t = threadIdx.x + u * 256, r = t / NB, c = t % NB;
+    if (r < bi && c < bj) W[(oi + r) * n + oj + c] = out[u];
   }
 }
 
@@ -207,7 +237,7 @@ int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int3
                              Buf<double>& W, Buf<double>& WT) {
   cudaStream_t s = al.stream;
   if (n <= 0) return SA_OK;
-  Buf<double> M;
+  Buf<double> M, Dinv;
   Buf<int> err;
   SA_TRY(M.alloc(&al, n * n));
   SA_TRY(W.alloc(&al, n * n));
@@ -218,12 +248,13 @@ int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int3
   k_densify<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, v, M.p);
   SA_LAUNCHED();
   const int nb = (int)((n + NB - 1) / NB);
+  SA_TRY(Dinv.alloc(&al, (int64_t)nb * NB * NB));
   for (int k = 0; k < nb; ++k) {
-    k_potrf_diag<<<1, 256, 0, s>>>(n, M.p, k, err.p);
+    k_potrf_diag<<<1, 256, 0, s>>>(n, M.p, k, err.p, Dinv.p);
     SA_LAUNCHED();
     const int m = nb - k - 1;
     if (m > 0) {
-      k_trsm_panel<<<m, NB, 0, s>>>(n, M.p, k);
+      k_trsm_panel<<<m, 256, 0, s>>>(n, M.p, k, Dinv.p);
       SA_LAUNCHED();
       k_syrk_update<<<(unsigned)((int64_t)m * (m + 1) / 2), 256, 0, s>>>(n, M.p, k);
       SA_LAUNCHED();
@@ -237,7 +268,7 @@ int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int3
   k_set_identity<<<blocks_for(n * n, 256), 256, 0, s>>>(n, W.p);
   SA_LAUNCHED();
   for (int i = 0; i < nb; ++i) {
-    k_trsm_lower_left<<<i + 1, NB, 0, s>>>(n, M.p, W.p, i);
+    k_trsm_lower_left<<<i + 1, 256, 0, s>>>(n, Dinv.p, W.p, i);
     SA_LAUNCHED();
     const int m = nb - i - 1;
     if (m > 0) {
@@ -275,12 +306,67 @@ __global__ void k_trmv_upper(int64_t n, const double* __restrict__ WT, const dou
   }
 }
 
+// the same two products for k right-hand sides stored interleaved (element
+// (i, c) at i*k + c); every column is summed in the one-vector order
+__global__ void k_btrmv_lower(int64_t n, int k, const double* __restrict__ W, const double* __restrict__ b,
+                              double* __restrict__ y) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    double s[KMAX_COARSE];
+#pragma unroll
+    for (int c = 0; c < KMAX_COARSE; ++c) s[c] = 0.0;
+    for (int64_t j = lane; j <= i; j += 32) {
+      const double w = W[i * n + j];
+#pragma unroll
+      for (int c = 0; c < KMAX_COARSE; ++c)
+        if (c < k) s[c] += w * b[j * k + c];
+    }
+#pragma unroll
+    for (int c = 0; c < KMAX_COARSE; ++c) {
+      const double t = warp_sum(s[c]);
+      if (lane == 0 && c < k) y[i * k + c] = t;
+    }
+  }
+}
+
+__global__ void k_btrmv_upper(int64_t n, int k, const double* __restrict__ WT, const double* __restrict__ y,
+                              double* __restrict__ x) {
+  const int lane = lane_id();
+  for (int64_t j = global_warp(); j < n; j += warp_stride()) {
+    double s[KMAX_COARSE];
+#pragma unroll
+    for (int c = 0; c < KMAX_COARSE; ++c) s[c] = 0.0;
+    for (int64_t i = j + lane; i < n; i += 32) {
+      const double w = WT[j * n + i];
+#pragma unroll
+      for (int c = 0; c < KMAX_COARSE; ++c)
+        if (c < k) s[c] += w * y[i * k + c];
+    }
+#pragma unroll
+    for (int c = 0; c < KMAX_COARSE; ++c) {
+      const double t = warp_sum(s[c]);
+      if (lane == 0 && c < k) x[j * k + c] = t;
+    }
+  }
+}
+
 int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
                         double* x) {
   if (n <= 0) return SA_OK;
   k_trmv_lower<<<warp_rows_grid(n), 256, 0, st>>>(n, W, b, y);
   SA_LAUNCHED();
   k_trmv_upper<<<warp_rows_grid(n), 256, 0, st>>>(n, WT, y, x);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_coarse_solve_block(cudaStream_t st, int64_t n, int k, const double* W, const double* WT, const double* b,
+                              double* y, double* x) {
+  if (n <= 0) return SA_OK;
+  if (k < 1 || k > KMAX_COARSE) return SA_ERR_INVALID_ARG;
+  k_btrmv_lower<<<warp_rows_grid(n), 256, 0, st>>>(n, k, W, b, y);
+  SA_LAUNCHED();
+  k_btrmv_upper<<<warp_rows_grid(n), 256, 0, st>>>(n, k, WT, y, x);
   SA_LAUNCHED();
   return SA_OK;
 }

@@ -66,6 +66,11 @@ struct sa_handle_s {
   int graph_failed = 0;
   sa::Buf<int> it_dev;
   sa::Buf<double> ctl;  // [0] tol * r0
+  // k-column solve workspace (interleaved n x KMAX_BLOCK blocks), made on first use
+  int kready = 0;
+  sa::Buf<double> kR, kP, kQ, kRp, kT, kX, kB, kStage, kpart, kdots;
+  sa::Buf<sa::CgScalars> kS;
+  sa::Buf<int> kact;
 };
 
 namespace sa {
@@ -547,6 +552,148 @@ static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_sol
   return cg_eager(h, b, x, tol, info);
 }
 
+
+// ---------------------------------------------------------------------------
+// k right-hand sides in lockstep (sa_solve_batch): every operator product,
+// cycle and vector update is one launch for all k columns, each column
+// following the one-vector CG's arithmetic in the same order, so column c
+// ends bitwise where sa_solve on that right-hand side ends.  One host
+// readback per iteration (squared residual norms and breakdown flags).
+// ---------------------------------------------------------------------------
+static int block_workspace(sa_handle h) {
+  if (h->kready) return SA_OK;
+  Alloc& al = h->al;
+  const int64_t nk = h->n * KMAX_BLOCK;
+  SA_TRY(h->kR.alloc(&al, nk));
+  SA_TRY(h->kP.alloc(&al, nk));
+  SA_TRY(h->kQ.alloc(&al, nk));
+  SA_TRY(h->kRp.alloc(&al, nk));
+  SA_TRY(h->kT.alloc(&al, nk));
+  SA_TRY(h->kX.alloc(&al, nk));
+  SA_TRY(h->kB.alloc(&al, nk));
+  SA_TRY(h->kStage.alloc(&al, nk));
+  const int64_t np = blocks_for(h->n, 256) + RED_BLOCKS;
+  SA_TRY(h->kpart.alloc(&al, 2 * KMAX_BLOCK * np));
+  SA_TRY(h->kdots.alloc(&al, 6 * KMAX_BLOCK));  // [0, 2K) dots, [2K, 3K) r.r, [3K, 5K) true residuals
+  SA_TRY(h->kS.alloc(&al, KMAX_BLOCK));
+  SA_TRY(h->kact.alloc(&al, KMAX_BLOCK));
+  h->kready = 1;
+  return SA_OK;
+}
+
+static int precondition_block(sa_handle h, int k, const double* R, double** Z) {
+  if (h->opt.precision == SA_PREC_FP32_VCYCLE) return vh_vcycle_block<float>(h->al, h->v32, h->al.stream, k, R, Z);
+  return vh_vcycle_block<double>(h->al, h->v64, h->al.stream, k, R, Z);
+}
+
+static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos, int* statuses) {
+  cudaStream_t s = h->al.stream;
+  const int64_t n = h->n;
+  const int flexible = h->opt.precision == SA_PREC_FP32_VCYCLE;
+  const int maxit = h->opt.maxit;
+  auto t0 = std::chrono::steady_clock::now();
+  SA_TRY(block_workspace(h));
+  double* R = h->kR.p; double* P = h->kP.p; double* Q = h->kQ.p; double* Rp = h->kRp.p;
+  double* T = h->kT.p; double* Xb = h->kX.p; double* Bb = h->kB.p;
+  double* part = h->kpart.p; double* dots = h->kdots.p;
+  // inputs: column-major (host or device) -> interleaved
+  SA_CUDA(cudaMemcpyAsync(h->kStage.p, B, sizeof(double) * n * k, cudaMemcpyDefault, s));
+  SA_TRY(launch_interleave(s, n, k, h->kStage.p, Bb, 1));
+  SA_CUDA(cudaMemcpyAsync(h->kStage.p, X, sizeof(double) * n * k, cudaMemcpyDefault, s));
+  SA_TRY(launch_interleave(s, n, k, h->kStage.p, Xb, 1));
+  // host view of the columns
+  double r0[KMAX_BLOCK], hb[2 * KMAX_BLOCK];
+  int act[KMAX_BLOCK], its[KMAX_BLOCK], st[KMAX_BLOCK];
+  struct { double rr[KMAX_BLOCK]; CgScalars S[KMAX_BLOCK]; } hr;
+  SA_TRY(launch_bsell_residual64(s, h->A0s, k, Bb, Xb, R));
+  SA_TRY(launch_bdots(s, n, k, R, R, nullptr, nullptr, part, dots));
+  SA_CUDA(cudaMemcpyAsync(hb, dots, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  SA_CUDA(cudaStreamSynchronize(s));
+  int nact = 0;
+  for (int c = 0; c < k; ++c) {
+    r0[c] = sqrt(hb[c]);
+    act[c] = r0[c] > 0.0;
+    its[c] = 0;
+    st[c] = act[c] ? SA_ERR_NO_CONVERGENCE : SA_OK;
+    nact += act[c];
+  }
+  SA_CUDA(cudaMemcpyAsync(h->kact.p, act, sizeof(int) * k, cudaMemcpyHostToDevice, s));
+  if (nact > 0) {
+    // first iteration
+    double* Z = nullptr;
+    SA_TRY(precondition_block(h, k, R, &Z));
+    SA_TRY(launch_bcg_pupdate(s, n, k, h->kS.p, h->kact.p, Z, P, 1));
+    SA_TRY(launch_bdots(s, n, k, R, Z, nullptr, nullptr, part, dots));
+    SA_TRY(launch_bcg_beta(s, k, h->kS.p, dots, -1, h->kact.p));
+    for (int it = 1;; ++it) {
+      int np = 0;
+      SA_TRY(launch_bsell_spmv_dot(s, h->A0s, k, P, Q, part, &np));
+      SA_TRY(launch_bfinish(s, part, np, k, dots));
+      SA_TRY(launch_bcg_alpha(s, k, h->kS.p, dots, h->kact.p));
+      SA_TRY(launch_bcg_update(s, n, k, h->kS.p, h->kact.p, P, Q, Xb, R, flexible ? Rp : nullptr, part));
+      SA_TRY(launch_bfinish(s, part, RED_BLOCKS, k, dots + 2 * KMAX_BLOCK));
+      SA_CUDA(cudaMemcpyAsync(hr.rr, dots + 2 * KMAX_BLOCK, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+      SA_CUDA(cudaMemcpyAsync(hr.S, h->kS.p, sizeof(CgScalars) * k, cudaMemcpyDeviceToHost, s));
+      SA_CUDA(cudaStreamSynchronize(s));
+      // per column: breakdown, convergence candidate (confirmed on the true
+      // residual, which replaces r when it does not confirm), maxit
+      bool cand = false;
+      for (int c = 0; c < k; ++c) {
+        if (!act[c]) continue;
+        its[c] = it;
+        if (hr.S[c].breakdown) { st[c] = SA_ERR_BREAKDOWN; act[c] = 0; continue; }
+        if (sqrt(hr.rr[c]) <= tol * r0[c]) cand = true;
+      }
+      if (cand) {
+        SA_TRY(launch_bsell_residual64(s, h->A0s, k, Bb, Xb, T));
+        SA_TRY(launch_bdots(s, n, k, T, T, nullptr, nullptr, part, dots + 3 * KMAX_BLOCK));
+        SA_CUDA(cudaMemcpyAsync(hb, dots + 3 * KMAX_BLOCK, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        SA_CUDA(cudaStreamSynchronize(s));
+        for (int c = 0; c < k; ++c) {
+          if (!act[c] || !(sqrt(hr.rr[c]) <= tol * r0[c])) continue;
+          if (sqrt(hb[c]) <= tol * r0[c]) {
+            st[c] = SA_OK;
+            act[c] = 0;
+          } else {
+            SA_CUDA(cudaMemcpy2DAsync(R + c, sizeof(double) * k, T + c, sizeof(double) * k, sizeof(double), n,
+                                      cudaMemcpyDeviceToDevice, s));
+          }
+        }
+      }
+      nact = 0;
+      for (int c = 0; c < k; ++c) {
+        if (act[c] && it >= maxit) act[c] = 0;  // status stays SA_ERR_NO_CONVERGENCE
+        nact += act[c];
+      }
+      SA_CUDA(cudaMemcpyAsync(h->kact.p, act, sizeof(int) * k, cudaMemcpyHostToDevice, s));
+      if (nact == 0) break;
+      SA_TRY(precondition_block(h, k, R, &Z));
+      SA_TRY(launch_bdots(s, n, k, R, Z, flexible ? Z : nullptr, flexible ? Rp : nullptr, part, dots));
+      SA_TRY(launch_bcg_beta(s, k, h->kS.p, dots, flexible, h->kact.p));
+      SA_TRY(launch_bcg_pupdate(s, n, k, h->kS.p, h->kact.p, Z, P, 0));
+    }
+  }
+  // true residuals at exit and the solutions
+  SA_TRY(launch_bsell_residual64(s, h->A0s, k, Bb, Xb, T));
+  SA_TRY(launch_bdots(s, n, k, T, T, nullptr, nullptr, part, dots + 3 * KMAX_BLOCK));
+  SA_CUDA(cudaMemcpyAsync(hb, dots + 3 * KMAX_BLOCK, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  SA_TRY(launch_interleave(s, n, k, Xb, h->kStage.p, 0));
+  SA_CUDA(cudaMemcpyAsync(X, h->kStage.p, sizeof(double) * n * k, cudaMemcpyDefault, s));
+  SA_CUDA(cudaStreamSynchronize(s));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int c = 0; c < k; ++c) {
+    statuses[c] = st[c];
+    if (infos) {
+      infos[c].iters = its[c];
+      infos[c].rel_res_true = r0[c] > 0.0 ? sqrt(hb[c]) / r0[c] : 0.0;
+      infos[c].setup_ms = h->setup_ms;
+      infos[c].solve_ms = ms;
+      infos[c].status = st[c];
+    }
+  }
+  return SA_OK;
+}
+
 template <typename T>
 static int upload(Alloc& al, Buf<T>& dst, const T* src, int64_t count) {
   SA_TRY(dst.alloc(&al, count));
@@ -653,8 +800,8 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   Level& Lc = *h->lev[nlev - 1];
   if (Lc.n > 16384) return SA_ERR_STAGNATION;
   // a15: smoother data (Chebyshev bounds from 10 power steps on D^-1/2 A D^-1/2)
-  PHASE_BEGIN(PK_S_CHEB, 0);
   for (int l = 0; l < nlev; ++l) {
+    PHASE_BEGIN(PK_S_CHEB, l);
     Level& L = *h->lev[l];
     SA_TRY(L.dinv.alloc(&al, L.n));
     SA_TRY(launch_reciprocal(s, L.n, L.diag.p, L.dinv.p));
@@ -669,8 +816,8 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
       L.lmax = o->cheb_boost * hl;
       L.lmin = L.lmax / o->cheb_ratio;
     }
+    PHASE_END(PK_S_CHEB);
   }
-  PHASE_END(PK_S_CHEB);
   h->nL = Lc.n;
   PHASE_BEGIN(PK_S_DENSE, nlev - 1);
   SA_TRY(run_dense_inverse_factor(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT));
@@ -772,12 +919,20 @@ int sa_solve(sa_handle h, const double* b, double* x, double tol, sa_solve_info*
 }
 
 int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos) {
-  if (!h || k < 0 || (k > 0 && (!B || !X))) return SA_ERR_INVALID_ARG;
+  if (!h || k < 0 || (k > 0 && (!B || !X)) || !(tol > 0.0)) return SA_ERR_INVALID_ARG;
   int worst = SA_OK;
-  for (int c = 0; c < k; ++c) {
-    int st = sa_solve(h, B + (int64_t)c * h->n, X + (int64_t)c * h->n, tol, infos ? infos + c : nullptr);
-    if (st != SA_OK && worst == SA_OK) worst = st;
-    if (st != SA_OK && st != SA_ERR_NO_CONVERGENCE) return st;
+  for (int c0 = 0; c0 < k; c0 += sa::KMAX_BLOCK) {
+    const int kk = (k - c0) < sa::KMAX_BLOCK ? (k - c0) : sa::KMAX_BLOCK;
+    int sts[sa::KMAX_BLOCK];
+    const int64_t off = (int64_t)c0 * h->n;
+    int st = kk == 1 ? sa_solve(h, B + off, X + off, tol, infos ? infos + c0 : nullptr)
+                     : sa::cg_block(h, kk, B + off, X + off, tol, infos ? infos + c0 : nullptr, sts);
+    if (kk == 1) sts[0] = st;
+    else if (st != SA_OK) return st;  // a CUDA or allocation failure of the whole block
+    for (int c = 0; c < kk; ++c) {
+      if (sts[c] != SA_OK && worst == SA_OK) worst = sts[c];
+      if (sts[c] != SA_OK && sts[c] != SA_ERR_NO_CONVERGENCE && kk == 1) return sts[c];
+    }
   }
   return worst;
 }
@@ -1193,6 +1348,8 @@ int sa_free(sa_handle h) {
   h->r.release(); h->p.release(); h->q.release(); h->rprev.release(); h->t.release();
   h->part.release(); h->dots.release(); h->xb.release(); h->bb.release(); h->cg.release();
   h->it_dev.release(); h->ctl.release();
+  h->kR.release(); h->kP.release(); h->kQ.release(); h->kRp.release(); h->kT.release(); h->kX.release();
+  h->kB.release(); h->kStage.release(); h->kpart.release(); h->kdots.release(); h->kS.release(); h->kact.release();
   cudaStreamSynchronize(h->al.stream);
   if (h->host_pin) cudaFreeHost(h->host_pin);
   delete h;

@@ -19,22 +19,25 @@ namespace sa {
   const int sl = (int)(gt % SW);                                        \
   const bool valid = i < n;
 
-// power method product: w_i = s_i * sum_p a_p (s_j v_j), v_j = X_j * sc[4]
-// (the previous product times the reciprocal of its norm; 1 for the start
-// vector) -- one reciprocal per step instead of a division per entry
+// power method: y_j = s_j v_j with v_j = X_j * sc[4] (the previous product
+// times the reciprocal of its norm; 1 for the start vector), formed once per
+// step so that the product below costs one FP64 FMA per stored entry
+__global__ void k_power_prep(int64_t n, const double* __restrict__ X, const double* __restrict__ s,
+                             const double* __restrict__ sc, double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = s[i] * (X[i] * sc[4]);
+}
+
+// w_i = s_i * sum_p a_p y_j
 template <int SW>
 __global__ void k_power_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const double* __restrict__ v, const double* __restrict__ s, const double* __restrict__ X,
-                             const double* __restrict__ sc, double* __restrict__ w) {
+                             const double* __restrict__ v, const double* __restrict__ s, const double* __restrict__ y,
+                             double* __restrict__ w) {
   ROW_SETUP(SW)
-  const double inv = sc[4];
   double acc = 0.0;
   if (valid) {
     const int64_t e = rp[i + 1];
-    for (int64_t p = rp[i] + sl; p < e; p += SW) {
-      int32_t j = ci[p];
-      acc += v[p] * (s[j] * (X[j] * inv));
-    }
+    for (int64_t p = rp[i] + sl; p < e; p += SW) acc += v[p] * y[ci[p]];
   }
 #pragma unroll
   for (int o = SW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SW);
@@ -70,9 +73,9 @@ __global__ void k_dots(int64_t n, const double* __restrict__ a0, const double* _
                        const double* __restrict__ b2, double* __restrict__ part) {
   double acc[3] = {0.0, 0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    acc[0] += a0[i] * b0[i];
-    if (a1) acc[1] += a1[i] * b1[i];
-    if (a2) acc[2] += a2[i] * b2[i];
+    acc[0] = fma(a0[i], b0[i], acc[0]);
+    if (a1) acc[1] = fma(a1[i], b1[i], acc[1]);
+    if (a2) acc[2] = fma(a2[i], b2[i], acc[2]);
   }
   block_sum_to<3>(acc, part, RED_BLOCKS);
 }
@@ -213,9 +216,10 @@ int run_power(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const 
               int steps, uint32_t tag, uint32_t seed, double* lam_dev) {
   cudaStream_t st = al.stream;
   if (n <= 0) return SA_OK;
-  Buf<double> x, w, part, sc;
+  Buf<double> x, w, y, part, sc;
   SA_TRY(x.alloc(&al, n));
   SA_TRY(w.alloc(&al, n));
+  SA_TRY(y.alloc(&al, n));
   SA_TRY(part.alloc(&al, 3 * RED_BLOCKS));
   SA_TRY(sc.alloc(&al, 5));
   const double init[5] = {0.0, 0.0, 1.0, 0.0, 1.0};
@@ -229,7 +233,9 @@ int run_power(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const 
   double* X = x.p;  // previous product (the start vector at first)
   double* W = w.p;
   for (int it = 0; it < steps; ++it) {
-    DISPATCH_SW(sw, k_power_spmv, n, n, rp, ci, v, s, X, sc.p, W);
+    k_power_prep<<<blocks_for(n, 256), 256, 0, st>>>(n, X, s, sc.p, y.p);
+    SA_LAUNCHED();
+    DISPATCH_SW(sw, k_power_spmv, n, n, rp, ci, v, s, y.p, W);
     SA_LAUNCHED();
     k_power_dots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, W, X, sc.p, part.p);
     SA_LAUNCHED();
@@ -281,10 +287,10 @@ __global__ void k_cg_update(int64_t n, const CgScalars* __restrict__ s, const do
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double ri = r[i];
     if (rprev) rprev[i] = ri;
-    x[i] += alpha * p[i];
-    ri -= alpha * q[i];
+    x[i] = fma(alpha, p[i], x[i]);
+    ri = fma(-alpha, q[i], ri);
     r[i] = ri;
-    acc[0] += ri * ri;
+    acc[0] = fma(ri, ri, acc[0]);
   }
   block_sum_to<1>(acc, part, 0);
 }
@@ -308,7 +314,7 @@ __global__ void k_cg_pupdate(int64_t n, const CgScalars* __restrict__ s, const d
                              double* __restrict__ p, int first) {
   const double beta = s->beta;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = first ? z[i] : z[i] + beta * p[i];
+    p[i] = first ? z[i] : fma(beta, p[i], z[i]);
 }
 
 int launch_finish(cudaStream_t st, const double* part, int np, double* out) {
@@ -338,6 +344,196 @@ int launch_cg_beta(cudaStream_t st, CgScalars* s, const double* dots, int flexib
 
 int launch_cg_pupdate(cudaStream_t st, int64_t n, const CgScalars* s, const double* z, double* p, int first) {
   k_cg_pupdate<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, z, p, first);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// k-column CG (k independent solves in lockstep, interleaved n x k storage).
+// Every column goes through the one-vector kernels' arithmetic in the same
+// order (same grid, same per-thread stride, same reduction trees), so column
+// c of a block solve equals the one-vector solve of that right-hand side.
+// Columns that are done (converged, broken down) are frozen by `active`.
+// ---------------------------------------------------------------------------
+constexpr int KB = KMAX_BLOCK;
+
+__global__ void k_bdots(int64_t n, int k, const double* __restrict__ a0, const double* __restrict__ b0,
+                        const double* __restrict__ a1, const double* __restrict__ b1, double* __restrict__ part) {
+  double acc[2 * KB];
+#pragma unroll
+  for (int c = 0; c < 2 * KB; ++c) acc[c] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = i * k;
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      if (c < k) {
+        acc[c] = fma(a0[o + c], b0[o + c], acc[c]);
+        if (a1) acc[KB + c] = fma(a1[o + c], b1[o + c], acc[KB + c]);
+      }
+    }
+  }
+  block_sum_to<2 * KB>(acc, part, RED_BLOCKS);
+}
+
+// out[v] = sum over np partials of value v (stride `stride`), in index order,
+// with the reduction of k_dots_finish
+template <int NV>
+__global__ void k_bdots_finish(const double* __restrict__ part, int np, int stride, double* __restrict__ out) {
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (int t = threadIdx.x; t < np; t += blockDim.x)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += part[(int64_t)v * stride + t];
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double t = warp_sum(acc[v]);
+    if (lane == 0) sh[v][w] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int q = 0; q < nw; ++q) s += sh[threadIdx.x][q];
+    out[threadIdx.x] = s;
+  }
+}
+
+__global__ void k_bcg_alpha(int k, CgScalars* __restrict__ s, const double* __restrict__ dots,
+                            const int* __restrict__ active) {
+  const int c = threadIdx.x;
+  if (c >= k) return;
+  CgScalars& S = s[c];
+  if (!active[c]) { S.alpha = 0.0; return; }
+  const double pq = dots[c];
+  S.pq = pq;
+  if (!(pq > 0.0)) { S.breakdown = 1; S.alpha = 0.0; return; }
+  S.alpha = S.rz / pq;
+}
+
+__global__ void k_bcg_update(int64_t n, int k, const CgScalars* __restrict__ s, const int* __restrict__ active,
+                             const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                             double* __restrict__ r, double* __restrict__ rprev, double* __restrict__ part) {
+  double alpha[KB], acc[KB];
+  bool on[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) {
+    on[c] = c < k && active[c];
+    alpha[c] = c < k ? s[c].alpha : 0.0;
+    acc[c] = 0.0;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = i * k;
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      if (c < k) {
+        double ri = r[o + c];
+        if (on[c]) {
+          if (rprev) rprev[o + c] = ri;
+          x[o + c] = fma(alpha[c], p[o + c], x[o + c]);
+          ri = fma(-alpha[c], q[o + c], ri);
+          r[o + c] = ri;
+        }
+        acc[c] = fma(ri, ri, acc[c]);
+      }
+    }
+  }
+  block_sum_to<KB>(acc, part, RED_BLOCKS);
+}
+
+__global__ void k_bcg_beta(int k, CgScalars* __restrict__ s, const double* __restrict__ dots, int flexible,
+                           const int* __restrict__ active) {
+  const int c = threadIdx.x;
+  if (c >= k || !active[c]) return;
+  CgScalars& S = s[c];
+  const double rz_new = dots[c];
+  if (flexible < 0) {
+    S.rz = rz_new;
+    S.beta = 0.0;
+    S.breakdown = 0;
+    return;
+  }
+  const double num = flexible ? rz_new - dots[KB + c] : rz_new;
+  S.beta = num / S.rz;
+  S.rz = rz_new;
+}
+
+__global__ void k_bcg_pupdate(int64_t n, int k, const CgScalars* __restrict__ s, const int* __restrict__ active,
+                              const double* __restrict__ z, double* __restrict__ p, int first) {
+  double beta[KB];
+  bool on[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) {
+    on[c] = c < k && active[c];
+    beta[c] = c < k ? s[c].beta : 0.0;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = i * k;
+#pragma unroll
+    for (int c = 0; c < KB; ++c)
+      if (on[c]) p[o + c] = first ? z[o + c] : fma(beta[c], p[o + c], z[o + c]);
+  }
+}
+
+__global__ void k_interleave(int64_t n, int k, const double* __restrict__ src, double* __restrict__ dst,
+                             int to_interleaved) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t i = e / k;
+  const int c = (int)(e % k);
+  if (to_interleaved) dst[e] = src[(int64_t)c * n + i];
+  else dst[(int64_t)c * n + i] = src[e];
+}
+
+int launch_bdots(cudaStream_t st, int64_t n, int k, const double* a0, const double* b0, const double* a1,
+                 const double* b1, double* part, double* out) {
+  if (k < 1 || k > KB) return SA_ERR_INVALID_ARG;
+  k_bdots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, a0, b0, a1, b1, part);
+  SA_LAUNCHED();
+  k_bdots_finish<2 * KB><<<1, 1024, 0, st>>>(part, RED_BLOCKS, RED_BLOCKS, out);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+// partials laid out as part[c * np + b] (c < KB)
+int launch_bfinish(cudaStream_t st, const double* part, int np, int k, double* out) {
+  if (k < 1 || k > KB) return SA_ERR_INVALID_ARG;
+  k_bdots_finish<KB><<<1, 1024, 0, st>>>(part, np, np, out);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_bcg_alpha(cudaStream_t st, int k, CgScalars* s, const double* dots, const int* active) {
+  k_bcg_alpha<<<1, 32, 0, st>>>(k, s, dots, active);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_bcg_update(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* p,
+                      const double* q, double* x, double* r, double* rprev, double* part) {
+  k_bcg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, s, active, p, q, x, r, rprev, part);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_bcg_beta(cudaStream_t st, int k, CgScalars* s, const double* dots, int flexible, const int* active) {
+  k_bcg_beta<<<1, 32, 0, st>>>(k, s, dots, flexible, active);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_bcg_pupdate(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* z,
+                       double* p, int first) {
+  k_bcg_pupdate<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, s, active, z, p, first);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_interleave(cudaStream_t st, int64_t n, int k, const double* src, double* dst, int to_interleaved) {
+  if (n * k <= 0) return SA_OK;
+  k_interleave<<<blocks_for(n * k, 256), 256, 0, st>>>(n, k, src, dst, to_interleaved);
   SA_LAUNCHED();
   return SA_OK;
 }

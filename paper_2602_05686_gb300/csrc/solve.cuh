@@ -13,6 +13,11 @@ struct CsrView {
   int sw = 8;  // lanes per row
 };
 
+// right-hand sides one multi-vector solve carries (interleaved storage:
+// element (i, c) of an n x k block at i*k + c)
+constexpr int KMAX_BLOCK = 8;
+constexpr int KMAX_COARSE = KMAX_BLOCK;
+
 struct CgScalars {
   double rz, pq, alpha, beta;
   int breakdown;
@@ -29,10 +34,26 @@ int launch_cg_update(cudaStream_t st, int64_t n, const CgScalars* s, const doubl
 int launch_cg_beta(cudaStream_t st, CgScalars* s, const double* dots, int flexible);
 int launch_cg_pupdate(cudaStream_t st, int64_t n, const CgScalars* s, const double* z, double* p, int first);
 
+// k-column versions (k <= KMAX_BLOCK), each column summed in the one-vector
+// order so that a column of a block solve equals the one-vector solve bitwise
+int launch_bdots(cudaStream_t st, int64_t n, int k, const double* a0, const double* b0, const double* a1,
+                 const double* b1, double* part, double* out);
+int launch_bfinish(cudaStream_t st, const double* part, int np, int k, double* out);
+int launch_bcg_alpha(cudaStream_t st, int k, CgScalars* s, const double* dots, const int* active);
+int launch_bcg_update(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* p,
+                      const double* q, double* x, double* r, double* rprev, double* part);
+int launch_bcg_beta(cudaStream_t st, int k, CgScalars* s, const double* dots, int flexible, const int* active);
+int launch_bcg_pupdate(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* z,
+                       double* p, int first);
+// column-major n x k <-> interleaved
+int launch_interleave(cudaStream_t st, int64_t n, int k, const double* src, double* dst, int to_interleaved);
+
 // dense coarse level (dense.cu)
 int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                              Buf<double>& W, Buf<double>& WT);
 int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
                         double* x);
+int launch_coarse_solve_block(cudaStream_t st, int64_t n, int k, const double* W, const double* WT, const double* b,
+                              double* y, double* x);
 
 }  // namespace sa

@@ -350,12 +350,14 @@ int run_spgemm(Alloc& al, int64_t n, int64_t m, int64_t kdim, const int64_t* Arp
     SA_TRY(Cv.alloc(&al, 0));
     return SA_OK;
   }
-  // tier choice by the expected products per row, (nnz(A)/n) (nnz(B)/kdim):
-  // narrow products start on the thread tier
+  // tier choice by the expected products per row, (nnz(A)/n) (nnz(B)/kdim),
+  // an upper bound of the distinct columns (FE products repeat columns
+  // about 8 times: 90 products per row give about 11 distinct columns in the
+  // aggregation prolongators); wide products go straight to the warp tier
   int64_t nnzA = 0, nnzB = 0;
   SA_TRY(copy_d2h(&nnzA, Arp + n, sizeof(int64_t), s));
   if (kdim > 0) SA_TRY(copy_d2h(&nnzB, Brp + kdim, sizeof(int64_t), s));
-  const bool thread_tier = kdim > 0 && ((double)nnzA / (double)n) * ((double)nnzB / (double)kdim) <= 96.0;
+  const bool thread_tier = kdim > 0 && ((double)nnzA / (double)n) * ((double)nnzB / (double)kdim) <= 256.0;
   Buf<int32_t> big, midl;
   Buf<unsigned long long> nbig_d, nmid_d;
   Buf<uint8_t> isbig, ismid;

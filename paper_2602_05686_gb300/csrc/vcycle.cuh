@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "solve.cuh"
 
 namespace sa {
 
@@ -58,6 +59,7 @@ struct VLevel {
   Mat<T> A, P, R;
   Buf<T> b, x, x2, r, d;
   Buf<double> sq;  // sqrt(diag) on the coarsest level
+  Buf<T> kb, kx, kx2, kr, kd;  // k-column (interleaved) cycle vectors, n x KMAX_BLOCK, made on first use
 };
 
 template <typename T>
@@ -69,6 +71,8 @@ struct VHier {
   Buf<double> ct, cy, cx;
   const double* W = nullptr;
   const double* WT = nullptr;
+  int kready = 0;                  // k-column buffers allocated
+  Buf<double> kz, kct, kcy, kcx;   // k-column output and coarse vectors
 };
 
 // SELL-32 copy with values left_i * a_ij * right_j (scale vectors may be NULL = 1)
@@ -83,10 +87,19 @@ template <typename T>
 int vh_vcycle(VHier<T>* m, cudaStream_t s, const double* r, double** z);
 template <typename T>
 void vh_free(VHier<T>* m);
+// k <= KMAX_BLOCK right-hand sides at once: R and *Z are interleaved n x k
+// FP64 blocks; column c of *Z equals vh_vcycle of column c of R bitwise
+template <typename T>
+int vh_vcycle_block(Alloc& al, VHier<T>* m, cudaStream_t s, int k, const double* R, double** Z);
 
 // outer CG on the unscaled fine operator in FP64 SELL
 int launch_sell_spmv_dot(cudaStream_t st, const Sell<double>& A, const double* p, double* q, double* part,
                          int* nparts);
 int launch_sell_residual64(cudaStream_t st, const Sell<double>& A, const double* b, const double* x, double* r);
+// k-column forms (interleaved blocks); partials at part[c * np + cta]
+int launch_bsell_spmv_dot(cudaStream_t st, const Sell<double>& A, int k, const double* P, double* Q, double* part,
+                          int* nparts);
+int launch_bsell_residual64(cudaStream_t st, const Sell<double>& A, int k, const double* B, const double* X,
+                            double* R);
 
 }  // namespace sa

@@ -15,10 +15,15 @@ processes and restarts: a built hierarchy is written there (sa_serialize)
 and a later miss on the same operator and options loads it (sa_deserialize)
 instead of running the setup.
 
-Every numerical step runs in the CUDA library; this module only schedules.
+Requests for the same operator that are waiting together are served as one
+multi-right-hand-side job (up to `batch` columns, sa_solve_batch): every
+operator product, V-cycle and vector update of the job is one launch for all
+its columns.  Every numerical step runs in the CUDA library; this module only
+schedules.
 Results do not depend on the schedule: every kernel of the library is
-deterministic, so a request solved alone and in the mix gives bit-identical
-solutions.
+deterministic and a column of a multi-right-hand-side solve equals the
+one-vector solve bitwise, so a request solved alone and in the mix gives
+bit-identical solutions.
 """
 from __future__ import annotations
 
@@ -60,7 +65,7 @@ class Server:
     make_problem(op) -> problem dict; options(op) -> Hierarchy keyword args."""
 
     def __init__(self, make_problem, options, slots=4, hbm_budget=64 << 30, tol=1e-8, hierarchy_factory=None,
-                 stream_factory=None, store_dir=None, store_key=None, hierarchy_loader=None):
+                 stream_factory=None, store_dir=None, store_key=None, hierarchy_loader=None, batch=8):
         if hierarchy_factory is None:
             from .api import Hierarchy as hierarchy_factory
         if hierarchy_loader is None and store_dir is not None:
@@ -84,7 +89,9 @@ class Server:
         self.cv = threading.Condition()
         self.streams = [stream_factory() for _ in range(slots)]
         self.free_slots = list(range(slots))
-        self.stats = dict(admitted=0, setups=0, hits=0, evictions=0, peak_committed=0, loads=0, stores=0)
+        self.batch = max(1, int(batch))
+        self.stats = dict(admitted=0, setups=0, hits=0, evictions=0, peak_committed=0, loads=0, stores=0, jobs=0,
+                          batched=0)
         self._problems = {}
         self.building = {}  # op -> threading.Event of an in-flight setup
 
@@ -191,30 +198,48 @@ class Server:
                     self.cv.notify_all()
                 ev.set()
 
-    def _run(self, req, slot, t0):
+    def _run(self, job, slot, t0):
+        """one job: requests of one operator, solved together"""
         stream = self.streams[slot]
+        req = job[0]
         with self._ctx(stream):
             entry = None
             try:
                 entry = self._acquire(req, stream)
-                rhs = req.rhs
-                if hasattr(rhs, "to") and stream is not None and hasattr(stream, "cuda_stream"):
-                    rhs = rhs.to(device="cuda", non_blocking=True)
+                for r in job[1:]:
+                    r.cache_hit = True
+                if len(job) > 1:
+                    with self.cv:
+                        self.stats["hits"] += len(job) - 1
+                rhs = [r.rhs for r in job]
+                if hasattr(rhs[0], "to") and stream is not None and hasattr(stream, "cuda_stream"):
+                    rhs = [v.to(device="cuda", non_blocking=True) for v in rhs]
                     stream.synchronize()  # the cached handle may run on another slot's stream
                 with entry.lock:
-                    x, info = entry.h.solve(rhs, tol=self.tol, check=False)
-                req.result = x
-                req.info.update(info)
-                req.status = info["status"]
-            except Exception as e:  # a failed request is retired with its status
-                req.status = getattr(e, "status", -1)
-                req.info["error"] = str(e)
-            req.done = time.perf_counter() - t0
+                    if len(job) == 1:
+                        x, info = entry.h.solve(rhs[0], tol=self.tol, check=False)
+                        results = [(x, info)]
+                    else:
+                        import torch
+                        B = torch.stack(rhs) if hasattr(rhs[0], "to") else rhs
+                        X, infos = entry.h.solve_batch(B, tol=self.tol, check=False)
+                        results = [(X[c], infos[c]) for c in range(len(job))]
+                for r, (x, info) in zip(job, results):
+                    r.result = x
+                    r.info.update(info)
+                    r.status = info["status"]
+            except Exception as e:  # a failed job retires its requests with the status
+                for r in job:
+                    r.status = getattr(e, "status", -1)
+                    r.info["error"] = str(e)
+            done = time.perf_counter() - t0
             with self.cv:
+                for r in job:
+                    r.done = done
+                    self.committed -= r.info.pop("_reserved", 0)
                 if entry is not None:
                     entry.users -= 1
-                    entry.last = req.done
-                self.committed -= req.info.pop("_reserved", 0)
+                    entry.last = done
                 self.free_slots.append(slot)
                 self.cv.notify_all()
 
@@ -241,13 +266,27 @@ class Server:
                     busy = any(e.users for e in self.cache.values()) or len(self.free_slots) < self.slots
                     if self._make_room(need) or not busy:
                         heapq.heappop(queue)
+                        # waiting requests of the same operator join this job
+                        job = [req]
+                        if self.batch > 1:
+                            same = sorted(e for e in queue if e[2].op == req.op)[: self.batch - 1]
+                            if same:
+                                job += [e[2] for e in same]
+                                ids = {id(e[2]) for e in same}
+                                queue[:] = [e for e in queue if id(e[2]) not in ids]
+                                heapq.heapify(queue)
                         slot = self.free_slots.pop()
                         self.committed += need
                         req.info["_reserved"] = need
                         self.stats["peak_committed"] = max(self.stats["peak_committed"], self.committed)
-                        req.start = time.perf_counter() - t0
-                        self.stats["admitted"] += 1
-                        th = threading.Thread(target=self._run, args=(req, slot, t0), daemon=True)
+                        now2 = time.perf_counter() - t0
+                        for r in job:
+                            r.start = now2
+                        self.stats["admitted"] += len(job)
+                        self.stats["jobs"] += 1
+                        if len(job) > 1:
+                            self.stats["batched"] += len(job)
+                        th = threading.Thread(target=self._run, args=(job, slot, t0), daemon=True)
                         th.start()
                         threads.append(th)
                         admitted = True

@@ -69,6 +69,11 @@ def test_alone_equals_mix(env):
         assert alone[k][1] == mix[k][1]
         assert np.array_equal(alone[k][0], mix[k][0]), k
     assert out["p50_s"] <= out["p99_s"]
+    # everything waiting at once: same-operator requests share multi-RHS jobs
+    out0, mix0 = run(slots=2, gaps=0.0)
+    assert out0["failed"] == 0 and out0["batched"] > 0 and out0["jobs"] < len(reqs)
+    for k in alone:
+        assert alone[k][1] == mix0[k][1] and np.array_equal(alone[k][0], mix0[k][0]), k
 
 
 def test_small_budget_evicts_but_stays_correct(env):

@@ -11,6 +11,7 @@ from paper_2602_05686_gb300.serving import Request, Server
 class FakeHierarchy:
     live = 0
     peak = 0
+    batches = []
     lock = threading.Lock()
 
     def __init__(self, problem, stream=None, **kw):
@@ -27,6 +28,11 @@ class FakeHierarchy:
     def solve(self, b, tol=1e-8, check=False):
         time.sleep(0.002)
         return [v * 2 for v in b], {"status": 0, "iters": 3, "rel_res": 1e-9}
+
+    def solve_batch(self, B, tol=1e-8, check=False):
+        FakeHierarchy.batches.append(len(B))
+        time.sleep(0.002)
+        return [[v * 2 for v in b] for b in B], [{"status": 0, "iters": 3, "rel_res": 1e-9} for _ in B]
 
     def free(self):
         with FakeHierarchy.lock:
@@ -126,13 +132,27 @@ def test_failed_request_is_retired_with_status():
 
     probs = {0: {"n": 10, "nnz": 30, "bytes": 10}}
     s = Server(lambda op: probs[op], lambda op: {}, slots=2, hbm_budget=10_000, hierarchy_factory=Failing,
-               stream_factory=lambda: None)
+               stream_factory=lambda: None, batch=1)
     s._estimate = lambda op: 10
     rs = reqs([0, 0, 0, 0])
     out = s.serve(rs, realtime=False)
     assert out["failed"] == 1
     assert [r.status != 0 for r in rs] == [False, False, True, False]
     assert s.committed == 10  # only the cached hierarchy stays committed
+    s.close()
+
+    # a failing multi-right-hand-side job retires all of its requests
+    class FailingBatch(FakeHierarchy):
+        def solve_batch(self, B, tol=1e-8, check=False):
+            raise RuntimeError("injected failure")
+
+    s = Server(lambda op: probs[op], lambda op: {}, slots=1, hbm_budget=10_000, hierarchy_factory=FailingBatch,
+               stream_factory=lambda: None, batch=4)
+    s._estimate = lambda op: 10
+    rs = reqs([0, 0, 0])
+    out = s.serve(rs, realtime=False)
+    assert out["failed"] == 3 and out["jobs"] == 1 and all(r.info.get("error") for r in rs)
+    assert s.committed == 10
     s.close()
 
 
@@ -187,3 +207,27 @@ def test_store_carries_setups_across_servers(tmp_path):
     out4 = s4.serve(reqs([1]), realtime=False)
     s4.close()
     assert out4["setups"] == 1 and out4["failed"] == 0
+
+
+def test_same_operator_requests_share_one_job():
+    """requests of one operator waiting together form one multi-right-hand-side
+    job (at most `batch` columns); results match the one-by-one schedule"""
+    FakeHierarchy.live = FakeHierarchy.peak = 0
+    FakeHierarchy.batches = []
+    probs = {op: {"n": 10, "nnz": 30, "bytes": 100} for op in range(2)}
+    s = Server(lambda op: probs[op], lambda op: {}, slots=1, hbm_budget=10_000, hierarchy_factory=FakeHierarchy,
+               stream_factory=lambda: None, batch=3)
+    s._estimate = lambda op: probs[op]["bytes"]
+    rs = reqs([0, 0, 0, 0, 1, 0, 1])
+    out = s.serve(rs, realtime=False)
+    s.close()
+    assert out["failed"] == 0 and out["requests"] == 7
+    assert all(r.result == [2.0 * r.rid, 2.0] for r in rs)
+    assert max(FakeHierarchy.batches) <= 3 and sum(FakeHierarchy.batches) + (out["jobs"] - len(FakeHierarchy.batches)) == 7
+    assert out["jobs"] < 7 and out["batched"] >= 2
+    assert out["hits"] + out["setups"] == 7
+    s1 = Server(lambda op: probs[op], lambda op: {}, slots=1, hbm_budget=10_000, hierarchy_factory=FakeHierarchy,
+                stream_factory=lambda: None, batch=1)
+    out1 = s1.serve(reqs([0, 0, 1]), realtime=False)
+    s1.close()
+    assert out1["jobs"] == 3 and out1["batched"] == 0
