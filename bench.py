@@ -238,9 +238,16 @@ def run_ours(args):
     # against one K-column solve (every launch shared), both forms, CUDA events
     multi = None
     if not args.no_multi_rhs:
+        # right-hand sides b_c = A x_c of smooth fields x_c (load cases of one
+        # stack: the rough N(0,1) loads do not converge on this operator)
+        import scipy.sparse as sps
         K = 8
-        Bk = torch.from_numpy(np.stack([gen.Stream(500 + c, 9).normal(n) * (1 - p["dir_mask"])
+        A = sps.csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(n, n))
+        X3 = p["coords"].reshape(-1, 3)
+        zn = (X3[:, 2] - X3[:, 2].min()) / np.ptp(X3[:, 2])
+        Bk = torch.from_numpy(np.stack([A @ (np.sin(np.pi * (c + 1) * zn) * (1.0 + 0.25 * c * X3[:, 0]))
                                         for c in range(K)])).cuda()
+        del A
         multi = {"rhs": K}
         for form in ("fp64", "fp32"):
             hm.set_precision(form)

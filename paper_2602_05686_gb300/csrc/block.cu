@@ -1,0 +1,395 @@
+// Several right-hand sides at once (K = 2, 4 or 8 columns, interleaved
+// storage: element (i, c) of an n x K block at i*K + c).  Every stored entry
+// of every V-cycle matrix and of the outer FP64 operator is read once per
+// launch and applied to all K columns; the K values a row needs from a
+// gathered x_j are one aligned vector load.  Each column is accumulated in
+// the one-vector order (entry order, same lane split, same shuffle tree) and
+// goes through the same row update, so a column equals the one-vector kernel
+// bitwise.
+#include "common.cuh"
+#include "solve.cuh"
+#include "vcycle.cuh"
+#include "vkern.cuh"
+
+namespace sa {
+
+// the K values of one row of an interleaved block
+template <typename T, int K>
+__device__ __forceinline__ void ldvec(const T* __restrict__ p, T (&v)[K]) {
+  if constexpr (sizeof(T) == 4 && K % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < K / 4; ++q) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + q);
+      v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && K == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x; v[1] = t.y;
+  } else if constexpr (sizeof(T) == 8 && K % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < K / 2; ++q) {
+      const double2 t = __ldg(reinterpret_cast<const double2*>(p) + q);
+      v[2 * q] = t.x; v[2 * q + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = __ldg(p + c);
+  }
+}
+
+template <typename T, int SW, int K>
+__device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restrict__ X, T (&acc)[K], int64_t& row) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = (T)0;
+  T xv[K];
+  if constexpr (SW == 0) {
+    row = gt;
+    if (gt >= M.n) return false;
+    const int64_t sl = gt >> 5, r = gt & 31;
+    const int64_t b = M.p[sl], e = M.p[sl + 1];
+    if (M.c16) {
+      const T* __restrict__ xs = X + (int64_t)M.base[sl] * K;
+      for (int64_t p = b + r; p < e; p += 32) {
+        const T a = __ldcs(&M.v[p]);
+        ldvec<T, K>(xs + (int64_t)__ldcs(&M.c16[p]) * K, xv);
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
+      }
+    } else {
+      for (int64_t p = b + r; p < e; p += 32) {
+        const T a = __ldcs(&M.v[p]);
+        ldvec<T, K>(X + (int64_t)__ldcs(&M.ci[p]) * K, xv);
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
+      }
+    }
+    return true;
+  } else {
+    const int64_t i = gt / SW;
+    const int sl = (int)(gt % SW);
+    row = i;
+    if (i < M.n) {
+      const int64_t e = M.p[i + 1];
+      for (int64_t q = M.p[i] + sl; q < e; q += SW) {
+        const T a = M.v[q];
+        ldvec<T, K>(X + (int64_t)M.ci[q] * K, xv);
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c)
+#pragma unroll
+      for (int o = SW / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(FULL, acc[c], o, SW);
+    return i < M.n && sl == 0;
+  }
+}
+
+template <typename T, int SW, int K>
+__global__ void k_bvc_cheb(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+                           T* __restrict__ d, T c1, T c2, int first) {
+  T y[K];
+  int64_t i;
+  if (!brow_apply<T, SW, K>(A, xin, y, i)) return;
+  const int64_t o = i * K;
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    const T dn = cheb_dir<T>(b[o + c], y[c], first ? (T)0 : d[o + c], c1, c2, first);
+    d[o + c] = dn;
+    xout[o + c] = xin[o + c] + dn;
+  }
+}
+
+template <typename T, int SW, int K>
+__global__ void k_bvc_residual(MatView<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
+  T y[K];
+  int64_t i;
+  if (!brow_apply<T, SW, K>(A, x, y, i)) return;
+  const int64_t o = i * K;
+#pragma unroll
+  for (int c = 0; c < K; ++c) r[o + c] = b[o + c] - y[c];
+}
+
+template <typename T, int SW, int K>
+__global__ void k_bvc_spmv(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
+  T y[K];
+  int64_t i;
+  if (!brow_apply<T, SW, K>(A, x, y, i)) return;
+  const int64_t o = i * K;
+#pragma unroll
+  for (int c = 0; c < K; ++c) out[o + c] = y[c];
+}
+
+template <typename T, int SW, int K>
+__global__ void k_bvc_spmv_add(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
+  T y[K];
+  int64_t i;
+  if (!brow_apply<T, SW, K>(A, x, y, i)) return;
+  const int64_t o = i * K;
+#pragma unroll
+  for (int c = 0; c < K; ++c) out[o + c] += y[c];
+}
+
+template <typename T, int SW, int K>
+__global__ void k_bvc_cheb_out(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin,
+                               const T* __restrict__ d, T c1, T c2, int first, const double* __restrict__ s,
+                               double* __restrict__ z) {
+  T y[K];
+  int64_t i;
+  if (!brow_apply<T, SW, K>(A, xin, y, i)) return;
+  const int64_t o = i * K;
+  const double si = s[i];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    const T dn = cheb_dir<T>(b[o + c], y[c], first ? (T)0 : d[o + c], c1, c2, first);
+    z[o + c] = si * (double)(xin[o + c] + dn);
+  }
+}
+
+// elementwise forms over the n*K elements
+template <typename T>
+__global__ void k_bvc_fine_in(int64_t n, int K, const double* __restrict__ r, const double* __restrict__ s, T c2,
+                              T* __restrict__ b, T* __restrict__ x, T* __restrict__ d) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n * K) {
+    const T bi = (T)(s[e / K] * r[e]);
+    b[e] = bi;
+    const T dn = c2 * bi;
+    d[e] = dn;
+    x[e] = dn;
+  }
+}
+
+template <typename T>
+__global__ void k_bvc_first(int64_t nk, const T* __restrict__ b, T c2, T* __restrict__ x, T* __restrict__ d) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nk) {
+    const T dn = c2 * b[e];
+    d[e] = dn;
+    x[e] = dn;
+  }
+}
+
+template <typename T>
+__global__ void k_bcoarse_in(int64_t n, int K, const T* __restrict__ b, const double* __restrict__ sq,
+                             double* __restrict__ t) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n * K) t[e] = sq[e / K] * (double)b[e];
+}
+
+template <typename T>
+__global__ void k_bcoarse_out(int64_t n, int K, const double* __restrict__ x, const double* __restrict__ sq,
+                              T* __restrict__ xo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n * K) xo[e] = (T)(sq[e / K] * x[e]);
+}
+
+// launch `Kern<T, sw, K>` over the rows of M
+#define BMAT_SW(Kern, KK, M, st, ...)                                                    \
+  do {                                                                                   \
+    const MatView<T> _mv = view(M);                                                      \
+    const int64_t _thr = (M).sw == 0 ? (M).n : (M).n * (int64_t)(M).sw;                  \
+    const unsigned _g = blocks_for(_thr, 256);                                           \
+    switch ((M).sw) {                                                                    \
+      case 0: Kern<T, 0, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;               \
+      case 4: Kern<T, 4, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;               \
+      case 8: Kern<T, 8, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;               \
+      case 16: Kern<T, 16, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;             \
+      default: Kern<T, 32, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;             \
+    }                                                                                    \
+  } while (0)
+
+#define LAUNCH_BMAT(Kern, M, st, K, ...)                                                 \
+  do {                                                                                   \
+    if ((K) == 2) BMAT_SW(Kern, 2, M, st, __VA_ARGS__);                                  \
+    else if ((K) == 4) BMAT_SW(Kern, 4, M, st, __VA_ARGS__);                             \
+    else BMAT_SW(Kern, 8, M, st, __VA_ARGS__);                                           \
+    SA_LAUNCHED();                                                                       \
+  } while (0)
+
+template <typename T>
+static int block_alloc(Alloc& al, VHier<T>* m) {
+  if (m->kready) return SA_OK;
+  const int nl = (int)m->lev.size();
+  for (int l = 0; l < nl; ++l) {
+    VLevel<T>* L = m->lev[l];
+    const int64_t nk = L->n * KMAX_BLOCK;
+    SA_TRY(L->kb.alloc(&al, nk));
+    SA_TRY(L->kx.alloc(&al, nk));
+    if (l + 1 < nl) {
+      SA_TRY(L->kx2.alloc(&al, nk));
+      SA_TRY(L->kr.alloc(&al, nk));
+      SA_TRY(L->kd.alloc(&al, nk));
+    }
+  }
+  const int64_t nL = m->lev[nl - 1]->n;
+  SA_TRY(m->kct.alloc(&al, nL * KMAX_BLOCK));
+  SA_TRY(m->kcy.alloc(&al, nL * KMAX_BLOCK));
+  SA_TRY(m->kcx.alloc(&al, nL * KMAX_BLOCK));
+  SA_TRY(m->kz.alloc(&al, m->lev[0]->n * KMAX_BLOCK));
+  m->kready = 1;
+  return SA_OK;
+}
+
+// the cycle of mv() (vcycle.cu) on K columns
+template <typename T>
+static int mv_block(VHier<T>* m, cudaStream_t st, int l, int K, const double* r64, T** xo) {
+  VLevel<T>* L = m->lev[l];
+  const int nl = (int)m->lev.size();
+  const int64_t n = L->n, nk = n * K;
+  if (l == nl - 1) {
+    k_bcoarse_in<T><<<g256(nk), 256, 0, st>>>(n, K, L->kb.p, L->sq.p, m->kct.p);
+    SA_LAUNCHED();
+    SA_TRY(launch_coarse_solve_block(st, n, K, m->W, m->WT, m->kct.p, m->kcy.p, m->kcx.p));
+    k_bcoarse_out<T><<<g256(nk), 256, 0, st>>>(n, K, m->kcx.p, L->sq.p, L->kx.p);
+    SA_LAUNCHED();
+    *xo = L->kx.p;
+    return SA_OK;
+  }
+  const int deg = m->deg;
+  const double th = 0.5 * (L->lmax + L->lmin), de = 0.5 * (L->lmax - L->lmin);
+  const double s1 = th / de;
+  T* xa = L->kx.p;
+  T* xb = L->kx2.p;
+  const Mat<T>& A = L->A;
+  if (l == 0) k_bvc_fine_in<T><<<g256(nk), 256, 0, st>>>(n, K, r64, m->s0.p, (T)(1.0 / th), L->kb.p, xa, L->kd.p);
+  else k_bvc_first<T><<<g256(nk), 256, 0, st>>>(nk, L->kb.p, (T)(1.0 / th), xa, L->kd.p);
+  SA_LAUNCHED();
+  double rho = 1.0 / s1;
+  for (int q = 1; q < deg; ++q) {
+    double rn = 1.0 / (2.0 * s1 - rho);
+    LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, L->kd.p, (T)(rn * rho), (T)(2.0 * rn / de), 0);
+    T* t = xa; xa = xb; xb = t;
+    rho = rn;
+  }
+  VLevel<T>* C = m->lev[l + 1];
+  LAUNCH_BMAT(k_bvc_residual, A, st, K, L->kb.p, xa, L->kr.p);
+  LAUNCH_BMAT(k_bvc_spmv, L->R, st, K, L->kr.p, C->kb.p);
+  T* xc = nullptr;
+  SA_TRY(mv_block(m, st, l + 1, K, nullptr, &xc));
+  LAUNCH_BMAT(k_bvc_spmv_add, L->P, st, K, xc, xa);
+  rho = 1.0 / s1;
+  for (int q = 0; q < deg; ++q) {
+    int first = (q == 0);
+    T c1 = (T)0, c2 = (T)(1.0 / th);
+    double rn = rho;
+    if (!first) {
+      rn = 1.0 / (2.0 * s1 - rho);
+      c1 = (T)(rn * rho);
+      c2 = (T)(2.0 * rn / de);
+    }
+    if (l == 0 && q == deg - 1) {
+      LAUNCH_BMAT(k_bvc_cheb_out, A, st, K, L->kb.p, xa, L->kd.p, c1, c2, first, m->s0.p, m->kz.p);
+    } else {
+      LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, L->kd.p, c1, c2, first);
+      T* t = xa; xa = xb; xb = t;
+    }
+    if (!first) rho = rn;
+  }
+  *xo = xa;
+  return SA_OK;
+}
+
+template <typename T>
+int vh_vcycle_block(Alloc& al, VHier<T>* m, cudaStream_t st, int K, const double* R, double** Z) {
+  if (K != 2 && K != 4 && K != 8) return SA_ERR_INVALID_ARG;
+  SA_TRY(block_alloc(al, m));
+  if (m->lev.size() == 1) {
+    const int64_t n = m->lev[0]->n;
+    SA_TRY(launch_coarse_solve_block(st, n, K, m->W, m->WT, R, m->kcy.p, m->kz.p));
+    *Z = m->kz.p;
+    return SA_OK;
+  }
+  T* xo = nullptr;
+  SA_TRY(mv_block<T>(m, st, 0, K, R, &xo));
+  *Z = m->kz.p;
+  return SA_OK;
+}
+
+template int vh_vcycle_block<double>(Alloc&, VHier<double>*, cudaStream_t, int, const double*, double**);
+template int vh_vcycle_block<float>(Alloc&, VHier<float>*, cudaStream_t, int, const double*, double**);
+
+// ---------------------------------------------------------------------------
+// outer CG on K columns: Q = A P with the per-column partial p.q sums (the
+// one-vector reduction tree per column) and R = B - A X, FP64 SELL
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void k_bsell_spmv_dot(MatView<double> A, const double* __restrict__ P, double* __restrict__ Q,
+                                 double* __restrict__ part) {
+  double y[K], c[K];
+  int64_t i;
+#pragma unroll
+  for (int j = 0; j < K; ++j) c[j] = 0.0;
+  if (brow_apply<double, 0, K>(A, P, y, i)) {
+    const int64_t o = i * K;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      Q[o + j] = y[j];
+      c[j] = y[j] * P[o + j];
+    }
+  }
+  __shared__ double sh[K][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const double t = warp_sum(c[j]);
+    if (lane == 0) sh[j][w] = t;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      double t = lane < (int)(blockDim.x >> 5) ? sh[j][lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) part[(int64_t)j * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+template <int K>
+__global__ void k_bsell_res64(MatView<double> A, const double* __restrict__ B, const double* __restrict__ X,
+                              double* __restrict__ R) {
+  double y[K];
+  int64_t i;
+  if (!brow_apply<double, 0, K>(A, X, y, i)) return;
+  const int64_t o = i * K;
+#pragma unroll
+  for (int j = 0; j < K; ++j) R[o + j] = B[o + j] - y[j];
+}
+
+static MatView<double> sell_view(const Sell<double>& A) {
+  MatView<double> m;
+  m.n = A.n;
+  m.p = A.sp.p;
+  m.ci = A.ci.p;
+  m.v = A.v.p;
+  m.base = A.idx16 ? A.base.p : nullptr;
+  m.c16 = A.idx16 ? A.c16.p : nullptr;
+  return m;
+}
+
+int launch_bsell_spmv_dot(cudaStream_t st, const Sell<double>& A, int K, const double* P, double* Q, double* part,
+                          int* nparts) {
+  *nparts = (int)g256(A.n);
+  const MatView<double> mv = sell_view(A);
+  if (K == 2) k_bsell_spmv_dot<2><<<g256(A.n), 256, 0, st>>>(mv, P, Q, part);
+  else if (K == 4) k_bsell_spmv_dot<4><<<g256(A.n), 256, 0, st>>>(mv, P, Q, part);
+  else if (K == 8) k_bsell_spmv_dot<8><<<g256(A.n), 256, 0, st>>>(mv, P, Q, part);
+  else return SA_ERR_INVALID_ARG;
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int launch_bsell_residual64(cudaStream_t st, const Sell<double>& A, int K, const double* B, const double* X,
+                            double* R) {
+  const MatView<double> mv = sell_view(A);
+  if (K == 2) k_bsell_res64<2><<<g256(A.n), 256, 0, st>>>(mv, B, X, R);
+  else if (K == 4) k_bsell_res64<4><<<g256(A.n), 256, 0, st>>>(mv, B, X, R);
+  else if (K == 8) k_bsell_res64<8><<<g256(A.n), 256, 0, st>>>(mv, B, X, R);
+  else return SA_ERR_INVALID_ARG;
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+}  // namespace sa

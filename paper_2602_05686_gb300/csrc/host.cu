@@ -587,6 +587,9 @@ static int precondition_block(sa_handle h, int k, const double* R, double** Z) {
 }
 
 static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos, int* statuses) {
+  // the block carries K in {2, 4, 8} columns; columns k..K-1 are zero and
+  // never active
+  const int K = k <= 2 ? 2 : (k <= 4 ? 4 : KMAX_BLOCK);
   cudaStream_t s = h->al.stream;
   const int64_t n = h->n;
   const int flexible = h->opt.precision == SA_PREC_FP32_VCYCLE;
@@ -598,86 +601,86 @@ static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, 
   double* part = h->kpart.p; double* dots = h->kdots.p;
   // inputs: column-major (host or device) -> interleaved
   SA_CUDA(cudaMemcpyAsync(h->kStage.p, B, sizeof(double) * n * k, cudaMemcpyDefault, s));
-  SA_TRY(launch_interleave(s, n, k, h->kStage.p, Bb, 1));
+  SA_TRY(launch_interleave(s, n, k, K, h->kStage.p, Bb, 1));
   SA_CUDA(cudaMemcpyAsync(h->kStage.p, X, sizeof(double) * n * k, cudaMemcpyDefault, s));
-  SA_TRY(launch_interleave(s, n, k, h->kStage.p, Xb, 1));
+  SA_TRY(launch_interleave(s, n, k, K, h->kStage.p, Xb, 1));
   // host view of the columns
   double r0[KMAX_BLOCK], hb[2 * KMAX_BLOCK];
   int act[KMAX_BLOCK], its[KMAX_BLOCK], st[KMAX_BLOCK];
   struct { double rr[KMAX_BLOCK]; CgScalars S[KMAX_BLOCK]; } hr;
-  SA_TRY(launch_bsell_residual64(s, h->A0s, k, Bb, Xb, R));
-  SA_TRY(launch_bdots(s, n, k, R, R, nullptr, nullptr, part, dots));
-  SA_CUDA(cudaMemcpyAsync(hb, dots, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  SA_TRY(launch_bsell_residual64(s, h->A0s, K, Bb, Xb, R));
+  SA_TRY(launch_bdots(s, n, K, R, R, nullptr, nullptr, part, dots));
+  SA_CUDA(cudaMemcpyAsync(hb, dots, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
   SA_CUDA(cudaStreamSynchronize(s));
   int nact = 0;
-  for (int c = 0; c < k; ++c) {
+  for (int c = 0; c < K; ++c) {
     r0[c] = sqrt(hb[c]);
-    act[c] = r0[c] > 0.0;
+    act[c] = c < k && r0[c] > 0.0;
     its[c] = 0;
     st[c] = act[c] ? SA_ERR_NO_CONVERGENCE : SA_OK;
     nact += act[c];
   }
-  SA_CUDA(cudaMemcpyAsync(h->kact.p, act, sizeof(int) * k, cudaMemcpyHostToDevice, s));
+  SA_CUDA(cudaMemcpyAsync(h->kact.p, act, sizeof(int) * K, cudaMemcpyHostToDevice, s));
   if (nact > 0) {
     // first iteration
     double* Z = nullptr;
-    SA_TRY(precondition_block(h, k, R, &Z));
-    SA_TRY(launch_bcg_pupdate(s, n, k, h->kS.p, h->kact.p, Z, P, 1));
-    SA_TRY(launch_bdots(s, n, k, R, Z, nullptr, nullptr, part, dots));
-    SA_TRY(launch_bcg_beta(s, k, h->kS.p, dots, -1, h->kact.p));
+    SA_TRY(precondition_block(h, K, R, &Z));
+    SA_TRY(launch_bcg_pupdate(s, n, K, h->kS.p, h->kact.p, Z, P, 1));
+    SA_TRY(launch_bdots(s, n, K, R, Z, nullptr, nullptr, part, dots));
+    SA_TRY(launch_bcg_beta(s, K, h->kS.p, dots, -1, h->kact.p));
     for (int it = 1;; ++it) {
       int np = 0;
-      SA_TRY(launch_bsell_spmv_dot(s, h->A0s, k, P, Q, part, &np));
-      SA_TRY(launch_bfinish(s, part, np, k, dots));
-      SA_TRY(launch_bcg_alpha(s, k, h->kS.p, dots, h->kact.p));
-      SA_TRY(launch_bcg_update(s, n, k, h->kS.p, h->kact.p, P, Q, Xb, R, flexible ? Rp : nullptr, part));
-      SA_TRY(launch_bfinish(s, part, RED_BLOCKS, k, dots + 2 * KMAX_BLOCK));
-      SA_CUDA(cudaMemcpyAsync(hr.rr, dots + 2 * KMAX_BLOCK, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-      SA_CUDA(cudaMemcpyAsync(hr.S, h->kS.p, sizeof(CgScalars) * k, cudaMemcpyDeviceToHost, s));
+      SA_TRY(launch_bsell_spmv_dot(s, h->A0s, K, P, Q, part, &np));
+      SA_TRY(launch_bfinish(s, part, np, K, dots));
+      SA_TRY(launch_bcg_alpha(s, K, h->kS.p, dots, h->kact.p));
+      SA_TRY(launch_bcg_update(s, n, K, h->kS.p, h->kact.p, P, Q, Xb, R, flexible ? Rp : nullptr, part));
+      SA_TRY(launch_bfinish(s, part, RED_BLOCKS, K, dots + 2 * KMAX_BLOCK));
+      SA_CUDA(cudaMemcpyAsync(hr.rr, dots + 2 * KMAX_BLOCK, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+      SA_CUDA(cudaMemcpyAsync(hr.S, h->kS.p, sizeof(CgScalars) * K, cudaMemcpyDeviceToHost, s));
       SA_CUDA(cudaStreamSynchronize(s));
       // per column: breakdown, convergence candidate (confirmed on the true
       // residual, which replaces r when it does not confirm), maxit
       bool cand = false;
-      for (int c = 0; c < k; ++c) {
+      for (int c = 0; c < K; ++c) {
         if (!act[c]) continue;
         its[c] = it;
         if (hr.S[c].breakdown) { st[c] = SA_ERR_BREAKDOWN; act[c] = 0; continue; }
         if (sqrt(hr.rr[c]) <= tol * r0[c]) cand = true;
       }
       if (cand) {
-        SA_TRY(launch_bsell_residual64(s, h->A0s, k, Bb, Xb, T));
-        SA_TRY(launch_bdots(s, n, k, T, T, nullptr, nullptr, part, dots + 3 * KMAX_BLOCK));
-        SA_CUDA(cudaMemcpyAsync(hb, dots + 3 * KMAX_BLOCK, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        SA_TRY(launch_bsell_residual64(s, h->A0s, K, Bb, Xb, T));
+        SA_TRY(launch_bdots(s, n, K, T, T, nullptr, nullptr, part, dots + 3 * KMAX_BLOCK));
+        SA_CUDA(cudaMemcpyAsync(hb, dots + 3 * KMAX_BLOCK, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
         SA_CUDA(cudaStreamSynchronize(s));
-        for (int c = 0; c < k; ++c) {
+        for (int c = 0; c < K; ++c) {
           if (!act[c] || !(sqrt(hr.rr[c]) <= tol * r0[c])) continue;
           if (sqrt(hb[c]) <= tol * r0[c]) {
             st[c] = SA_OK;
             act[c] = 0;
           } else {
-            SA_CUDA(cudaMemcpy2DAsync(R + c, sizeof(double) * k, T + c, sizeof(double) * k, sizeof(double), n,
+            SA_CUDA(cudaMemcpy2DAsync(R + c, sizeof(double) * K, T + c, sizeof(double) * K, sizeof(double), n,
                                       cudaMemcpyDeviceToDevice, s));
           }
         }
       }
       nact = 0;
-      for (int c = 0; c < k; ++c) {
+      for (int c = 0; c < K; ++c) {
         if (act[c] && it >= maxit) act[c] = 0;  // status stays SA_ERR_NO_CONVERGENCE
         nact += act[c];
       }
-      SA_CUDA(cudaMemcpyAsync(h->kact.p, act, sizeof(int) * k, cudaMemcpyHostToDevice, s));
+      SA_CUDA(cudaMemcpyAsync(h->kact.p, act, sizeof(int) * K, cudaMemcpyHostToDevice, s));
       if (nact == 0) break;
-      SA_TRY(precondition_block(h, k, R, &Z));
-      SA_TRY(launch_bdots(s, n, k, R, Z, flexible ? Z : nullptr, flexible ? Rp : nullptr, part, dots));
-      SA_TRY(launch_bcg_beta(s, k, h->kS.p, dots, flexible, h->kact.p));
-      SA_TRY(launch_bcg_pupdate(s, n, k, h->kS.p, h->kact.p, Z, P, 0));
+      SA_TRY(precondition_block(h, K, R, &Z));
+      SA_TRY(launch_bdots(s, n, K, R, Z, flexible ? Z : nullptr, flexible ? Rp : nullptr, part, dots));
+      SA_TRY(launch_bcg_beta(s, K, h->kS.p, dots, flexible, h->kact.p));
+      SA_TRY(launch_bcg_pupdate(s, n, K, h->kS.p, h->kact.p, Z, P, 0));
     }
   }
   // true residuals at exit and the solutions
-  SA_TRY(launch_bsell_residual64(s, h->A0s, k, Bb, Xb, T));
-  SA_TRY(launch_bdots(s, n, k, T, T, nullptr, nullptr, part, dots + 3 * KMAX_BLOCK));
-  SA_CUDA(cudaMemcpyAsync(hb, dots + 3 * KMAX_BLOCK, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-  SA_TRY(launch_interleave(s, n, k, Xb, h->kStage.p, 0));
+  SA_TRY(launch_bsell_residual64(s, h->A0s, K, Bb, Xb, T));
+  SA_TRY(launch_bdots(s, n, K, T, T, nullptr, nullptr, part, dots + 3 * KMAX_BLOCK));
+  SA_CUDA(cudaMemcpyAsync(hb, dots + 3 * KMAX_BLOCK, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+  SA_TRY(launch_interleave(s, n, k, K, Xb, h->kStage.p, 0));
   SA_CUDA(cudaMemcpyAsync(X, h->kStage.p, sizeof(double) * n * k, cudaMemcpyDefault, s));
   SA_CUDA(cudaStreamSynchronize(s));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

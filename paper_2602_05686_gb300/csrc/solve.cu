@@ -477,14 +477,15 @@ __global__ void k_bcg_pupdate(int64_t n, int k, const CgScalars* __restrict__ s,
   }
 }
 
-__global__ void k_interleave(int64_t n, int k, const double* __restrict__ src, double* __restrict__ dst,
+// column-major n x k <-> interleaved n x K (columns k..K-1 of the block are zero)
+__global__ void k_interleave(int64_t n, int k, int K, const double* __restrict__ src, double* __restrict__ dst,
                              int to_interleaved) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * k) return;
-  const int64_t i = e / k;
-  const int c = (int)(e % k);
-  if (to_interleaved) dst[e] = src[(int64_t)c * n + i];
-  else dst[(int64_t)c * n + i] = src[e];
+  if (e >= n * K) return;
+  const int64_t i = e / K;
+  const int c = (int)(e % K);
+  if (to_interleaved) dst[e] = c < k ? src[(int64_t)c * n + i] : 0.0;
+  else if (c < k) dst[(int64_t)c * n + i] = src[e];
 }
 
 int launch_bdots(cudaStream_t st, int64_t n, int k, const double* a0, const double* b0, const double* a1,
@@ -531,9 +532,9 @@ int launch_bcg_pupdate(cudaStream_t st, int64_t n, int k, const CgScalars* s, co
   return SA_OK;
 }
 
-int launch_interleave(cudaStream_t st, int64_t n, int k, const double* src, double* dst, int to_interleaved) {
-  if (n * k <= 0) return SA_OK;
-  k_interleave<<<blocks_for(n * k, 256), 256, 0, st>>>(n, k, src, dst, to_interleaved);
+int launch_interleave(cudaStream_t st, int64_t n, int k, int K, const double* src, double* dst, int to_interleaved) {
+  if (n * K <= 0) return SA_OK;
+  k_interleave<<<blocks_for(n * K, 256), 256, 0, st>>>(n, k, K, src, dst, to_interleaved);
   SA_LAUNCHED();
   return SA_OK;
 }

@@ -45,8 +45,8 @@ int launch_bcg_update(cudaStream_t st, int64_t n, int k, const CgScalars* s, con
 int launch_bcg_beta(cudaStream_t st, int k, CgScalars* s, const double* dots, int flexible, const int* active);
 int launch_bcg_pupdate(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* z,
                        double* p, int first);
-// column-major n x k <-> interleaved
-int launch_interleave(cudaStream_t st, int64_t n, int k, const double* src, double* dst, int to_interleaved);
+// column-major n x k <-> interleaved n x K (K >= k; columns k..K-1 zero)
+int launch_interleave(cudaStream_t st, int64_t n, int k, int K, const double* src, double* dst, int to_interleaved);
 
 // dense coarse level (dense.cu)
 int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,

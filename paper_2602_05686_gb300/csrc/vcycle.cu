@@ -19,6 +19,7 @@
 #include "profile.cuh"
 #include "solve.cuh"
 #include "vcycle.cuh"
+#include "vkern.cuh"
 
 namespace sa {
 
@@ -256,115 +257,6 @@ template int vh_build<float>(Alloc&, const VLevelIn*, int, int, const double*, c
 // ---------------------------------------------------------------------------
 // kernels (one thread per row)
 // ---------------------------------------------------------------------------
-// Row products of one thread: the entries of row i sit 32 apart inside its
-// slice.  Four entries per iteration keep four value / column loads and
-// four gathers in flight per thread (the kernels are latency bound
-// otherwise); the products are still added in entry order.  Values and
-// columns are read once (evict-first loads), so the gathered x stays cached.
-template <typename T>
-__device__ __forceinline__ T sell_row(const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
-                                      const T* __restrict__ v, const T* __restrict__ x, int64_t i) {
-  const int64_t sl = i >> 5, r = i & 31;
-  const int64_t b = sp[sl], e = sp[sl + 1];
-  T acc = (T)0;
-  int64_t p = b + r;
-  for (; p + 96 < e; p += 128) {
-    const T v0 = __ldcs(&v[p]), v1 = __ldcs(&v[p + 32]), v2 = __ldcs(&v[p + 64]), v3 = __ldcs(&v[p + 96]);
-    const int32_t c0 = __ldcs(&ci[p]), c1 = __ldcs(&ci[p + 32]), c2 = __ldcs(&ci[p + 64]), c3 = __ldcs(&ci[p + 96]);
-    const T x0 = __ldg(&x[c0]), x1 = __ldg(&x[c1]), x2 = __ldg(&x[c2]), x3 = __ldg(&x[c3]);
-    acc += v0 * x0;
-    acc += v1 * x1;
-    acc += v2 * x2;
-    acc += v3 * x3;
-  }
-  for (; p < e; p += 32) acc += __ldcs(&v[p]) * __ldg(&x[__ldcs(&ci[p])]);
-  return acc;
-}
-
-// compressed columns: x[base[slice] + offset]
-template <typename T>
-__device__ __forceinline__ T sell_row16(const int64_t* __restrict__ sp, const int32_t* __restrict__ base,
-                                        const uint16_t* __restrict__ c16, const T* __restrict__ v,
-                                        const T* __restrict__ x, int64_t i) {
-  const int64_t sl = i >> 5, r = i & 31;
-  const int64_t b = sp[sl], e = sp[sl + 1];
-  const T* __restrict__ xs = x + base[sl];
-  T acc = (T)0;
-  int64_t p = b + r;
-  for (; p + 96 < e; p += 128) {
-    const T v0 = __ldcs(&v[p]), v1 = __ldcs(&v[p + 32]), v2 = __ldcs(&v[p + 64]), v3 = __ldcs(&v[p + 96]);
-    const unsigned c0 = __ldcs(&c16[p]), c1 = __ldcs(&c16[p + 32]), c2 = __ldcs(&c16[p + 64]),
-                   c3 = __ldcs(&c16[p + 96]);
-    const T x0 = __ldg(&xs[c0]), x1 = __ldg(&xs[c1]), x2 = __ldg(&xs[c2]), x3 = __ldg(&xs[c3]);
-    acc += v0 * x0;
-    acc += v1 * x1;
-    acc += v2 * x2;
-    acc += v3 * x3;
-  }
-  for (; p < e; p += 32) acc += __ldcs(&v[p]) * __ldg(&xs[__ldcs(&c16[p])]);
-  return acc;
-}
-
-template <typename T>
-struct MatView {
-  int64_t n;
-  const int64_t* p;  // SELL slice offsets or CSR row pointers
-  const int32_t* ci;
-  const T* v;
-  const int32_t* base;   // compressed SELL columns (else NULL)
-  const uint16_t* c16;
-};
-
-template <typename T>
-static MatView<T> view(const Mat<T>& M) {
-  MatView<T> m;
-  m.n = M.n;
-  m.base = nullptr;
-  m.c16 = nullptr;
-  if (M.sw == 0) {
-    m.p = M.sell.sp.p; m.ci = M.sell.ci.p; m.v = M.sell.v.p;
-    if (M.sell.idx16) { m.base = M.sell.base.p; m.c16 = M.sell.c16.p; }
-  } else {
-    m.p = M.rp.p; m.ci = M.ci.p; m.v = M.v.p;
-  }
-  return m;
-}
-
-// the row product of this thread's row; SW = 0: SELL-32, one thread per row;
-// SW > 0: CSR, SW lanes per row, reduced by shuffles (every lane of the warp
-// reaches the shuffles).  Returns true for the thread that owns the row.
-template <typename T, int SW>
-__device__ __forceinline__ bool row_apply(const MatView<T>& M, const T* __restrict__ x, T& out, int64_t& row) {
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if constexpr (SW == 0) {
-    row = gt;
-    if (gt >= M.n) return false;
-    out = M.c16 ? sell_row16<T>(M.p, M.base, M.c16, M.v, x, gt) : sell_row<T>(M.p, M.ci, M.v, x, gt);
-    return true;
-  } else {
-    const int64_t i = gt / SW;
-    const int sl = (int)(gt % SW);
-    row = i;
-    T acc = (T)0;
-    if (i < M.n) {
-      const int64_t e = M.p[i + 1];
-      for (int64_t q = M.p[i] + sl; q < e; q += SW) acc += M.v[q] * __ldg(&x[M.ci[q]]);
-    }
-#pragma unroll
-    for (int o = SW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SW);
-    out = acc;
-    return i < M.n && sl == 0;
-  }
-}
-
-// Chebyshev direction d = first ? c2 r : c1 d + c2 r with r = b - y, written
-// once and shared by the one- and multi-vector kernels (same rounding)
-template <typename T>
-__device__ __forceinline__ T cheb_dir(T b, T y, T d, T c1, T c2, int first) {
-  const T r = b - y;
-  return first ? c2 * r : fma(c1, d, c2 * r);
-}
-
 // x_out = x_in + d,  d = first ? c2 r : c1 d + c2 r,  r = b - A~ x_in
 template <typename T, int SW>
 __global__ void k_vc_cheb(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
@@ -434,163 +326,6 @@ __global__ void k_vc_fine_in(int64_t n, const double* __restrict__ r, const doub
   }
 }
 
-// ---------------------------------------------------------------------------
-// k right-hand sides at once (interleaved n x k blocks, element (i, c) at
-// i*k + c): every stored entry is read once and applied to all k columns;
-// each column is accumulated in the one-vector order (entry order, same lane
-// split and shuffle tree), so a column equals the one-vector kernel bitwise
-// ---------------------------------------------------------------------------
-constexpr int KB = KMAX_BLOCK;
-
-template <typename T, int SW>
-__device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restrict__ X, int k, T (&acc)[KB],
-                                           int64_t& row) {
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-#pragma unroll
-  for (int c = 0; c < KB; ++c) acc[c] = (T)0;
-  if constexpr (SW == 0) {
-    row = gt;
-    if (gt >= M.n) return false;
-    const int64_t sl = gt >> 5, r = gt & 31;
-    const int64_t b = M.p[sl], e = M.p[sl + 1];
-    if (M.c16) {
-      const T* __restrict__ xs = X + (int64_t)M.base[sl] * k;
-      for (int64_t p = b + r; p < e; p += 32) {
-        const T a = __ldcs(&M.v[p]);
-        const T* __restrict__ xr = xs + (int64_t)__ldcs(&M.c16[p]) * k;
-#pragma unroll
-        for (int c = 0; c < KB; ++c)
-          if (c < k) acc[c] += a * __ldg(&xr[c]);
-      }
-    } else {
-      for (int64_t p = b + r; p < e; p += 32) {
-        const T a = __ldcs(&M.v[p]);
-        const T* __restrict__ xr = X + (int64_t)__ldcs(&M.ci[p]) * k;
-#pragma unroll
-        for (int c = 0; c < KB; ++c)
-          if (c < k) acc[c] += a * __ldg(&xr[c]);
-      }
-    }
-    return true;
-  } else {
-    const int64_t i = gt / SW;
-    const int sl = (int)(gt % SW);
-    row = i;
-    if (i < M.n) {
-      const int64_t e = M.p[i + 1];
-      for (int64_t q = M.p[i] + sl; q < e; q += SW) {
-        const T a = M.v[q];
-        const T* __restrict__ xr = X + (int64_t)M.ci[q] * k;
-#pragma unroll
-        for (int c = 0; c < KB; ++c)
-          if (c < k) acc[c] += a * __ldg(&xr[c]);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-#pragma unroll
-      for (int o = SW / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(FULL, acc[c], o, SW);
-    return i < M.n && sl == 0;
-  }
-}
-
-template <typename T, int SW>
-__global__ void k_bvc_cheb(MatView<T> A, int k, const T* __restrict__ b, const T* __restrict__ xin,
-                           T* __restrict__ xout, T* __restrict__ d, T c1, T c2, int first) {
-  T y[KB];
-  int64_t i;
-  if (!brow_apply<T, SW>(A, xin, k, y, i)) return;
-  const int64_t o = i * k;
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    if (c < k) {
-      const T dn = cheb_dir<T>(b[o + c], y[c], first ? (T)0 : d[o + c], c1, c2, first);
-      d[o + c] = dn;
-      xout[o + c] = xin[o + c] + dn;
-    }
-  }
-}
-
-template <typename T, int SW>
-__global__ void k_bvc_residual(MatView<T> A, int k, const T* __restrict__ b, const T* __restrict__ x,
-                               T* __restrict__ r) {
-  T y[KB];
-  int64_t i;
-  if (!brow_apply<T, SW>(A, x, k, y, i)) return;
-  const int64_t o = i * k;
-#pragma unroll
-  for (int c = 0; c < KB; ++c)
-    if (c < k) r[o + c] = b[o + c] - y[c];
-}
-
-template <typename T, int SW>
-__global__ void k_bvc_spmv(MatView<T> A, int k, const T* __restrict__ x, T* __restrict__ out) {
-  T y[KB];
-  int64_t i;
-  if (!brow_apply<T, SW>(A, x, k, y, i)) return;
-  const int64_t o = i * k;
-#pragma unroll
-  for (int c = 0; c < KB; ++c)
-    if (c < k) out[o + c] = y[c];
-}
-
-template <typename T, int SW>
-__global__ void k_bvc_spmv_add(MatView<T> A, int k, const T* __restrict__ x, T* __restrict__ out) {
-  T y[KB];
-  int64_t i;
-  if (!brow_apply<T, SW>(A, x, k, y, i)) return;
-  const int64_t o = i * k;
-#pragma unroll
-  for (int c = 0; c < KB; ++c)
-    if (c < k) out[o + c] += y[c];
-}
-
-template <typename T, int SW>
-__global__ void k_bvc_cheb_out(MatView<T> A, int k, const T* __restrict__ b, const T* __restrict__ xin,
-                               const T* __restrict__ d, T c1, T c2, int first, const double* __restrict__ s,
-                               double* __restrict__ z) {
-  T y[KB];
-  int64_t i;
-  if (!brow_apply<T, SW>(A, xin, k, y, i)) return;
-  const int64_t o = i * k;
-  const double si = s[i];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    if (c < k) {
-      const T dn = cheb_dir<T>(b[o + c], y[c], first ? (T)0 : d[o + c], c1, c2, first);
-      z[o + c] = si * (double)(xin[o + c] + dn);
-    }
-  }
-}
-
-// elementwise forms over the n*k elements
-template <typename T>
-__global__ void k_bvc_fine_in(int64_t n, int k, const double* __restrict__ r, const double* __restrict__ s, T c2,
-                              T* __restrict__ b, T* __restrict__ x, T* __restrict__ d) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n * k) {
-    const T bi = (T)(s[e / k] * r[e]);
-    b[e] = bi;
-    const T dn = c2 * bi;
-    d[e] = dn;
-    x[e] = dn;
-  }
-}
-
-template <typename T>
-__global__ void k_bcoarse_in(int64_t n, int k, const T* __restrict__ b, const double* __restrict__ sq,
-                             double* __restrict__ t) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n * k) t[e] = sq[e / k] * (double)b[e];
-}
-
-template <typename T>
-__global__ void k_bcoarse_out(int64_t n, int k, const double* __restrict__ x, const double* __restrict__ sq,
-                              T* __restrict__ xo) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n * k) xo[e] = (T)(sq[e / k] * x[e]);
-}
-
 // launch `K<T, sw>` over the rows of M (SELL: one thread per row; CSR: sw lanes)
 #define LAUNCH_MAT(K, M, st, ...)                                                        \
   do {                                                                                   \
@@ -623,7 +358,6 @@ __global__ void k_coarse_out(int64_t n, const double* __restrict__ x, const doub
 // ---------------------------------------------------------------------------
 // the cycle
 // ---------------------------------------------------------------------------
-static inline unsigned g256(int64_t n) { return blocks_for(n, 256); }
 
 // algorithmic bytes: S-byte value + int32 column per stored entry of the
 // unpadded matrix, 8-byte slice offsets, each vector element once
@@ -742,128 +476,6 @@ int vh_vcycle(VHier<T>* m, cudaStream_t st, const double* r, double** z) {
 template int vh_vcycle<double>(VHier<double>*, cudaStream_t, const double*, double**);
 template int vh_vcycle<float>(VHier<float>*, cudaStream_t, const double*, double**);
 
-// ---------------------------------------------------------------------------
-// the cycle for k right-hand sides (same schedule as mv; k-column kernels)
-// ---------------------------------------------------------------------------
-template <typename T>
-static int block_alloc(Alloc& al, VHier<T>* m) {
-  if (m->kready) return SA_OK;
-  const int nl = (int)m->lev.size();
-  for (int l = 0; l < nl; ++l) {
-    VLevel<T>* L = m->lev[l];
-    const int64_t nk = L->n * KB;
-    SA_TRY(L->kb.alloc(&al, nk));
-    SA_TRY(L->kx.alloc(&al, nk));
-    if (l + 1 < nl) {
-      SA_TRY(L->kx2.alloc(&al, nk));
-      SA_TRY(L->kr.alloc(&al, nk));
-      SA_TRY(L->kd.alloc(&al, nk));
-    }
-  }
-  const int64_t nL = m->lev[nl - 1]->n;
-  SA_TRY(m->kct.alloc(&al, nL * KB));
-  SA_TRY(m->kcy.alloc(&al, nL * KB));
-  SA_TRY(m->kcx.alloc(&al, nL * KB));
-  SA_TRY(m->kz.alloc(&al, m->lev[0]->n * KB));
-  m->kready = 1;
-  return SA_OK;
-}
-
-#define LAUNCH_BMAT(K, M, st, ...)                                                       \
-  do {                                                                                   \
-    const MatView<T> _mv = view(M);                                                      \
-    const int64_t _thr = (M).sw == 0 ? (M).n : (M).n * (int64_t)(M).sw;                  \
-    const unsigned _g = blocks_for(_thr, 256);                                           \
-    switch ((M).sw) {                                                                    \
-      case 0: K<T, 0><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
-      case 4: K<T, 4><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
-      case 8: K<T, 8><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
-      case 16: K<T, 16><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                    \
-      default: K<T, 32><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                    \
-    }                                                                                    \
-    SA_LAUNCHED();                                                                       \
-  } while (0)
-
-template <typename T>
-static int mv_block(VHier<T>* m, cudaStream_t st, int l, int k, const double* r64, T** xo) {
-  VLevel<T>* L = m->lev[l];
-  const int nl = (int)m->lev.size();
-  const int64_t n = L->n, nk = n * k;
-  if (l == nl - 1) {
-    k_bcoarse_in<T><<<g256(nk), 256, 0, st>>>(n, k, L->kb.p, L->sq.p, m->kct.p);
-    SA_LAUNCHED();
-    SA_TRY(launch_coarse_solve_block(st, n, k, m->W, m->WT, m->kct.p, m->kcy.p, m->kcx.p));
-    k_bcoarse_out<T><<<g256(nk), 256, 0, st>>>(n, k, m->kcx.p, L->sq.p, L->kx.p);
-    SA_LAUNCHED();
-    *xo = L->kx.p;
-    return SA_OK;
-  }
-  const int deg = m->deg;
-  const double th = 0.5 * (L->lmax + L->lmin), de = 0.5 * (L->lmax - L->lmin);
-  const double s1 = th / de;
-  T* xa = L->kx.p;
-  T* xb = L->kx2.p;
-  const Mat<T>& A = L->A;
-  if (l == 0) {
-    k_bvc_fine_in<T><<<g256(nk), 256, 0, st>>>(n, k, r64, m->s0.p, (T)(1.0 / th), L->kb.p, xa, L->kd.p);
-  } else {
-    k_vc_first<T><<<g256(nk), 256, 0, st>>>(nk, L->kb.p, (T)(1.0 / th), xa, L->kd.p);
-  }
-  SA_LAUNCHED();
-  double rho = 1.0 / s1;
-  for (int q = 1; q < deg; ++q) {
-    double rn = 1.0 / (2.0 * s1 - rho);
-    LAUNCH_BMAT(k_bvc_cheb, A, st, k, L->kb.p, xa, xb, L->kd.p, (T)(rn * rho), (T)(2.0 * rn / de), 0);
-    T* t = xa; xa = xb; xb = t;
-    rho = rn;
-  }
-  VLevel<T>* C = m->lev[l + 1];
-  LAUNCH_BMAT(k_bvc_residual, A, st, k, L->kb.p, xa, L->kr.p);
-  LAUNCH_BMAT(k_bvc_spmv, L->R, st, k, L->kr.p, C->kb.p);
-  T* xc = nullptr;
-  SA_TRY(mv_block(m, st, l + 1, k, nullptr, &xc));
-  LAUNCH_BMAT(k_bvc_spmv_add, L->P, st, k, xc, xa);
-  rho = 1.0 / s1;
-  for (int q = 0; q < deg; ++q) {
-    int first = (q == 0);
-    T c1 = (T)0, c2 = (T)(1.0 / th);
-    double rn = rho;
-    if (!first) {
-      rn = 1.0 / (2.0 * s1 - rho);
-      c1 = (T)(rn * rho);
-      c2 = (T)(2.0 * rn / de);
-    }
-    if (l == 0 && q == deg - 1) {
-      LAUNCH_BMAT(k_bvc_cheb_out, A, st, k, L->kb.p, xa, L->kd.p, c1, c2, first, m->s0.p, m->kz.p);
-    } else {
-      LAUNCH_BMAT(k_bvc_cheb, A, st, k, L->kb.p, xa, xb, L->kd.p, c1, c2, first);
-      T* t = xa; xa = xb; xb = t;
-    }
-    if (!first) rho = rn;
-  }
-  *xo = xa;
-  return SA_OK;
-}
-
-template <typename T>
-int vh_vcycle_block(Alloc& al, VHier<T>* m, cudaStream_t st, int k, const double* R, double** Z) {
-  if (k < 1 || k > KB) return SA_ERR_INVALID_ARG;
-  SA_TRY(block_alloc(al, m));
-  if (m->lev.size() == 1) {
-    const int64_t n = m->lev[0]->n;
-    SA_TRY(launch_coarse_solve_block(st, n, k, m->W, m->WT, R, m->kcy.p, m->kz.p));
-    *Z = m->kz.p;
-    return SA_OK;
-  }
-  T* xo = nullptr;
-  SA_TRY(mv_block<T>(m, st, 0, k, R, &xo));
-  *Z = m->kz.p;
-  return SA_OK;
-}
-
-template int vh_vcycle_block<double>(Alloc&, VHier<double>*, cudaStream_t, int, const double*, double**);
-template int vh_vcycle_block<float>(Alloc&, VHier<float>*, cudaStream_t, int, const double*, double**);
-
 template <typename T>
 void vh_free(VHier<T>* m) {
   if (!m) return;
@@ -926,80 +538,5 @@ int launch_sell_residual64(cudaStream_t st, const Sell<double>& A, const double*
   return SA_OK;
 }
 
-
-// k-column outer-CG products: Q = A P with the per-column partial p.q sums
-// (the one-vector reduction tree per column) and R = B - A X
-__global__ void k_bsell_spmv_dot(int64_t n, int k, MatView<double> A, const double* __restrict__ P,
-                                 double* __restrict__ Q, double* __restrict__ part) {
-  double y[KB];
-  int64_t i;
-  double c[KB];
-#pragma unroll
-  for (int j = 0; j < KB; ++j) c[j] = 0.0;
-  if (brow_apply<double, 0>(A, P, k, y, i)) {
-    const int64_t o = i * k;
-#pragma unroll
-    for (int j = 0; j < KB; ++j)
-      if (j < k) {
-        Q[o + j] = y[j];
-        c[j] = y[j] * P[o + j];
-      }
-  }
-  __shared__ double sh[KB][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < KB; ++j) {
-    const double t = warp_sum(c[j]);
-    if (lane == 0) sh[j][w] = t;
-  }
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int j = 0; j < KB; ++j) {
-      double t = lane < (int)(blockDim.x >> 5) ? sh[j][lane] : 0.0;
-      t = warp_sum(t);
-      if (lane == 0 && j < k) part[(int64_t)j * gridDim.x + blockIdx.x] = t;
-    }
-  }
-}
-
-__global__ void k_bsell_res64(int64_t n, int k, MatView<double> A, const double* __restrict__ B,
-                              const double* __restrict__ X, double* __restrict__ R) {
-  double y[KB];
-  int64_t i;
-  if (!brow_apply<double, 0>(A, X, k, y, i)) return;
-  const int64_t o = i * k;
-#pragma unroll
-  for (int j = 0; j < KB; ++j)
-    if (j < k) R[o + j] = B[o + j] - y[j];
-}
-
-static MatView<double> sell_view(const Sell<double>& A) {
-  MatView<double> m;
-  m.n = A.n;
-  m.p = A.sp.p;
-  m.ci = A.ci.p;
-  m.v = A.v.p;
-  m.base = A.idx16 ? A.base.p : nullptr;
-  m.c16 = A.idx16 ? A.c16.p : nullptr;
-  return m;
-}
-
-int launch_bsell_spmv_dot(cudaStream_t st, const Sell<double>& A, int k, const double* P, double* Q, double* part,
-                          int* nparts) {
-  if (k < 1 || k > KB) return SA_ERR_INVALID_ARG;
-  *nparts = (int)g256(A.n);
-  k_bsell_spmv_dot<<<g256(A.n), 256, 0, st>>>(A.n, k, sell_view(A), P, Q, part);
-  SA_LAUNCHED();
-  return SA_OK;
-}
-
-int launch_bsell_residual64(cudaStream_t st, const Sell<double>& A, int k, const double* B, const double* X,
-                            double* R) {
-  if (k < 1 || k > KB) return SA_ERR_INVALID_ARG;
-  k_bsell_res64<<<g256(A.n), 256, 0, st>>>(A.n, k, sell_view(A), B, X, R);
-  SA_LAUNCHED();
-  return SA_OK;
-}
 
 }  // namespace sa

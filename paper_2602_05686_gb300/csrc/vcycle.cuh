@@ -87,7 +87,7 @@ template <typename T>
 int vh_vcycle(VHier<T>* m, cudaStream_t s, const double* r, double** z);
 template <typename T>
 void vh_free(VHier<T>* m);
-// k <= KMAX_BLOCK right-hand sides at once: R and *Z are interleaved n x k
+// K in {2, 4, 8} right-hand sides at once: R and *Z are interleaved n x K
 // FP64 blocks; column c of *Z equals vh_vcycle of column c of R bitwise
 template <typename T>
 int vh_vcycle_block(Alloc& al, VHier<T>* m, cudaStream_t s, int k, const double* R, double** Z);
