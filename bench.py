@@ -62,8 +62,10 @@ def peaks():
 
 
 def kernel_source_hash():
+    """hash of the sources that define the V-cycle kernels (a recorded ncu
+    traffic figure is used only while they are unchanged)"""
     h = hashlib.sha256()
-    for f in ("vcycle.cu", "vcycle.cuh", "solve.cu", "solve.cuh", "host.cu"):
+    for f in ("vcycle.cu", "vcycle.cuh", "vkern.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2602_05686_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -360,6 +362,7 @@ def run_ours(args):
         "kernel_profile_top": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
                                for r in krows[:8]],
         "setup_phases_ms": setup_phases(prof, args.steps),
+        "kernel_profile_all": [[r["kind"], r["level"], r["launches"], round(r["ms"], 3)] for r in krows],
         "multi_rhs": multi,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:

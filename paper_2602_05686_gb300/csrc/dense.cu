@@ -63,18 +63,25 @@ __global__ void k_potrf_diag(int64_t n, double* __restrict__ M, int k, int* __re
     int r = t / bs, c = t % bs;
     M[(o + r) * n + o + c] = (c <= r) ? T[r][c] : 0.0;
   }
-  // inverse by forward substitution, one column per thread: L y = e_c
+  // inverse by forward substitution, L y = e_c for every column c: eight
+  // threads per column (one warp holds four columns) split each row's dot
+  // product and combine it with shuffles
   __shared__ double Y[NB][NB + 1];
-  const int c = threadIdx.x;
-  if (c < NB) {
+  {
+    const int c = threadIdx.x >> 3, g = threadIdx.x & 7;
     for (int r = 0; r < NB; ++r) {
-      double y = 0.0;
-      if (r < bs && c < bs && r >= c) {
-        y = (r == c) ? 1.0 : 0.0;
-        for (int q = c; q < r; ++q) y -= T[r][q] * Y[q][c];
-        y *= rinv[r];
+      double part = 0.0;
+      if (r < bs && c < bs && r > c)
+        for (int q = c + g; q < r; q += 8) part += T[r][q] * Y[q][c];
+      part += __shfl_xor_sync(FULL, part, 4, 8);
+      part += __shfl_xor_sync(FULL, part, 2, 8);
+      part += __shfl_xor_sync(FULL, part, 1, 8);
+      if (g == 0) {
+        double y = 0.0;
+        if (r < bs && c < bs && r >= c) y = ((r == c ? 1.0 : 0.0) - part) * rinv[r];
+        Y[r][c] = y;
       }
-      Y[r][c] = y;
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -287,8 +294,19 @@ __global__ void k_trmv_lower(int64_t n, const double* __restrict__ W, const doub
                              double* __restrict__ y) {
   const int lane = lane_id();
   for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    // four row loads in flight per lane (the loop is latency bound otherwise);
+    // the products are added in j order
+    const double* __restrict__ Wi = W + i * n;
     double s = 0.0;
-    for (int64_t j = lane; j <= i; j += 32) s += W[i * n + j] * b[j];
+    int64_t j = lane;
+    for (; j + 96 <= i; j += 128) {
+      const double w0 = __ldcs(&Wi[j]), w1 = __ldcs(&Wi[j + 32]), w2 = __ldcs(&Wi[j + 64]), w3 = __ldcs(&Wi[j + 96]);
+      s += w0 * b[j];
+      s += w1 * b[j + 32];
+      s += w2 * b[j + 64];
+      s += w3 * b[j + 96];
+    }
+    for (; j <= i; j += 32) s += Wi[j] * b[j];
     s = warp_sum(s);
     if (lane == 0) y[i] = s;
   }
@@ -299,8 +317,17 @@ __global__ void k_trmv_upper(int64_t n, const double* __restrict__ WT, const dou
                              double* __restrict__ x) {
   const int lane = lane_id();
   for (int64_t j = global_warp(); j < n; j += warp_stride()) {
+    const double* __restrict__ Wj = WT + j * n;
     double s = 0.0;
-    for (int64_t i = j + lane; i < n; i += 32) s += WT[j * n + i] * y[i];
+    int64_t i = j + lane;
+    for (; i + 96 < n; i += 128) {
+      const double w0 = __ldcs(&Wj[i]), w1 = __ldcs(&Wj[i + 32]), w2 = __ldcs(&Wj[i + 64]), w3 = __ldcs(&Wj[i + 96]);
+      s += w0 * y[i];
+      s += w1 * y[i + 32];
+      s += w2 * y[i + 64];
+      s += w3 * y[i + 96];
+    }
+    for (; i < n; i += 32) s += Wj[i] * y[i];
     s = warp_sum(s);
     if (lane == 0) x[j] = s;
   }
@@ -315,8 +342,21 @@ __global__ void k_btrmv_lower(int64_t n, int k, const double* __restrict__ W, co
     double s[KMAX_COARSE];
 #pragma unroll
     for (int c = 0; c < KMAX_COARSE; ++c) s[c] = 0.0;
-    for (int64_t j = lane; j <= i; j += 32) {
-      const double w = W[i * n + j];
+    const double* __restrict__ Wi = W + i * n;
+    int64_t j = lane;
+    for (; j + 96 <= i; j += 128) {
+      const double w0 = __ldcs(&Wi[j]), w1 = __ldcs(&Wi[j + 32]), w2 = __ldcs(&Wi[j + 64]), w3 = __ldcs(&Wi[j + 96]);
+#pragma unroll
+      for (int c = 0; c < KMAX_COARSE; ++c)
+        if (c < k) {
+          s[c] += w0 * b[j * k + c];
+          s[c] += w1 * b[(j + 32) * k + c];
+          s[c] += w2 * b[(j + 64) * k + c];
+          s[c] += w3 * b[(j + 96) * k + c];
+        }
+    }
+    for (; j <= i; j += 32) {
+      const double w = Wi[j];
 #pragma unroll
       for (int c = 0; c < KMAX_COARSE; ++c)
         if (c < k) s[c] += w * b[j * k + c];
@@ -336,8 +376,21 @@ __global__ void k_btrmv_upper(int64_t n, int k, const double* __restrict__ WT, c
     double s[KMAX_COARSE];
 #pragma unroll
     for (int c = 0; c < KMAX_COARSE; ++c) s[c] = 0.0;
-    for (int64_t i = j + lane; i < n; i += 32) {
-      const double w = WT[j * n + i];
+    const double* __restrict__ Wj = WT + j * n;
+    int64_t i = j + lane;
+    for (; i + 96 < n; i += 128) {
+      const double w0 = __ldcs(&Wj[i]), w1 = __ldcs(&Wj[i + 32]), w2 = __ldcs(&Wj[i + 64]), w3 = __ldcs(&Wj[i + 96]);
+#pragma unroll
+      for (int c = 0; c < KMAX_COARSE; ++c)
+        if (c < k) {
+          s[c] += w0 * y[i * k + c];
+          s[c] += w1 * y[(i + 32) * k + c];
+          s[c] += w2 * y[(i + 64) * k + c];
+          s[c] += w3 * y[(i + 96) * k + c];
+        }
+    }
+    for (; i < n; i += 32) {
+      const double w = Wj[i];
 #pragma unroll
       for (int c = 0; c < KMAX_COARSE; ++c)
         if (c < k) s[c] += w * y[i * k + c];

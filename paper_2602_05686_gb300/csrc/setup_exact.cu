@@ -208,33 +208,79 @@ __device__ __forceinline__ double quad_form(int dim, const double* __restrict__ 
          d[2] * (si[4] * d[0] + si[5] * d[1] + si[2] * d[2]);
 }
 
+// w_ij = 1 / max(q_ij, q_ji) for the entries above the diagonal (j > i);
+// the diagonal gets 0 and the lower entries are mirrored afterwards.  For
+// (j, i) the difference vector is exactly -(x_i - x_j), and both quadratic
+// forms are even in it with sign-symmetric rounding, so w_ji computed from row
+// j would be the same bits: computing each pair once halves the FP64 work.
+// One thread per row: the FP64 pipe issues a warp instruction whatever its
+// active lanes, so the upper entries of 32 rows share each instruction.
 template <int DIM>
 __global__ void k_material_w(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                              const double* __restrict__ x, const double* __restrict__ sinv, double* __restrict__ w) {
   constexpr int KP = DIM == 3 ? 6 : 3;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = rp[i], e = rp[i + 1];
+  double xi[3], si_i[KP];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) xi[c] = x[i * DIM + c];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) si_i[c] = sinv[i * KP + c];
+  for (int64_t p = b; p < e; ++p) {
+    const int32_t j = ci[p];
+    if (j < (int32_t)i) continue;  // mirrored by k_material_w_mirror
+    double wv = 0.0;
+    if (j != (int32_t)i) {
+      double d[3], sj[KP];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) d[c] = xi[c] - x[(int64_t)j * DIM + c];
+#pragma unroll
+      for (int c = 0; c < KP; ++c) sj[c] = sinv[(int64_t)j * KP + c];
+      double qij = quad_form(DIM, si_i, d);
+      double qji = quad_form(DIM, sj, d);
+      double m = qij > qji ? qij : qji;
+      wv = 1.0 / m;
+    }
+    w[p] = wv;
+  }
+}
+
+// lower entries: w_ij = w_ji, the (j, i) entry found by binary search in row
+// j; a pattern without that entry (not structurally symmetric) gets w_ij
+// computed here by the same expression
+template <int DIM>
+__global__ void k_material_w_mirror(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                    const double* __restrict__ x, const double* __restrict__ sinv,
+                                    double* __restrict__ w) {
+  constexpr int KP = DIM == 3 ? 6 : 3;
   const int lane = lane_id();
   for (int64_t i = global_warp(); i < n; i += warp_stride()) {
-    const int64_t b = rp[i], e = rp[i + 1];
-    double xi[3], si_i[KP];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) xi[c] = x[i * DIM + c];
-#pragma unroll
-    for (int c = 0; c < KP; ++c) si_i[c] = sinv[i * KP + c];
-    for (int64_t p = b + lane; p < e; p += 32) {
-      int32_t j = ci[p];
-      double wv = 0.0;
-      if (j != (int32_t)i) {
-        double d[3], sj[KP];
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) d[c] = xi[c] - x[(int64_t)j * DIM + c];
-#pragma unroll
-        for (int c = 0; c < KP; ++c) sj[c] = sinv[(int64_t)j * KP + c];
-        double qij = quad_form(DIM, si_i, d);
-        double qji = quad_form(DIM, sj, d);
-        double m = qij > qji ? qij : qji;
-        wv = 1.0 / m;
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+      const int32_t j = ci[p];
+      if (j >= (int32_t)i) break;  // columns ascend: the rest of the row is upper
+      int64_t lo = rp[j], hi = rp[j + 1] - 1, f = -1;
+      while (lo <= hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t c = ci[mid];
+        if (c == (int32_t)i) { f = mid; break; }
+        if (c < (int32_t)i) lo = mid + 1; else hi = mid - 1;
       }
-      w[p] = wv;
+      if (f >= 0) {
+        w[p] = w[f];
+      } else {
+        double d[3], si[KP], sj[KP];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) d[c] = x[i * DIM + c] - x[(int64_t)j * DIM + c];
+#pragma unroll
+        for (int c = 0; c < KP; ++c) {
+          si[c] = sinv[i * KP + c];
+          sj[c] = sinv[(int64_t)j * KP + c];
+        }
+        double qij = quad_form(DIM, si, d);
+        double qji = quad_form(DIM, sj, d);
+        w[p] = 1.0 / (qij > qji ? qij : qji);
+      }
     }
   }
 }
@@ -584,8 +630,11 @@ int launch_strength_material(cudaStream_t s, int dim, int64_t n, const int64_t* 
                              double* w, double* D, uint8_t* keep, int64_t* cnt) {
   if (n <= 0) return SA_OK;
   const double t2 = theta * theta;
-  if (dim == 3) k_material_w<3><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
-  else k_material_w<2><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
+  if (dim == 3) k_material_w<3><<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, x, sinv, w);
+  else k_material_w<2><<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, x, sinv, w);
+  SA_LAUNCHED();
+  if (dim == 3) k_material_w_mirror<3><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
+  else k_material_w_mirror<2><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
   SA_LAUNCHED();
   k_row_sum_ordered<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, w, D);
   SA_LAUNCHED();

@@ -26,16 +26,24 @@ namespace sa {
 // ---------------------------------------------------------------------------
 // SELL-32 construction
 // ---------------------------------------------------------------------------
-__global__ void k_slice_width(int64_t n, const int64_t* __restrict__ rp, int64_t* __restrict__ sz) {
-  int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t ns = (n + 31) / 32;
-  if (sl >= ns) return;
+// slice widths (longest row of each 32-row slice) x 32 into sz[sl + 1]; with
+// mx, also the longest row overall (one atomic per warp)
+__global__ void k_slice_width(int64_t n, const int64_t* __restrict__ rp, int64_t* __restrict__ sz,
+                              unsigned int* __restrict__ mx) {
+  const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ns = (n + 31) / 32;
   int64_t w = 0;
-  for (int64_t r = sl * 32; r < sl * 32 + 32 && r < n; ++r) {
-    int64_t len = rp[r + 1] - rp[r];
-    w = len > w ? len : w;
+  if (sl < ns) {
+    for (int64_t r = sl * 32; r < sl * 32 + 32 && r < n; ++r) {
+      int64_t len = rp[r + 1] - rp[r];
+      w = len > w ? len : w;
+    }
+    sz[sl + 1] = w * 32;
   }
-  sz[sl + 1] = w * 32;
+  if (mx) {
+    const unsigned int m = __reduce_max_sync(FULL, (unsigned int)w);
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(mx, m);
+  }
 }
 
 // out = left_i * a_ij * right_j with precomputed scale vectors (NULL = 1);
@@ -119,7 +127,7 @@ int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32
     SA_TRY(S.v.alloc(&al, 0));
     return SA_OK;
   }
-  k_slice_width<<<blocks_for(S.nslices, 256), 256, 0, s>>>(n, rp, S.sp.p);
+  k_slice_width<<<blocks_for(S.nslices, 256), 256, 0, s>>>(n, rp, S.sp.p, nullptr);
   SA_LAUNCHED();
   SA_TRY(scan_inplace(al, S.sp.p + 1, S.nslices));
   SA_TRY(copy_d2h(&S.stored, S.sp.p + S.nslices, sizeof(int64_t), s));
@@ -164,8 +172,9 @@ __global__ void k_csr_scale(int64_t n, const int64_t* __restrict__ rp, const int
   for (int64_t p = rp[i]; p < rp[i + 1]; ++p) ov[p] = (T)(li * v[p] * (right ? right[ci[p]] : 1.0));
 }
 
-// SELL-32 if it stores at most 25 % padding and rows average <= 40 entries,
-// else CSR with 4..32 lanes per row by average row length
+// SELL-32 (one thread per row, one FP64 FMA per stored entry) if it stores at
+// most 25 % padding, else CSR with 4..32 lanes per row by average row length
+// (rows of very different lengths in one slice would pad too much)
 template <typename T>
 int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
               const double* left, const double* right, Mat<T>& M) {
@@ -175,20 +184,30 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
   M.nslices = (n + 31) / 32;
   const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
   int64_t stored = 0;
+  unsigned int max_width = 0;
   if (n > 0) {
     Buf<int64_t> sz;
+    Buf<unsigned int> mx;
     SA_TRY(sz.alloc(&al, M.nslices + 1));
+    SA_TRY(mx.alloc(&al, 1));
     SA_TRY(memset_d(sz.p, 0, sz.bytes(), s));
-    k_slice_width<<<blocks_for(M.nslices, 256), 256, 0, s>>>(n, rp, sz.p);
+    SA_TRY(memset_d(mx.p, 0, sizeof(unsigned int), s));
+    k_slice_width<<<blocks_for(M.nslices, 256), 256, 0, s>>>(n, rp, sz.p, mx.p);
     SA_LAUNCHED();
     SA_TRY(scan_inplace(al, sz.p + 1, M.nslices));
     SA_TRY(copy_d2h(&stored, sz.p + M.nslices, sizeof(int64_t), s));
+    SA_TRY(copy_d2h(&max_width, mx.p, sizeof(unsigned int), s));
   }
-  if (n == 0 || ((double)stored <= 1.25 * (double)nnz && avg <= 40.0)) {
+  if (n == 0 || (double)stored <= 1.25 * (double)nnz) {
     M.sw = 0;
     return build_sell<T>(al, n, nnz, rp, ci, v, left, right, M.sell);
   }
   M.sw = avg <= 12.0 ? 4 : (avg <= 40.0 ? 8 : (avg <= 96.0 ? 16 : 32));
+  // on a small level a few very long rows (coarse levels of the stretched
+  // battery stack reach 30x the average) hold their warp longer than the
+  // rest of the launch takes: a warp per row then.  On large levels the five
+  // FP64 shuffle additions per row of a warp per row cost more.
+  if (n <= 65536 && (double)max_width > 8.0 * avg) M.sw = 32;
   SA_TRY(M.rp.alloc(&al, n + 1));
   SA_TRY(M.ci.alloc(&al, nnz));
   SA_TRY(M.v.alloc(&al, nnz));
