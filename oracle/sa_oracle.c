@@ -212,13 +212,20 @@ void or_strength_classical(int64_t n, const int64_t* rp, const int32_t* ci, cons
   free(dg);
 }
 
-/* squared material distance d~(x_i, x_j)^2 = d^T sigma_i^-1 d, d = x_i - x_j */
+/* squared material distance d~(x_i, x_j)^2 = d^T sigma_i^-1 d, d = x_i - x_j:
+ * t = sigma_i^-1 d, then d . t, each a running sum of fused multiply-adds
+ * (one rounding per term) in index order.  The value is even in d bit for
+ * bit (negating d negates t exactly), so d~ is the same from either end. */
 static double quad_form(int dim, const double* si, const double* d) {
-  if (dim == 2)
-    return d[0] * (si[0] * d[0] + si[2] * d[1]) + d[1] * (si[2] * d[0] + si[1] * d[1]);
-  return d[0] * (si[0] * d[0] + si[3] * d[1] + si[4] * d[2]) +
-         d[1] * (si[3] * d[0] + si[1] * d[1] + si[5] * d[2]) +
-         d[2] * (si[4] * d[0] + si[5] * d[1] + si[2] * d[2]);
+  if (dim == 2) {
+    const double t0 = fma(si[2], d[1], si[0] * d[0]);
+    const double t1 = fma(si[1], d[1], si[2] * d[0]);
+    return fma(d[1], t1, d[0] * t0);
+  }
+  const double t0 = fma(si[4], d[2], fma(si[3], d[1], si[0] * d[0]));
+  const double t1 = fma(si[5], d[2], fma(si[1], d[1], si[3] * d[0]));
+  const double t2 = fma(si[2], d[2], fma(si[5], d[1], si[4] * d[0]));
+  return fma(d[2], t2, fma(d[1], t1, d[0] * t0));
 }
 
 /* ------------------------------------------------------------------------ */

@@ -201,11 +201,18 @@ __global__ void k_strength_classical(int64_t n, const int64_t* __restrict__ rp, 
 //   D_i = sum_{j != i} w_ij (ascending column order).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double quad_form(int dim, const double* __restrict__ si, const double* d) {
-  if (dim == 2)
-    return d[0] * (si[0] * d[0] + si[2] * d[1]) + d[1] * (si[2] * d[0] + si[1] * d[1]);
-  return d[0] * (si[0] * d[0] + si[3] * d[1] + si[4] * d[2]) +
-         d[1] * (si[3] * d[0] + si[1] * d[1] + si[5] * d[2]) +
-         d[2] * (si[4] * d[0] + si[5] * d[1] + si[2] * d[2]);
+  // t = sigma^-1 d, then d . t, as running sums of fused multiply-adds in
+  // index order (explicit __fma_rn: one rounding per term even under
+  // -fmad=false); even in d bit for bit
+  if (dim == 2) {
+    const double t0 = __fma_rn(si[2], d[1], si[0] * d[0]);
+    const double t1 = __fma_rn(si[1], d[1], si[2] * d[0]);
+    return __fma_rn(d[1], t1, d[0] * t0);
+  }
+  const double t0 = __fma_rn(si[4], d[2], __fma_rn(si[3], d[1], si[0] * d[0]));
+  const double t1 = __fma_rn(si[5], d[2], __fma_rn(si[1], d[1], si[3] * d[0]));
+  const double t2 = __fma_rn(si[2], d[2], __fma_rn(si[5], d[1], si[4] * d[0]));
+  return __fma_rn(d[2], t2, __fma_rn(d[1], t1, d[0] * t0));
 }
 
 // w_ij = 1 / max(q_ij, q_ji) for the entries above the diagonal (j > i);

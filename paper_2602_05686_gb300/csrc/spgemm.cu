@@ -179,6 +179,7 @@ k_spgemm_fill(int64_t n, const int32_t* __restrict__ rows, const int64_t* __rest
 // ---------------------------------------------------------------------------
 constexpr int TB = 128;
 constexpr int TCAP = 32;
+constexpr int TG = 4;  // A entries whose B rows are looked up together
 
 __device__ __forceinline__ int tlower(const int32_t* cols, int c, int32_t j) {
   int lo = 0, hi = c;
@@ -200,17 +201,31 @@ k_spgemm_tcount(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __res
   int c = 0;
   bool over = false;
   const int64_t e = Arp[i + 1];
-  for (int64_t p = Arp[i]; p < e && !over; ++p) {
-    const int32_t k = Aci[p];
-    const int64_t qe = Brp[k + 1];
-    for (int64_t q = Brp[k]; q < qe; ++q) {
-      const int32_t j = Bci[q];
-      const int pos = tlower(cols, c, j);
-      if (pos < c && cols[pos * TB] == j) continue;
-      if (c == TCAP) { over = true; break; }
-      for (int t = c; t > pos; --t) cols[t * TB] = cols[(t - 1) * TB];
-      cols[pos * TB] = j;
-      ++c;
+  // A entries in groups of TG: their columns and B row bounds are fetched
+  // together (one dependent load chain per group instead of per entry); the
+  // B rows are then inserted in ascending A order
+  for (int64_t p0 = Arp[i]; p0 < e && !over; p0 += TG) {
+    int64_t qb[TG], qe[TG];
+#pragma unroll
+    for (int u = 0; u < TG; ++u) {
+      qb[u] = 0;
+      qe[u] = 0;
+      if (p0 + u < e) {
+        const int32_t k = Aci[p0 + u];
+        qb[u] = Brp[k];
+        qe[u] = Brp[k + 1];
+      }
+    }
+    for (int u = 0; u < TG && !over; ++u) {
+      for (int64_t q = qb[u]; q < qe[u]; ++q) {
+        const int32_t j = Bci[q];
+        const int pos = tlower(cols, c, j);
+        if (pos < c && cols[pos * TB] == j) continue;
+        if (c == TCAP) { over = true; break; }
+        for (int t = c; t > pos; --t) cols[t * TB] = cols[(t - 1) * TB];
+        cols[pos * TB] = j;
+        ++c;
+      }
     }
   }
   if (over) {
@@ -238,24 +253,38 @@ k_spgemm_tfill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __rest
   const int32_t jmin = upper_only ? (int32_t)i : INT32_MIN;
   int c = 0;
   const int64_t e = Arp[i + 1];
-  for (int64_t p = Arp[i]; p < e; ++p) {
-    const int32_t k = Aci[p];
-    const double a = Av[p];
-    const int64_t qe = Brp[k + 1];
-    for (int64_t q = Brp[k]; q < qe; ++q) {
-      const int32_t j = Bci[q];
-      const int pos = tlower(cols, c, j);
-      if (!(pos < c && cols[pos * TB] == j)) {
-        if (c == TCAP) return;  // cannot happen: the count held this row
-        for (int t = c; t > pos; --t) {
-          cols[t * TB] = cols[(t - 1) * TB];
-          vals[t * TB] = vals[(t - 1) * TB];
-        }
-        cols[pos * TB] = j;
-        vals[pos * TB] = 0.0;
-        ++c;
+  for (int64_t p0 = Arp[i]; p0 < e; p0 += TG) {
+    int64_t qb[TG], qe[TG];
+    double av[TG];
+#pragma unroll
+    for (int u = 0; u < TG; ++u) {
+      qb[u] = 0;
+      qe[u] = 0;
+      av[u] = 0.0;
+      if (p0 + u < e) {
+        const int32_t k = Aci[p0 + u];
+        av[u] = Av[p0 + u];
+        qb[u] = Brp[k];
+        qe[u] = Brp[k + 1];
       }
-      if (j >= jmin) vals[pos * TB] = __dadd_rn(vals[pos * TB], __dmul_rn(a, Bv[q]));
+    }
+    for (int u = 0; u < TG; ++u) {
+      const double a = av[u];
+      for (int64_t q = qb[u]; q < qe[u]; ++q) {
+        const int32_t j = Bci[q];
+        const int pos = tlower(cols, c, j);
+        if (!(pos < c && cols[pos * TB] == j)) {
+          if (c == TCAP) return;  // cannot happen: the count held this row
+          for (int t = c; t > pos; --t) {
+            cols[t * TB] = cols[(t - 1) * TB];
+            vals[t * TB] = vals[(t - 1) * TB];
+          }
+          cols[pos * TB] = j;
+          vals[pos * TB] = 0.0;
+          ++c;
+        }
+        if (j >= jmin) vals[pos * TB] = __dadd_rn(vals[pos * TB], __dmul_rn(a, Bv[q]));
+      }
     }
   }
   const int64_t cb = Crp[i];

@@ -9,25 +9,37 @@
 namespace sa {
 
 // Row products of one thread: the entries of row i sit 32 apart inside its
-// slice.  Four entries per iteration keep four value / column loads and
-// four gathers in flight per thread (the kernels are latency bound
-// otherwise); the products are still added in entry order.  Values and
+// slice.  Several entries per iteration keep their value / column loads and
+// gathers in flight together (the kernels are latency bound otherwise); the
+// products are still added in entry order.  Values and
 // columns are read once (evict-first loads), so the gathered x stays cached.
+// entries per iteration: FP32 rows are latency bound and want more loads in
+// flight; FP64 rows are bound by the FP64 pipe
+template <typename T>
+struct RowUnroll {
+  static constexpr int U = sizeof(T) == 4 ? 8 : 4;
+};
+
 template <typename T>
 __device__ __forceinline__ T sell_row(const int64_t* __restrict__ sp, const int32_t* __restrict__ ci,
                                       const T* __restrict__ v, const T* __restrict__ x, int64_t i) {
+  constexpr int U = RowUnroll<T>::U;
   const int64_t sl = i >> 5, r = i & 31;
   const int64_t b = sp[sl], e = sp[sl + 1];
   T acc = (T)0;
   int64_t p = b + r;
-  for (; p + 96 < e; p += 128) {
-    const T v0 = __ldcs(&v[p]), v1 = __ldcs(&v[p + 32]), v2 = __ldcs(&v[p + 64]), v3 = __ldcs(&v[p + 96]);
-    const int32_t c0 = __ldcs(&ci[p]), c1 = __ldcs(&ci[p + 32]), c2 = __ldcs(&ci[p + 64]), c3 = __ldcs(&ci[p + 96]);
-    const T x0 = __ldg(&x[c0]), x1 = __ldg(&x[c1]), x2 = __ldg(&x[c2]), x3 = __ldg(&x[c3]);
-    acc += v0 * x0;
-    acc += v1 * x1;
-    acc += v2 * x2;
-    acc += v3 * x3;
+  for (; p + 32 * (U - 1) < e; p += 32 * U) {
+    T vv[U], xx[U];
+    int32_t cc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      vv[u] = __ldcs(&v[p + 32 * u]);
+      cc[u] = __ldcs(&ci[p + 32 * u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) xx[u] = __ldg(&x[cc[u]]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc += vv[u] * xx[u];
   }
   for (; p < e; p += 32) acc += __ldcs(&v[p]) * __ldg(&x[__ldcs(&ci[p])]);
   return acc;
@@ -38,20 +50,24 @@ template <typename T>
 __device__ __forceinline__ T sell_row16(const int64_t* __restrict__ sp, const int32_t* __restrict__ base,
                                         const uint16_t* __restrict__ c16, const T* __restrict__ v,
                                         const T* __restrict__ x, int64_t i) {
+  constexpr int U = RowUnroll<T>::U;
   const int64_t sl = i >> 5, r = i & 31;
   const int64_t b = sp[sl], e = sp[sl + 1];
   const T* __restrict__ xs = x + base[sl];
   T acc = (T)0;
   int64_t p = b + r;
-  for (; p + 96 < e; p += 128) {
-    const T v0 = __ldcs(&v[p]), v1 = __ldcs(&v[p + 32]), v2 = __ldcs(&v[p + 64]), v3 = __ldcs(&v[p + 96]);
-    const unsigned c0 = __ldcs(&c16[p]), c1 = __ldcs(&c16[p + 32]), c2 = __ldcs(&c16[p + 64]),
-                   c3 = __ldcs(&c16[p + 96]);
-    const T x0 = __ldg(&xs[c0]), x1 = __ldg(&xs[c1]), x2 = __ldg(&xs[c2]), x3 = __ldg(&xs[c3]);
-    acc += v0 * x0;
-    acc += v1 * x1;
-    acc += v2 * x2;
-    acc += v3 * x3;
+  for (; p + 32 * (U - 1) < e; p += 32 * U) {
+    T vv[U], xx[U];
+    unsigned cc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      vv[u] = __ldcs(&v[p + 32 * u]);
+      cc[u] = __ldcs(&c16[p + 32 * u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) xx[u] = __ldg(&xs[cc[u]]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc += vv[u] * xx[u];
   }
   for (; p < e; p += 32) acc += __ldcs(&v[p]) * __ldg(&xs[__ldcs(&c16[p])]);
   return acc;
