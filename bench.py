@@ -52,6 +52,20 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(x, ws, op="max"):
+    """max (or sum) of a host scalar over the ranks of the default process
+    group (NCCL on the GPUs, gloo on CPU); the only collective of the
+    replicas-only multi-GPU run"""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(MEASURED_PEAKS) as f:
@@ -226,11 +240,8 @@ def run_ours(args):
     clocks = clk.stop()
     ms_total = t0.elapsed_time(t1)
     ms_step = ms_total / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = reduce_over_ranks(ms_step, ws, "max")        # the slowest replica sets the step time
+    launches = int(reduce_over_ranks(launches, ws, "sum"))  # kernels of all replicas
 
     # material hierarchy statistics (untimed)
     hm = sa.Hierarchy(dprob, theta=MAT_THETA, measure="material")
