@@ -219,10 +219,10 @@ def run_ours(args):
     # warm-up
     for _ in range(args.warmup):
         one_step(dprob, b)
-    # timed region (device-resident inputs), with live kernel profiling
+    # timed region (device-resident inputs): the production path -- CG loops
+    # in CUDA graphs, no per-launch instrumentation
     clk = ClockSampler(local)
     clk.start()
-    sa.profile_enable(True)
     l0 = sa.launch_count()
     barrier()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -235,11 +235,24 @@ def run_ours(args):
     t1.record(stream)
     barrier()
     launches = sa.launch_count() - l0
-    prof = sa.profile_read()
-    sa.profile_enable(False)
     clocks = clk.stop()
     ms_total = t0.elapsed_time(t1)
     ms_step = ms_total / args.steps
+    # the same steps again with every launch bracketed by CUDA events on the
+    # library's stream (host-driven CG iterations, so each launch is seen):
+    # the per-kernel rows, the roofline and the setup phases come from here
+    sa.profile_enable(True)
+    barrier()
+    t2 = torch.cuda.Event(enable_timing=True)
+    t3 = torch.cuda.Event(enable_timing=True)
+    t2.record(stream)
+    for _ in range(args.steps):
+        one_step(dprob, b)
+    t3.record(stream)
+    barrier()
+    prof = sa.profile_read()
+    sa.profile_enable(False)
+    ms_step_prof = t2.elapsed_time(t3) / args.steps
     ms_step = reduce_over_ranks(ms_step, ws, "max")        # the slowest replica sets the step time
     launches = int(reduce_over_ranks(launches, ws, "sum"))  # kernels of all replicas
 
@@ -354,6 +367,7 @@ def run_ours(args):
     result = {
         "metric": METRIC, "value": round(ms_step / 1000.0, 4), "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 2), "higher_is_better": False,
+        "ms_per_step_instrumented": round(ms_step_prof, 2),
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 inside the mixed V-cycle)",
         "data": "synthetic (seeded generator; paper's battery meshes are not public)",
         "config": {"workload": desc, "dofs": n, "nnz": p["nnz"], "material_theta": MAT_THETA,

@@ -154,11 +154,17 @@ __device__ __forceinline__ void tile_gemm_nt_sub(int64_t n, double* __restrict__
   }
 }
 
-// trailing update after panel k: A_ij -= L_ik L_jk^T, k < j <= i
-__global__ void k_syrk_update(int64_t n, double* __restrict__ M, int k) {
+// trailing update after panel k: A_ij -= L_ik L_jk^T for tiles first <= j <= i
+// (col_only: the tiles of block column j = first only)
+__global__ void k_syrk_update(int64_t n, double* __restrict__ M, int k, int first, int col_only) {
   int ti, tj;
-  tri_index(blockIdx.x, &ti, &tj);
-  const int i = k + 1 + ti, j = k + 1 + tj;
+  if (col_only) {
+    ti = (int)blockIdx.x;
+    tj = 0;
+  } else {
+    tri_index(blockIdx.x, &ti, &tj);
+  }
+  const int i = first + ti, j = first + tj;
   const int64_t oi = (int64_t)i * NB, oj = (int64_t)j * NB, ok = (int64_t)k * NB;
   const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
   const int bj = (int)((n - oj) < NB ? (n - oj) : NB);
@@ -198,9 +204,10 @@ __global__ void k_trsm_lower_left(int64_t n, const double* __restrict__ Dinv, do
   }
 }
 
-// W_mj -= L_mi W_ij for m > i, j <= i
-__global__ void k_gemm_left(int64_t n, const double* __restrict__ L, double* __restrict__ W, int i, int ncolb) {
-  const int m = i + 1 + blockIdx.x / ncolb;
+// W_mj -= L_mi W_ij for block rows m >= m0 (m0 > i), j <= i
+__global__ void k_gemm_left(int64_t n, const double* __restrict__ L, double* __restrict__ W, int i, int ncolb,
+                            int m0) {
+  const int m = m0 + blockIdx.x / ncolb;
   const int j = blockIdx.x % ncolb;
   const int64_t om = (int64_t)m * NB, oi = (int64_t)i * NB, oj = (int64_t)j * NB;
   const int bm = (int)((n - om) < NB ? (n - om) : NB);
@@ -256,33 +263,105 @@ int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int3
   SA_LAUNCHED();
   const int nb = (int)((n + NB - 1) / NB);
   SA_TRY(Dinv.alloc(&al, (int64_t)nb * NB * NB));
-  for (int k = 0; k < nb; ++k) {
+  // Look-ahead on a second stream: after panel k, the main stream updates
+  // only block column k+1 and goes on to factor panel k+1, while the side
+  // stream updates the rest of the trailing matrix (columns >= k+2); the
+  // main stream waits for that before it updates column k+2.  The same for
+  // the inverse: row i+1 on the main stream, rows >= i+2 on the side.
+  // Without a second stream every update runs on the main one.
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t e_main = nullptr, e_side = nullptr;
+  bool la = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&e_main, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&e_side, cudaEventDisableTiming) == cudaSuccess;
+  if (!la) cudaGetLastError();
+  auto cleanup = [&]() {
+    if (e_main) cudaEventDestroy(e_main);
+    if (e_side) cudaEventDestroy(e_side);
+    if (s2) cudaStreamDestroy(s2);
+  };
+  int st = SA_OK;
+  bool side_pending = false;
+  for (int k = 0; k < nb && st == SA_OK; ++k) {
     k_potrf_diag<<<1, 256, 0, s>>>(n, M.p, k, err.p, Dinv.p);
-    SA_LAUNCHED();
+    count_launch();
     const int m = nb - k - 1;
     if (m > 0) {
       k_trsm_panel<<<m, 256, 0, s>>>(n, M.p, k, Dinv.p);
-      SA_LAUNCHED();
-      k_syrk_update<<<(unsigned)((int64_t)m * (m + 1) / 2), 256, 0, s>>>(n, M.p, k);
-      SA_LAUNCHED();
+      count_launch();
+      if (la) {
+        if (side_pending && cudaStreamWaitEvent(s, e_side, 0) != cudaSuccess) st = SA_ERR_CUDA;
+        k_syrk_update<<<m, 256, 0, s>>>(n, M.p, k, k + 1, 1);
+        count_launch();
+        if (m > 1) {
+          if (cudaEventRecord(e_main, s) != cudaSuccess || cudaStreamWaitEvent(s2, e_main, 0) != cudaSuccess)
+            st = SA_ERR_CUDA;
+          k_syrk_update<<<(unsigned)((int64_t)(m - 1) * m / 2), 256, 0, s2>>>(n, M.p, k, k + 2, 0);
+          count_launch();
+          if (cudaEventRecord(e_side, s2) != cudaSuccess) st = SA_ERR_CUDA;
+          side_pending = true;
+        } else {
+          side_pending = false;
+        }
+      } else {
+        k_syrk_update<<<(unsigned)((int64_t)m * (m + 1) / 2), 256, 0, s>>>(n, M.p, k, k + 1, 0);
+        count_launch();
+      }
     }
+    if (cudaGetLastError() != cudaSuccess) st = SA_ERR_CUDA;
+  }
+  if (la && side_pending && cudaStreamWaitEvent(s, e_side, 0) != cudaSuccess) st = SA_ERR_CUDA;
+  if (st != SA_OK) {
+    cudaStreamSynchronize(s);
+    if (s2) cudaStreamSynchronize(s2);
+    cleanup();
+    return st;
   }
   int h_err = 0;
-  SA_TRY(copy_d2h(&h_err, err.p, sizeof(int), s));
-  if (h_err) return SA_ERR_NOT_SPD;
+  st = copy_d2h(&h_err, err.p, sizeof(int), s);
+  if (st != SA_OK || h_err) {
+    cleanup();
+    return st != SA_OK ? st : SA_ERR_NOT_SPD;
+  }
   // strict upper triangle of M outside the diagonal tiles still holds A: W
   // reads only the lower triangle of L, so it is left as is.
   k_set_identity<<<blocks_for(n * n, 256), 256, 0, s>>>(n, W.p);
-  SA_LAUNCHED();
-  for (int i = 0; i < nb; ++i) {
+  count_launch();
+  side_pending = false;
+  for (int i = 0; i < nb && st == SA_OK; ++i) {
     k_trsm_lower_left<<<i + 1, 256, 0, s>>>(n, Dinv.p, W.p, i);
-    SA_LAUNCHED();
+    count_launch();
     const int m = nb - i - 1;
     if (m > 0) {
-      k_gemm_left<<<(unsigned)(m * (i + 1)), 256, 0, s>>>(n, M.p, W.p, i, i + 1);
-      SA_LAUNCHED();
+      if (la) {
+        if (side_pending && cudaStreamWaitEvent(s, e_side, 0) != cudaSuccess) st = SA_ERR_CUDA;
+        k_gemm_left<<<(unsigned)(i + 1), 256, 0, s>>>(n, M.p, W.p, i, i + 1, i + 1);
+        count_launch();
+        if (m > 1) {
+          if (cudaEventRecord(e_main, s) != cudaSuccess || cudaStreamWaitEvent(s2, e_main, 0) != cudaSuccess)
+            st = SA_ERR_CUDA;
+          k_gemm_left<<<(unsigned)((m - 1) * (i + 1)), 256, 0, s2>>>(n, M.p, W.p, i, i + 1, i + 2);
+          count_launch();
+          if (cudaEventRecord(e_side, s2) != cudaSuccess) st = SA_ERR_CUDA;
+          side_pending = true;
+        } else {
+          side_pending = false;
+        }
+      } else {
+        k_gemm_left<<<(unsigned)(m * (i + 1)), 256, 0, s>>>(n, M.p, W.p, i, i + 1, i + 1);
+        count_launch();
+      }
     }
+    if (cudaGetLastError() != cudaSuccess) st = SA_ERR_CUDA;
   }
+  if (la && side_pending && cudaStreamWaitEvent(s, e_side, 0) != cudaSuccess) st = SA_ERR_CUDA;
+  if (st != SA_OK) {
+    cudaStreamSynchronize(s);
+    if (s2) cudaStreamSynchronize(s2);
+    cleanup();
+    return st;
+  }
+  cleanup();  // destroying the side stream after the main stream's wait is safe: pending work completes
   dim3 tb(32, 8), tg((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
   k_transpose_dense<<<tg, tb, 0, s>>>(n, W.p, WT.p);
   SA_LAUNCHED();
