@@ -45,6 +45,28 @@ MAT_THETA, CLS_THETA, TOL = 0.05, 0.04, 1e-8
 METRIC = "time-to-1e-8 residual per step (material setup + FP64 PCG + FP32-V-cycle FCG + classical setup + FP64 PCG)"
 
 
+def battery_nnz(nx, ny, nz):
+    """stored entries of the battery stack's matrix after the Dirichlet
+    elimination at z = 0 and at the top (rows there keep their diagonal)"""
+    sxy = (3 * (nx + 1) - 2) * (3 * (ny + 1) - 2)
+    total = 0
+    for k in range(nz + 1):
+        if k == 0 or k == nz:
+            total += (nx + 1) * (ny + 1)
+        else:
+            total += sxy * (3 - (k - 1 == 0) - (k + 1 == nz))
+    return total
+
+
+def workload_config(args, ws):
+    """the `config` object of the JSON line (both arms)"""
+    kw, desc = WORKLOADS[args.workload]
+    return {"workload": desc, "dofs": (kw["nx"] + 1) * (kw["ny"] + 1) * (kw["nz"] + 1),
+            "nnz": battery_nnz(kw["nx"], kw["ny"], kw["nz"]), "material_theta": MAT_THETA,
+            "classical_theta": CLS_THETA, "tol": TOL, "cheb_degree": 2, "max_coarse": 5000,
+            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -79,7 +101,7 @@ def kernel_source_hash():
     """hash of the sources that define the V-cycle kernels (a recorded ncu
     traffic figure is used only while they are unchanged)"""
     h = hashlib.sha256()
-    for f in ("vcycle.cu", "vcycle.cuh", "vkern.cuh", "common.cuh"):
+    for f in ("vcycle.cu", "vkern.cuh"):
         with open(os.path.join(ROOT, "paper_2602_05686_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -370,9 +392,7 @@ def run_ours(args):
         "ms_per_step_instrumented": round(ms_step_prof, 2),
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 inside the mixed V-cycle)",
         "data": "synthetic (seeded generator; paper's battery meshes are not public)",
-        "config": {"workload": desc, "dofs": n, "nnz": p["nnz"], "material_theta": MAT_THETA,
-                   "classical_theta": CLS_THETA, "tol": TOL, "cheb_degree": 2, "max_coarse": 5000,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
+        "config": workload_config(args, ws),
         "parts_ms": avg,
         "iters": {"material_fp64": infos["fp64"]["iters"], "material_fp32": infos["fp32"]["iters"],
                   "classical_fp64": infos["classical"]["iters"]},
@@ -454,7 +474,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(sec, 3), "unit": "s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1000, 1),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][1], "dofs": nfull},
+           "data": "synthetic (seeded generator; paper's battery meshes are not public)",
+           "config": workload_config(args, ws),
            "iters_sample": {"material_fp64": its[0], "material_flexible": its[1], "classical_fp64": its[2]},
            "cpu_baseline": {"value": round(sec, 3), "unit": "s", "cores": 1, "kind": "oracle",
                             "sample": f"battery stack 48x48x96 ({p["n"]} dofs) per step, scaled by dofs to "

@@ -107,7 +107,10 @@ typedef struct {
  *   max_levels = 10, Chebyshev degree 2 with lambda_max boost 1.1 and ratio
  *   30, 10 power steps, omega_sym = 4/3, maxit = 500.
  * alloc/dealloc: optional device allocator (e.g. a caching allocator);
- *   NULL = stream-ordered cudaMallocAsync/cudaFreeAsync on `stream`.
+ *   NULL = stream-ordered cudaMallocAsync/cudaFreeAsync on `stream`, from the
+ *   current device's default pool, whose release threshold the library raises
+ *   so that freed memory stays cached for later setups in this process (pass
+ *   an allocator to keep memory elsewhere).
  */
 typedef struct {
   double theta;
@@ -159,8 +162,17 @@ int sa_setup(const sa_problem* prob, const sa_options* opt, sa_handle* out);
 int sa_solve(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info);
 
 /*
- * k independent solves with the same hierarchy; B and X are column-major
- * n x k (column c starts at B + c*n); infos (may be NULL) receives k entries.
+ * k independent solves with the same hierarchy (several load cases of one
+ * operator, Sec. 4.3: the setup is amortised over right-hand sides); B and X
+ * are column-major n x k (column c starts at B + c*n), both device or both
+ * host pointers; infos (may be NULL) receives k entries.  The columns run in
+ * blocks of up to 8 that share every launch (operator products, V-cycle,
+ * vector updates); each column follows the one-vector arithmetic in the same
+ * order, so column c ends bitwise where sa_solve(b_c) ends (same iterations,
+ * status and x).  Returns SA_OK, SA_ERR_NO_CONVERGENCE or SA_ERR_BREAKDOWN
+ * (the first failing column's status; every column's status is in infos),
+ * or an error of the whole call.  Block buffers (about 7 n x 8 doubles plus
+ * the V-cycle's n_l x 8 vectors) are allocated on the first call.
  */
 int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos);
 

@@ -33,6 +33,8 @@ void set_error_text(const char* text);
 
 // after every kernel launch: error check + launch count
 void count_launch();
+void count_launches(long long k);  // k may be negative (kernels captured into a graph, not run)
+long long launch_counter();
 #define SA_LAUNCHED()        \
   do {                       \
     ::sa::count_launch();    \

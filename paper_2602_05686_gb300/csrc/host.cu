@@ -4,6 +4,7 @@
 // host only sequences launches and reads back sizes and convergence flags.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -64,6 +65,7 @@ struct sa_handle_s {
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   int graph_failed = 0;
+  long long body_launches[2] = {0, 0};  // kernels of one captured CG iteration
   sa::Buf<int> it_dev;
   sa::Buf<double> ctl;  // [0] tol * r0
   // k-column solve workspace (interleaved n x KMAX_BLOCK blocks), made on first use
@@ -451,7 +453,10 @@ static int capture_loop(sa_handle h, int form) {
       cudaSuccess) {
     st = SA_ERR_CUDA;
   } else {
+    const long long c0 = launch_counter();
     st = cg_body(h, ch);
+    h->body_launches[form] = launch_counter() - c0;
+    count_launches(-h->body_launches[form]);  // captured, not run: counted per replayed iteration
     cudaGraph_t out = nullptr;
     if (cudaStreamEndCapture(h->cap_stream, &out) != cudaSuccess) st = SA_ERR_CUDA;
   }
@@ -504,6 +509,7 @@ static int cg_graph(sa_handle h, const double* b, double* x, double tol, sa_solv
     SA_TRY(launch_finish(s, h->part.p, RED_BLOCKS, h->dots.p + 4));
     int one = 1;
     SA_CUDA(cudaMemcpyAsync(h->it_dev.p, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    bool graph_launched = false;
     for (;;) {
       SA_CUDA(cudaMemcpyAsync(hp, h->dots.p + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
       SA_CUDA(cudaMemcpyAsync(hp + 1, &h->cg.p->breakdown, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -523,7 +529,9 @@ static int cg_graph(sa_handle h, const double* b, double* x, double tol, sa_solv
       }
       if (it >= h->opt.maxit) break;
       SA_CUDA(cudaGraphLaunch(h->gexec[form], s));
+      graph_launched = true;
     }
+    if (graph_launched && it > 1) count_launches((long long)(it - 1) * h->body_launches[form]);
   } else {
     status = SA_OK;
   }
@@ -543,9 +551,17 @@ static int cg_graph(sa_handle h, const double* b, double* x, double tol, sa_solv
   return status;
 }
 
+// SA_CG_GRAPH=0 in the environment keeps every CG iteration host-driven (the
+// same kernels in the same order, launched one by one): for tools that do not
+// look inside conditional graph nodes, such as per-kernel profilers
+static bool graphs_allowed() {
+  const char* e = getenv("SA_CG_GRAPH");
+  return !(e && e[0] == '0');
+}
+
 static int cg_device(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
   const int form = h->opt.precision == SA_PREC_FP32_VCYCLE ? 1 : 0;
-  if (!prof_on() && !h->graph_failed) {
+  if (!prof_on() && !h->graph_failed && graphs_allowed()) {
     if (!h->gexec[form] && capture_loop(h, form) != SA_OK) h->graph_failed = 1;
     if (h->gexec[form]) return cg_graph(h, b, x, tol, info);
   }

@@ -2,6 +2,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace sa {
@@ -16,6 +18,33 @@ void set_error_text(const char* text) { snprintf(g_last_error, sizeof(g_last_err
 
 static unsigned long long g_launches = 0;
 void count_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+// kernels run by graph replays (captured kernels are counted when they run,
+// not when they are captured)
+void count_launches(long long k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+long long launch_counter() { return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+// The stream-ordered pool of this process keeps freed memory cached instead
+// of returning it to the driver at every synchronisation (a setup allocates
+// and frees hundreds of level buffers; a later setup reuses them).  Applies
+// to this process's default pool of the current device only.
+static void keep_pool_memory() {
+  static bool done[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  done[dev] = true;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+}
 
 int Alloc::get(void** p, size_t bytes) {
   *p = nullptr;
@@ -23,6 +52,7 @@ int Alloc::get(void** p, size_t bytes) {
     *p = fn_alloc(bytes, ctx);
     if (!*p) return SA_ERR_OOM;
   } else {
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync(p, bytes, stream);
     if (e != cudaSuccess) {
       set_cuda_error(e, "cudaMallocAsync");

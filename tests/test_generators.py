@@ -120,3 +120,15 @@ def test_annulus_trends_against_table1(orc, gen_mod):
     # and theta = 0.05 grows more than theta = 0.1, in both
     assert its[(0.05, 4)] / its[(0.05, 0)] > its[(0.1, 4)] / its[(0.1, 0)]
     assert paper[(0.05, 4)] / paper[(0.05, 0)] > paper[(0.1, 4)] / paper[(0.1, 0)]
+
+
+def test_bench_config_nnz_closed_form(gen_mod):
+    """the bench's config reports the battery stack's stored entries from a
+    closed form (the reference arm does not assemble the full matrix)"""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    for nx, ny, nz in ((4, 4, 8), (8, 6, 16), (16, 16, 32)):
+        p = gen_mod.battery_3d(nx, ny, nz)
+        assert bench.battery_nnz(nx, ny, nz) == p["nnz"]
+    assert bench.battery_nnz(128, 128, 256) == 113128957

@@ -77,3 +77,34 @@ def test_fine_level_setup_parity_full_size(sa, orc, gen_mod, case):
     _, i32 = h.solve(b)
     assert i64["status"] == 0 and i64["rel_res"] <= 1e-8
     assert i32["status"] == 0 and i32["rel_res"] <= 1e-8
+
+
+def test_cut_drop_mask_full_size(sa, orc, gen_mod):
+    """cut-drop (Sec. 2.1, the paper's recommended criterion with the material
+    measure at theta = 0.08) on the full battery stack: the fine-level kept
+    mask equals the oracle's on the same inputs, bit for bit"""
+    p = gen_mod.battery_3d()
+    n, rp, ci = p["n"], p["row_ptr"], p["col"]
+    h = sa.Hierarchy(p, theta=0.08, measure="material", keep_setup_data=True, drop="cut")
+    s0 = h.export_strength(0, keep=True, root=False, aux=False)
+    dm = orc.dirichlet(n, rp, ci, p["val"])
+    sig = orc.nodal_from_elements(3, n, p["elem_nodes"], p["elem_measure"], p["tensors"])
+    sinv = orc.invert_tensors(3, sig)
+    w, D, _ = orc.strength_material(3, n, rp, ci, dm, p["coords"], sinv, 0.08)
+    keep = orc.cut_drop(n, rp, ci, dm, orc.strength2_material(n, rp, ci, w, D), 0.08)
+    assert np.array_equal(keep, s0["keep"])
+
+
+def test_multi_rhs_columns_full_size(sa, gen_mod):
+    """two load cases on the full battery stack in one multi-RHS solve, FP32
+    V-cycle form: each column equals its one-vector solve bitwise"""
+    import torch
+    p = gen_mod.battery_3d()
+    h = sa.Hierarchy(p, theta=0.05, measure="material", precision="fp32")
+    b = torch.from_numpy(p["b"]).cuda()
+    B = torch.stack([b, 3.0 * b])
+    X, infos = h.solve_batch(B)
+    for c in range(2):
+        x1, i1 = h.solve(B[c].clone())
+        assert infos[c]["iters"] == i1["iters"] and torch.equal(X[c], x1)
+        assert infos[c]["status"] == 0 and infos[c]["rel_res"] <= 1e-8

@@ -95,6 +95,8 @@ CASES = [
     ("battery-classical", lambda g: g.battery_3d(16, 16, 32), 0.04, "classical", 200),
     ("voronoi-material", lambda g: g.voronoi_3d(14, seed=1), 0.05, "material", 150),
     ("voronoi-classical", lambda g: g.voronoi_3d(14, seed=1), 0.04, "classical", 150),
+    ("inclusions-material", lambda g: g.inclusions_3d(20, nrhs=1), 0.05, "material", 200),
+    ("inclusions-classical", lambda g: g.inclusions_3d(20, nrhs=1), 0.04, "classical", 200),
     ("annulus-material-0.05", lambda g: g.annulus_3d(0, kappa=1e4), 0.05, "material", 500),
     ("annulus-material-0.1", lambda g: g.annulus_3d(0, kappa=1e4), 0.1, "material", 500),
 ]
@@ -139,7 +141,10 @@ def test_hierarchy_parity_cut_drop(sa, orc, gen_mod, case):
     assert info["status"] == 0 and abs(info["iters"] - oinfo["iters"]) <= 1
 
 
-@pytest.mark.parametrize("case", CASES[:2] + CASES[5:8], ids=[c[0] for c in CASES[:2] + CASES[5:8]])
+SOLVE_CASES = CASES[:2] + CASES[5:8] + CASES[9:11]
+
+
+@pytest.mark.parametrize("case", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
 def test_solve_parity_fp64(sa, orc, gen_mod, case):
     import torch
     _, mk, theta, measure, mc = case
@@ -155,7 +160,7 @@ def test_solve_parity_fp64(sa, orc, gen_mod, case):
     assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("case", CASES[:2] + CASES[5:8], ids=[c[0] for c in CASES[:2] + CASES[5:8]])
+@pytest.mark.parametrize("case", SOLVE_CASES[:5], ids=[c[0] for c in SOLVE_CASES[:5]])
 def test_solve_mixed_precision(sa, orc, gen_mod, case):
     import torch
     _, mk, theta, measure, mc = case
