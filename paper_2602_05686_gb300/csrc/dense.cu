@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "profile.cuh"
 #include "solve.cuh"
 
 namespace sa {
@@ -247,125 +248,147 @@ __global__ void k_transpose_dense(int64_t n, const double* __restrict__ W, doubl
   }
 }
 
-int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
-                             Buf<double>& W, Buf<double>& WT) {
+DenseJob::~DenseJob() {
+  // left without dense_finish (an error in between): the temporaries are
+  // released on the caller's stream after this returns, so the dense
+  // launches must have ended first
+  if (pending) {
+    if (sd) cudaStreamSynchronize(sd);
+    if (s2) cudaStreamSynchronize(s2);
+  }
+  if (e_fork) cudaEventDestroy(e_fork);
+  if (e_done) cudaEventDestroy(e_done);
+  if (e_main) cudaEventDestroy(e_main);
+  if (e_side) cudaEventDestroy(e_side);
+  if (s2) cudaStreamDestroy(s2);   // pending work still completes
+  if (sd) cudaStreamDestroy(sd);
+}
+
+int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, Buf<double>& W,
+                Buf<double>& WT, DenseJob& job) {
   cudaStream_t s = al.stream;
+  job.main = s;
+  job.n = n;
   if (n <= 0) return SA_OK;
-  Buf<double> M, Dinv;
-  Buf<int> err;
-  SA_TRY(M.alloc(&al, n * n));
+  SA_TRY(job.M.alloc(&al, n * n));
   SA_TRY(W.alloc(&al, n * n));
   SA_TRY(WT.alloc(&al, n * n));
-  SA_TRY(err.alloc(&al, 1));
-  SA_TRY(memset_d(M.p, 0, M.bytes(), s));
-  SA_TRY(memset_d(err.p, 0, sizeof(int), s));
-  k_densify<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, v, M.p);
+  SA_TRY(job.err.alloc(&al, 1));
+  SA_TRY(memset_d(job.M.p, 0, job.M.bytes(), s));
+  SA_TRY(memset_d(job.err.p, 0, sizeof(int), s));
+  k_densify<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, v, job.M.p);
   SA_LAUNCHED();
   const int nb = (int)((n + NB - 1) / NB);
-  SA_TRY(Dinv.alloc(&al, (int64_t)nb * NB * NB));
-  // Look-ahead on a second stream: after panel k, the main stream updates
-  // only block column k+1 and goes on to factor panel k+1, while the side
-  // stream updates the rest of the trailing matrix (columns >= k+2); the
-  // main stream waits for that before it updates column k+2.  The same for
-  // the inverse: row i+1 on the main stream, rows >= i+2 on the side.
-  // Without a second stream every update runs on the main one.
-  cudaStream_t s2 = nullptr;
-  cudaEvent_t e_main = nullptr, e_side = nullptr;
-  bool la = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaEventCreateWithFlags(&e_main, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&e_side, cudaEventDisableTiming) == cudaSuccess;
+  SA_TRY(job.Dinv.alloc(&al, (int64_t)nb * NB * NB));
+  // The factor runs on its own stream `sd`, forked from the caller's stream
+  // after the dense copy; the caller goes on with work that does not read
+  // W (Chebyshev bounds, SELL packing) and joins in dense_finish.  Within
+  // it, look-ahead on a second stream: after panel k, `sd` updates only
+  // block column k+1 and goes on to factor panel k+1, while `s2` updates
+  // the rest of the trailing matrix (columns >= k+2); `sd` waits for that
+  // before it updates column k+2.  The same for the inverse: row i+1 on `sd`,
+  // rows >= i+2 on `s2`.  Without the extra streams everything runs on the
+  // caller's stream in the same order.
+  bool own = cudaStreamCreateWithFlags(&job.sd, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&job.e_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&job.e_done, cudaEventDisableTiming) == cudaSuccess;
+  bool la = own && cudaStreamCreateWithFlags(&job.s2, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&job.e_main, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&job.e_side, cudaEventDisableTiming) == cudaSuccess;
   if (!la) cudaGetLastError();
-  auto cleanup = [&]() {
-    if (e_main) cudaEventDestroy(e_main);
-    if (e_side) cudaEventDestroy(e_side);
-    if (s2) cudaStreamDestroy(s2);
-  };
-  int st = SA_OK;
+  cudaStream_t m = s;
+  if (own) {
+    SA_CUDA(cudaEventRecord(job.e_fork, s));
+    SA_CUDA(cudaStreamWaitEvent(job.sd, job.e_fork, 0));
+    m = job.sd;
+  }
+  job.pending = own;
+  cudaStream_t s2 = job.s2;
+  double* M = job.M.p;
+  double* D = job.Dinv.p;
+  const int ph = prof_begin(m, PK_S_DENSE, job.level, 0.0);
   bool side_pending = false;
-  for (int k = 0; k < nb && st == SA_OK; ++k) {
-    k_potrf_diag<<<1, 256, 0, s>>>(n, M.p, k, err.p, Dinv.p);
+  for (int k = 0; k < nb; ++k) {
+    k_potrf_diag<<<1, 256, 0, m>>>(n, M, k, job.err.p, D);
     count_launch();
-    const int m = nb - k - 1;
-    if (m > 0) {
-      k_trsm_panel<<<m, 256, 0, s>>>(n, M.p, k, Dinv.p);
+    const int r = nb - k - 1;
+    if (r > 0) {
+      k_trsm_panel<<<r, 256, 0, m>>>(n, M, k, D);
       count_launch();
       if (la) {
-        if (side_pending && cudaStreamWaitEvent(s, e_side, 0) != cudaSuccess) st = SA_ERR_CUDA;
-        k_syrk_update<<<m, 256, 0, s>>>(n, M.p, k, k + 1, 1);
+        if (side_pending) SA_CUDA(cudaStreamWaitEvent(m, job.e_side, 0));
+        k_syrk_update<<<r, 256, 0, m>>>(n, M, k, k + 1, 1);
         count_launch();
-        if (m > 1) {
-          if (cudaEventRecord(e_main, s) != cudaSuccess || cudaStreamWaitEvent(s2, e_main, 0) != cudaSuccess)
-            st = SA_ERR_CUDA;
-          k_syrk_update<<<(unsigned)((int64_t)(m - 1) * m / 2), 256, 0, s2>>>(n, M.p, k, k + 2, 0);
+        if (r > 1) {
+          SA_CUDA(cudaEventRecord(job.e_main, m));
+          SA_CUDA(cudaStreamWaitEvent(s2, job.e_main, 0));
+          k_syrk_update<<<(unsigned)((int64_t)(r - 1) * r / 2), 256, 0, s2>>>(n, M, k, k + 2, 0);
           count_launch();
-          if (cudaEventRecord(e_side, s2) != cudaSuccess) st = SA_ERR_CUDA;
+          SA_CUDA(cudaEventRecord(job.e_side, s2));
           side_pending = true;
         } else {
           side_pending = false;
         }
       } else {
-        k_syrk_update<<<(unsigned)((int64_t)m * (m + 1) / 2), 256, 0, s>>>(n, M.p, k, k + 1, 0);
+        k_syrk_update<<<(unsigned)((int64_t)r * (r + 1) / 2), 256, 0, m>>>(n, M, k, k + 1, 0);
         count_launch();
       }
     }
-    if (cudaGetLastError() != cudaSuccess) st = SA_ERR_CUDA;
+    SA_LAUNCHED();
   }
-  if (la && side_pending && cudaStreamWaitEvent(s, e_side, 0) != cudaSuccess) st = SA_ERR_CUDA;
-  if (st != SA_OK) {
-    cudaStreamSynchronize(s);
-    if (s2) cudaStreamSynchronize(s2);
-    cleanup();
-    return st;
-  }
-  int h_err = 0;
-  st = copy_d2h(&h_err, err.p, sizeof(int), s);
-  if (st != SA_OK || h_err) {
-    cleanup();
-    return st != SA_OK ? st : SA_ERR_NOT_SPD;
-  }
-  // strict upper triangle of M outside the diagonal tiles still holds A: W
-  // reads only the lower triangle of L, so it is left as is.
-  k_set_identity<<<blocks_for(n * n, 256), 256, 0, s>>>(n, W.p);
+  if (la && side_pending) SA_CUDA(cudaStreamWaitEvent(m, job.e_side, 0));
+  // W = L^-1 block row by block row.  A pivot that was not positive is
+  // recorded in err and replaced by 1, so the inverse is computed on finite
+  // data either way; dense_finish reports it.  The strict upper triangle of
+  // M outside the diagonal tiles still holds A: W reads only the lower
+  // triangle of L, so it is left as is.
+  k_set_identity<<<blocks_for(n * n, 256), 256, 0, m>>>(n, W.p);
   count_launch();
   side_pending = false;
-  for (int i = 0; i < nb && st == SA_OK; ++i) {
-    k_trsm_lower_left<<<i + 1, 256, 0, s>>>(n, Dinv.p, W.p, i);
+  for (int i = 0; i < nb; ++i) {
+    k_trsm_lower_left<<<i + 1, 256, 0, m>>>(n, D, W.p, i);
     count_launch();
-    const int m = nb - i - 1;
-    if (m > 0) {
+    const int r = nb - i - 1;
+    if (r > 0) {
       if (la) {
-        if (side_pending && cudaStreamWaitEvent(s, e_side, 0) != cudaSuccess) st = SA_ERR_CUDA;
-        k_gemm_left<<<(unsigned)(i + 1), 256, 0, s>>>(n, M.p, W.p, i, i + 1, i + 1);
+        if (side_pending) SA_CUDA(cudaStreamWaitEvent(m, job.e_side, 0));
+        k_gemm_left<<<(unsigned)(i + 1), 256, 0, m>>>(n, M, W.p, i, i + 1, i + 1);
         count_launch();
-        if (m > 1) {
-          if (cudaEventRecord(e_main, s) != cudaSuccess || cudaStreamWaitEvent(s2, e_main, 0) != cudaSuccess)
-            st = SA_ERR_CUDA;
-          k_gemm_left<<<(unsigned)((m - 1) * (i + 1)), 256, 0, s2>>>(n, M.p, W.p, i, i + 1, i + 2);
+        if (r > 1) {
+          SA_CUDA(cudaEventRecord(job.e_main, m));
+          SA_CUDA(cudaStreamWaitEvent(s2, job.e_main, 0));
+          k_gemm_left<<<(unsigned)((r - 1) * (i + 1)), 256, 0, s2>>>(n, M, W.p, i, i + 1, i + 2);
           count_launch();
-          if (cudaEventRecord(e_side, s2) != cudaSuccess) st = SA_ERR_CUDA;
+          SA_CUDA(cudaEventRecord(job.e_side, s2));
           side_pending = true;
         } else {
           side_pending = false;
         }
       } else {
-        k_gemm_left<<<(unsigned)(m * (i + 1)), 256, 0, s>>>(n, M.p, W.p, i, i + 1, i + 1);
+        k_gemm_left<<<(unsigned)(r * (i + 1)), 256, 0, m>>>(n, M, W.p, i, i + 1, i + 1);
         count_launch();
       }
     }
-    if (cudaGetLastError() != cudaSuccess) st = SA_ERR_CUDA;
+    SA_LAUNCHED();
   }
-  if (la && side_pending && cudaStreamWaitEvent(s, e_side, 0) != cudaSuccess) st = SA_ERR_CUDA;
-  if (st != SA_OK) {
-    cudaStreamSynchronize(s);
-    if (s2) cudaStreamSynchronize(s2);
-    cleanup();
-    return st;
-  }
-  cleanup();  // destroying the side stream after the main stream's wait is safe: pending work completes
+  if (la && side_pending) SA_CUDA(cudaStreamWaitEvent(m, job.e_side, 0));
   dim3 tb(32, 8), tg((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
-  k_transpose_dense<<<tg, tb, 0, s>>>(n, W.p, WT.p);
+  k_transpose_dense<<<tg, tb, 0, m>>>(n, W.p, WT.p);
   SA_LAUNCHED();
+  prof_end(m, ph);
+  if (own) SA_CUDA(cudaEventRecord(job.e_done, m));
   return SA_OK;
+}
+
+int dense_finish(DenseJob& job) {
+  if (job.n <= 0) return SA_OK;
+  if (job.pending) {
+    SA_CUDA(cudaStreamWaitEvent(job.main, job.e_done, 0));
+    job.pending = false;
+  }
+  int h_err = 0;
+  SA_TRY(copy_d2h(&h_err, job.err.p, sizeof(int), job.main));
+  return h_err ? SA_ERR_NOT_SPD : SA_OK;
 }
 
 // y = W b (W lower triangular): warp per row over j <= i

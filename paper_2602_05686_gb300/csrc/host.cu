@@ -818,6 +818,13 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   const int nlev = (int)h->lev.size();
   Level& Lc = *h->lev[nlev - 1];
   if (Lc.n > 16384) return SA_ERR_STAGNATION;
+  h->nL = Lc.n;
+  // a15: the coarse Cholesky factor and its inverse, on streams of their own:
+  // the Chebyshev bounds and the packing of the hierarchy below overlap it
+  // (the packing stores the addresses of W and WT, not their contents)
+  DenseJob dj;
+  dj.level = nlev - 1;
+  SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT, dj));
   // a15: smoother data (Chebyshev bounds from 10 power steps on D^-1/2 A D^-1/2)
   for (int l = 0; l < nlev; ++l) {
     PHASE_BEGIN(PK_S_CHEB, l);
@@ -837,10 +844,6 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
     }
     PHASE_END(PK_S_CHEB);
   }
-  h->nL = Lc.n;
-  PHASE_BEGIN(PK_S_DENSE, nlev - 1);
-  SA_TRY(run_dense_inverse_factor(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT));
-  PHASE_END(PK_S_DENSE);
   SA_TRY(alloc_workspace(h));
   PHASE_BEGIN(PK_S_SELL, 0);
   {
@@ -851,6 +854,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   }
   PHASE_END(PK_S_SELL);
   if (o->precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
+  SA_TRY(dense_finish(dj));
   SA_CUDA(cudaStreamSynchronize(s));
   auto t1 = std::chrono::steady_clock::now();
   h->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -1153,14 +1157,18 @@ static int finish_loaded(sa_handle h) {
   }
   Level& Lc = *h->lev[nlev - 1];
   h->nL = Lc.n;
-  SA_TRY(run_dense_inverse_factor(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT));
+  // the coarse factorisation overlaps the packing below (which stores the
+  // addresses of W and WT, not their contents)
+  DenseJob dj;
+  dj.level = nlev - 1;
+  SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT, dj));
   SA_TRY(alloc_workspace(h));
   Level& L0 = *h->lev[0];
   SA_TRY(build_sell<double>(al, L0.n, L0.nnz, L0.rp.p, L0.ci.p, L0.v.p, nullptr, nullptr, h->A0s));
   std::vector<VLevelIn> in = vlevel_inputs(h);
   SA_TRY(vh_build<double>(al, in.data(), nlev, h->opt.cheb_degree, h->W.p, h->WT.p, &h->v64));
   if (h->opt.precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
-  return SA_OK;
+  return dense_finish(dj);
 }
 
 static int load_impl(const unsigned char* buf, uint64_t bytes, sa_handle h) {

@@ -48,9 +48,27 @@ int launch_bcg_pupdate(cudaStream_t st, int64_t n, int k, const CgScalars* s, co
 // column-major n x k <-> interleaved n x K (K >= k; columns k..K-1 zero)
 int launch_interleave(cudaStream_t st, int64_t n, int k, int K, const double* src, double* dst, int to_interleaved);
 
-// dense coarse level (dense.cu)
-int run_dense_inverse_factor(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
-                             Buf<double>& W, Buf<double>& WT);
+// dense coarse level (dense.cu): Cholesky factor L of the coarse matrix and
+// W = L^-1 (WT its transpose).  dense_start enqueues the whole factorisation
+// on streams of its own, forked from al.stream after the dense copy of A;
+// dense_finish makes al.stream wait for it and reports a pivot that was not
+// positive (SA_ERR_NOT_SPD).  Work on al.stream in between must not read W.
+struct DenseJob {
+  Buf<double> M, Dinv;
+  Buf<int> err;
+  cudaStream_t main = nullptr, sd = nullptr, s2 = nullptr;
+  cudaEvent_t e_fork = nullptr, e_done = nullptr, e_main = nullptr, e_side = nullptr;
+  int64_t n = 0;
+  int level = 0;         // for the setup-phase profile
+  bool pending = false;  // forked and not yet joined
+  DenseJob() = default;
+  DenseJob(const DenseJob&) = delete;
+  DenseJob& operator=(const DenseJob&) = delete;
+  ~DenseJob();
+};
+int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, Buf<double>& W,
+                Buf<double>& WT, DenseJob& job);
+int dense_finish(DenseJob& job);
 int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
                         double* x);
 int launch_coarse_solve_block(cudaStream_t st, int64_t n, int k, const double* W, const double* WT, const double* b,
