@@ -204,6 +204,17 @@ int sa_hierarchy_stats(sa_handle h, int* levels, int64_t* n_l, int64_t* nnz_l, d
 int sa_level_sizes(sa_handle h, int l, int64_t* out);
 
 /*
+ * Storage the FP64 V-cycle chose for the scaled operator of level l
+ * (inspection only): out[0] = 0 for SELL-32, else the CSR lanes per row,
+ * -1 on the coarsest (dense) level; out[1] = rows in the CSR long-row bin
+ * (one warp each); out[2] = the entry count above which a row is in that
+ * bin (-1: no bin); out[3] = stored entries (SELL: with padding); out[4] =
+ * SELL-32 lanes per row (1 or 2; 0 otherwise).  out: 5 host int64.  Errors:
+ * SA_ERR_INVALID_ARG for a NULL handle or out, or l out of range.
+ */
+int sa_level_format(sa_handle h, int l, int64_t* out);
+
+/*
  * Copies level l to HOST arrays (any pointer may be NULL to skip it):
  * aggregate map agg[n_l] (-1 = Dirichlet), P_l in CSR (n_l x n_{l+1}) and A_l
  * in CSR.  Used by the parity tests.

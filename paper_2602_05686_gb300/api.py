@@ -20,8 +20,8 @@ PRECISION = {"fp64": 0, "fp32": 1}
 DROP = {"pointwise": 0, "cut": 1}
 
 EXPORTED = ["sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle", "sa_hierarchy_stats",
-            "sa_level_sizes", "sa_export_level", "sa_export_strength", "sa_free", "sa_status_string",
-            "sa_last_error", "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
+            "sa_level_sizes", "sa_level_format", "sa_export_level", "sa_export_strength", "sa_free",
+            "sa_status_string", "sa_last_error", "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
             "sa_launch_count", "sa_strength_material_noalloc", "sa_serialized_size", "sa_serialize",
             "sa_deserialize"]
 
@@ -82,6 +82,7 @@ def lib(build_if_missing: bool = True):
         L.sa_vcycle.argtypes = [P, P, P]
         L.sa_hierarchy_stats.argtypes = [P, P, P, P, P, P]
         L.sa_level_sizes.argtypes = [P, I, P]
+        L.sa_level_format.argtypes = [P, I, P]
         L.sa_export_level.argtypes = [P, I] + [P] * 7
         L.sa_export_strength.argtypes = [P, I] + [P] * 6
         L.sa_free.argtypes = [P]
@@ -101,7 +102,8 @@ def lib(build_if_missing: bool = True):
         L.sa_serialize.argtypes = [P, P, ctypes.c_uint64]
         L.sa_deserialize.argtypes = [P, ctypes.c_uint64, P, P]
         for f in ("sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle",
-                  "sa_hierarchy_stats", "sa_level_sizes", "sa_export_level", "sa_export_strength", "sa_free",
+                  "sa_hierarchy_stats", "sa_level_sizes", "sa_level_format", "sa_export_level",
+                  "sa_export_strength", "sa_free",
                   "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
                   "sa_serialized_size", "sa_serialize", "sa_deserialize"):
             getattr(L, f).restype = I
@@ -314,6 +316,15 @@ class Hierarchy:
         out = np.zeros(5, np.int64)
         _check(lib().sa_level_sizes(self.h, int(l), out.ctypes.data), "sa_level_sizes")
         return dict(n=int(out[0]), nnz=int(out[1]), nnz_P=int(out[2]), nc=int(out[3]), nnz_gc=int(out[4]))
+
+    def level_format(self, l):
+        """storage of the FP64 V-cycle operator of level l: CSR lanes (0 = SELL-32,
+        -1 = dense coarsest level), rows in the long-row bin, its threshold
+        (-1: none), stored entries, SELL-32 lanes per row"""
+        out = np.zeros(5, np.int64)
+        _check(lib().sa_level_format(self.h, int(l), out.ctypes.data), "sa_level_format")
+        return dict(lanes=int(out[0]), nlong=int(out[1]), long_threshold=int(out[2]), stored=int(out[3]),
+                    sell_lanes=int(out[4]))
 
     def export_level(self, l):
         s = self.level_sizes(l)

@@ -43,7 +43,27 @@ __device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restr
 #pragma unroll
   for (int c = 0; c < K; ++c) acc[c] = (T)0;
   T xv[K];
-  if constexpr (SW == 0) {
+  if constexpr (SW == -2) {
+    // two lanes per SELL row: even and odd entries, one shuffle
+    const int64_t sl = gt >> 6;
+    const int r = (int)((gt & 63) >> 1), h = (int)(gt & 1);
+    const int64_t i = sl * 32 + r;
+    row = i;
+    if (i < M.n) {
+      const int64_t e = M.p[sl + 1];
+      const T* __restrict__ xs = M.c16 ? X + (int64_t)M.base[sl] * K : X;
+      for (int64_t p = M.p[sl] + 32 * h + r; p < e; p += 64) {
+        const T a = __ldcs(&M.v[p]);
+        const int64_t c = M.c16 ? (int64_t)__ldcs(&M.c16[p]) : (int64_t)__ldcs(&M.ci[p]);
+        ldvec<T, K>(xs + c * K, xv);
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc[j] += a * xv[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc[j] += __shfl_xor_sync(FULL, acc[j], 1);
+    return i < M.n && h == 0;
+  } else if constexpr (SW == 0) {
     row = gt;
     if (gt >= M.n) return false;
     const int64_t sl = gt >> 5, r = gt & 31;
@@ -66,23 +86,49 @@ __device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restr
     }
     return true;
   } else {
-    const int64_t i = gt / SW;
-    const int sl = (int)(gt % SW);
-    row = i;
-    if (i < M.n) {
+    if (blockIdx.x < M.nlb) {
+      // the long-row bin: one row per warp (warp-uniform), lane-strided
+      // sums and the 32-lane shuffle tree of the one-vector kernel
+      const int64_t w = gt >> 5;
+      if (w >= M.nlong) return false;
+      const int lane = (int)(threadIdx.x & 31);
+      const int64_t i = M.lrows[w];
+      row = i;
       const int64_t e = M.p[i + 1];
-      for (int64_t q = M.p[i] + sl; q < e; q += SW) {
+      for (int64_t q = M.p[i] + lane; q < e; q += 32) {
         const T a = M.v[q];
         ldvec<T, K>(X + (int64_t)M.ci[q] * K, xv);
 #pragma unroll
         for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
+      }
+#pragma unroll
+      for (int c = 0; c < K; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(FULL, acc[c], o);
+      return lane == 0;
+    }
+    const int64_t g = (int64_t)(blockIdx.x - M.nlb) * blockDim.x + threadIdx.x;
+    const int64_t i = g / SW;
+    const int sl = (int)(g % SW);
+    row = i;
+    bool own = false;
+    if (i < M.n) {
+      const int64_t b = M.p[i], e = M.p[i + 1];
+      if (e - b <= M.lt) {
+        own = sl == 0;
+        for (int64_t q = b + sl; q < e; q += SW) {
+          const T a = M.v[q];
+          ldvec<T, K>(X + (int64_t)M.ci[q] * K, xv);
+#pragma unroll
+          for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
+        }
       }
     }
 #pragma unroll
     for (int c = 0; c < K; ++c)
 #pragma unroll
       for (int o = SW / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(FULL, acc[c], o, SW);
-    return i < M.n && sl == 0;
+    return own;
   }
 }
 
@@ -189,15 +235,10 @@ __global__ void k_bcoarse_out(int64_t n, int K, const double* __restrict__ x, co
 #define BMAT_SW(Kern, KK, M, st, ...)                                                    \
   do {                                                                                   \
     const MatView<T> _mv = view(M);                                                      \
-    const int64_t _thr = (M).sw == 0 ? (M).n : (M).n * (int64_t)(M).sw;                  \
-    const unsigned _g = blocks_for(_thr, 256);                                           \
-    switch ((M).sw) {                                                                    \
-      case 0: Kern<T, 0, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;               \
-      case 4: Kern<T, 4, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;               \
-      case 8: Kern<T, 8, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;               \
-      case 16: Kern<T, 16, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;             \
-      default: Kern<T, 32, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;             \
-    }                                                                                    \
+    const unsigned _g = mat_grid(M);                                                     \
+    if ((M).sw == 0 && (M).sell_lanes == 2) Kern<T, -2, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
+    else if ((M).sw == 0) Kern<T, 0, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
+    else Kern<T, CSR_LANES, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                   \
   } while (0)
 
 #define LAUNCH_BMAT(Kern, M, st, K, ...)                                                 \
@@ -366,6 +407,10 @@ static MatView<double> sell_view(const Sell<double>& A) {
   m.v = A.v.p;
   m.base = A.idx16 ? A.base.p : nullptr;
   m.c16 = A.idx16 ? A.c16.p : nullptr;
+  m.lrows = nullptr;
+  m.nlong = 0;
+  m.lt = INT64_MAX;
+  m.nlb = 0;
   return m;
 }
 

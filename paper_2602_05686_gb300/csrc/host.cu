@@ -1008,6 +1008,21 @@ int sa_level_sizes(sa_handle h, int l, int64_t* out) {
   return SA_OK;
 }
 
+int sa_level_format(sa_handle h, int l, int64_t* out) {
+  if (!h || !out || !h->v64 || l < 0 || l >= (int)h->v64->lev.size()) return SA_ERR_INVALID_ARG;
+  if (l + 1 == (int)h->v64->lev.size()) {
+    out[0] = -1; out[1] = 0; out[2] = -1; out[3] = h->v64->lev[l]->n * h->v64->lev[l]->n; out[4] = 0;
+    return SA_OK;
+  }
+  const sa::Mat<double>& A = h->v64->lev[l]->A;
+  out[0] = A.sw;
+  out[1] = A.sw == 0 ? 0 : A.nlong;
+  out[2] = (A.sw == 0 || A.nlong == 0) ? -1 : A.lt;
+  out[3] = A.sw == 0 ? A.sell.stored : A.nnz;
+  out[4] = A.sw == 0 ? A.sell_lanes : 0;
+  return SA_OK;
+}
+
 int sa_export_level(sa_handle h, int l, int32_t* agg, int64_t* P_rowptr, int32_t* P_col, double* P_val,
                     int64_t* A_rowptr, int32_t* A_col, double* A_val) {
   if (!h || l < 0 || l >= (int)h->lev.size()) return SA_ERR_INVALID_ARG;

@@ -172,9 +172,28 @@ __global__ void k_csr_scale(int64_t n, const int64_t* __restrict__ rp, const int
   for (int64_t p = rp[i]; p < rp[i + 1]; ++p) ov[p] = (T)(li * v[p] * (right ? right[ci[p]] : 1.0));
 }
 
-// SELL-32 (one thread per row, one FP64 FMA per stored entry) if it stores at
-// most 25 % padding, else CSR with 4..32 lanes per row by average row length
-// (rows of very different lengths in one slice would pad too much)
+// rows with more than lt entries: flags, then their list (ascending)
+__global__ void k_long_flag(int64_t n, const int64_t* __restrict__ rp, int64_t lt, int64_t* __restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) cnt[i + 1] = (rp[i + 1] - rp[i] > lt) ? 1 : 0;
+}
+
+__global__ void k_long_fill(int64_t n, const int64_t* __restrict__ rp, int64_t lt, const int64_t* __restrict__ cnt,
+                            int32_t* __restrict__ lrows) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && rp[i + 1] - rp[i] > lt) lrows[cnt[i]] = (int32_t)i;
+}
+
+// SELL-32 (one thread per row, one FMA per stored entry) if it stores at most
+// 25 % padding; else CSR with CSR_LANES lanes per row, and the rows longer
+// than LONG_ROW entries in the long-row bin (a warp per row, launched first).
+// On the coarse levels of the stretched battery stack a few rows are 10-40x
+// longer than the rest: a few lanes per row keep the FP64 shuffle additions
+// and idle lanes down (the FP64 pipe is the scarce unit), the bin keeps the
+// long rows from holding the launch.  Measured on its material hierarchy
+// against 8 lanes, 8 lanes with a bin, and 4 lanes with bins from 32 to
+// 128 entries, this was the fastest for both value types.
+
 template <typename T>
 int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
               const double* left, const double* right, Mat<T>& M) {
@@ -182,7 +201,6 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
   M.n = n;
   M.nnz = nnz;
   M.nslices = (n + 31) / 32;
-  const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
   int64_t stored = 0;
   unsigned int max_width = 0;
   if (n > 0) {
@@ -200,14 +218,29 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
   }
   if (n == 0 || (double)stored <= 1.25 * (double)nnz) {
     M.sw = 0;
+    M.sell_lanes = n < SELL2_ROWS ? 2 : 1;
     return build_sell<T>(al, n, nnz, rp, ci, v, left, right, M.sell);
   }
-  M.sw = avg <= 12.0 ? 4 : (avg <= 40.0 ? 8 : (avg <= 96.0 ? 16 : 32));
-  // on a small level a few very long rows (coarse levels of the stretched
-  // battery stack reach 30x the average) hold their warp longer than the
-  // rest of the launch takes: a warp per row then.  On large levels the five
-  // FP64 shuffle additions per row of a warp per row cost more.
-  if (n <= 65536 && (double)max_width > 8.0 * avg) M.sw = 32;
+  M.sw = CSR_LANES;
+  M.nlong = 0;
+  M.lt = INT64_MAX;
+  if ((int64_t)max_width > LONG_ROW) {
+    M.lt = LONG_ROW;
+    Buf<int64_t> cnt;
+    SA_TRY(cnt.alloc(&al, n + 1));
+    SA_TRY(memset_d(cnt.p, 0, sizeof(int64_t), s));
+    k_long_flag<<<blocks_for(n, 256), 256, 0, s>>>(n, rp, M.lt, cnt.p);
+    SA_LAUNCHED();
+    SA_TRY(scan_inplace(al, cnt.p + 1, n));
+    SA_TRY(copy_d2h(&M.nlong, cnt.p + n, sizeof(int64_t), s));
+    SA_TRY(M.lrows.alloc(&al, M.nlong));
+    if (M.nlong > 0) {
+      k_long_fill<<<blocks_for(n, 256), 256, 0, s>>>(n, rp, M.lt, cnt.p, M.lrows.p);
+      SA_LAUNCHED();
+    } else {
+      M.lt = INT64_MAX;
+    }
+  }
   SA_TRY(M.rp.alloc(&al, n + 1));
   SA_TRY(M.ci.alloc(&al, nnz));
   SA_TRY(M.v.alloc(&al, nnz));
@@ -349,15 +382,10 @@ __global__ void k_vc_fine_in(int64_t n, const double* __restrict__ r, const doub
 #define LAUNCH_MAT(K, M, st, ...)                                                        \
   do {                                                                                   \
     const MatView<T> _mv = view(M);                                                      \
-    const int64_t _thr = (M).sw == 0 ? (M).n : (M).n * (int64_t)(M).sw;                  \
-    const unsigned _g = blocks_for(_thr, 256);                                           \
-    switch ((M).sw) {                                                                    \
-      case 0: K<T, 0><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
-      case 4: K<T, 4><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
-      case 8: K<T, 8><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                      \
-      case 16: K<T, 16><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                    \
-      default: K<T, 32><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); break;                    \
-    }                                                                                    \
+    const unsigned _g = mat_grid(M);                                                     \
+    if ((M).sw == 0 && (M).sell_lanes == 2) K<T, -2><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
+    else if ((M).sw == 0) K<T, 0><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                 \
+    else K<T, CSR_LANES><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                          \
   } while (0)
 
 template <typename T>

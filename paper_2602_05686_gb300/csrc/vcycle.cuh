@@ -44,7 +44,11 @@ struct VLevelIn {
 // small, else CSR with sw lanes per row; values scaled and stored in T
 template <typename T>
 struct Mat {
-  int sw = 0;  // 0: SELL-32; 4/8/16/32: CSR lanes per row
+  int sw = 0;  // 0: SELL-32; else CSR with sw lanes per row
+  int sell_lanes = 1;  // SELL-32: lanes per row (1 or 2)
+  // CSR: rows with more than lt entries, taken by one warp each
+  Buf<int32_t> lrows;
+  int64_t nlong = 0, lt = INT64_MAX;
   int64_t n = 0, nnz = 0, nslices = 0;
   Sell<T> sell;
   Buf<int64_t> rp;

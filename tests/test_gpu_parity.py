@@ -190,6 +190,43 @@ def test_vcycle_matches_oracle(sa, orc, gen_mod):
     assert np.linalg.norm(zm - zo) <= 1e-3 * np.linalg.norm(zo)
 
 
+@pytest.mark.parametrize("sig", [(1e2, 1e-2, 1.0), (1e3, 1e-3, 10.0)])
+def test_vcycle_long_row_bin_matches_oracle(sa, orc, gen_mod, sig):
+    """On the 48x48x96 battery stack with these layer conductivities, coarse
+    levels hold rows far longer than the rest (up to 150 and 490 entries
+    against averages near 30-45): they are stored as CSR with a long-row bin
+    (a warp per row).  The V-cycle over them equals the oracle's, and a block
+    solve's columns equal the one-vector solves bitwise."""
+    import torch
+    import scipy.sparse as sp
+    p = gen_mod.battery_3d(48, 48, 96, sig=sig)
+    h = sa.Hierarchy(p, theta=0.05, measure="material")
+    fm = [h.level_format(l) for l in range(h.stats()["levels"])]
+    assert fm[0]["lanes"] == 0 and fm[-1]["lanes"] == -1
+    assert any(f["lanes"] > 0 and f["nlong"] > 0 for f in fm), fm
+    for f in fm:
+        if f["lanes"] > 0:
+            assert f["lanes"] == 4 and f["long_threshold"] in (-1, 64)
+            assert (f["nlong"] > 0) == (f["long_threshold"] == 64)
+    o = orc.Hierarchy(p, 0.05, "material")
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(p["n"])
+    zg = h.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+    zo = o.vcycle(r)
+    assert np.linalg.norm(zg - zo) <= 1e-10 * np.linalg.norm(zo)
+    hm = sa.Hierarchy(p, theta=0.05, measure="material", precision="fp32")
+    zm = hm.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert np.linalg.norm(zm - zo) <= 1e-3 * np.linalg.norm(zo)
+    A = sp.csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(p["n"], p["n"]))
+    b = torch.from_numpy(np.stack([p["b"], A @ rng.standard_normal(p["n"])])).cuda()
+    for hh in (h, hm):
+        X, infos = hh.solve_batch(b)
+        for c in range(2):
+            x1, i1 = hh.solve(b[c].contiguous())
+            assert infos[c]["iters"] == i1["iters"]
+            assert torch.equal(X[c], x1)
+
+
 def test_standalone_strength_worked_example(sa, orc, gen_mod):
     import torch
     for kappa in (1.0, 100.0, 1e4):
