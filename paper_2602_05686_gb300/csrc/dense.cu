@@ -391,139 +391,89 @@ int dense_finish(DenseJob& job) {
   return h_err ? SA_ERR_NOT_SPD : SA_OK;
 }
 
-// y = W b (W lower triangular): warp per row over j <= i
-__global__ void k_trmv_lower(int64_t n, const double* __restrict__ W, const double* __restrict__ b,
-                             double* __restrict__ y) {
-  const int lane = lane_id();
-  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
-    // four row loads in flight per lane (the loop is latency bound otherwise);
-    // the products are added in j order
-    const double* __restrict__ Wi = W + i * n;
-    double s = 0.0;
-    int64_t j = lane;
-    for (; j + 96 <= i; j += 128) {
-      const double w0 = __ldcs(&Wi[j]), w1 = __ldcs(&Wi[j + 32]), w2 = __ldcs(&Wi[j + 64]), w3 = __ldcs(&Wi[j + 96]);
-      s += w0 * b[j];
-      s += w1 * b[j + 32];
-      s += w2 * b[j + 64];
-      s += w3 * b[j + 96];
+// ---------------------------------------------------------------------------
+// Coarse solve x = W^T (W b), W = L^-1 lower triangular (row-major), WT = W^T:
+// y_i = sum_{j <= i} W_ij b_j, then x_j = sum_{i >= j} WT_ji y_i.  One CTA of
+// TRI_WARPS warps per row: warp q takes the q-th of TRI_WARPS consecutive
+// column segments of the row (segments of a multiple of 32 columns; lanes
+// stride the segment with four loads in flight, each lane summing in column
+// order; a shuffle tree adds the lanes), and the warps' sums are added in
+// warp order.  A single warp per row left the longest rows (n entries) a
+// chain of n/128 dependent load rounds.  The K-column forms run the same sums
+// for every column as the one-column form (bitwise equal columns).
+// ---------------------------------------------------------------------------
+constexpr int TRI_WARPS = 4;
+
+template <bool LOWER, int K>
+__global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_row(int64_t n, const double* __restrict__ M,
+                                                            const double* __restrict__ v, double* __restrict__ out) {
+  __shared__ double sh[TRI_WARPS][K];
+  const int64_t i = blockIdx.x;
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  const int64_t lo = LOWER ? 0 : i, hi = LOWER ? i + 1 : n;
+  const int64_t seg = (((hi - lo) + TRI_WARPS - 1) / TRI_WARPS + 31) & ~(int64_t)31;
+  const int64_t b = lo + warp * seg;
+  const int64_t e = b + seg < hi ? b + seg : hi;
+  const double* __restrict__ Mi = M + i * n;
+  double sum[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) sum[c] = 0.0;
+  int64_t j = b + lane;
+  for (; j + 96 < e; j += 128) {
+    const double w0 = __ldcs(&Mi[j]), w1 = __ldcs(&Mi[j + 32]), w2 = __ldcs(&Mi[j + 64]), w3 = __ldcs(&Mi[j + 96]);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      sum[c] += w0 * v[j * K + c];
+      sum[c] += w1 * v[(j + 32) * K + c];
+      sum[c] += w2 * v[(j + 64) * K + c];
+      sum[c] += w3 * v[(j + 96) * K + c];
     }
-    for (; j <= i; j += 32) s += Wi[j] * b[j];
-    s = warp_sum(s);
-    if (lane == 0) y[i] = s;
+  }
+  for (; j < e; j += 32) {
+    const double w = Mi[j];
+#pragma unroll
+    for (int c = 0; c < K; ++c) sum[c] += w * v[j * K + c];
+  }
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    const double t = warp_sum(sum[c]);
+    if (lane == 0) sh[warp][c] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    const int c = (int)threadIdx.x;
+    double t = sh[0][c];
+#pragma unroll
+    for (int q = 1; q < TRI_WARPS; ++q) t += sh[q][c];
+    out[i * K + c] = t;
   }
 }
 
-// x = W^T y: row j of W^T over i >= j
-__global__ void k_trmv_upper(int64_t n, const double* __restrict__ WT, const double* __restrict__ y,
-                             double* __restrict__ x) {
-  const int lane = lane_id();
-  for (int64_t j = global_warp(); j < n; j += warp_stride()) {
-    const double* __restrict__ Wj = WT + j * n;
-    double s = 0.0;
-    int64_t i = j + lane;
-    for (; i + 96 < n; i += 128) {
-      const double w0 = __ldcs(&Wj[i]), w1 = __ldcs(&Wj[i + 32]), w2 = __ldcs(&Wj[i + 64]), w3 = __ldcs(&Wj[i + 96]);
-      s += w0 * y[i];
-      s += w1 * y[i + 32];
-      s += w2 * y[i + 64];
-      s += w3 * y[i + 96];
-    }
-    for (; i < n; i += 32) s += Wj[i] * y[i];
-    s = warp_sum(s);
-    if (lane == 0) x[j] = s;
-  }
-}
-
-// the same two products for k right-hand sides stored interleaved (element
-// (i, c) at i*k + c); every column is summed in the one-vector order
-__global__ void k_btrmv_lower(int64_t n, int k, const double* __restrict__ W, const double* __restrict__ b,
-                              double* __restrict__ y) {
-  const int lane = lane_id();
-  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
-    double s[KMAX_COARSE];
-#pragma unroll
-    for (int c = 0; c < KMAX_COARSE; ++c) s[c] = 0.0;
-    const double* __restrict__ Wi = W + i * n;
-    int64_t j = lane;
-    for (; j + 96 <= i; j += 128) {
-      const double w0 = __ldcs(&Wi[j]), w1 = __ldcs(&Wi[j + 32]), w2 = __ldcs(&Wi[j + 64]), w3 = __ldcs(&Wi[j + 96]);
-#pragma unroll
-      for (int c = 0; c < KMAX_COARSE; ++c)
-        if (c < k) {
-          s[c] += w0 * b[j * k + c];
-          s[c] += w1 * b[(j + 32) * k + c];
-          s[c] += w2 * b[(j + 64) * k + c];
-          s[c] += w3 * b[(j + 96) * k + c];
-        }
-    }
-    for (; j <= i; j += 32) {
-      const double w = Wi[j];
-#pragma unroll
-      for (int c = 0; c < KMAX_COARSE; ++c)
-        if (c < k) s[c] += w * b[j * k + c];
-    }
-#pragma unroll
-    for (int c = 0; c < KMAX_COARSE; ++c) {
-      const double t = warp_sum(s[c]);
-      if (lane == 0 && c < k) y[i * k + c] = t;
-    }
-  }
-}
-
-__global__ void k_btrmv_upper(int64_t n, int k, const double* __restrict__ WT, const double* __restrict__ y,
-                              double* __restrict__ x) {
-  const int lane = lane_id();
-  for (int64_t j = global_warp(); j < n; j += warp_stride()) {
-    double s[KMAX_COARSE];
-#pragma unroll
-    for (int c = 0; c < KMAX_COARSE; ++c) s[c] = 0.0;
-    const double* __restrict__ Wj = WT + j * n;
-    int64_t i = j + lane;
-    for (; i + 96 < n; i += 128) {
-      const double w0 = __ldcs(&Wj[i]), w1 = __ldcs(&Wj[i + 32]), w2 = __ldcs(&Wj[i + 64]), w3 = __ldcs(&Wj[i + 96]);
-#pragma unroll
-      for (int c = 0; c < KMAX_COARSE; ++c)
-        if (c < k) {
-          s[c] += w0 * y[i * k + c];
-          s[c] += w1 * y[(i + 32) * k + c];
-          s[c] += w2 * y[(i + 64) * k + c];
-          s[c] += w3 * y[(i + 96) * k + c];
-        }
-    }
-    for (; i < n; i += 32) {
-      const double w = Wj[i];
-#pragma unroll
-      for (int c = 0; c < KMAX_COARSE; ++c)
-        if (c < k) s[c] += w * y[i * k + c];
-    }
-#pragma unroll
-    for (int c = 0; c < KMAX_COARSE; ++c) {
-      const double t = warp_sum(s[c]);
-      if (lane == 0 && c < k) x[j * k + c] = t;
-    }
-  }
+template <int K>
+static int coarse_solve_k(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
+                          double* x) {
+  k_tri_row<true, K><<<(unsigned)n, TRI_WARPS * 32, 0, st>>>(n, W, b, y);
+  SA_LAUNCHED();
+  k_tri_row<false, K><<<(unsigned)n, TRI_WARPS * 32, 0, st>>>(n, WT, y, x);
+  SA_LAUNCHED();
+  return SA_OK;
 }
 
 int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
                         double* x) {
   if (n <= 0) return SA_OK;
-  k_trmv_lower<<<warp_rows_grid(n), 256, 0, st>>>(n, W, b, y);
-  SA_LAUNCHED();
-  k_trmv_upper<<<warp_rows_grid(n), 256, 0, st>>>(n, WT, y, x);
-  SA_LAUNCHED();
-  return SA_OK;
+  return coarse_solve_k<1>(st, n, W, WT, b, y, x);
 }
 
 int launch_coarse_solve_block(cudaStream_t st, int64_t n, int k, const double* W, const double* WT, const double* b,
                               double* y, double* x) {
   if (n <= 0) return SA_OK;
-  if (k < 1 || k > KMAX_COARSE) return SA_ERR_INVALID_ARG;
-  k_btrmv_lower<<<warp_rows_grid(n), 256, 0, st>>>(n, k, W, b, y);
-  SA_LAUNCHED();
-  k_btrmv_upper<<<warp_rows_grid(n), 256, 0, st>>>(n, k, WT, y, x);
-  SA_LAUNCHED();
-  return SA_OK;
+  switch (k) {
+    case 2: return coarse_solve_k<2>(st, n, W, WT, b, y, x);
+    case 4: return coarse_solve_k<4>(st, n, W, WT, b, y, x);
+    case 8: return coarse_solve_k<8>(st, n, W, WT, b, y, x);
+    default: return SA_ERR_INVALID_ARG;
+  }
 }
 
 }  // namespace sa

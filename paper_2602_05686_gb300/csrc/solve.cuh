@@ -16,7 +16,6 @@ struct CsrView {
 // right-hand sides one multi-vector solve carries (interleaved storage:
 // element (i, c) of an n x k block at i*k + c)
 constexpr int KMAX_BLOCK = 8;
-constexpr int KMAX_COARSE = KMAX_BLOCK;
 
 struct CgScalars {
   double rz, pq, alpha, beta;
@@ -69,6 +68,8 @@ struct DenseJob {
 int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, Buf<double>& W,
                 Buf<double>& WT, DenseJob& job);
 int dense_finish(DenseJob& job);
+// x = W^T (W b) (y: workspace for W b); the block form takes k in {2, 4, 8}
+// interleaved columns
 int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
                         double* x);
 int launch_coarse_solve_block(cudaStream_t st, int64_t n, int k, const double* W, const double* WT, const double* b,
