@@ -266,6 +266,7 @@ static int block_alloc(Alloc& al, VHier<T>* m) {
   }
   const int64_t nL = m->lev[nl - 1]->n;
   SA_TRY(m->kct.alloc(&al, nL * KMAX_BLOCK));
+  SA_TRY(m->kcs.alloc(&al, nL * KMAX_BLOCK));
   SA_TRY(m->kcy.alloc(&al, nL * KMAX_BLOCK));
   SA_TRY(m->kcx.alloc(&al, nL * KMAX_BLOCK));
   SA_TRY(m->kz.alloc(&al, m->lev[0]->n * KMAX_BLOCK));
@@ -282,7 +283,7 @@ static int mv_block(VHier<T>* m, cudaStream_t st, int l, int K, const double* r6
   if (l == nl - 1) {
     k_bcoarse_in<T><<<g256(nk), 256, 0, st>>>(n, K, L->kb.p, L->sq.p, m->kct.p);
     SA_LAUNCHED();
-    SA_TRY(launch_coarse_solve_block(st, n, K, m->W, m->WT, m->kct.p, m->kcy.p, m->kcx.p));
+    SA_TRY(launch_coarse_solve_block(st, m->cf, K, m->kct.p, m->kcs.p, m->kcy.p, m->kcx.p));
     k_bcoarse_out<T><<<g256(nk), 256, 0, st>>>(n, K, m->kcx.p, L->sq.p, L->kx.p);
     SA_LAUNCHED();
     *xo = L->kx.p;
@@ -338,7 +339,7 @@ int vh_vcycle_block(Alloc& al, VHier<T>* m, cudaStream_t st, int K, const double
   SA_TRY(block_alloc(al, m));
   if (m->lev.size() == 1) {
     const int64_t n = m->lev[0]->n;
-    SA_TRY(launch_coarse_solve_block(st, n, K, m->W, m->WT, R, m->kcy.p, m->kz.p));
+    SA_TRY(launch_coarse_solve_block(st, m->cf, K, R, m->kcs.p, m->kcy.p, m->kz.p));
     *Z = m->kz.p;
     return SA_OK;
   }

@@ -173,12 +173,13 @@ __global__ void k_syrk_update(int64_t n, double* __restrict__ M, int k, int firs
   tile_gemm_nt_sub(n, M, oi, oj, bi, bj, M, oi, ok, M, oj, ok, bk, n, n);
 }
 
-// W_ij <- L_ii^-1 W_ij for block columns j <= i, a tile product with the
-// stored L_ii^-1 (one CTA of 256 threads per j, 4 outputs per thread)
-__global__ void k_trsm_lower_left(int64_t n, const double* __restrict__ Dinv, double* __restrict__ W, int i) {
+// W_ij <- L_ii^-1 W_ij for block columns j0 <= j <= i, a tile product with
+// the stored L_ii^-1 (one CTA of 256 threads per j, 4 outputs per thread)
+__global__ void k_trsm_lower_left(int64_t n, const double* __restrict__ Dinv, double* __restrict__ W, int i,
+                                  int j0) {
   __shared__ double Li[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
-  const int j = blockIdx.x;
+  const int j = j0 + (int)blockIdx.x;
   const int64_t oi = (int64_t)i * NB, oj = (int64_t)j * NB;
   const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
   const int bj = (int)((n - oj) < NB ? (n - oj) : NB);
@@ -205,11 +206,12 @@ __global__ void k_trsm_lower_left(int64_t n, const double* __restrict__ Dinv, do
   }
 }
 
-// W_mj -= L_mi W_ij for block rows m >= m0 (m0 > i), j <= i
+// W_mj -= L_mi W_ij for block rows m >= m0 (m0 > i), block columns
+// j0 <= j < j0 + ncolb (j <= i)
 __global__ void k_gemm_left(int64_t n, const double* __restrict__ L, double* __restrict__ W, int i, int ncolb,
-                            int m0) {
-  const int m = m0 + blockIdx.x / ncolb;
-  const int j = blockIdx.x % ncolb;
+                            int m0, int j0) {
+  const int m = m0 + (int)blockIdx.x / ncolb;
+  const int j = j0 + (int)blockIdx.x % ncolb;
   const int64_t om = (int64_t)m * NB, oi = (int64_t)i * NB, oj = (int64_t)j * NB;
   const int bm = (int)((n - om) < NB ? (n - om) : NB);
   const int bi = (int)((n - oi) < NB ? (n - oi) : NB);
@@ -264,31 +266,33 @@ DenseJob::~DenseJob() {
   if (sd) cudaStreamDestroy(sd);
 }
 
-int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, Buf<double>& W,
-                Buf<double>& WT, DenseJob& job) {
+int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, CoarseFactor& F,
+                DenseJob& job) {
   cudaStream_t s = al.stream;
   job.main = s;
   job.n = n;
   if (n <= 0) return SA_OK;
-  SA_TRY(job.M.alloc(&al, n * n));
-  SA_TRY(W.alloc(&al, n * n));
-  SA_TRY(WT.alloc(&al, n * n));
+  SA_TRY(F.L.alloc(&al, n * n));
+  SA_TRY(F.LT.alloc(&al, n * n));
+  SA_TRY(F.W.alloc(&al, n * n));
+  SA_TRY(F.WT.alloc(&al, n * n));
   SA_TRY(job.err.alloc(&al, 1));
-  SA_TRY(memset_d(job.M.p, 0, job.M.bytes(), s));
+  SA_TRY(memset_d(F.L.p, 0, F.L.bytes(), s));
   SA_TRY(memset_d(job.err.p, 0, sizeof(int), s));
-  k_densify<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, v, job.M.p);
+  k_densify<<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, v, F.L.p);
   SA_LAUNCHED();
   const int nb = (int)((n + NB - 1) / NB);
   SA_TRY(job.Dinv.alloc(&al, (int64_t)nb * NB * NB));
   // The factor runs on its own stream `sd`, forked from the caller's stream
   // after the dense copy; the caller goes on with work that does not read
-  // W (Chebyshev bounds, SELL packing) and joins in dense_finish.  Within
-  // it, look-ahead on a second stream: after panel k, `sd` updates only
-  // block column k+1 and goes on to factor panel k+1, while `s2` updates
-  // the rest of the trailing matrix (columns >= k+2); `sd` waits for that
-  // before it updates column k+2.  The same for the inverse: row i+1 on `sd`,
-  // rows >= i+2 on `s2`.  Without the extra streams everything runs on the
-  // caller's stream in the same order.
+  // the factor (Chebyshev bounds, SELL packing) and joins in dense_finish.
+  // Within it, look-ahead on a second stream: after panel k, `sd` updates
+  // only block column k+1 and goes on to factor panel k+1, while `s2`
+  // updates the rest of the trailing matrix (columns >= k+2); `sd` waits for
+  // that before it updates column k+2.  The same for the diagonal-block
+  // inverses: row i+1 on `sd`, rows >= i+2 of the same diagonal block on
+  // `s2`.  Without the extra streams everything runs on the caller's stream
+  // in the same order.
   bool own = cudaStreamCreateWithFlags(&job.sd, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&job.e_fork, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&job.e_done, cudaEventDisableTiming) == cudaSuccess;
@@ -304,7 +308,7 @@ int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, cons
   }
   job.pending = own;
   cudaStream_t s2 = job.s2;
-  double* M = job.M.p;
+  double* M = F.L.p;
   double* D = job.Dinv.p;
   const int ph = prof_begin(m, PK_S_DENSE, job.level, 0.0);
   bool side_pending = false;
@@ -337,27 +341,32 @@ int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, cons
     SA_LAUNCHED();
   }
   if (la && side_pending) SA_CUDA(cudaStreamWaitEvent(m, job.e_side, 0));
-  // W = L^-1 block row by block row.  A pivot that was not positive is
+  // W_KK = L_KK^-1 for the diagonal blocks of COARSE_BS rows, block row by
+  // block row (NB rows) inside each.  A pivot that was not positive is
   // recorded in err and replaced by 1, so the inverse is computed on finite
   // data either way; dense_finish reports it.  The strict upper triangle of
-  // M outside the diagonal tiles still holds A: W reads only the lower
-  // triangle of L, so it is left as is.
-  k_set_identity<<<blocks_for(n * n, 256), 256, 0, m>>>(n, W.p);
+  // L outside the NB x NB diagonal tiles still holds A: the solve reads
+  // only the lower triangle of L and the diagonal blocks of W.
+  k_set_identity<<<blocks_for(n * n, 256), 256, 0, m>>>(n, F.W.p);
   count_launch();
   side_pending = false;
+  constexpr int BB = (int)(COARSE_BS / NB);  // NB-blocks per diagonal block
   for (int i = 0; i < nb; ++i) {
-    k_trsm_lower_left<<<i + 1, 256, 0, m>>>(n, D, W.p, i);
+    const int j0 = (i / BB) * BB;                   // first NB-block column of this diagonal block
+    const int e = j0 + BB < nb ? j0 + BB : nb;      // end of its NB-block rows
+    const int ncolb = i + 1 - j0;
+    k_trsm_lower_left<<<(unsigned)ncolb, 256, 0, m>>>(n, D, F.W.p, i, j0);
     count_launch();
-    const int r = nb - i - 1;
+    const int r = e - i - 1;
     if (r > 0) {
       if (la) {
         if (side_pending) SA_CUDA(cudaStreamWaitEvent(m, job.e_side, 0));
-        k_gemm_left<<<(unsigned)(i + 1), 256, 0, m>>>(n, M, W.p, i, i + 1, i + 1);
+        k_gemm_left<<<(unsigned)ncolb, 256, 0, m>>>(n, M, F.W.p, i, ncolb, i + 1, j0);
         count_launch();
         if (r > 1) {
           SA_CUDA(cudaEventRecord(job.e_main, m));
           SA_CUDA(cudaStreamWaitEvent(s2, job.e_main, 0));
-          k_gemm_left<<<(unsigned)((r - 1) * (i + 1)), 256, 0, s2>>>(n, M, W.p, i, i + 1, i + 2);
+          k_gemm_left<<<(unsigned)((r - 1) * ncolb), 256, 0, s2>>>(n, M, F.W.p, i, ncolb, i + 2, j0);
           count_launch();
           SA_CUDA(cudaEventRecord(job.e_side, s2));
           side_pending = true;
@@ -365,7 +374,7 @@ int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, cons
           side_pending = false;
         }
       } else {
-        k_gemm_left<<<(unsigned)(r * (i + 1)), 256, 0, m>>>(n, M, W.p, i, i + 1, i + 1);
+        k_gemm_left<<<(unsigned)(r * ncolb), 256, 0, m>>>(n, M, F.W.p, i, ncolb, i + 1, j0);
         count_launch();
       }
     }
@@ -373,7 +382,9 @@ int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, cons
   }
   if (la && side_pending) SA_CUDA(cudaStreamWaitEvent(m, job.e_side, 0));
   dim3 tb(32, 8), tg((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
-  k_transpose_dense<<<tg, tb, 0, m>>>(n, W.p, WT.p);
+  k_transpose_dense<<<tg, tb, 0, m>>>(n, F.W.p, F.WT.p);
+  SA_LAUNCHED();
+  k_transpose_dense<<<tg, tb, 0, m>>>(n, F.L.p, F.LT.p);
   SA_LAUNCHED();
   prof_end(m, ph);
   if (own) SA_CUDA(cudaEventRecord(job.e_done, m));
@@ -392,25 +403,33 @@ int dense_finish(DenseJob& job) {
 }
 
 // ---------------------------------------------------------------------------
-// Coarse solve x = W^T (W b), W = L^-1 lower triangular (row-major), WT = W^T:
-// y_i = sum_{j <= i} W_ij b_j, then x_j = sum_{i >= j} WT_ji y_i.  One CTA of
-// TRI_WARPS warps per row: warp q takes the q-th of TRI_WARPS consecutive
-// column segments of the row (segments of a multiple of 32 columns; lanes
-// stride the segment with four loads in flight, each lane summing in column
-// order; a shuffle tree adds the lanes), and the warps' sums are added in
-// warp order.  A single warp per row left the longest rows (n entries) a
-// chain of n/128 dependent load rounds.  The K-column forms run the same sums
-// for every column as the one-column form (bitwise equal columns).
+// Coarse solve x = A_c^-1 b = L^-T (L^-1 b) by substitution over the diagonal
+// blocks K (rows [r0, r1) of COARSE_BS):
+//   forward   t_K = b_K - L_{K,<K} y_{<K};  y_K = W_KK t_K   (W_KK = L_KK^-1)
+//   backward  t_K = y_K - (L^T)_{K,>K} x_{>K};  x_K = W_KK^T t_K
+// Each step is a row-parallel product over one row range: one CTA of
+// TRI_WARPS warps per row, warp q taking the q-th of TRI_WARPS consecutive
+// column segments of the row's range (segments of a multiple of 32 columns;
+// lanes stride the segment with four loads in flight, each lane summing in
+// column order; a shuffle tree adds the lanes), the warps' sums added in warp
+// order.  MODE: 0 sum over [r0, i] (lower triangle of a diagonal block),
+// 1 over [i, r1) (upper), 2 rhs_i minus the sum over [0, r0), 3 rhs_i minus
+// the sum over [r1, n).  The K-column forms run the same sums for every
+// column as the one-column form (bitwise equal columns).
 // ---------------------------------------------------------------------------
 constexpr int TRI_WARPS = 4;
 
-template <bool LOWER, int K>
-__global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_row(int64_t n, const double* __restrict__ M,
-                                                            const double* __restrict__ v, double* __restrict__ out) {
+template <int MODE, int K>
+__global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_row(int64_t n, int64_t r0, int64_t r1,
+                                                            const double* __restrict__ M,
+                                                            const double* __restrict__ v,
+                                                            const double* __restrict__ rhs,
+                                                            double* __restrict__ out) {
   __shared__ double sh[TRI_WARPS][K];
-  const int64_t i = blockIdx.x;
+  const int64_t i = r0 + blockIdx.x;
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-  const int64_t lo = LOWER ? 0 : i, hi = LOWER ? i + 1 : n;
+  const int64_t lo = MODE == 0 ? r0 : (MODE == 1 ? i : (MODE == 2 ? 0 : r1));
+  const int64_t hi = MODE == 0 ? i + 1 : (MODE == 1 ? r1 : (MODE == 2 ? r0 : n));
   const int64_t seg = (((hi - lo) + TRI_WARPS - 1) / TRI_WARPS + 31) & ~(int64_t)31;
   const int64_t b = lo + warp * seg;
   const int64_t e = b + seg < hi ? b + seg : hi;
@@ -445,33 +464,50 @@ __global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_row(int64_t n, const dou
     double t = sh[0][c];
 #pragma unroll
     for (int q = 1; q < TRI_WARPS; ++q) t += sh[q][c];
-    out[i * K + c] = t;
+    out[i * K + c] = MODE >= 2 ? rhs[i * K + c] - t : t;
   }
 }
 
 template <int K>
-static int coarse_solve_k(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
-                          double* x) {
-  k_tri_row<true, K><<<(unsigned)n, TRI_WARPS * 32, 0, st>>>(n, W, b, y);
-  SA_LAUNCHED();
-  k_tri_row<false, K><<<(unsigned)n, TRI_WARPS * 32, 0, st>>>(n, WT, y, x);
-  SA_LAUNCHED();
+static int coarse_solve_k(cudaStream_t st, const CoarseView& F, const double* b, double* t, double* y, double* x) {
+  const int64_t n = F.n;
+  const int nbk = (int)((n + COARSE_BS - 1) / COARSE_BS);
+  const unsigned T = TRI_WARPS * 32;
+  for (int q = 0; q < nbk; ++q) {
+    const int64_t r0 = q * COARSE_BS, r1 = r0 + COARSE_BS < n ? r0 + COARSE_BS : n;
+    const unsigned g = (unsigned)(r1 - r0);
+    if (q > 0) {
+      k_tri_row<2, K><<<g, T, 0, st>>>(n, r0, r1, F.L, y, b, t);
+      SA_LAUNCHED();
+    }
+    k_tri_row<0, K><<<g, T, 0, st>>>(n, r0, r1, F.W, q > 0 ? t : b, nullptr, y);
+    SA_LAUNCHED();
+  }
+  for (int q = nbk - 1; q >= 0; --q) {
+    const int64_t r0 = q * COARSE_BS, r1 = r0 + COARSE_BS < n ? r0 + COARSE_BS : n;
+    const unsigned g = (unsigned)(r1 - r0);
+    if (q < nbk - 1) {
+      k_tri_row<3, K><<<g, T, 0, st>>>(n, r0, r1, F.LT, x, y, t);
+      SA_LAUNCHED();
+    }
+    k_tri_row<1, K><<<g, T, 0, st>>>(n, r0, r1, F.WT, q < nbk - 1 ? t : y, nullptr, x);
+    SA_LAUNCHED();
+  }
   return SA_OK;
 }
 
-int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
-                        double* x) {
-  if (n <= 0) return SA_OK;
-  return coarse_solve_k<1>(st, n, W, WT, b, y, x);
+int launch_coarse_solve(cudaStream_t st, const CoarseView& F, const double* b, double* t, double* y, double* x) {
+  if (F.n <= 0) return SA_OK;
+  return coarse_solve_k<1>(st, F, b, t, y, x);
 }
 
-int launch_coarse_solve_block(cudaStream_t st, int64_t n, int k, const double* W, const double* WT, const double* b,
-                              double* y, double* x) {
-  if (n <= 0) return SA_OK;
+int launch_coarse_solve_block(cudaStream_t st, const CoarseView& F, int k, const double* b, double* t, double* y,
+                              double* x) {
+  if (F.n <= 0) return SA_OK;
   switch (k) {
-    case 2: return coarse_solve_k<2>(st, n, W, WT, b, y, x);
-    case 4: return coarse_solve_k<4>(st, n, W, WT, b, y, x);
-    case 8: return coarse_solve_k<8>(st, n, W, WT, b, y, x);
+    case 2: return coarse_solve_k<2>(st, F, b, t, y, x);
+    case 4: return coarse_solve_k<4>(st, F, b, t, y, x);
+    case 8: return coarse_solve_k<8>(st, F, b, t, y, x);
     default: return SA_ERR_INVALID_ARG;
   }
 }

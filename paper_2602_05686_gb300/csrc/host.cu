@@ -50,7 +50,7 @@ struct sa_handle_s {
   int dim = 0;
   int64_t n = 0;
   std::vector<std::unique_ptr<sa::Level>> lev;
-  sa::Buf<double> W, WT;
+  sa::CoarseFactor cf;  // coarse Cholesky factor and diagonal-block inverses
   int64_t nL = 0;
   sa::Sell<double> A0s;  // fine operator (unscaled) for the outer CG
   // Krylov workspace (FP64, fine level)
@@ -738,7 +738,8 @@ static std::vector<VLevelIn> vlevel_inputs(sa_handle h) {
 static int build_mixed(sa_handle h) {
   if (h->v32) return SA_OK;
   std::vector<VLevelIn> in = vlevel_inputs(h);
-  return vh_build<float>(h->al, in.data(), (int)in.size(), h->opt.cheb_degree, h->W.p, h->WT.p, &h->v32);
+  return vh_build<float>(h->al, in.data(), (int)in.size(), h->opt.cheb_degree, sa::coarse_view(h->cf, h->nL),
+                         &h->v32);
 }
 
 static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
@@ -824,7 +825,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   // (the packing stores the addresses of W and WT, not their contents)
   DenseJob dj;
   dj.level = nlev - 1;
-  SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT, dj));
+  SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->cf, dj));
   // a15: smoother data (Chebyshev bounds from 10 power steps on D^-1/2 A D^-1/2)
   for (int l = 0; l < nlev; ++l) {
     PHASE_BEGIN(PK_S_CHEB, l);
@@ -850,7 +851,7 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
     Level& L0 = *h->lev[0];
     SA_TRY(build_sell<double>(al, L0.n, L0.nnz, L0.rp.p, L0.ci.p, L0.v.p, nullptr, nullptr, h->A0s));
     std::vector<VLevelIn> in = vlevel_inputs(h);
-    SA_TRY(vh_build<double>(al, in.data(), nlev, o->cheb_degree, h->W.p, h->WT.p, &h->v64));
+    SA_TRY(vh_build<double>(al, in.data(), nlev, o->cheb_degree, coarse_view(h->cf, h->nL), &h->v64));
   }
   PHASE_END(PK_S_SELL);
   if (o->precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
@@ -1176,12 +1177,12 @@ static int finish_loaded(sa_handle h) {
   // addresses of W and WT, not their contents)
   DenseJob dj;
   dj.level = nlev - 1;
-  SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->W, h->WT, dj));
+  SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->cf, dj));
   SA_TRY(alloc_workspace(h));
   Level& L0 = *h->lev[0];
   SA_TRY(build_sell<double>(al, L0.n, L0.nnz, L0.rp.p, L0.ci.p, L0.v.p, nullptr, nullptr, h->A0s));
   std::vector<VLevelIn> in = vlevel_inputs(h);
-  SA_TRY(vh_build<double>(al, in.data(), nlev, h->opt.cheb_degree, h->W.p, h->WT.p, &h->v64));
+  SA_TRY(vh_build<double>(al, in.data(), nlev, h->opt.cheb_degree, coarse_view(h->cf, h->nL), &h->v64));
   if (h->opt.precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
   return dense_finish(dj);
 }
@@ -1385,8 +1386,10 @@ int sa_free(sa_handle h) {
   h->A0s.ci.release();
   h->A0s.v.release();
   h->lev.clear();
-  h->W.release();
-  h->WT.release();
+  h->cf.L.release();
+  h->cf.LT.release();
+  h->cf.W.release();
+  h->cf.WT.release();
   h->r.release(); h->p.release(); h->q.release(); h->rprev.release(); h->t.release();
   h->part.release(); h->dots.release(); h->xb.release(); h->bb.release(); h->cg.release();
   h->it_dev.release(); h->ctl.release();

@@ -47,13 +47,38 @@ int launch_bcg_pupdate(cudaStream_t st, int64_t n, int k, const CgScalars* s, co
 // column-major n x k <-> interleaved n x K (K >= k; columns k..K-1 zero)
 int launch_interleave(cudaStream_t st, int64_t n, int k, int K, const double* src, double* dst, int to_interleaved);
 
-// dense coarse level (dense.cu): Cholesky factor L of the coarse matrix and
-// W = L^-1 (WT its transpose).  dense_start enqueues the whole factorisation
-// on streams of its own, forked from al.stream after the dense copy of A;
-// dense_finish makes al.stream wait for it and reports a pivot that was not
-// positive (SA_ERR_NOT_SPD).  Work on al.stream in between must not read W.
+// dense coarse level (dense.cu).  The coarse matrix A_c = L L^T (Cholesky)
+// is solved by block substitution over diagonal blocks of COARSE_BS rows:
+// L (row-major, lower triangle), LT = L^T, W = the inverses of the diagonal
+// blocks L_KK (stored at their place in an n x n array; the rest unused) and
+// WT = W^T.  Only the diagonal blocks are inverted (n COARSE_BS^2 / 3 flops
+// instead of n^3 / 3 for the whole inverse).
+constexpr int64_t COARSE_BS = 1024;
+
+struct CoarseFactor {
+  Buf<double> L, LT, W, WT;
+};
+
+struct CoarseView {
+  int64_t n = 0;
+  const double* L = nullptr;
+  const double* LT = nullptr;
+  const double* W = nullptr;
+  const double* WT = nullptr;
+};
+
+inline CoarseView coarse_view(const CoarseFactor& F, int64_t n) {
+  CoarseView v;
+  v.n = n; v.L = F.L.p; v.LT = F.LT.p; v.W = F.W.p; v.WT = F.WT.p;
+  return v;
+}
+
+// dense_start enqueues the whole factorisation on streams of its own, forked
+// from al.stream after the dense copy of A; dense_finish makes al.stream wait
+// for it and reports a pivot that was not positive (SA_ERR_NOT_SPD).  Work on
+// al.stream in between must not read the factor.
 struct DenseJob {
-  Buf<double> M, Dinv;
+  Buf<double> Dinv;
   Buf<int> err;
   cudaStream_t main = nullptr, sd = nullptr, s2 = nullptr;
   cudaEvent_t e_fork = nullptr, e_done = nullptr, e_main = nullptr, e_side = nullptr;
@@ -65,14 +90,13 @@ struct DenseJob {
   DenseJob& operator=(const DenseJob&) = delete;
   ~DenseJob();
 };
-int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, Buf<double>& W,
-                Buf<double>& WT, DenseJob& job);
+int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, CoarseFactor& F,
+                DenseJob& job);
 int dense_finish(DenseJob& job);
-// x = W^T (W b) (y: workspace for W b); the block form takes k in {2, 4, 8}
-// interleaved columns
-int launch_coarse_solve(cudaStream_t st, int64_t n, const double* W, const double* WT, const double* b, double* y,
-                        double* x);
-int launch_coarse_solve_block(cudaStream_t st, int64_t n, int k, const double* W, const double* WT, const double* b,
-                              double* y, double* x);
+// x = A_c^-1 b = L^-T (L^-1 b); t and y: n-vector workspaces (t may not
+// alias b, y or x).  The block form takes k in {2, 4, 8} interleaved columns.
+int launch_coarse_solve(cudaStream_t st, const CoarseView& F, const double* b, double* t, double* y, double* x);
+int launch_coarse_solve_block(cudaStream_t st, const CoarseView& F, int k, const double* b, double* t, double* y,
+                              double* x);
 
 }  // namespace sa

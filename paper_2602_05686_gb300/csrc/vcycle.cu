@@ -252,13 +252,12 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
 }
 
 template <typename T>
-int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const double* W, const double* WT,
+int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const CoarseView& cf,
              VHier<T>** out) {
   VHier<T>* m = new VHier<T>();
   *out = m;
   m->deg = cheb_degree;
-  m->W = W;
-  m->WT = WT;
+  m->cf = cf;
   cudaStream_t s = al.stream;
   // D_l^-1/2 and D_l^1/2 of every level, once (FP64 square roots are costly)
   std::vector<Buf<double>> isq(nlev), sq(nlev);
@@ -291,6 +290,7 @@ int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const dou
     } else {
       L->sq = std::move(sq[l]);
       SA_TRY(m->ct.alloc(&al, I.n));
+      SA_TRY(m->cs.alloc(&al, I.n));
       SA_TRY(m->cy.alloc(&al, I.n));
       SA_TRY(m->cx.alloc(&al, I.n));
     }
@@ -303,8 +303,8 @@ int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const dou
   return SA_OK;
 }
 
-template int vh_build<double>(Alloc&, const VLevelIn*, int, int, const double*, const double*, VHier<double>**);
-template int vh_build<float>(Alloc&, const VLevelIn*, int, int, const double*, const double*, VHier<float>**);
+template int vh_build<double>(Alloc&, const VLevelIn*, int, int, const CoarseView&, VHier<double>**);
+template int vh_build<float>(Alloc&, const VLevelIn*, int, int, const CoarseView&, VHier<float>**);
 
 // ---------------------------------------------------------------------------
 // kernels (one thread per row)
@@ -443,7 +443,7 @@ static int mv(VHier<T>* m, cudaStream_t st, int l, const double* r64, T** xo) {
     int pi = prof_begin(st, PK_COARSE, l, 8.0 * n * n + 48.0 * n);
     k_coarse_in<T><<<g256(n), 256, 0, st>>>(n, L->b.p, L->sq.p, m->ct.p);
     SA_LAUNCHED();
-    SA_TRY(launch_coarse_solve(st, n, m->W, m->WT, m->ct.p, m->cy.p, m->cx.p));
+    SA_TRY(launch_coarse_solve(st, m->cf, m->ct.p, m->cs.p, m->cy.p, m->cx.p));
     k_coarse_out<T><<<g256(n), 256, 0, st>>>(n, m->cx.p, L->sq.p, L->x.p);
     prof_end(st, pi);
     SA_LAUNCHED();
@@ -508,7 +508,7 @@ int vh_vcycle(VHier<T>* m, cudaStream_t st, const double* r, double** z) {
     // one level: the dense solve on r directly
     const int64_t n = m->lev[0]->n;
     int pi = prof_begin(st, PK_COARSE, 0, 8.0 * n * n + 32.0 * n);
-    int s = launch_coarse_solve(st, n, m->W, m->WT, r, m->cy.p, m->z.p);
+    int s = launch_coarse_solve(st, m->cf, r, m->cs.p, m->cy.p, m->z.p);
     prof_end(st, pi);
     SA_TRY(s);
     *z = m->z.p;

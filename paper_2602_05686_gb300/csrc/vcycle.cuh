@@ -72,11 +72,10 @@ struct VHier {
   std::vector<VLevel<T>*> lev;
   Buf<double> s0;  // fine-level D^-1/2
   Buf<double> z;   // FP64 output of the cycle
-  Buf<double> ct, cy, cx;
-  const double* W = nullptr;
-  const double* WT = nullptr;
-  int kready = 0;                  // k-column buffers allocated
-  Buf<double> kz, kct, kcy, kcx;   // k-column output and coarse vectors
+  Buf<double> ct, cs, cy, cx;       // coarse right-hand side and solve vectors
+  CoarseView cf;                    // coarse factor
+  int kready = 0;                   // k-column buffers allocated
+  Buf<double> kz, kct, kcs, kcy, kcx;   // k-column output and coarse vectors
 };
 
 // SELL-32 copy with values left_i * a_ij * right_j (scale vectors may be NULL = 1)
@@ -84,7 +83,7 @@ template <typename T>
 int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
                const double* left, const double* right, Sell<T>& S);
 template <typename T>
-int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const double* W, const double* WT,
+int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const CoarseView& cf,
              VHier<T>** out);
 // z = D^-1/2 V~(D^-1/2 r); *z points to hierarchy-owned FP64 memory
 template <typename T>

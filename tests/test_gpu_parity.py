@@ -253,6 +253,32 @@ def test_single_level_is_a_direct_solve(sa, gen_mod):
     assert info["status"] == 0 and info["iters"] <= 2 and info["rel_res"] <= 1e-8
 
 
+@pytest.mark.parametrize("n_el", [31, 48])
+def test_coarse_block_substitution_is_a_direct_solve(sa, gen_mod, n_el):
+    """A one-level hierarchy is the coarse direct solve alone: 1024 rows (one
+    diagonal block, the whole inverse) and 2401 rows (three diagonal blocks,
+    the last one ragged).  Its V-cycle equals a sparse direct solve, and a
+    block solve's columns equal the one-vector solves bitwise."""
+    import torch
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    p = gen_mod.layered_2d(n_el, contrast=1e-2)
+    h = sa.Hierarchy(p, theta=0.08, measure="material", max_coarse=5000)
+    assert h.stats()["levels"] == 1 and h.level_format(0)["lanes"] == -1
+    A = sp.csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(p["n"], p["n"]))
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(p["n"])
+    z = h.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+    ze = spla.spsolve(A.tocsc(), r)
+    assert np.linalg.norm(z - ze) <= 1e-9 * np.linalg.norm(ze)
+    b = torch.from_numpy(np.stack([r, A @ rng.standard_normal(p["n"])])).cuda()
+    X, infos = h.solve_batch(b)
+    for c in range(2):
+        x1, i1 = h.solve(b[c].contiguous())
+        assert infos[c]["iters"] == i1["iters"] <= 2
+        assert torch.equal(X[c], x1)
+
+
 def test_host_pointer_path_matches_device_path(sa, gen_mod):
     import torch
     p = gen_mod.battery_3d(12, 12, 24)
