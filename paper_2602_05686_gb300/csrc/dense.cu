@@ -293,10 +293,19 @@ int dense_start(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, cons
   // inverses: row i+1 on `sd`, rows >= i+2 of the same diagonal block on
   // `s2`.  Without the extra streams everything runs on the caller's stream
   // in the same order.
-  bool own = cudaStreamCreateWithFlags(&job.sd, cudaStreamNonBlocking) == cudaSuccess &&
+  // Both streams get the highest priority: the factor is the setup's
+  // critical path (a chain of small panel launches), the work it overlaps
+  // has slack, and the block scheduler then hands free SM slots to the
+  // factor first.
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+    cudaGetLastError();
+    prio_hi = 0;
+  }
+  bool own = cudaStreamCreateWithPriority(&job.sd, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
              cudaEventCreateWithFlags(&job.e_fork, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&job.e_done, cudaEventDisableTiming) == cudaSuccess;
-  bool la = own && cudaStreamCreateWithFlags(&job.s2, cudaStreamNonBlocking) == cudaSuccess &&
+  bool la = own && cudaStreamCreateWithPriority(&job.s2, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
             cudaEventCreateWithFlags(&job.e_main, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&job.e_side, cudaEventDisableTiming) == cudaSuccess;
   if (!la) cudaGetLastError();
