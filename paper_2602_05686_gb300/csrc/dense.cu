@@ -53,10 +53,17 @@ __global__ void k_potrf_diag(int64_t n, double* __restrict__ M, int k, int* __re
     const double ri = rinv[j];
     for (int r = j + 1 + threadIdx.x; r < bs; r += blockDim.x) T[r][j] *= ri;
     __syncthreads();
-    const int m = bs - j - 1;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-      int r = j + 1 + t / m, c = j + 1 + t % m;
-      if (c <= r) T[r][c] -= T[r][j] * T[c][j];
+    // thread (warp w, lane r) owns T[r][w + 8q], q = 0..3 (256 threads)
+    {
+      const int r = (int)(threadIdx.x & 31), w = (int)(threadIdx.x >> 5);
+      if (r > j && r < bs) {
+        const double lrj = T[r][j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = w + 8 * q;
+          if (c > j && c <= r) T[r][c] -= lrj * T[c][j];
+        }
+      }
     }
     __syncthreads();
   }
