@@ -279,6 +279,24 @@ def test_coarse_block_substitution_is_a_direct_solve(sa, gen_mod, n_el):
         assert torch.equal(X[c], x1)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_zero_right_hand_side(sa, gen_mod, precision):
+    """b = 0 ends before the first iteration with x = 0 and status OK, alone and
+    as one column of a block beside a column that iterates (the columns stay
+    independent)."""
+    import torch
+    p = gen_mod.battery_3d(12, 12, 24)
+    h = sa.Hierarchy(p, theta=0.05, measure="material", max_coarse=100, precision=precision)
+    z = torch.zeros(p["n"], dtype=torch.float64, device="cuda")
+    x, info = h.solve(z)
+    assert info["status"] == 0 and info["iters"] == 0 and torch.count_nonzero(x) == 0
+    b = torch.from_numpy(p["b"]).cuda()
+    xs, i1 = h.solve(b)
+    X, infos = h.solve_batch(torch.stack([z, b]))
+    assert infos[0]["iters"] == 0 and infos[0]["status"] == 0 and torch.count_nonzero(X[0]) == 0
+    assert infos[1]["iters"] == i1["iters"] and torch.equal(X[1], xs)
+
+
 def test_host_pointer_path_matches_device_path(sa, gen_mod):
     import torch
     p = gen_mod.battery_3d(12, 12, 24)
