@@ -80,54 +80,99 @@ __global__ void k_mis_init(int64_t n, const uint8_t* __restrict__ dir, uint32_t 
   tag[i] = key + 1;
 }
 
-// neighbour maxima with MIS_SW lanes per G_C row (rows hold 0..26 entries)
+// neighbour maxima with MIS_SW lanes per G_C row (rows hold 0..26 entries),
+// over the rows of `list` (NULL: every row)
 constexpr int MIS_SW = 8;
 
-__global__ void k_mis_max1(int64_t n, const int64_t* __restrict__ gcrp, const int32_t* __restrict__ gcci,
-                           const uint64_t* __restrict__ tag, uint64_t* __restrict__ m1) {
+__device__ __forceinline__ bool mis_undecided(uint64_t t) { return t != 0 && t != TAG_SEL; }
+
+__global__ void k_mis_max1(int64_t nl, const int32_t* __restrict__ list, const int64_t* __restrict__ gcrp,
+                           const int32_t* __restrict__ gcci, const uint64_t* __restrict__ tag,
+                           uint64_t* __restrict__ m1) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = gt / MIS_SW;
+  const int64_t t = gt / MIS_SW;
   const int sl = (int)(gt % MIS_SW);
   uint64_t m = 0;
-  if (i < n) {
+  int64_t i = -1;
+  if (t < nl) {
+    i = list ? list[t] : t;
     if (sl == 0) m = tag[i];
     for (int64_t p = gcrp[i] + sl; p < gcrp[i + 1]; p += MIS_SW) {
-      uint64_t t = tag[gcci[p]];
-      m = t > m ? t : m;
+      uint64_t v = tag[gcci[p]];
+      m = v > m ? v : m;
     }
   }
   for (int o = MIS_SW / 2; o > 0; o >>= 1) {
-    uint64_t t = __shfl_xor_sync(FULL, m, o, MIS_SW);
-    m = t > m ? t : m;
+    uint64_t v = __shfl_xor_sync(FULL, m, o, MIS_SW);
+    m = v > m ? v : m;
   }
-  if (i < n && sl == 0) m1[i] = m;
+  if (t < nl && sl == 0) m1[i] = m;
 }
 
-__global__ void k_mis_max2(int64_t n, const int64_t* __restrict__ gcrp, const int32_t* __restrict__ gcci,
-                           const uint64_t* __restrict__ m1, uint64_t* __restrict__ tag,
-                           unsigned long long* __restrict__ undecided) {
+__global__ void k_mis_max2(int64_t nl, const int32_t* __restrict__ list, const int64_t* __restrict__ gcrp,
+                           const int32_t* __restrict__ gcci, const uint64_t* __restrict__ m1,
+                           uint64_t* __restrict__ tag, unsigned long long* __restrict__ undecided) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = gt / MIS_SW;
+  const int64_t t = gt / MIS_SW;
   const int sl = (int)(gt % MIS_SW);
-  const uint64_t ti = i < n ? tag[i] : 0;
-  const bool active = i < n && ti != 0 && ti != TAG_SEL;
+  const int64_t i = t < nl ? (list ? list[t] : t) : 0;
+  const uint64_t ti = t < nl ? tag[i] : 0;
+  const bool active = t < nl && mis_undecided(ti);
   uint64_t m = 0;
   if (active) {
     if (sl == 0) m = m1[i];
     for (int64_t p = gcrp[i] + sl; p < gcrp[i + 1]; p += MIS_SW) {
-      uint64_t t = m1[gcci[p]];
-      m = t > m ? t : m;
+      uint64_t v = m1[gcci[p]];
+      m = v > m ? v : m;
     }
   }
   for (int o = MIS_SW / 2; o > 0; o >>= 1) {
-    uint64_t t = __shfl_xor_sync(FULL, m, o, MIS_SW);
-    m = t > m ? t : m;
+    uint64_t v = __shfl_xor_sync(FULL, m, o, MIS_SW);
+    m = v > m ? v : m;
   }
   if (active && sl == 0) {
     uint64_t nt = (m == TAG_SEL) ? 0 : (m == ti ? TAG_SEL : ti);
     tag[i] = nt;
-    if (nt != 0 && nt != TAG_SEL) atomicAdd(undecided, 1ull);
+    if (mis_undecided(nt)) atomicAdd(undecided, 1ull);
   }
+}
+
+// active sets for the later rounds: flag every undecided row of `list` and
+// its G_C neighbours (the rows whose m1 a round still reads)
+__global__ void k_mis_flag(int64_t nl, const int32_t* __restrict__ list, const int64_t* __restrict__ gcrp,
+                           const int32_t* __restrict__ gcci, const uint64_t* __restrict__ tag,
+                           uint8_t* __restrict__ flag) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = gt / MIS_SW;
+  const int sl = (int)(gt % MIS_SW);
+  if (t >= nl) return;
+  const int64_t i = list ? list[t] : t;
+  if (!mis_undecided(tag[i])) return;
+  if (sl == 0) flag[i] = 1;
+  for (int64_t p = gcrp[i] + sl; p < gcrp[i + 1]; p += MIS_SW) flag[gcci[p]] = 1;
+}
+
+// over the rows of the previous neighbourhood list: counts of the new
+// undecided list and of the new neighbourhood list (both subsets of it)
+__global__ void k_mis_listcount(int64_t nl, const int32_t* __restrict__ list, const uint64_t* __restrict__ tag,
+                                const uint8_t* __restrict__ flag, int64_t* __restrict__ cu,
+                                int64_t* __restrict__ cn) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const int64_t i = list ? list[t] : t;
+  cu[t + 1] = mis_undecided(tag[i]) ? 1 : 0;
+  cn[t + 1] = flag[i] ? 1 : 0;
+}
+
+__global__ void k_mis_listfill(int64_t nl, const int32_t* __restrict__ list, const uint64_t* __restrict__ tag,
+                               const uint8_t* __restrict__ flag, const int64_t* __restrict__ cu,
+                               const int64_t* __restrict__ cn, int32_t* __restrict__ ulist,
+                               int32_t* __restrict__ nlist) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const int32_t i = list ? list[t] : (int32_t)t;
+  if (mis_undecided(tag[i])) ulist[cu[t]] = i;
+  if (flag[i]) nlist[cn[t]] = i;
 }
 
 int run_mis2(Alloc& al, int64_t n, const int64_t* gcrp, const int32_t* gcci, const uint8_t* dir, int level,
@@ -142,21 +187,65 @@ int run_mis2(Alloc& al, int64_t n, const int64_t* gcrp, const int32_t* gcci, con
   const uint32_t salt = 0x9E3779B9u * (uint32_t)(level + 1);
   k_mis_init<<<blocks_for(n, 256), 256, 0, s>>>(n, dir, salt, seed, tag);
   SA_LAUNCHED();
-  // rounds are launched in groups between read-backs of the undecided count;
-  // a round after convergence changes nothing (every node is decided)
+  // Rounds are launched in groups between read-backs of the undecided count;
+  // a round after convergence changes nothing (every node is decided).  Once
+  // few nodes are undecided, the rounds run over two lists instead of all
+  // rows: U, the undecided rows (the only ones max2 changes), and N, U with
+  // its G_C neighbours (the only m1 values max2 reads).  Both lists are
+  // rebuilt after every group from the previous N (they only shrink), in
+  // ascending row order; the rounds decide exactly as over all rows.
+  Buf<int32_t> ul, nla, nlb;
+  Buf<uint8_t> flag;
+  Buf<int64_t> cu, cn;
+  const int32_t* U = nullptr;  // NULL: every row
+  const int32_t* N = nullptr;
+  int64_t nu = n, nn = n;
   unsigned long long h_cnt = 1;
   const int group = 4;
   while (h_cnt > 0) {
     if (*rounds >= max_rounds) return SA_ERR_CAPACITY;
     for (int g = 0; g < group; ++g) {
       SA_TRY(memset_d(cnt.p, 0, sizeof(unsigned long long), s));
-      k_mis_max1<<<blocks_for(n * MIS_SW, 256), 256, 0, s>>>(n, gcrp, gcci, tag, m1.p);
-      SA_LAUNCHED();
-      k_mis_max2<<<blocks_for(n * MIS_SW, 256), 256, 0, s>>>(n, gcrp, gcci, m1.p, tag, cnt.p);
-      SA_LAUNCHED();
+      if (nn > 0) {
+        k_mis_max1<<<blocks_for(nn * MIS_SW, 256), 256, 0, s>>>(nn, N, gcrp, gcci, tag, m1.p);
+        SA_LAUNCHED();
+      }
+      if (nu > 0) {
+        k_mis_max2<<<blocks_for(nu * MIS_SW, 256), 256, 0, s>>>(nu, U, gcrp, gcci, m1.p, tag, cnt.p);
+        SA_LAUNCHED();
+      }
       ++*rounds;
     }
     SA_TRY(copy_d2h(&h_cnt, cnt.p, sizeof(h_cnt), s));
+    if (h_cnt > 0 && (int64_t)h_cnt * 8 < nn) {
+      if (!flag.p) {
+        SA_TRY(flag.alloc(&al, n));
+        SA_TRY(ul.alloc(&al, n));
+        SA_TRY(nla.alloc(&al, n));
+        SA_TRY(nlb.alloc(&al, n));
+        SA_TRY(cu.alloc(&al, n + 1));
+        SA_TRY(cn.alloc(&al, n + 1));
+      }
+      SA_TRY(memset_d(flag.p, 0, flag.bytes(), s));
+      k_mis_flag<<<blocks_for(nu * MIS_SW, 256), 256, 0, s>>>(nu, U, gcrp, gcci, tag, flag.p);
+      SA_LAUNCHED();
+      SA_TRY(memset_d(cu.p, 0, sizeof(int64_t), s));
+      SA_TRY(memset_d(cn.p, 0, sizeof(int64_t), s));
+      k_mis_listcount<<<blocks_for(nn, 256), 256, 0, s>>>(nn, N, tag, flag.p, cu.p, cn.p);
+      SA_LAUNCHED();
+      SA_TRY(scan_inplace(al, cu.p + 1, nn));
+      SA_TRY(scan_inplace(al, cn.p + 1, nn));
+      int32_t* nnew = (N == nla.p) ? nlb.p : nla.p;
+      k_mis_listfill<<<blocks_for(nn, 256), 256, 0, s>>>(nn, N, tag, flag.p, cu.p, cn.p, ul.p, nnew);
+      SA_LAUNCHED();
+      int64_t tot[2] = {0, 0};
+      SA_TRY(copy_d2h(&tot[0], cu.p + nn, sizeof(int64_t), s));
+      SA_TRY(copy_d2h(&tot[1], cn.p + nn, sizeof(int64_t), s));
+      U = ul.p;
+      N = nnew;
+      nu = tot[0];
+      nn = tot[1];
+    }
   }
   return SA_OK;
 }
