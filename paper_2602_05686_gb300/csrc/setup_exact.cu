@@ -253,6 +253,42 @@ __global__ void k_material_w(int64_t n, const int64_t* __restrict__ rp, const in
   }
 }
 
+// the same per pair with a warp per row (lanes stride the row): on coarse
+// levels a few rows are 10-40x longer than the rest, and a thread per row
+// leaves them a long sequential tail.  Every w_ij comes from the same
+// expression, so the values equal those of the thread-per-row form.
+template <int DIM>
+__global__ void k_material_w_warp(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                  const double* __restrict__ x, const double* __restrict__ sinv,
+                                  double* __restrict__ w) {
+  constexpr int KP = DIM == 3 ? 6 : 3;
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    double xi[3], si_i[KP];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) xi[c] = x[i * DIM + c];
+#pragma unroll
+    for (int c = 0; c < KP; ++c) si_i[c] = sinv[i * KP + c];
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+      const int32_t j = ci[p];
+      if (j < (int32_t)i) continue;  // mirrored by k_material_w_mirror
+      double wv = 0.0;
+      if (j != (int32_t)i) {
+        double d[3], sj[KP];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) d[c] = xi[c] - x[(int64_t)j * DIM + c];
+#pragma unroll
+        for (int c = 0; c < KP; ++c) sj[c] = sinv[(int64_t)j * KP + c];
+        double qij = quad_form(DIM, si_i, d);
+        double qji = quad_form(DIM, sj, d);
+        double m = qij > qji ? qij : qji;
+        wv = 1.0 / m;
+      }
+      w[p] = wv;
+    }
+  }
+}
+
 // lower entries: w_ij = w_ji, the (j, i) entry found by binary search in row
 // j; a pattern without that entry (not structurally symmetric) gets w_ij
 // computed here by the same expression
@@ -301,7 +337,18 @@ __global__ void k_row_sum_ordered(int64_t n, const int64_t* __restrict__ rp, con
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double acc = 0.0;
-  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc += w[p];
+  const int64_t e = rp[i + 1];
+  int64_t p = rp[i];
+  // eight loads in flight per round (long coarse-level rows are otherwise a
+  // chain of dependent load rounds); still added one by one in column order
+  for (; p + 8 <= e; p += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = w[p + u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u];
+  }
+  for (; p < e; ++p) acc += w[p];
   D[i] = acc;
 }
 
@@ -637,8 +684,15 @@ int launch_strength_material(cudaStream_t s, int dim, int64_t n, const int64_t* 
                              double* w, double* D, uint8_t* keep, int64_t* cnt) {
   if (n <= 0) return SA_OK;
   const double t2 = theta * theta;
-  if (dim == 3) k_material_w<3><<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, x, sinv, w);
-  else k_material_w<2><<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, x, sinv, w);
+  // a thread per row on large levels (uniform rows: 32 rows share each FP64
+  // instruction), a warp per row below 2^19 rows (coarse levels, long rows)
+  if (n >= (int64_t(1) << 19)) {
+    if (dim == 3) k_material_w<3><<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, x, sinv, w);
+    else k_material_w<2><<<blocks_for(n, 128), 128, 0, s>>>(n, rp, ci, x, sinv, w);
+  } else {
+    if (dim == 3) k_material_w_warp<3><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
+    else k_material_w_warp<2><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
+  }
   SA_LAUNCHED();
   if (dim == 3) k_material_w_mirror<3><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
   else k_material_w_mirror<2><<<warp_rows_grid(n), 256, 0, s>>>(n, rp, ci, x, sinv, w);
