@@ -53,3 +53,14 @@ def test_setup_rejects_bad_arguments_before_touching_a_gpu():
     pr.dim, pr.n, pr.nnz = 2, 0, 0
     assert L.sa_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == -1
     assert L.sa_setup(None, ctypes.byref(o), ctypes.byref(h)) == -1
+
+
+def test_inspection_calls_reject_bad_arguments_without_gpu():
+    import ctypes
+    import numpy as np
+    import paper_2602_05686_gb300 as sa
+    L = sa.lib(build_if_missing=False)
+    out = np.zeros(5, np.int64)
+    assert L.sa_level_format(None, 0, out.ctypes.data) == -1
+    assert L.sa_level_sizes(None, 0, out.ctypes.data) == -1
+    assert L.sa_level_format(ctypes.c_void_p(), 0, None) == -1
