@@ -238,6 +238,7 @@ __global__ void k_bcoarse_out(int64_t n, int K, const double* __restrict__ x, co
     const unsigned _g = mat_grid(M);                                                     \
     if ((M).sw == 0 && (M).sell_lanes == 2) Kern<T, -2, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
     else if ((M).sw == 0) Kern<T, 0, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
+    else if ((M).sw == 1) Kern<T, 1, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
     else Kern<T, CSR_LANES, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                   \
   } while (0)
 

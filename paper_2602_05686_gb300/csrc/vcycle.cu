@@ -185,7 +185,8 @@ __global__ void k_long_fill(int64_t n, const int64_t* __restrict__ rp, int64_t l
 }
 
 // SELL-32 (one thread per row, one FMA per stored entry) if it stores at most
-// 25 % padding; else CSR with CSR_LANES lanes per row, and the rows longer
+// 25 % padding; else CSR with CSR_LANES lanes per row (one for matrices of at
+// most three entries per row on average), and the rows longer
 // than LONG_ROW entries in the long-row bin (a warp per row, launched first).
 // On the coarse levels of the stretched battery stack a few rows are 10-40x
 // longer than the rest: a few lanes per row keep the FP64 shuffle additions
@@ -221,7 +222,9 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
     M.sell_lanes = n < SELL2_ROWS ? 2 : 1;
     return build_sell<T>(al, n, nnz, rp, ci, v, left, right, M.sell);
   }
-  M.sw = CSR_LANES;
+  // prolongators hold 1-3 entries per row: one thread per row there (no
+  // idle lanes, no shuffle additions)
+  M.sw = (double)nnz <= 3.0 * (double)n ? 1 : CSR_LANES;
   M.nlong = 0;
   M.lt = INT64_MAX;
   if ((int64_t)max_width > LONG_ROW) {
@@ -385,6 +388,7 @@ __global__ void k_vc_fine_in(int64_t n, const double* __restrict__ r, const doub
     const unsigned _g = mat_grid(M);                                                     \
     if ((M).sw == 0 && (M).sell_lanes == 2) K<T, -2><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
     else if ((M).sw == 0) K<T, 0><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                 \
+    else if ((M).sw == 1) K<T, 1><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                 \
     else K<T, CSR_LANES><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                          \
   } while (0)
 
