@@ -217,14 +217,20 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
     SA_TRY(copy_d2h(&stored, sz.p + M.nslices, sizeof(int64_t), s));
     SA_TRY(copy_d2h(&max_width, mx.p, sizeof(unsigned int), s));
   }
-  if (n == 0 || (double)stored <= 1.25 * (double)nnz) {
+  // short rows (prolongators): SELL also above 25 % padding when its padding
+  // costs fewer bytes than the CSR row pointers it saves (value + 32-bit
+  // column per padded entry against 8 bytes per row less a slice pointer)
+  const bool short_rows = (double)nnz <= 3.0 * (double)n;
+  const bool sell_smaller =
+      short_rows && (double)(sizeof(T) + 4) * (double)(stored - nnz) < 8.0 * (double)(n - M.nslices);
+  if (n == 0 || (double)stored <= 1.25 * (double)nnz || sell_smaller) {
     M.sw = 0;
     M.sell_lanes = n < SELL2_ROWS ? 2 : 1;
     return build_sell<T>(al, n, nnz, rp, ci, v, left, right, M.sell);
   }
   // prolongators hold 1-3 entries per row: one thread per row there (no
   // idle lanes, no shuffle additions)
-  M.sw = (double)nnz <= 3.0 * (double)n ? 1 : CSR_LANES;
+  M.sw = short_rows ? 1 : CSR_LANES;
   M.nlong = 0;
   M.lt = INT64_MAX;
   if ((int64_t)max_width > LONG_ROW) {
