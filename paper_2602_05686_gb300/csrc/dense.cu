@@ -1,10 +1,12 @@
-// Coarsest level (Sec. 4: "the coarsest level is solved with a direct
-// method").  A_L (n_L <= a few thousand) is densified and factored
-// A_L = L L^T by a blocked right-looking Cholesky in FP64 (32 x 32 tiles);
-// then W = L^-1 is formed by blocked forward substitution on the identity,
-// so that every coarse solve is x = W^T (W b): two triangular matrix-vector
-// products that use every SM, instead of two sequential triangular sweeps.
-// W^T is stored explicitly so both products read contiguous rows.
+// Coarsest level (Sec. 4: the coarsest level is solved directly).  A_L
+// (n_L <= a few thousand) is densified and factored A_L = L L^T by a blocked
+// right-looking Cholesky in FP64 (32 x 32 tiles); then the inverses of the
+// diagonal blocks of COARSE_BS rows, W_KK = L_KK^-1, are formed by blocked
+// forward substitution on the identity.  Every coarse solve is block
+// substitution: per diagonal block a row-parallel product with the blocks
+// already solved and one with W_KK (forward with L, backward with L^T and
+// W_KK^T), so it uses every SM instead of running row-by-row sweeps.  L^T and
+// W^T are stored explicitly so all products read contiguous rows.
 #include <math.h>
 
 #include "common.cuh"
