@@ -820,9 +820,10 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   Level& Lc = *h->lev[nlev - 1];
   if (Lc.n > 16384) return SA_ERR_STAGNATION;
   h->nL = Lc.n;
-  // a15: the coarse Cholesky factor and its inverse, on streams of their own:
-  // the Chebyshev bounds and the packing of the hierarchy below overlap it
-  // (the packing stores the addresses of W and WT, not their contents)
+  // a15: the coarse Cholesky factor and its diagonal-block inverses, on
+  // streams of their own: the Chebyshev bounds and the packing of the
+  // hierarchy below overlap it (the packing stores the addresses of the
+  // factor's arrays, not their contents)
   DenseJob dj;
   dj.level = nlev - 1;
   SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->cf, dj));
@@ -1174,7 +1175,7 @@ static int finish_loaded(sa_handle h) {
   Level& Lc = *h->lev[nlev - 1];
   h->nL = Lc.n;
   // the coarse factorisation overlaps the packing below (which stores the
-  // addresses of W and WT, not their contents)
+  // addresses of the factor's arrays, not their contents)
   DenseJob dj;
   dj.level = nlev - 1;
   SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->cf, dj));

@@ -33,7 +33,7 @@ enum ProfKind {
   PK_S_RAP = 22,       // a13 Galerkin product (two SpGEMMs + symmetrise)
   PK_S_AUX = 23,       // a9 coarse coordinates / tensors
   PK_S_CHEB = 24,      // a15 Chebyshev bounds
-  PK_S_DENSE = 25,     // a15 coarse Cholesky + inverse factor
+  PK_S_DENSE = 25,     // a15 coarse Cholesky + diagonal-block inverses
   PK_S_SELL = 26,      // a15 SELL packing of the scaled hierarchy
   PK_S_RAP_AP = 27,    // part of PK_S_RAP: the product A P
   PK_S_RAP_RAP = 28,   // part of PK_S_RAP: R (A P) and the mirror of its upper triangle

@@ -5,12 +5,13 @@
 // with a unit diagonal equals Chebyshev on D^-1 A in the original variables,
 // and z = D_0^-1/2 V~(D_0^-1/2 r).  One templated code path serves both solve
 // forms: T = double (FP64 PCG) and T = float (FP32 V-cycle inside FP64
-// flexible CG).  Matrices are SELL-32: slices of 32 consecutive rows stored
-// column-major with one thread per row, so every warp load of values and
-// column indices is one contiguous segment, and for finite-element stencils
-// (consecutive rows share their stencil shape) the gathers of x are
-// contiguous too.  The coarsest level is solved in FP64 with the dense
-// inverse factor.
+// flexible CG).  Large matrices are SELL-32: slices of 32 consecutive rows
+// stored column-major with one thread per row, so every warp load of values
+// and column indices is one contiguous segment, and for finite-element
+// stencils (consecutive rows share their stencil shape) the gathers of x are
+// contiguous too; coarse levels with a few very long rows are CSR with a
+// long-row bin (build_mat).  The coarsest level is solved in FP64 by block
+// substitution with the dense coarse factor.
 #include <math.h>
 
 #include <vector>
