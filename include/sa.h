@@ -312,15 +312,22 @@ int sa_strength(sa_measure measure, int dim, int64_t n, int64_t nnz, const int64
  * an application that owns all device memory and passes only inputs and
  * outputs.  (The paper has no counterpart; this is a deployment variant.)
  *   - Allocates nothing: its scratch (w and D, nnz + n doubles) is a fixed
- *     16 MiB static device array that every GPU loading this library holds
- *     until the process exits.  Sizes with nnz + n > 2,097,152 return
- *     SA_ERR_CAPACITY (see sa_last_error) without launching anything.
+ *     16 MiB static device array (plus one 256-byte line for an input-check
+ *     flag) that every GPU loading this library holds until the process
+ *     exits.  Sizes with nnz + n > 2,097,152 return SA_ERR_CAPACITY (see
+ *     sa_last_error) without launching anything.
  *   - Inputs and outputs are caller-owned DEVICE buffers as for sa_strength:
  *     row_ptr[n+1], col[nnz], coords[n*dim], sigma_inv[n*kp] (inverse nodal
  *     tensors; identity tensors give the plain distance Laplacian),
  *     dirichlet[n] (may be NULL), keep[nnz] (output).  Ordered on `stream`.
- *   - The first call on a device looks up the device address of the array
- *     (cudaGetSymbolAddress) with that device current; make that first call
+ *   - The CSR is checked on the device before any weight is computed
+ *     (row_ptr[0] = 0, monotone, row_ptr[n] = nnz, columns strictly
+ *     ascending in [0, n)); the call waits for `stream` once to read that
+ *     check, and a malformed CSR returns SA_ERR_INVALID_ARG with nothing
+ *     written to keep or beyond the scratch array.
+ *   - Each call looks up the device address of the array
+ *     (cudaGetSymbolAddress) with the calling device current; the first
+ *     call on a device loads the module there, so make that first call
  *     outside any stream capture.
  *   - All calls share the one array and every call overwrites it completely
  *     before reading it, so nothing carries over between calls; calls whose

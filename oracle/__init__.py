@@ -76,6 +76,8 @@ def lib():
             "or_operator_complexity": (D, [P]),
             "or_set_cheb": (None, [P, I32, D, D]),
             "or_pcg": (I32, [P, P, P, D, I32, I32, P, P]),
+            "or_pcg_hist": (I32, [P, P, P, D, I32, I32, P, P, P]),
+            "or_pcg_diag_cycle": (I32, [I64, P, P, P, I32, P, P, P, D, I32, I32, P, P, P]),
             "or_vcycle": (None, [P, P, P]),
             "or_coarsest_solve": (None, [P, P, P]),
             "or_csr_info": (None, [P, P]),
@@ -229,6 +231,21 @@ def coarse_aux(dim, n, nc, agg, x, sigma):
     return xc, sc
 
 
+def pcg_diag_cycle(n, rp, ci, v, dinvs, b, tol=1e-10, maxit=200, flexible=False):
+    """CG whose k-th preconditioner application is diag(dinvs[k mod len(dinvs)]);
+    returns x, status, iterations, true relative residual and the recursive
+    residual history ||r_k|| / ||r_0||"""
+    D = _c(np.stack([np.asarray(d, np.float64) for d in dinvs]), np.float64)
+    x = np.zeros(n)
+    hist = np.full(maxit + 1, np.nan)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = lib().or_pcg_diag_cycle(n, _p(_c(rp, np.int64)), _p(_c(ci, np.int32)), _p(_c(v, np.float64)), D.shape[0],
+                                 _p(D), _p(_c(b, np.float64)), _p(x), float(tol), int(maxit), int(flexible),
+                                 ctypes.byref(it), ctypes.byref(rel), _p(hist))
+    return x, dict(status=int(st), iters=int(it.value), rel_res=float(rel.value), hist=hist[:it.value + 1])
+
+
 def tentative(n, nc, agg):
     return _unbox(lib().or_step_tentative(n, nc, _p(_c(agg, np.int32))))
 
@@ -371,3 +388,13 @@ class Hierarchy:
         st = lib().or_pcg(self.h, _p(_c(b, np.float64)), _p(x), float(tol), int(maxit), int(flexible),
                           ctypes.byref(it), ctypes.byref(rel))
         return x, dict(status=int(st), iters=int(it.value), rel_res=float(rel.value))
+
+    def solve_hist(self, b, x0=None, tol=1e-8, maxit=500, flexible=False):
+        """solve() plus the recursive residual history ||r_k|| / ||r_0||"""
+        x = np.zeros(self.n) if x0 is None else _c(x0, np.float64).copy()
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        hist = np.full(maxit + 1, np.nan)
+        st = lib().or_pcg_hist(self.h, _p(_c(b, np.float64)), _p(x), float(tol), int(maxit), int(flexible),
+                               ctypes.byref(it), ctypes.byref(rel), _p(hist))
+        return x, dict(status=int(st), iters=int(it.value), rel_res=float(rel.value), hist=hist[:it.value + 1])

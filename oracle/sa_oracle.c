@@ -979,15 +979,20 @@ static void vcycle(const or_hier_t* h, int l, const double* b, double* x, int de
 void or_vcycle(const or_hier_t* h, const double* b, double* x) { vcycle(h, 0, b, x, 2); }
 
 /*
- * CG preconditioned by one V-cycle (Sec. 4).  Converged when
- * ||b - A x_k|| <= tol ||b - A x_0||; the recursive residual is confirmed by
- * the true residual.  flexible = 1 uses beta = z_k^T (r_k - r_{k-1}) /
- * z_{k-1}^T r_{k-1}.  Returns a status; *iters counts operator products
- * with the search direction; *relres is the final true relative residual.
+ * CG preconditioned by z = M r (Sec. 4: one V-cycle per iteration).
+ * Converged when ||b - A x_k|| <= tol ||b - A x_0||; the recursive residual is
+ * confirmed by the true residual.  flexible = 1 uses the Polak-Ribiere form
+ * beta = z_k^T (r_k - r_{k-1}) / z_{k-1}^T r_{k-1}, which stays a
+ * conjugate-direction method when M changes between iterations; flexible = 0
+ * uses the plain beta = z_k^T r_k / z_{k-1}^T r_{k-1}.  Returns a status;
+ * *iters counts operator products with the search direction; *relres is the
+ * final true relative residual; hist (may be NULL, maxit + 1 entries)
+ * receives ||r_k|| / ||r_0|| of the recursive residual after each step.
  */
-int or_pcg(const or_hier_t* h, const double* b, double* x, double tol, int maxit, int flexible,
-           int* iters, double* relres) {
-  const csr_t* A = &h->lev[0].A;
+typedef void (*or_prec_fn)(void* ctx, int k, const double* r, double* z);
+
+static int pcg_core(const csr_t* A, or_prec_fn prec, void* ctx, const double* b, double* x, double tol,
+                    int maxit, int flexible, int* iters, double* relres, double* hist) {
   int64_t n = A->nrows;
   double* r = (double*)malloc(sizeof(double) * (size_t)n);
   double* z = (double*)malloc(sizeof(double) * (size_t)n);
@@ -997,10 +1002,11 @@ int or_pcg(const or_hier_t* h, const double* b, double* x, double tol, int maxit
   spmv(A, x, r);
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
   double r0 = sqrt(dot(n, r, r));
-  int st = OR_ERR_NO_CONVERGENCE, it = 0;
+  int st = OR_ERR_NO_CONVERGENCE, it = 0, napp = 0;
   double rel = 0.0;
+  if (hist) hist[0] = 1.0;
   if (r0 == 0.0) { st = OR_OK; goto done; }
-  or_vcycle(h, r, z);
+  prec(ctx, napp++, r, z);
   memcpy(p, z, sizeof(double) * (size_t)n);
   double rz = dot(n, r, z);
   for (it = 1; it <= maxit; ++it) {
@@ -1011,6 +1017,7 @@ int or_pcg(const or_hier_t* h, const double* b, double* x, double tol, int maxit
     if (flexible) memcpy(rp, r, sizeof(double) * (size_t)n);
     for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
     double rn = sqrt(dot(n, r, r));
+    if (hist) hist[it] = rn / r0;
     if (rn <= tol * r0) {
       spmv(A, x, q);
       for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
@@ -1018,7 +1025,7 @@ int or_pcg(const or_hier_t* h, const double* b, double* x, double tol, int maxit
       if (tn <= tol * r0) { st = OR_OK; break; }
       memcpy(r, q, sizeof(double) * (size_t)n);
     }
-    or_vcycle(h, r, z);
+    prec(ctx, napp++, r, z);
     double rzn = dot(n, r, z), beta;
     if (flexible) {
       double s = 0.0;
@@ -1039,6 +1046,44 @@ done:
   *relres = rel;
   free(r); free(z); free(p); free(q); free(rp);
   return st;
+}
+
+static void prec_vcycle(void* ctx, int k, const double* r, double* z) {
+  (void)k;
+  or_vcycle((const or_hier_t*)ctx, r, z);
+}
+
+int or_pcg(const or_hier_t* h, const double* b, double* x, double tol, int maxit, int flexible,
+           int* iters, double* relres) {
+  return pcg_core(&h->lev[0].A, prec_vcycle, (void*)h, b, x, tol, maxit, flexible, iters, relres, NULL);
+}
+
+/* or_pcg with the residual history (hist: maxit + 1 entries) */
+int or_pcg_hist(const or_hier_t* h, const double* b, double* x, double tol, int maxit, int flexible,
+                int* iters, double* relres, double* hist) {
+  return pcg_core(&h->lev[0].A, prec_vcycle, (void*)h, b, x, tol, maxit, flexible, iters, relres, hist);
+}
+
+/* CG with a preconditioner that changes between applications: the k-th
+ * application (k = 0, 1, ...) is z = diag(dinv[k mod ndiag]) r, dinv holding
+ * ndiag vectors of n entries.  A test device for the flexible beta: with
+ * ndiag > 1 only the Polak-Ribiere form keeps the search directions
+ * A-conjugate. */
+typedef struct { int64_t n; int ndiag; const double* dinv; } diag_cycle_t;
+
+static void prec_diag_cycle(void* ctx, int k, const double* r, double* z) {
+  const diag_cycle_t* c = (const diag_cycle_t*)ctx;
+  const double* d = c->dinv + (size_t)(k % c->ndiag) * (size_t)c->n;
+  for (int64_t i = 0; i < c->n; ++i) z[i] = d[i] * r[i];
+}
+
+int or_pcg_diag_cycle(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, int ndiag,
+                      const double* dinv, const double* b, double* x, double tol, int maxit, int flexible,
+                      int* iters, double* relres, double* hist) {
+  csr_t A;
+  A.nrows = n; A.ncols = n; A.rp = (int64_t*)rp; A.ci = (int32_t*)ci; A.v = (double*)v;
+  diag_cycle_t c = {n, ndiag, dinv};
+  return pcg_core(&A, prec_diag_cycle, &c, b, x, tol, maxit, flexible, iters, relres, hist);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -410,6 +410,15 @@ def strength_material_noalloc(dim, row_ptr, col, coords, sigma_inv, dirichlet, t
     torch = _torch()
     n = row_ptr.numel() - 1
     nnz = col.numel()
+    for t, dt, size, name in ((row_ptr, torch.int64, n + 1, "row_ptr"), (col, torch.int32, nnz, "col"),
+                              (coords, torch.float64, n * dim, "coords"),
+                              (sigma_inv, torch.float64, n * (6 if dim == 3 else 3), "sigma_inv"),
+                              (dirichlet, torch.uint8, n, "dirichlet"), (keep, torch.uint8, nnz, "keep")):
+        if t is None and name == "dirichlet":
+            continue
+        if t is None or t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() < size:
+            raise ValueError(f"strength_material_noalloc: {name} must be a contiguous CUDA {dt} tensor "
+                             f"of at least {size} elements")
     s = (stream or torch.cuda.current_stream()).cuda_stream
 
     def P(t):

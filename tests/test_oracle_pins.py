@@ -628,3 +628,142 @@ def test_chain_sensitivity(orc, gen_mod, drop, theta):
         spread = max(spread, e)
         assert e <= chain_tol(l) / 10, (l, e)   # a tenth of the bar: GPU sums differ in more than one ulp
     assert spread > 1e-14   # the chain does amplify last-bit differences
+
+
+# ---------------------------------------------------------------------------
+# a1: Dirichlet detection (Sec. 3: eliminated rows keep only their diagonal)
+# against the generator's own record of the constrained nodes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["layered_2d", "battery_3d", "voronoi_3d", "two_domain"])
+def test_dirichlet_flags_equal_generator_mask(orc, gen_mod, case):
+    p = {"layered_2d": lambda: gen_mod.layered_2d(16),
+         "battery_3d": lambda: gen_mod.battery_3d(6, 6, 12),
+         "voronoi_3d": lambda: gen_mod.voronoi_3d(6, nseeds=4, seed=1),
+         "two_domain": lambda: gen_mod.two_domain(16, 1e4)}[case]()
+    dm = orc.dirichlet(p["n"], p["row_ptr"], p["col"], p["val"])
+    want = np.asarray(p["dir_mask"], np.uint8)
+    assert want.sum() > 0
+    assert np.array_equal(dm, want)
+    # a plain Neumann row with a single zero-valued off-diagonal stays free
+    rp = np.array([0, 2, 4], np.int64)
+    ci = np.array([0, 1, 0, 1], np.int32)
+    assert orc.dirichlet(2, rp, ci, np.array([1.0, 0.0, -1.0, 1.0])).tolist() == [1, 0]
+
+
+# ---------------------------------------------------------------------------
+# a9: coarse auxiliary data (Sec. 3, auxiliary transfer): coordinates and
+# tensors sigma (not sigma^-1) averaged over the members of each aggregate;
+# Dirichlet members (agg = -1) are not members
+# ---------------------------------------------------------------------------
+def test_coarse_aux_means_on_hand_made_aggregates(orc):
+    agg = np.array([0, 1, -1, 0, 1, 1, 2], np.int32)
+    x = np.array([[0.0, 1.0], [4.0, 0.0], [1e6, 1e6], [2.0, 3.0], [5.0, 1.0], [6.0, 2.0], [7.0, 7.0]])
+    # (xx, yy, xy) per node; node 2 (Dirichlet) would move every mean it entered
+    sig = np.array([[1.0, 2.0, 0.5], [1.0, 1.0, 0.0], [1e9, 1e9, 1e9], [3.0, 4.0, -0.5],
+                    [2.0, 1.0, 0.25], [3.0, 4.0, 0.5], [8.0, 2.0, 1.0]])
+    xc, sc = orc.coarse_aux(2, 7, 3, agg, x.ravel(), sig.ravel())
+    assert xc.reshape(3, 2).tolist() == [[1.0, 2.0], [5.0, 1.0], [7.0, 7.0]]
+    assert sc.reshape(3, 3).tolist() == [[2.0, 3.0, 0.0], [2.0, 2.0, 0.25], [8.0, 2.0, 1.0]]
+    # the mean of sigma, not the inverse of the mean of sigma^-1: for members
+    # with sigma = 1 and 3 the two differ (2 against 1.5)
+    x1 = np.zeros((2, 2))
+    s1 = np.array([[1.0, 1.0, 0.0], [3.0, 3.0, 0.0]])
+    _, sc1 = orc.coarse_aux(2, 2, 1, np.array([0, 0], np.int32), x1.ravel(), s1.ravel())
+    assert sc1.tolist() == [2.0, 2.0, 0.0]
+    # 3D packing (xx, yy, zz, xy, xz, yz)
+    s3 = np.array([[1, 2, 3, 0.5, 0.25, 0.125], [3, 2, 1, -0.5, 0.75, 0.375]], np.float64)
+    xc3, sc3 = orc.coarse_aux(3, 2, 1, np.array([0, 0], np.int32), np.arange(6.0), s3.ravel())
+    assert xc3.tolist() == [1.5, 2.5, 3.5]
+    assert sc3.tolist() == [2.0, 2.0, 2.0, 0.0, 0.5, 0.25]
+
+
+def test_hierarchy_coarse_aux_is_mean_then_inverse(orc, gen_mod):
+    # level 1 of a material hierarchy carries the aggregate means of level 0's
+    # coordinates and tensors, and sigma^-1 of the mean tensor (numpy here)
+    p = gen_mod.voronoi_3d(6, nseeds=4, seed=3)
+    h = orc.Hierarchy(p, 0.05, "material", max_coarse=30)
+    assert h.nlev >= 2
+    l0, l1 = h.level(0), h.level(1)
+    sig0 = orc.nodal_from_elements(3, p["n"], p["elem_nodes"], p["elem_measure"], p["tensors"]).reshape(-1, 6)
+    x0 = l0["x"].reshape(-1, 3)
+    nc = l1["n"]
+    agg = l0["agg"]
+    xm = np.zeros((nc, 3))
+    sm = np.zeros((nc, 6))
+    for a in range(nc):
+        mem = np.flatnonzero(agg == a)
+        assert mem.size > 0
+        xm[a] = x0[mem].mean(axis=0)
+        sm[a] = sig0[mem].mean(axis=0)
+    np.testing.assert_allclose(l1["x"].reshape(-1, 3), xm, rtol=1e-14, atol=1e-15)
+
+    def full(t):
+        return np.array([[t[0], t[3], t[4]], [t[3], t[1], t[5]], [t[4], t[5], t[2]]])
+
+    si1 = l1["sinv"].reshape(-1, 6)
+    for a in range(nc):
+        np.testing.assert_allclose(full(si1[a]), np.linalg.inv(full(sm[a])), rtol=1e-11,
+                                   atol=1e-11 * np.abs(np.linalg.inv(full(sm[a]))).max())
+
+
+# ---------------------------------------------------------------------------
+# flexible CG (the mixed-precision outer iteration): beta in the
+# Polak-Ribiere form, restated densely here; a preconditioner that changes
+# between applications separates it from the plain beta
+# ---------------------------------------------------------------------------
+def _fcg_dense(A, dinvs, b, iters, flexible):
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = dinvs[0] * r
+    p = z.copy()
+    rz = r @ z
+    hist = [1.0]
+    r0 = np.linalg.norm(r)
+    for k in range(1, iters + 1):
+        q = A @ p
+        alpha = rz / (p @ q)
+        x = x + alpha * p
+        r_old = r
+        r = r - alpha * q
+        hist.append(np.linalg.norm(r) / r0)
+        z = dinvs[k % len(dinvs)] * r
+        beta = (z @ (r - r_old)) / rz if flexible else (z @ r) / rz
+        rz = r @ z
+        p = z + beta * p
+    return np.array(hist)
+
+
+def test_flexible_beta_is_polak_ribiere(orc, gen_mod):
+    p = gen_mod.layered_2d(8, contrast=1e-2)
+    A = csr(p).toarray()
+    n = p["n"]
+    d = 1.0 / np.diag(A)
+    f = 0.3 + 2.7 * np.random.default_rng(5).random(n)
+    dinvs = [d, d * f]
+    K = 12
+    want_flex = _fcg_dense(A, dinvs, p["b"], K, flexible=True)
+    want_plain = _fcg_dense(A, dinvs, p["b"], K, flexible=False)
+    _, fl = orc.pcg_diag_cycle(n, p["row_ptr"], p["col"], p["val"], dinvs, p["b"], tol=1e-30, maxit=K,
+                               flexible=True)
+    _, pl = orc.pcg_diag_cycle(n, p["row_ptr"], p["col"], p["val"], dinvs, p["b"], tol=1e-30, maxit=K,
+                               flexible=False)
+    np.testing.assert_allclose(fl["hist"], want_flex, rtol=1e-8)
+    np.testing.assert_allclose(pl["hist"], want_plain, rtol=1e-8)
+    # the two recurrences part ways once the preconditioner changes
+    assert np.max(np.abs(fl["hist"] - want_plain) / want_plain) > 1e-3
+    # with one fixed preconditioner the two betas agree in exact arithmetic
+    _, f1 = orc.pcg_diag_cycle(n, p["row_ptr"], p["col"], p["val"], [d], p["b"], tol=1e-30, maxit=K, flexible=True)
+    _, p1 = orc.pcg_diag_cycle(n, p["row_ptr"], p["col"], p["val"], [d], p["b"], tol=1e-30, maxit=K, flexible=False)
+    np.testing.assert_allclose(f1["hist"], p1["hist"], rtol=1e-6)
+
+
+def test_pcg_history_and_true_residual(orc, gen_mod):
+    # the V-cycle solver's recorded history ends at or below tol and the
+    # final true residual meets it
+    p = gen_mod.layered_2d(32)
+    h = orc.Hierarchy(p, 0.08, "material", max_coarse=64)
+    _, info = h.solve_hist(p["b"])
+    assert info["status"] == 0
+    assert info["hist"][0] == 1.0 and info["hist"][-1] <= 1e-8 and info["rel_res"] <= 1e-8
+    _, base = h.solve(p["b"])
+    assert base["iters"] == info["iters"]

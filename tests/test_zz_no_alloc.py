@@ -64,3 +64,34 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     assert st == -8
     assert b"static scratch" in L.sa_last_error()
     assert int(keep.sum()) == 0
+
+
+def test_noalloc_rejects_a_malformed_csr_before_any_weight(env):
+    torch, gen, orc, sa = env
+    p = gen.layered_2d(8)
+    a = _inputs(torch, gen, orc, p)
+    keep = torch.zeros(p["nnz"], dtype=torch.uint8, device="cuda")
+    L = sa.lib()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n, nnz = p["n"], p["nnz"]
+    # row_ptr[n] beyond nnz: the check reads only row_ptr and the columns
+    # below nnz, so nothing outside the caller's buffers is touched
+    rp_long = a["rp"].clone()
+    rp_long[n] = nnz + 5
+    st = L.sa_strength_material_noalloc(2, n, nnz, rp_long.data_ptr(), a["ci"].data_ptr(), a["x"].data_ptr(),
+                                        a["sinv"].data_ptr(), None, 0.05, keep.data_ptr(), s)
+    assert st == -1
+    assert b"invalid CSR" in L.sa_last_error()
+    # a column index outside [0, n)
+    ci_bad = a["ci"].clone()
+    ci_bad[int(p["row_ptr"][3])] = n + 7
+    st = L.sa_strength_material_noalloc(2, n, nnz, a["rp"].data_ptr(), ci_bad.data_ptr(), a["x"].data_ptr(),
+                                        a["sinv"].data_ptr(), None, 0.05, keep.data_ptr(), s)
+    assert st == -1
+    torch.cuda.synchronize()
+    assert int(keep.sum()) == 0
+    # the entry point still works after the refusals
+    st = sa.api.strength_material_noalloc(2, a["rp"], a["ci"], a["x"], a["sinv"], a["dirm"], 0.08, keep)
+    ref = sa.strength("material", 2, a["rp"], a["ci"], None, a["x"], a["sinv"], a["dirm"], 0.08)
+    torch.cuda.synchronize()
+    assert st == 0 and torch.equal(keep, ref)
