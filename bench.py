@@ -1,17 +1,33 @@
 """Benchmark of the SA-AMG hot path on one GB300 (or N replicas).
 
-One step = the whole hot path on the battery-stack workload (Q1 hex
-128 x 128 x 256 elements, 4,276,737 dofs, z-spacing 0.01 of the x/y
-spacing, layer cycle sigma = 1e5 / 1e-5 / 1e2 of 8 elements each, u = 0 at
-z = 0 and u = 1 at the top):
-  material-aware setup (theta 0.05) + FP64 PCG to 1e-8
-  + FP32-V-cycle flexible CG to 1e-8 on the same hierarchy
-  + classical setup (theta 0.04) + FP64 PCG to 1e-8 (the paper's comparison).
-Inputs are resident in HBM before the timed region and are larger than L2
-(A alone is 1.36 GB), so no L2 flush is needed between steps.
+Default step, the largest single-GPU configuration ("inclusions_320"): Q1
+hexahedra on 320^3 elements of [0,1]^3 (33,076,161 dofs, 884,836,159 stored
+entries), seeded random spheres (radius 4-12 elements, >= 20 % of the
+volume) with sigma = 1e6 I inside a matrix of sigma = diag(1, 1, 1e-2),
+u = 0 on x = 0, and 8 right-hand sides ~ N(0,1) on the free dofs:
 
-Prints one JSON line (rank 0).  --impl reference times the CPU oracle
-instead (bounded sample, extrapolated to the full workload by dof count).
+  classical SA setup (theta 0.04)
+  + FP64 PCG on the 8 right-hand sides as one block
+  + FP32-V-cycle flexible CG on the same 8 right-hand sides as one block,
+  each column to a true relative residual <= 1e-8.
+
+`value` is the step's throughput in dof-solves per second (dofs x
+right-hand sides brought to 1e-8, 16 per step, divided by the step time;
+MDoF-solves/s, higher is better); `ms_per_step` is the step's time to
+solution.  Inputs are resident in HBM before the timed region and far larger
+than L2 (the matrix alone is 10.6 GB), so no L2 flush is needed.
+
+Besides the timed step the run reports, untimed: the same step once more with
+per-launch CUDA events (roofline, kernel table, setup phases), the step
+through the C ABI from pinned host buffers (`e2e`), the battery stack and
+the Voronoi workload in both forms and both measures, the material measure
+on the inclusions, and the CPU oracle: a measured sample step
+(`cpu_baseline`) and full-size oracle solves of every configuration it can
+finish within the run (iteration counts and the GPU solutions' error against
+the oracle's).
+
+--impl reference times the oracle on a bounded sample of the same workload
+(the inclusions at 32^3 elements, same step) in the same unit.
 """
 from __future__ import annotations
 
@@ -19,9 +35,11 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -35,36 +53,27 @@ FALLBACK_HBM_GBS = 6800.0
 N_SM, FP64_FLOP_PER_SM_CYCLE, SM_MAX_MHZ = 152, 4.0, 2070.0
 
 WORKLOADS = {
-    # name: (generator kwargs, description)
-    "battery_128x128x256": (dict(nx=128, ny=128, nz=256), "battery-like stack, Q1 hex 128x128x256 (4.28M dofs)"),
-    "battery_96x96x192": (dict(nx=96, ny=96, nz=192), "battery-like stack, Q1 hex 96x96x192 (1.8M dofs)"),
-    "battery_64x64x128": (dict(nx=64, ny=64, nz=128), "battery-like stack, Q1 hex 64x64x128 (0.54M dofs)"),
-    "battery_32x32x64": (dict(nx=32, ny=32, nz=64), "battery-like stack, Q1 hex 32x32x64 (71k dofs)"),
+    "inclusions_320": 320, "inclusions_160": 160, "inclusions_96": 96, "inclusions_48": 48, "inclusions_32": 32,
 }
-MAT_THETA, CLS_THETA, TOL = 0.05, 0.04, 1e-8
-METRIC = "time-to-1e-8 residual per step (material setup + FP64 PCG + FP32-V-cycle FCG + classical setup + FP64 PCG)"
+CLS_THETA, MAT_THETA, TOL, NRHS = 0.04, 0.05, 1e-8, 8
+SAMPLE_N_EL = 32         # the oracle's bounded sample of the inclusions workload
+METRIC = ("time-to-1e-8 residual as throughput: dofs x right-hand sides solved per second over the step "
+          "(classical setup + 8-RHS FP64 PCG + 8-RHS FP32-V-cycle FCG)")
+UNIT = "MDoF-solves/s"
 
 
-def battery_nnz(nx, ny, nz):
-    """stored entries of the battery stack's matrix after the Dirichlet
-    elimination at z = 0 and at the top (rows there keep their diagonal)"""
-    sxy = (3 * (nx + 1) - 2) * (3 * (ny + 1) - 2)
-    total = 0
-    for k in range(nz + 1):
-        if k == 0 or k == nz:
-            total += (nx + 1) * (ny + 1)
-        else:
-            total += sxy * (3 - (k - 1 == 0) - (k + 1 == nz))
-    return total
+def workload_desc(n_el):
+    n = (n_el + 1) ** 3
+    return (f"inclusions: Q1 hex {n_el}^3 ({n / 1e6:.2f}M dofs), seeded spheres sigma=1e6 in diag(1,1,1e-2), "
+            f"u=0 on x=0, {NRHS} RHS ~ N(0,1)")
 
 
-def workload_config(args, ws):
+def workload_config(n_el, ws):
     """the `config` object of the JSON line (both arms)"""
-    kw, desc = WORKLOADS[args.workload]
-    return {"workload": desc, "dofs": (kw["nx"] + 1) * (kw["ny"] + 1) * (kw["nz"] + 1),
-            "nnz": battery_nnz(kw["nx"], kw["ny"], kw["nz"]), "material_theta": MAT_THETA,
-            "classical_theta": CLS_THETA, "tol": TOL, "cheb_degree": 2, "max_coarse": 5000,
-            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"}
+    return {"workload": workload_desc(n_el), "dofs": (n_el + 1) ** 3, "rhs": NRHS, "measure": "classical",
+            "theta": CLS_THETA, "tol": TOL, "forms": "FP64 PCG and FP32-V-cycle FCG, 8 RHS per block",
+            "cheb_degree": 2, "max_coarse": 5000, "l2": "inputs larger than L2 (no flush)",
+            "parallelism": f"replicas x{ws}"}
 
 
 def dist_env():
@@ -98,10 +107,10 @@ def peaks():
 
 
 def kernel_source_hash():
-    """hash of the sources that define the V-cycle kernels (a recorded ncu
-    traffic figure is used only while they are unchanged)"""
+    """hash of the sources that define the V-cycle and outer-product kernels
+    (a recorded ncu traffic figure is used only while they are unchanged)"""
     h = hashlib.sha256()
-    for f in ("vcycle.cu", "vkern.cuh"):
+    for f in ("vcycle.cu", "vkern.cuh", "block.cu"):
         with open(os.path.join(ROOT, "paper_2602_05686_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -119,6 +128,26 @@ def traffic_for(kernel, workload):
     except Exception:
         pass
     return None
+
+
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "machine": platform.machine()}
 
 
 class ClockSampler:
@@ -174,38 +203,200 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# the CPU oracle: bounded sample step and full-size parity solves, run in
+# processes of their own (spawned before the first CUDA call)
+# ---------------------------------------------------------------------------
+def make_problem(name):
+    import gen
+    gen.build()
+    if name == "c1":
+        return gen.layered_2d(32)
+    if name == "c2":
+        return gen.battery_3d(128, 128, 256)
+    if name == "c3":
+        return gen.voronoi_3d(160)
+    if name.startswith("inclusions_"):
+        return gen.inclusions_3d(int(name.split("_")[1]))
+    raise KeyError(name)
+
+
+# (configuration, measure, theta, max_coarse) of the full-size FP64 parity solves
+PARITY = {
+    "c1": [("material", 0.08, 64), ("classical", 0.08, 64)],
+    "c2": [("material", MAT_THETA, 5000), ("classical", CLS_THETA, 5000)],
+    "c3": [("material", MAT_THETA, 5000), ("classical", CLS_THETA, 5000)],
+    "c5": [("classical", CLS_THETA, 5000)],
+}
+PARITY_JOBS = [("c1", "c1", None), ("c2", "c2", None), ("c3", "c3", "material"), ("c3", "c3", "classical"),
+               ("c5", None, None)]   # c5: the bench's own workload
+
+
+def oracle_step(p, nrhs=NRHS):
+    """the GPU arm's step run by the serial CPU oracle: classical setup, FP64
+    PCG and flexible CG (the oracle's V-cycle is FP64 in both) on nrhs
+    right-hand sides; returns seconds and iteration counts"""
+    import oracle
+    t = time.perf_counter()
+    h = oracle.Hierarchy(p, CLS_THETA, "classical")
+    it64 = [h.solve(p["B"][c], tol=TOL)[1]["iters"] for c in range(nrhs)]
+    itf = [h.solve(p["B"][c], tol=TOL, flexible=True)[1]["iters"] for c in range(nrhs)]
+    del h
+    return time.perf_counter() - t, it64, itf
+
+
+def _oracle_job(kind, cfg, problem_name, measure, outdir):
+    """one oracle job (a spawned process): 'sample' times the bounded sample
+    step twice; 'parity' solves the configuration at full size with the FP64
+    form and stores iterations and solutions"""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    res = {"kind": kind, "cfg": cfg, "measure": measure}
+    try:
+        p = make_problem(problem_name)
+        if kind == "sample":
+            ts = []
+            for _ in range(2):
+                t, it64, itf = oracle_step(p)
+                ts.append(t)
+            res.update(seconds=ts, n=int(p["n"]), iters_fp64=it64, iters_flexible=itf)
+        else:
+            b = p["B"][0] if "B" in p else p["b"]
+            rows = []
+            for (m, theta, mc) in PARITY[cfg]:
+                if measure and m != measure:
+                    continue
+                t = time.perf_counter()
+                h = oracle.Hierarchy(p, theta, m, max_coarse=mc)
+                ts = time.perf_counter() - t
+                x, info = h.solve(b, tol=TOL)
+                tt = time.perf_counter() - t - ts
+                f = os.path.join(outdir, f"x_{cfg}_{m}.npy")
+                np.save(f, x)
+                rows.append(dict(measure=m, theta=theta, iters=info["iters"], status=info["status"],
+                                 rel_res=info["rel_res"], levels=h.nlev, setup_s=round(ts, 2),
+                                 solve_s=round(tt, 2), x=f))
+                del h
+            res["rows"] = rows
+    except Exception as e:  # reported, never fatal to the bench
+        res["error"] = repr(e)
+    with open(os.path.join(outdir, f"{kind}_{cfg}_{measure or 'all'}.json"), "w") as fh:
+        json.dump(res, fh)
+
+
+class OracleJobs:
+    """the oracle jobs of one bench run, as spawned processes (spawn, not
+    fork: they start before the first CUDA call and share nothing with it)"""
+
+    def __init__(self, workload, parity_cfgs, with_sample=True):
+        import multiprocessing as mp
+        self.dir = tempfile.mkdtemp(prefix="sa_oracle_")
+        ctx = mp.get_context("spawn")
+        self.procs = []
+        jobs = []
+        if with_sample:
+            jobs.append(("sample", "sample", f"inclusions_{SAMPLE_N_EL}", None))
+        jobs += [("parity", c, pn or workload, m) for (c, pn, m) in PARITY_JOBS if c in parity_cfgs]
+        for j in jobs:
+            pr = ctx.Process(target=_oracle_job, args=(*j, self.dir), daemon=True)
+            pr.start()
+            self.procs.append((j, pr))
+        self.t0 = time.perf_counter()
+
+    def cleanup(self):
+        import shutil
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+    def collect(self, deadline_s):
+        """results of the jobs that finished within deadline_s of their start;
+        the rest are stopped and reported as not finished"""
+        out = []
+        for (j, pr) in self.procs:
+            left = deadline_s - (time.perf_counter() - self.t0)
+            pr.join(timeout=max(0.0, left))
+            if pr.is_alive():
+                pr.terminate()
+                pr.join(timeout=10)
+                out.append({"kind": j[0], "cfg": j[1], "measure": j[3],
+                            "error": f"not finished within the run's {deadline_s:.0f} s oracle budget"})
+                continue
+            f = os.path.join(self.dir, f"{j[0]}_{j[1]}_{j[3] or 'all'}.json")
+            try:
+                with open(f) as fh:
+                    out.append(json.load(fh))
+            except OSError:
+                out.append({"kind": j[0], "cfg": j[1], "measure": j[3], "error": "no result written"})
+        return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def setup_phases(prof, steps):
-    """stream time per setup phase, summed over levels, per step"""
+def setup_phases(prof):
+    """stream time per setup phase, summed over levels"""
     out = {}
     for r in prof:
         if r["kind"].startswith("setup_"):
-            out[r["kind"][6:]] = out.get(r["kind"][6:], 0.0) + r["ms"] / steps
+            out[r["kind"][6:]] = out.get(r["kind"][6:], 0.0) + r["ms"]
     return {k: round(v, 2) for k, v in sorted(out.items(), key=lambda kv: -kv[1])}
+
+
+def fp64_flops(kind, level, nnz0, n0, K):
+    """FP64 FLOPs per launch of a level-0 FP64 kernel: one FMA per stored
+    entry and column plus the row updates"""
+    if level != 0:
+        return None
+    per_row = {"cheb64": 5, "resid64": 1, "cg_spmv": 2}
+    per_row_k = {"bcheb64": 5, "bresid64": 1, "bcg_spmv": 2}
+    if kind in per_row:
+        return 2.0 * nnz0 + per_row[kind] * n0
+    if kind in per_row_k:
+        return K * (2.0 * nnz0 + per_row_k[kind] * n0)
+    return None
+
+
+def rel_err(x, ref):
+    import numpy as np
+    x = np.asarray(x, np.float64)
+    ref = np.asarray(ref, np.float64)
+    d = np.linalg.norm(ref)
+    return float(np.linalg.norm(x - ref) / d) if d > 0 else float(np.linalg.norm(x))
 
 
 def run_ours(args):
     import numpy as np
+
+    ws, rank, local = dist_env()
+    n_el = WORKLOADS[args.workload]
+    # the oracle processes start before the first CUDA call (spawned)
+    jobs = None
+    cfgs = [] if args.no_oracle_parity else [c for c in args.oracle_configs.split(",") if c]
+    if args.no_extras:
+        cfgs = [c for c in cfgs if c == "c5"]
+    if rank == 0 and ws == 1 and (cfgs or not args.no_cpu_baseline):
+        jobs = OracleJobs(args.workload, cfgs, with_sample=not args.no_cpu_baseline)
+
     import torch
 
     import gen
     import paper_2602_05686_gb300 as sa
 
-    ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sa.build()
-    kw, desc = WORKLOADS[args.workload]
-    p = gen.battery_3d(**kw)
-    n = p["n"]
-    dev = {k: torch.from_numpy(np.ascontiguousarray(p[k])).cuda()
-           for k in ("row_ptr", "col", "val", "coords", "tensors", "elem_nodes", "elem_measure")}
-    dprob = dict(p, **dev)
-    b = torch.from_numpy(p["b"]).cuda()
+    t_gen = time.perf_counter()
+    p = gen.inclusions_3d(n_el, nrhs=NRHS)
+    gen_s = time.perf_counter() - t_gen
+    n, nnz0 = int(p["n"]), int(p["nnz"])
+    keys = ("row_ptr", "col", "val")     # what the classical setup reads
+    dprob = dict(p, **{k: torch.from_numpy(np.ascontiguousarray(p[k])).cuda()
+                       for k in keys + ("coords", "tensors", "elem_nodes", "elem_measure")})
+    B = torch.from_numpy(np.ascontiguousarray(p["B"])).cuda()
     stream = torch.cuda.current_stream()
+    units = float(n) * 2 * NRHS    # dof-solves per step: every RHS in both forms
 
     def barrier():
         torch.cuda.synchronize()
@@ -214,36 +405,28 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def one_step(prob, rhs, host=False):
-        """returns per-part times (ms, CUDA events) and solve infos"""
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    def one_step(prob, rhs, host=False, outs=None):
+        """the step; per-part times (ms, CUDA events), solve infos, solutions"""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         ev[0].record(stream)
-        hm = sa.Hierarchy(prob, theta=MAT_THETA, measure="material", precision="fp64", host_inputs=host)
+        h = sa.Hierarchy(prob, theta=CLS_THETA, measure="classical", precision="fp64", host_inputs=host)
         ev[1].record(stream)
-        x64, i64 = hm.solve(rhs, tol=TOL)
+        X64, i64 = h.solve_batch(rhs, out=outs[0] if outs else None)
         ev[2].record(stream)
-        hm.set_precision("fp32")
+        h.set_precision("fp32")
         ev[3].record(stream)
-        x32, i32 = hm.solve(rhs, tol=TOL)
+        X32, i32 = h.solve_batch(rhs, out=outs[1] if outs else None)
         ev[4].record(stream)
-        hm.free()
-        hc = sa.Hierarchy(prob, theta=CLS_THETA, measure="classical", precision="fp64", host_inputs=host)
-        ev[5].record(stream)
-        xc, ic = hc.solve(rhs, tol=TOL)
-        ev[6].record(stream)
-        st = hc.stats()
-        hc.free()
+        st = h.stats()
+        h.free()
         torch.cuda.synchronize()
-        t = [ev[k].elapsed_time(ev[k + 1]) for k in range(6)]
-        parts = dict(material_setup_ms=t[0], material_fp64_solve_ms=t[1], fp32_build_ms=t[2],
-                     material_fp32_solve_ms=t[3], classical_setup_ms=t[4], classical_fp64_solve_ms=t[5])
-        return parts, dict(fp64=i64, fp32=i32, classical=ic), st
+        t = [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+        parts = dict(setup_ms=t[0], fp64_solve_ms=t[1], fp32_build_ms=t[2], fp32_solve_ms=t[3])
+        return parts, dict(fp64=i64, fp32=i32), st, (X64, X32)
 
-    # warm-up
     for _ in range(args.warmup):
-        one_step(dprob, b)
-    # timed region (device-resident inputs): the production path -- CG loops
-    # in CUDA graphs, no per-launch instrumentation
+        one_step(dprob, B)
+    # timed region (device-resident inputs): the production path
     clk = ClockSampler(local)
     clk.start()
     l0 = sa.launch_count()
@@ -251,110 +434,70 @@ def run_ours(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    parts_all, infos = [], None
+    parts_all, infos, hst, sols = [], None, None, None
     for _ in range(args.steps):
-        parts, infos, _ = one_step(dprob, b)
+        parts, infos, hst, sols = one_step(dprob, B)
         parts_all.append(parts)
     t1.record(stream)
     barrier()
     launches = sa.launch_count() - l0
     clocks = clk.stop()
-    ms_total = t0.elapsed_time(t1)
-    ms_step = ms_total / args.steps
-    # the same steps again with every launch bracketed by CUDA events on the
-    # library's stream (host-driven CG iterations, so each launch is seen):
-    # the per-kernel rows, the roofline and the setup phases come from here
+    ms_step = t0.elapsed_time(t1) / args.steps
+    ms_step = reduce_over_ranks(ms_step, ws, "max")        # the slowest replica sets the step time
+    launches = int(reduce_over_ranks(launches, ws, "sum"))  # kernels of all replicas
+    value = units * ws / (ms_step * 1e-3) / 1e6
+
+    # one more step with every launch bracketed by CUDA events on the
+    # library's stream: the kernel table, the roofline, the setup phases
     sa.profile_enable(True)
     barrier()
     t2 = torch.cuda.Event(enable_timing=True)
     t3 = torch.cuda.Event(enable_timing=True)
     t2.record(stream)
-    for _ in range(args.steps):
-        one_step(dprob, b)
+    one_step(dprob, B)
     t3.record(stream)
     barrier()
     prof = sa.profile_read()
     sa.profile_enable(False)
-    ms_step_prof = t2.elapsed_time(t3) / args.steps
-    ms_step = reduce_over_ranks(ms_step, ws, "max")        # the slowest replica sets the step time
-    launches = int(reduce_over_ranks(launches, ws, "sum"))  # kernels of all replicas
+    ms_step_prof = t2.elapsed_time(t3)
+    x64_0 = sols[0][0].cpu().numpy()
+    x32_0 = sols[1][0].cpu().numpy()
+    del sols
 
-    # material hierarchy statistics (untimed)
-    hm = sa.Hierarchy(dprob, theta=MAT_THETA, measure="material")
-    mst = hm.stats()
-
-    # several right-hand sides on the cached hierarchy: K one-vector solves
-    # against one K-column solve (every launch shared), both forms, CUDA events
-    multi = None
-    if not args.no_multi_rhs:
-        # right-hand sides b_c = A x_c of smooth fields x_c (load cases of one
-        # stack: the rough N(0,1) loads do not converge on this operator)
-        import scipy.sparse as sps
-        K = 8
-        A = sps.csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(n, n))
-        X3 = p["coords"].reshape(-1, 3)
-        zn = (X3[:, 2] - X3[:, 2].min()) / np.ptp(X3[:, 2])
-        Bk = torch.from_numpy(np.stack([A @ (np.sin(np.pi * (c + 1) * zn) * (1.0 + 0.25 * c * X3[:, 0]))
-                                        for c in range(K)])).cuda()
-        del A
-        multi = {"rhs": K}
-        for form in ("fp64", "fp32"):
-            hm.set_precision(form)
-            hm.solve(Bk[0].clone())    # warm (graph capture, buffers)
-            hm.solve_batch(Bk[:2])
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record(stream)
-            its1 = [hm.solve(Bk[c].clone())[1]["iters"] for c in range(K)]
-            e[1].record(stream)
-            _, inf = hm.solve_batch(Bk)
-            e[2].record(stream)
-            torch.cuda.synchronize()
-            t1, tk = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
-            multi[form] = {"one_by_one_ms": round(t1, 2), "block_ms": round(tk, 2),
-                           "speedup": round(t1 / tk, 3), "iters": [i["iters"] for i in inf],
-                           "iters_equal": its1 == [i["iters"] for i in inf],
-                           "max_rel_res": max(i["rel_res"] for i in inf)}
-    hm.free()
-
-    # end-to-end through the C ABI with host buffers (copies inside)
+    # end to end through the C ABI from pinned host buffers: the matrix and
+    # the right-hand sides are copied to the device, and the solutions back,
+    # inside the timed region
     e2e = None
     if not args.no_e2e:
-        # the step's inputs in pinned host memory (numpy views of pinned torch
-        # tensors), copied to the device inside the timed region
-        hkeys = ("row_ptr", "col", "val", "coords", "tensors", "elem_nodes", "elem_measure")
-        ph = dict(p, **{k: torch.from_numpy(np.ascontiguousarray(p[k])).pin_memory().numpy() for k in hkeys})
-        bh = torch.from_numpy(p["b"].copy()).pin_memory().numpy()
-        inb = sum(int(np.asarray(p[k]).nbytes) for k in hkeys)
+        ph = dict(p, **{k: torch.from_numpy(np.ascontiguousarray(p[k])).pin_memory().numpy() for k in keys})
+        Bh = torch.from_numpy(np.ascontiguousarray(p["B"])).pin_memory().numpy()
+        outs = (torch.empty(Bh.shape, dtype=torch.float64).pin_memory().numpy(),
+                torch.empty(Bh.shape, dtype=torch.float64).pin_memory().numpy())
+        one_step(ph, Bh, host=True, outs=outs)    # warm
         barrier()
+        reps = max(1, min(args.steps, 2))
         te = time.perf_counter()
-        for _ in range(max(1, min(args.steps, 2))):
-            one_step(ph, bh, host=True)
+        for _ in range(reps):
+            one_step(ph, Bh, host=True, outs=outs)
         barrier()
-        e_ms = (time.perf_counter() - te) * 1000.0 / max(1, min(args.steps, 2))
-        e2e = {"value": round(e_ms / 1000.0, 4), "unit": "s",
-               "h2d_bytes_per_step": 2 * inb + 3 * 2 * n * 8, "d2h_bytes_per_step": 3 * n * 8}
+        e_s = (time.perf_counter() - te) / reps
+        inb = sum(int(np.asarray(p[k]).nbytes) for k in keys)
+        e2e = {"value": round(units / e_s / 1e6, 3), "unit": UNIT, "seconds_per_step": round(e_s, 4),
+               "h2d_bytes_per_step": inb + 2 * 2 * int(Bh.nbytes), "d2h_bytes_per_step": 2 * int(Bh.nbytes)}
+        del ph, Bh, outs
 
-    # roofline of the dominant kernel (largest total time in the timed region):
-    # the HBM floor (algorithmic bytes / measured copy bandwidth) and, for the
-    # FP64 fine-level kernels, the FP64-pipe floor (algorithmic FLOPs / the FP64
-    # peak at the sampled SM clock); the larger floor names the bound
+    # roofline of the dominant kernel (largest total time in the profiled
+    # step): algorithmic bytes per launch / mean CUDA-event duration against
+    # the measured copy bandwidth, with the FP64-pipe floor beside it for the
+    # FP64 fine-level kernels; the larger floor names the bound
     peak, peak_kind = peaks()
     mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
     fp64_peak = N_SM * FP64_FLOP_PER_SM_CYCLE * mhz * 1e6 / 1e12   # TFLOP/s
-    nnz0 = int(p["nnz"])
-
-    def fp64_flops(kind, level):
-        """FP64 FLOPs per launch: one FMA per stored entry plus the row updates"""
-        if level != 0:
-            return None
-        per_row = {"cheb64": 5, "resid64": 1, "cg_spmv": 2}.get(kind)
-        return None if per_row is None else 2.0 * nnz0 + per_row * n
-
     rows = sorted(prof, key=lambda r: -r["ms"])
-    krows = [r for r in rows if r["bytes"] > 0]   # kernels with an algorithmic-bytes model
-    dom = krows[0] if krows else None
+    krows = [r for r in rows if r["bytes"] > 0]
     roof = None
-    if dom:
+    if krows:
+        dom = krows[0]
         per_launch_ms = dom["ms"] / dom["launches"]
         per_launch_bytes = dom["bytes"] / dom["launches"]
         ach = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
@@ -363,7 +506,7 @@ def run_ours(args):
                 "frac": round(ach / peak, 4), "traffic": traffic_for(kname, args.workload),
                 "kernel": kname, "peak_source": peak_kind, "launches": dom["launches"],
                 "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": round(per_launch_ms, 5)}
-        fl = fp64_flops(dom["kind"], dom["level"])
+        fl = fp64_flops(dom["kind"], dom["level"], nnz0, n, NRHS)
         if fl:
             t_hbm = per_launch_bytes / (peak * 1e9)
             t_fp64 = fl / (fp64_peak * 1e12)
@@ -376,43 +519,69 @@ def run_ours(args):
                 roof.update(bound="alu", achieved=roof["fp64_pipe"]["achieved"], peak=roof["fp64_pipe"]["peak"],
                             unit="TFLOP/s", frac=roof["fp64_pipe"]["frac"],
                             peak_source=roof["fp64_pipe"]["peak_source"], hbm=hb)
-    # V-cycle bandwidth per form (all V-cycle kernels; algorithmic bytes / time)
+
+    # V-cycle bandwidth per form (all V-cycle kernels of the profiled step)
     def vgb(kinds):
         sel = [r for r in prof if r["kind"] in kinds]
         ms = sum(r["ms"] for r in sel)
         by = sum(r["bytes"] for r in sel)
-        return round(by / (ms * 1e-3) / 1e9, 1) if ms > 0 else None
+        return {"GBs": round(by / (ms * 1e-3) / 1e9, 1), "frac_of_hbm": round(by / (ms * 1e-3) / 1e9 / peak, 3),
+                "ms": round(ms, 1)} if ms > 0 else None
 
-    vc64 = vgb({"cheb64", "resid64", "restrict64", "prolong64", "first64", "coarse"})
-    vc32 = vgb({"cheb32", "resid32", "restrict32", "prolong32", "first32"})
+    vc64 = vgb({"bcheb64", "bresid64", "brestrict64", "bprolong64", "bfirst64"})
+    vc32 = vgb({"bcheb32", "bresid32", "brestrict32", "bprolong32", "bfirst32"})
     avg = {k: round(statistics.mean(pp[k] for pp in parts_all), 2) for k in parts_all[0]}
 
+    extras = None if args.no_extras else run_extras(sa, torch, dprob)
+
     result = {
-        "metric": METRIC, "value": round(ms_step / 1000.0, 4), "unit": "s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_step, 2), "higher_is_better": False,
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 2), "higher_is_better": True,
         "ms_per_step_instrumented": round(ms_step_prof, 2),
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 inside the mixed V-cycle)",
-        "data": "synthetic (seeded generator; paper's battery meshes are not public)",
-        "config": workload_config(args, ws),
+        "data": "synthetic (seeded generator; the paper's meshes are not public)",
+        "config": workload_config(n_el, ws),
+        "time_to_solution_s": {"step": round(ms_step / 1e3, 4), "setup": round(avg["setup_ms"] / 1e3, 4),
+                               "fp64_solve_8rhs": round(avg["fp64_solve_ms"] / 1e3, 4),
+                               "fp32_solve_8rhs": round((avg["fp32_build_ms"] + avg["fp32_solve_ms"]) / 1e3, 4)},
         "parts_ms": avg,
-        "iters": {"material_fp64": infos["fp64"]["iters"], "material_fp32": infos["fp32"]["iters"],
-                  "classical_fp64": infos["classical"]["iters"]},
-        "rel_res": {k: infos[k]["rel_res"] for k in infos},
-        "hierarchy_material": {"levels": mst["levels"], "n": mst["n"], "op_complexity": round(mst["op_complexity"], 3)},
-        "vcycle_GBs": {"fp64": vc64, "fp32": vc32},
-        "fp32_speedup_vs_fp64_solve": round(avg["material_fp64_solve_ms"] / avg["material_fp32_solve_ms"], 3),
+        "fp32_speedup_vs_fp64_solve": round(avg["fp64_solve_ms"] / (avg["fp32_build_ms"] + avg["fp32_solve_ms"]), 3),
+        "iters": {"fp64": [i["iters"] for i in infos["fp64"]], "fp32": [i["iters"] for i in infos["fp32"]]},
+        "rel_res_max": {"fp64": max(i["rel_res"] for i in infos["fp64"]),
+                        "fp32": max(i["rel_res"] for i in infos["fp32"])},
+        "fp32_vs_fp64_solution_rel_diff_rhs0": rel_err(x32_0, x64_0),
+        "hierarchy": {"levels": hst["levels"], "n": hst["n"], "op_complexity": round(hst["op_complexity"], 4)},
+        "vcycle_bandwidth": {"fp64": vc64, "fp32": vc32},
         "roofline": roof,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": int(launches),
+        "generation_s": round(gen_s, 1),
         "kernel_profile_top": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
-                               for r in krows[:8]],
-        "setup_phases_ms": setup_phases(prof, args.steps),
+                               for r in krows[:10]],
+        "setup_phases_ms": setup_phases(prof),
         "kernel_profile_all": [[r["kind"], r["level"], r["launches"], round(r["ms"], 3)] for r in krows],
-        "multi_rhs": multi,
+        "extras": extras,
     }
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        result["cpu_baseline"] = cpu_baseline(args)
+    if jobs is not None:
+        res = jobs.collect(args.oracle_deadline)
+        sample = next((r for r in res if r["kind"] == "sample"), None)
+        if sample is not None and "seconds" in sample:
+            t = statistics.mean(sample["seconds"])
+            result["cpu_baseline"] = {
+                "value": round(sample["n"] * 2 * NRHS / t / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": (f"measured: the same step (classical setup + 8 FP64 PCG + 8 flexible-CG solves, FP64 "
+                           f"V-cycle) on the inclusions workload at {SAMPLE_N_EL}^3 elements ({sample['n']} dofs), "
+                           f"{t:.2f} s per step, mean of 2 steps, one thread"),
+                "iters_fp64": sample["iters_fp64"], "iters_flexible": sample["iters_flexible"],
+                "host": host_info()}
+        elif sample is not None:
+            result["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                      "sample": sample.get("error", "failed"), "host": host_info()}
+        par = [r for r in res if r["kind"] == "parity"]
+        if par:
+            result["oracle_parity"] = parity_report(par, extras, infos, x64_0, x32_0)
+        jobs.cleanup()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if ws > 1:
@@ -421,40 +590,106 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_extras(sa, torch, c5prob):
+    """the other configurations, one solve each (untimed region, CUDA events):
+    the 2D layered square (c1), the battery stack (c2) and the Voronoi
+    anisotropic cube (c3) with both measures and both forms, and the material
+    measure on the inclusions (both dropping criteria, FP64 form, capped)"""
+    import numpy as np
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    out = {}
+    for cfg in ("c1", "c2", "c3"):
+        p = make_problem(cfg)
+        dp = dict(p, **{k: torch.from_numpy(np.ascontiguousarray(p[k])).cuda()
+                        for k in ("row_ptr", "col", "val", "coords", "tensors", "elem_nodes", "elem_measure")})
+        b = torch.from_numpy(p["b"]).cuda()
+        res = {"dofs": int(p["n"])}
+        for (m, theta, mc) in PARITY[cfg]:
+            h, ts = timed(lambda: sa.Hierarchy(dp, theta=theta, measure=m, precision="fp64", max_coarse=mc))
+            h.solve(b, tol=TOL, check=False)       # first use of a form captures its CG graph
+            (x64, i64), t64 = timed(lambda: h.solve(b, tol=TOL, check=False))
+            h.set_precision("fp32")
+            h.solve(b, tol=TOL, check=False)
+            (x32, i32), t32 = timed(lambda: h.solve(b, tol=TOL, check=False))
+            st = h.stats()
+            h.free()
+            res[m] = {"theta": theta, "setup_ms": round(ts, 2), "fp64_solve_ms": round(t64, 2),
+                      "fp32_solve_ms": round(t32, 2), "fp32_speedup_vs_fp64_solve": round(t64 / t32, 3),
+                      "iters_fp64": i64["iters"], "iters_fp32": i32["iters"], "rel_res_fp64": i64["rel_res"],
+                      "rel_res_fp32": i32["rel_res"], "status_fp64": i64["status"], "status_fp32": i32["status"],
+                      "levels": st["levels"], "op_complexity": round(st["op_complexity"], 4),
+                      "_x64": x64.cpu().numpy(), "_x32": x32.cpu().numpy()}
+        out[cfg] = res
+        del dp, p
+    # the material measure on the inclusions (the paper's measure, both
+    # dropping criteria): FP64 form, capped at 200 iterations
+    res = {}
+    b = c5prob["B"][0]
+    bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    for name, kw in (("pointwise_0.05", dict(theta=MAT_THETA, drop="pointwise")),
+                     ("cut_0.08", dict(theta=0.08, drop="cut"))):
+        h, ts = timed(lambda: sa.Hierarchy(c5prob, measure="material", precision="fp64", maxit=200, **kw))
+        (_, inf), t64 = timed(lambda: h.solve(bt, tol=TOL, check=False))
+        st = h.stats()
+        h.free()
+        res[name] = {"setup_ms": round(ts, 2), "fp64_solve_ms": round(t64, 2), "iters": inf["iters"],
+                     "status": inf["status"], "rel_res": inf["rel_res"], "levels": st["levels"],
+                     "op_complexity": round(st["op_complexity"], 4)}
+    out["c5_material"] = res
+    return out
+
+
+def parity_report(par, extras, infos, x64_0, x32_0):
+    """iteration counts of the full-size oracle solves beside the GPU's, and
+    the GPU solutions' relative error against the oracle's (FP64 form and
+    FP32-V-cycle form)"""
+    import numpy as np
+    rep = {}
+    for r in par:
+        cfg = r["cfg"]
+        if "error" in r:
+            rep.setdefault(cfg, {})[r.get("measure") or "all"] = {"oracle": r["error"]}
+            continue
+        for row in r["rows"]:
+            m = row["measure"]
+            xo = np.load(row["x"])
+            e = {"iters_oracle": row["iters"], "oracle_status": row["status"], "oracle_rel_res": row["rel_res"],
+                 "oracle_setup_s": row["setup_s"], "oracle_solve_s": row["solve_s"]}
+            if cfg == "c5":
+                e.update(iters=infos["fp64"][0]["iters"], iters_fp32=infos["fp32"][0]["iters"],
+                         err_fp64_vs_oracle=rel_err(x64_0, xo), err_fp32_vs_oracle=rel_err(x32_0, xo))
+            elif extras and cfg in extras and m in extras[cfg]:
+                g = extras[cfg][m]
+                e.update(iters=g["iters_fp64"], iters_fp32=g["iters_fp32"],
+                         err_fp64_vs_oracle=rel_err(g["_x64"], xo), err_fp32_vs_oracle=rel_err(g["_x32"], xo))
+            e["iters_within_1"] = abs(e.get("iters", -99) - row["iters"]) <= 1 if "iters" in e else None
+            rep.setdefault(cfg, {})[m] = e
+            try:
+                os.remove(row["x"])
+            except OSError:
+                pass
+    if extras:
+        for cfg in ("c1", "c2", "c3"):
+            for m in list(extras.get(cfg, {})):
+                if isinstance(extras[cfg][m], dict):
+                    extras[cfg][m].pop("_x64", None)
+                    extras[cfg][m].pop("_x32", None)
+    return rep
+
+
 # ---------------------------------------------------------------------------
-# the oracle (CPU) on a bounded sample
+# reference arm: the oracle on a bounded sample, same metric and unit
 # ---------------------------------------------------------------------------
-SAMPLE = dict(nx=48, ny=48, nz=96)
-
-
-def oracle_step(p):
-    """the same step as the GPU arm, run by the serial CPU oracle; seconds"""
-    import oracle
-    t = time.perf_counter()
-    h = oracle.Hierarchy(p, MAT_THETA, "material")
-    _, a = h.solve(p["b"], tol=TOL)
-    _, f = h.solve(p["b"], tol=TOL, flexible=True)
-    del h
-    h = oracle.Hierarchy(p, CLS_THETA, "classical")
-    _, c = h.solve(p["b"], tol=TOL)
-    del h
-    return time.perf_counter() - t, (a["iters"], f["iters"], c["iters"])
-
-
-def cpu_baseline(args, steps=1):
-    import gen
-    import oracle
-    oracle.build()
-    p = gen.battery_3d(**SAMPLE)
-    full_n = WORKLOADS[args.workload][0]
-    nfull = (full_n["nx"] + 1) * (full_n["ny"] + 1) * (full_n["nz"] + 1)
-    ts = [oracle_step(p)[0] for _ in range(steps)]
-    t = statistics.mean(ts)
-    return {"value": round(t * nfull / p["n"], 3), "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"full step on the battery stack 48x48x96 ({p['n']} dofs, {t:.2f} s), scaled by dofs x"
-                       f"{nfull / p['n']:.1f} to the {nfull}-dof workload (assumes O(n) cost)")}
-
-
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -462,29 +697,34 @@ def run_reference(args):
     import gen
     import oracle
     oracle.build()
-    p = gen.battery_3d(**SAMPLE)
-    kw = WORKLOADS[args.workload][0]
-    nfull = (kw["nx"] + 1) * (kw["ny"] + 1) * (kw["nz"] + 1)
+    gen.build()
+    n_el = WORKLOADS[args.workload]
+    p = gen.inclusions_3d(SAMPLE_N_EL, nrhs=NRHS)
     for _ in range(args.warmup):
         oracle_step(p)
-    ts, its = [], None
+    ts, it64, itf = [], None, None
     for _ in range(args.steps):
-        t, its = oracle_step(p)
+        t, it64, itf = oracle_step(p)
         ts.append(t)
-    sec = statistics.mean(ts) * nfull / p["n"]
-    out = {"impl": "reference", "metric": METRIC, "value": round(sec, 3), "unit": "s", "n_gpus": ws,
+    sec = statistics.mean(ts)
+    val = p["n"] * 2 * NRHS / sec / 1e6
+    sample = (f"measured: the same step (classical setup + 8 FP64 PCG + 8 flexible-CG solves, FP64 V-cycle) on the "
+              f"inclusions workload at {SAMPLE_N_EL}^3 elements ({p['n']} dofs) per step, one thread")
+    out = {"impl": "reference", "metric": METRIC, "value": round(val, 5), "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1000, 1),
-           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded generator; paper's battery meshes are not public)",
-           "config": workload_config(args, ws),
-           "iters_sample": {"material_fp64": its[0], "material_flexible": its[1], "classical_fp64": its[2]},
-           "cpu_baseline": {"value": round(sec, 3), "unit": "s", "cores": 1, "kind": "oracle",
-                            "sample": f"battery stack 48x48x96 ({p["n"]} dofs) per step, scaled by dofs to "
-                                      f"{nfull} dofs"},
-           "e2e": {"value": round(sec, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator; the paper's meshes are not public)",
+           "config": workload_config(n_el, ws),
+           "iters_sample": {"fp64": it64, "flexible": itf},
+           "cpu_baseline": {"value": round(val, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "host": host_info()},
+           "e2e": {"value": round(val, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# other modes
+# ---------------------------------------------------------------------------
 def run_serving(args):
     """Serving workload: seeded Poisson-arrival requests on 2D/3D layered
     operators (contrast 10^U(2,10)), several right-hand sides per operator with
@@ -593,10 +833,15 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="battery_128x128x256", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="inclusions_320", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-multi-rhs", action="store_true")
+    ap.add_argument("--no-oracle-parity", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--oracle-configs", default="c1,c2,c3,c5",
+                    help="configurations the oracle solves at full size beside the GPU (c5 = the workload)")
+    ap.add_argument("--oracle-deadline", type=float, default=1080.0,
+                    help="seconds after the start of the run within which the oracle jobs must finish")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--slots", type=int, default=4)

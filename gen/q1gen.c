@@ -142,6 +142,33 @@ static void eliminate_dirichlet(int64_t n, int64_t* row_ptr, int32_t* col, doubl
  *   b[n], coords[n*dim], elem_nodes[n_e * 2^dim], elem_measure[n_e]
  * Returns the number of stored entries after elimination (<= nnz_max), or -1.
  */
+/* Element matrices depend only on the box edge lengths and the tensor, and a
+ * workload has few distinct pairs (two tensors on a uniform grid for the
+ * inclusions, one per layer for the stacks), so they are memoised in a small
+ * hash table keyed by the exact bytes of (h, K): a hit returns the matrix the
+ * same routine computed for the same inputs, bit for bit. */
+#define EM_SLOTS 256
+typedef struct { int used; double key[9]; double Ke[64]; } em_slot_t;
+
+static void elem_matrix_cached(em_slot_t* cache, int dim, const double h[3], const double* K, double* Ke) {
+  const int kp = (dim == 3) ? 6 : 3, nl = 1 << dim;
+  double key[9] = {0};
+  key[0] = h[0]; key[1] = h[1]; key[2] = h[2];
+  memcpy(key + 3, K, sizeof(double) * (size_t)kp);
+  uint64_t hs = 1469598103934665603ull;
+  const unsigned char* kb = (const unsigned char*)key;
+  for (size_t i = 0; i < sizeof(key); ++i) { hs ^= kb[i]; hs *= 1099511628211ull; }
+  em_slot_t* sl = &cache[hs & (EM_SLOTS - 1)];
+  if (sl->used && memcmp(sl->key, key, sizeof(key)) == 0) {
+    memcpy(Ke, sl->Ke, sizeof(double) * (size_t)(nl * nl));
+    return;
+  }
+  elem_matrix(dim, h, K, Ke);
+  sl->used = 1;
+  memcpy(sl->key, key, sizeof(key));
+  memcpy(sl->Ke, Ke, sizeof(double) * (size_t)(nl * nl));
+}
+
 int64_t q1_assemble(int dim, int nx, int ny, int nz,
                     const double* xc, const double* yc, const double* zc,
                     const double* elem_K, const double* elem_f,
@@ -189,6 +216,8 @@ int64_t q1_assemble(int dim, int nx, int ny, int nz,
       }
   const int ez_n = (dim == 3) ? nz : 1;
   double Ke[64];
+  em_slot_t* cache = (em_slot_t*)calloc(EM_SLOTS, sizeof(em_slot_t));
+  if (!cache) return -1;
   for (int ez = 0; ez < ez_n; ++ez)
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
@@ -196,7 +225,7 @@ int64_t q1_assemble(int dim, int nx, int ny, int nz,
         double h[3] = {xc[ex + 1] - xc[ex], yc[ey + 1] - yc[ey], (dim == 3) ? zc[ez + 1] - zc[ez] : 1.0};
         double meas = h[0] * h[1] * ((dim == 3) ? h[2] : 1.0);
         elem_measure[e] = meas;
-        elem_matrix(dim, h, elem_K + e * kp, Ke);
+        elem_matrix_cached(cache, dim, h, elem_K + e * kp, Ke);
         double fe = elem_f ? elem_f[e] * meas / (double)nl : 0.0;
         for (int a = 0; a < nl; ++a) {
           int ia = ex + (a & 1), ja = ey + ((a >> 1) & 1), ka = (dim == 3) ? ez + ((a >> 2) & 1) : 0;
@@ -210,6 +239,7 @@ int64_t q1_assemble(int dim, int nx, int ny, int nz,
           }
         }
       }
+  free(cache);
   if (dir_mask) eliminate_dirichlet(n, row_ptr, col, val, b, dir_mask, dir_val);
   return row_ptr[n];
 }

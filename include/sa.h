@@ -352,7 +352,11 @@ int sa_strength_material_noalloc(int dim, int64_t n, int64_t nnz, const int64_t*
  * 13 nodal tensors, 14 strength, 15 filtered graph, 16 MIS-2, 17
  * aggregation, 18 filtered matrix, 19 omega, 20 smoothed P, 21 transpose,
  * 22 Galerkin product, 23 coarse aux data, 24 Chebyshev bounds, 25 dense
- * coarse factor, 26 SELL packing), level, launches, total milliseconds, and
+ * coarse factor, 26 SELL packing, 27 Galerkin A*P, 28 Galerkin R*(AP); the
+ * K-column kernels of sa_solve_batch: 29-33 FP64 Chebyshev step, residual,
+ * restriction, prolongation, first step, 34 dense coarse solve, 35-39 the
+ * same five in FP32, 40 outer FP64 product with the p.q partials), level,
+ * launches, total milliseconds, and
  * total algorithmic bytes (bytes the kernel must move at least once; 0 for
  * the setup phases).  *rows receives the number of
  * rows available.  Host-side timing arrays, any may be NULL.

@@ -266,11 +266,13 @@ class Hierarchy:
         return x, dict(status=int(st), iters=info.iters, rel_res=info.rel_res_true, setup_ms=info.setup_ms,
                        solve_ms=info.solve_ms)
 
-    def solve_batch(self, B, X0=None, tol=1e-8, check=True):
+    def solve_batch(self, B, X0=None, tol=1e-8, check=True, out=None):
         """k right-hand sides at once (sa_solve_batch: up to 8 columns share every
         launch; each column ends bitwise where solve() on it ends).  B: (k, n)
         CUDA tensor (float64) or numpy array; returns (X of the same kind,
-        list of per-column info dicts)."""
+        list of per-column info dicts).  Host path: `out` (a C-contiguous
+        float64 (k, n) numpy array, e.g. a view of pinned memory) receives X;
+        it is zeroed first unless X0 is given."""
         torch = self.torch
         if isinstance(B, torch.Tensor):
             B = B.to(device="cuda", dtype=torch.float64).contiguous()
@@ -281,7 +283,13 @@ class Hierarchy:
         else:
             B = np.ascontiguousarray(B, np.float64)
             k = int(B.shape[0])
-            X = np.zeros_like(B) if X0 is None else np.array(X0, np.float64)
+            if out is not None:
+                if out.shape != B.shape or out.dtype != np.float64 or not out.flags.c_contiguous:
+                    raise ValueError("solve_batch: out must be a C-contiguous float64 array shaped like B")
+                X = out
+                X[...] = 0.0 if X0 is None else X0
+            else:
+                X = np.zeros_like(B) if X0 is None else np.array(X0, np.float64)
             bp, xp = B.ctypes.data, X.ctypes.data
         infos = (SolveInfo * max(k, 1))()
         st = lib().sa_solve_batch(self.h, k, bp, xp, float(tol), infos)
@@ -375,7 +383,9 @@ PROFILE_KINDS = ["cheb64", "resid64", "restrict64", "prolong64", "first64", "cg_
                  "cheb32", "resid32", "restrict32", "prolong32", "first32",
                  "setup_nodal", "setup_strength", "setup_graph", "setup_mis2", "setup_aggregate", "setup_filter",
                  "setup_omega", "setup_smooth_p", "setup_transpose", "setup_galerkin", "setup_aux",
-                 "setup_cheb_bounds", "setup_dense", "setup_sell", "setup_galerkin_ap", "setup_galerkin_rap"]
+                 "setup_cheb_bounds", "setup_dense", "setup_sell", "setup_galerkin_ap", "setup_galerkin_rap",
+                 "bcheb64", "bresid64", "brestrict64", "bprolong64", "bfirst64", "bcoarse",
+                 "bcheb32", "bresid32", "brestrict32", "bprolong32", "bfirst32", "bcg_spmv"]
 
 
 def profile_enable(on=True):

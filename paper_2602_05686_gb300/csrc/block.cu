@@ -7,6 +7,7 @@
 // goes through the same row update, so a column equals the one-vector kernel
 // bitwise.
 #include "common.cuh"
+#include "profile.cuh"
 #include "solve.cuh"
 #include "vcycle.cuh"
 #include "vkern.cuh"
@@ -275,17 +276,33 @@ static int block_alloc(Alloc& al, VHier<T>* m) {
   return SA_OK;
 }
 
-// the cycle of mv() (vcycle.cu) on K columns
+// one profiled launch (CUDA events around it when profiling is on)
+#define BPROF(kind, level, bytes, launch)               \
+  do {                                                  \
+    int _pi = prof_begin(st, (kind), (level), (bytes)); \
+    launch;                                             \
+    prof_end(st, _pi);                                  \
+  } while (0)
+
+// the cycle of mv() (vcycle.cu) on K columns.  Algorithmic bytes of a
+// K-column launch: the matrix once, each vector element K times.
 template <typename T>
 static int mv_block(VHier<T>* m, cudaStream_t st, int l, int K, const double* r64, T** xo) {
+  constexpr bool F64 = sizeof(T) == 8;
+  const int K_CHEB = F64 ? PK_B_CHEB64 : PK_B_CHEB32, K_RES = F64 ? PK_B_RESID64 : PK_B_RESID32;
+  const int K_RST = F64 ? PK_B_RESTRICT64 : PK_B_RESTRICT32, K_PRL = F64 ? PK_B_PROLONG64 : PK_B_PROLONG32;
+  const int K_FST = F64 ? PK_B_FIRST64 : PK_B_FIRST32;
+  const double S = sizeof(T);
   VLevel<T>* L = m->lev[l];
   const int nl = (int)m->lev.size();
   const int64_t n = L->n, nk = n * K;
   if (l == nl - 1) {
+    int pi = prof_begin(st, PK_B_COARSE, l, 8.0 * n * n + 48.0 * n * K);
     k_bcoarse_in<T><<<g256(nk), 256, 0, st>>>(n, K, L->kb.p, L->sq.p, m->kct.p);
     SA_LAUNCHED();
     SA_TRY(launch_coarse_solve_block(st, m->cf, K, m->kct.p, m->kcs.p, m->kcy.p, m->kcx.p));
     k_bcoarse_out<T><<<g256(nk), 256, 0, st>>>(n, K, m->kcx.p, L->sq.p, L->kx.p);
+    prof_end(st, pi);
     SA_LAUNCHED();
     *xo = L->kx.p;
     return SA_OK;
@@ -296,22 +313,29 @@ static int mv_block(VHier<T>* m, cudaStream_t st, int l, int K, const double* r6
   T* xa = L->kx.p;
   T* xb = L->kx2.p;
   const Mat<T>& A = L->A;
-  if (l == 0) k_bvc_fine_in<T><<<g256(nk), 256, 0, st>>>(n, K, r64, m->s0.p, (T)(1.0 / th), L->kb.p, xa, L->kd.p);
-  else k_bvc_first<T><<<g256(nk), 256, 0, st>>>(nk, L->kb.p, (T)(1.0 / th), xa, L->kd.p);
+  if (l == 0) {
+    BPROF(K_FST, l, 8.0 * K * n + 8.0 * n + 3.0 * S * K * n,
+          (k_bvc_fine_in<T><<<g256(nk), 256, 0, st>>>(n, K, r64, m->s0.p, (T)(1.0 / th), L->kb.p, xa, L->kd.p)));
+  } else {
+    BPROF(K_FST, l, 3.0 * S * K * n,
+          (k_bvc_first<T><<<g256(nk), 256, 0, st>>>(nk, L->kb.p, (T)(1.0 / th), xa, L->kd.p)));
+  }
   SA_LAUNCHED();
+  const double b_chebK = b_mat(A) + 5.0 * S * K * n;
   double rho = 1.0 / s1;
   for (int q = 1; q < deg; ++q) {
     double rn = 1.0 / (2.0 * s1 - rho);
-    LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, L->kd.p, (T)(rn * rho), (T)(2.0 * rn / de), 0);
+    BPROF(K_CHEB, l, b_chebK,
+          LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, L->kd.p, (T)(rn * rho), (T)(2.0 * rn / de), 0));
     T* t = xa; xa = xb; xb = t;
     rho = rn;
   }
   VLevel<T>* C = m->lev[l + 1];
-  LAUNCH_BMAT(k_bvc_residual, A, st, K, L->kb.p, xa, L->kr.p);
-  LAUNCH_BMAT(k_bvc_spmv, L->R, st, K, L->kr.p, C->kb.p);
+  BPROF(K_RES, l, b_mat(A) + 3.0 * S * K * n, LAUNCH_BMAT(k_bvc_residual, A, st, K, L->kb.p, xa, L->kr.p));
+  BPROF(K_RST, l, b_mat(L->R) + S * K * (n + C->n), LAUNCH_BMAT(k_bvc_spmv, L->R, st, K, L->kr.p, C->kb.p));
   T* xc = nullptr;
   SA_TRY(mv_block(m, st, l + 1, K, nullptr, &xc));
-  LAUNCH_BMAT(k_bvc_spmv_add, L->P, st, K, xc, xa);
+  BPROF(K_PRL, l, b_mat(L->P) + S * K * (C->n + 2.0 * n), LAUNCH_BMAT(k_bvc_spmv_add, L->P, st, K, xc, xa));
   rho = 1.0 / s1;
   for (int q = 0; q < deg; ++q) {
     int first = (q == 0);
@@ -323,9 +347,12 @@ static int mv_block(VHier<T>* m, cudaStream_t st, int l, int K, const double* r6
       c2 = (T)(2.0 * rn / de);
     }
     if (l == 0 && q == deg - 1) {
-      LAUNCH_BMAT(k_bvc_cheb_out, A, st, K, L->kb.p, xa, L->kd.p, c1, c2, first, m->s0.p, m->kz.p);
+      // the last step reads b, x, d and the scaling, and writes the FP64
+      // output block in place of x and d
+      BPROF(K_CHEB, l, b_mat(A) + 3.0 * S * K * n + 8.0 * K * n + 8.0 * n,
+            LAUNCH_BMAT(k_bvc_cheb_out, A, st, K, L->kb.p, xa, L->kd.p, c1, c2, first, m->s0.p, m->kz.p));
     } else {
-      LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, L->kd.p, c1, c2, first);
+      BPROF(K_CHEB, l, b_chebK, LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, L->kd.p, c1, c2, first));
       T* t = xa; xa = xb; xb = t;
     }
     if (!first) rho = rn;
@@ -420,10 +447,15 @@ int launch_bsell_spmv_dot(cudaStream_t st, const Sell<double>& A, int K, const d
                           int* nparts) {
   *nparts = (int)g256(A.n);
   const MatView<double> mv = sell_view(A);
+  // the matrix once; P read and Q written for each of the K columns
+  const double bytes = (8.0 + A.idx_bytes()) * A.nnz + 8.0 * (A.nslices + 1) + (A.idx16 ? 4.0 * A.nslices : 0.0) +
+                       16.0 * K * A.n;
+  if (K != 2 && K != 4 && K != 8) return SA_ERR_INVALID_ARG;
+  const int pi = prof_begin(st, PK_B_CG_SPMV, 0, bytes);
   if (K == 2) k_bsell_spmv_dot<2><<<g256(A.n), 256, 0, st>>>(mv, P, Q, part);
   else if (K == 4) k_bsell_spmv_dot<4><<<g256(A.n), 256, 0, st>>>(mv, P, Q, part);
-  else if (K == 8) k_bsell_spmv_dot<8><<<g256(A.n), 256, 0, st>>>(mv, P, Q, part);
-  else return SA_ERR_INVALID_ARG;
+  else k_bsell_spmv_dot<8><<<g256(A.n), 256, 0, st>>>(mv, P, Q, part);
+  prof_end(st, pi);
   SA_LAUNCHED();
   return SA_OK;
 }

@@ -37,7 +37,20 @@ enum ProfKind {
   PK_S_SELL = 26,      // a15 SELL packing of the scaled hierarchy
   PK_S_RAP_AP = 27,    // part of PK_S_RAP: the product A P
   PK_S_RAP_RAP = 28,   // part of PK_S_RAP: R (A P) and the mirror of its upper triangle
-  PK_NKINDS = 29
+  // the multi-right-hand-side (K-column) kernels of block.cu and the block CG
+  PK_B_CHEB64 = 29,
+  PK_B_RESID64 = 30,
+  PK_B_RESTRICT64 = 31,
+  PK_B_PROLONG64 = 32,
+  PK_B_FIRST64 = 33,
+  PK_B_COARSE = 34,    // dense coarse solve on K columns (either form)
+  PK_B_CHEB32 = 35,
+  PK_B_RESID32 = 36,
+  PK_B_RESTRICT32 = 37,
+  PK_B_PROLONG32 = 38,
+  PK_B_FIRST32 = 39,
+  PK_B_CG_SPMV = 40,   // Q = A P on K columns with the p.q partials (FP64 SELL)
+  PK_NKINDS = 41
 };
 
 bool prof_on();

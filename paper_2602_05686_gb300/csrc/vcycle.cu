@@ -417,21 +417,6 @@ __global__ void k_coarse_out(int64_t n, const double* __restrict__ x, const doub
 // the cycle
 // ---------------------------------------------------------------------------
 
-// algorithmic bytes: S-byte value + int32 column per stored entry of the
-// unpadded matrix, 8-byte slice offsets, each vector element once
-template <typename T>
-static double b_ptr(const Mat<T>& M) {  // row-pointer or slice-offset (+ slice base) bytes
-  if (M.sw != 0) return 8.0 * (M.n + 1);
-  return 8.0 * (M.nslices + 1) + (M.sell.idx16 ? 4.0 * M.nslices : 0.0);
-}
-template <typename T>
-static double b_idx(const Mat<T>& M) { return M.sw == 0 ? M.sell.idx_bytes() : 4.0; }
-template <typename T>
-static double b_cheb(const VLevel<T>* L) {
-  const double S = sizeof(T);
-  return (S + b_idx(L->A)) * L->A.nnz + b_ptr(L->A) + 5.0 * S * L->n;
-}
-
 #define PROFK(kind, level, bytes, launch)               \
   do {                                                  \
     int _pi = prof_begin(st, (kind), (level), (bytes)); \

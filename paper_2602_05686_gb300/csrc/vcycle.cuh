@@ -78,6 +78,25 @@ struct VHier {
   Buf<double> kz, kct, kcs, kcy, kcx;   // k-column output and coarse vectors
 };
 
+// algorithmic bytes: S-byte value + int32 (or 16-bit) column per stored entry
+// of the unpadded matrix, 8-byte row pointers or slice offsets (+ slice
+// bases), each vector element once
+template <typename T>
+inline double b_ptr(const Mat<T>& M) {  // row-pointer or slice-offset (+ slice base) bytes
+  if (M.sw != 0) return 8.0 * (M.n + 1);
+  return 8.0 * (M.nslices + 1) + (M.sell.idx16 ? 4.0 * M.nslices : 0.0);
+}
+template <typename T>
+inline double b_idx(const Mat<T>& M) { return M.sw == 0 ? M.sell.idx_bytes() : 4.0; }
+template <typename T>
+inline double b_mat(const Mat<T>& M) { return (sizeof(T) + b_idx(M)) * M.nnz + b_ptr(M); }
+template <typename T>
+inline double b_cheb(const VLevel<T>* L) {
+  const double S = sizeof(T);
+  return (S + b_idx(L->A)) * L->A.nnz + b_ptr(L->A) + 5.0 * S * L->n;
+}
+
+
 // SELL-32 copy with values left_i * a_ij * right_j (scale vectors may be NULL = 1)
 template <typename T>
 int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
