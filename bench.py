@@ -68,9 +68,20 @@ def workload_desc(n_el):
             f"u=0 on x=0, {NRHS} RHS ~ N(0,1)")
 
 
+def inclusions_nnz(n_el):
+    """stored entries of the inclusions matrix: the full trilinear pattern,
+    prod over the axes of (3N - 2) with N = n_el + 1 nodes per axis, less the
+    off-diagonals of the Dirichlet rows on x = 0 and the entries of their
+    neighbours' rows in the eliminated columns"""
+    N = n_el + 1
+    s = 3 * N - 2
+    return s ** 3 - 3 * s ** 2 + N ** 2
+
+
 def workload_config(n_el, ws):
     """the `config` object of the JSON line (both arms)"""
-    return {"workload": workload_desc(n_el), "dofs": (n_el + 1) ** 3, "rhs": NRHS, "measure": "classical",
+    return {"workload": workload_desc(n_el), "dofs": (n_el + 1) ** 3, "nnz": inclusions_nnz(n_el), "rhs": NRHS,
+            "measure": "classical",
             "theta": CLS_THETA, "tol": TOL, "forms": "FP64 PCG and FP32-V-cycle FCG, 8 RHS per block",
             "cheb_degree": 2, "max_coarse": 5000, "l2": "inputs larger than L2 (no flush)",
             "parallelism": f"replicas x{ws}"}

@@ -123,12 +123,12 @@ def test_annulus_trends_against_table1(orc, gen_mod):
 
 
 def test_bench_config_nnz_closed_form(gen_mod):
-    """the bench's config reports the battery stack's stored entries from a
+    """the bench's config reports the inclusions matrix's stored entries from a
     closed form (the reference arm does not assemble the full matrix)"""
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
-    for nx, ny, nz in ((4, 4, 8), (8, 6, 16), (16, 16, 32)):
-        p = gen_mod.battery_3d(nx, ny, nz)
-        assert bench.battery_nnz(nx, ny, nz) == p["nnz"]
-    assert bench.battery_nnz(128, 128, 256) == 113128957
+    for n_el in (4, 7, 16):
+        p = gen_mod.inclusions_3d(n_el, rmin=1.0, rmax=2.0, nrhs=1)
+        assert bench.inclusions_nnz(n_el) == p["nnz"]
+    assert bench.inclusions_nnz(320) == 884836159
