@@ -745,9 +745,13 @@ def run_serving(args):
     import torch
 
     import gen
-    from paper_2602_05686_gb300.serving import Request, Server
+    from paper_2602_05686_gb300.serving import Request, Server, gather_stats, partition
 
-    torch.cuda.set_device(0)
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     nreq = args.requests
     ops, reqs = gen.serving_requests(nreq, seed=11, max2d=args.max2d, max3d=args.max3d)
     t = time.perf_counter()
@@ -765,22 +769,31 @@ def run_serving(args):
         return dict(theta=0.05, measure="material", precision="fp32", max_coarse=5000)
 
     def run(scale, realtime):
+        """all requests at the given arrival-time scale; under torchrun each
+        rank serves the operators placed on it and the stats are gathered"""
         srv = Server(lambda op: probs[op], options, slots=args.slots, hbm_budget=args.hbm_gb << 30)
         rs, tt = [], 0.0
         for k, r in enumerate(reqs):
             tt += r["gap"] * scale
             rs.append(Request(rid=k, op=r["op"], arrival=tt, rhs=rhs[k]))
-        out = srv.serve(rs, realtime=realtime)
+        mine, _ = partition(rs, srv._estimate, rank, ws) if ws > 1 else (rs, None)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        local_out = srv.serve(mine, realtime=realtime)
         srv.close()
-        return out, rs
+        out = gather_stats(local_out, ws)
+        return out, mine
 
     warm, _ = run(0.0, False)
     rate = 0.8 * warm["throughput_rps"]
     out, rs = run(1.0 / rate, True)
     iters = [r.info.get("iters", 0) for r in rs]
+    if rank != 0:
+        return
     res = {"metric": "serving latency p50/p99 (continuous batching, cached hierarchies)",
            "value": round(out["p99_s"], 4), "unit": "s (p99 latency)", "higher_is_better": False,
-           "n_gpus": 1, "p50_s": round(out["p50_s"], 4), "p99_s": round(out["p99_s"], 4),
+           "n_gpus": ws, "per_gpu_requests": out.get("per_device_requests"), "p50_s": round(out["p50_s"], 4), "p99_s": round(out["p99_s"], 4),
            "throughput_rps": round(out["throughput_rps"], 2), "arrival_rate_rps": round(rate, 2),
            "warmup_throughput_rps": round(warm["throughput_rps"], 2), "requests": nreq, "operators": len(ops),
            "slots": args.slots, "setups": out["setups"], "cache_hits": out["hits"], "evictions": out["evictions"],

@@ -24,6 +24,14 @@ Results do not depend on the schedule: every kernel of the library is
 deterministic and a column of a multi-right-hand-side solve equals the
 one-vector solve bitwise, so a request solved alone and in the mix gives
 bit-identical solutions.
+
+Several GPUs serve as replicas: each operator is placed on one device (the
+one with the least committed bytes when the operator first arrives, by the
+ledger's estimate), every device runs its own Server (slots, streams,
+ledger, cache), and the requests of an operator always go to its device.
+MultiServer does this in one process; under torch.distributed each rank
+serves the operators placed on it (`partition`) and the latencies are
+gathered on the host (`gather_stats`), the only exchange between replicas.
 """
 from __future__ import annotations
 
@@ -35,6 +43,12 @@ import statistics
 import threading
 import time
 from dataclasses import dataclass, field
+
+
+def _pct(sorted_vals, q):
+    if not sorted_vals:
+        return 0.0
+    return sorted_vals[min(len(sorted_vals) - 1, int(round(q * (len(sorted_vals) - 1))))]
 
 
 @dataclass
@@ -65,7 +79,10 @@ class Server:
     make_problem(op) -> problem dict; options(op) -> Hierarchy keyword args."""
 
     def __init__(self, make_problem, options, slots=4, hbm_budget=64 << 30, tol=1e-8, hierarchy_factory=None,
-                 stream_factory=None, store_dir=None, store_key=None, hierarchy_loader=None, batch=8):
+                 stream_factory=None, store_dir=None, store_key=None, hierarchy_loader=None, batch=8, device=None):
+        # device: the CUDA device this server's slots run on (made current in
+        # every slot thread); None keeps the caller's current device
+        self.device = device
         if hierarchy_factory is None:
             from .api import Hierarchy as hierarchy_factory
         if hierarchy_loader is None and store_dir is not None:
@@ -200,6 +217,9 @@ class Server:
 
     def _run(self, job, slot, t0):
         """one job: requests of one operator, solved together"""
+        if self.device is not None:
+            import torch
+            torch.cuda.set_device(self.device)
         stream = self.streams[slot]
         req = job[0]
         with self._ctx(stream):
@@ -302,14 +322,110 @@ class Server:
         lat.sort()
 
         def pct(q):
-            return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+            return _pct(lat, q)
 
         return dict(requests=len(requests), wall_s=wall, throughput_rps=len(requests) / wall,
                     p50_s=pct(0.50), p99_s=pct(0.99), mean_s=statistics.mean(lat), **self.stats,
-                    failed=sum(1 for r in requests if r.status not in (0,)))
+                    failed=sum(1 for r in requests if r.status not in (0,)), latencies=lat)
 
     def close(self):
         for e in self.cache.values():
             e.h.free()
         self.cache.clear()
         self.committed = 0
+
+
+# ---------------------------------------------------------------------------
+# several GPUs: replicas with operator placement
+# ---------------------------------------------------------------------------
+def place_operators(requests, estimate, ndev):
+    """Deterministic placement of operators on ndev devices: operators are
+    taken in the order of their first arrival (ties by operator id) and each
+    goes to the device with the least committed bytes so far (ties: lowest
+    index), committing estimate(op) bytes there.  Every process that computes
+    it from the same request list gets the same map.  Returns (op -> device,
+    committed bytes per device)."""
+    first = {}
+    for r in sorted(requests, key=lambda r: (r.arrival, r.rid)):
+        first.setdefault(r.op, r.arrival)
+    committed = [0] * max(1, int(ndev))
+    place = {}
+    for op in sorted(first, key=lambda o: (first[o], o)):
+        d = min(range(len(committed)), key=lambda k: (committed[k], k))
+        place[op] = d
+        committed[d] += int(estimate(op))
+    return place, committed
+
+
+def partition(requests, estimate, rank, world):
+    """the requests this rank serves: those of the operators placed on it"""
+    place, _ = place_operators(requests, estimate, world)
+    return [r for r in requests if place[r.op] == rank], place
+
+
+def merge_stats(parts):
+    """one latency report from per-device serve() results (each with its
+    `latencies`): percentiles over all requests, throughput over the slowest
+    device's wall time, counters summed"""
+    lat = sorted(x for p in parts for x in p["latencies"])
+    wall = max(p["wall_s"] for p in parts)
+    out = dict(requests=len(lat), wall_s=wall, throughput_rps=len(lat) / wall if wall > 0 else 0.0,
+               p50_s=_pct(lat, 0.50), p99_s=_pct(lat, 0.99), mean_s=statistics.mean(lat) if lat else 0.0,
+               devices=len(parts), per_device_requests=[p["requests"] for p in parts],
+               per_device_peak_committed=[p["peak_committed"] for p in parts])
+    for k in ("admitted", "setups", "hits", "evictions", "loads", "stores", "jobs", "batched", "failed"):
+        out[k] = sum(p.get(k, 0) for p in parts)
+    return out
+
+
+def gather_stats(local, world):
+    """the per-rank serve() results gathered on every rank (host objects over
+    the default process group), merged"""
+    if world <= 1:
+        return merge_stats([local])
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, local)
+    return merge_stats(parts)
+
+
+class MultiServer:
+    """Replicas on several devices in one process: operators are placed by
+    place_operators on the ledgers' estimates, each device runs its own
+    Server (own slots, streams, ledger of hbm_budget bytes and cache), and
+    serve() runs the devices' request streams concurrently."""
+
+    def __init__(self, make_problem, options, devices, slots=4, hbm_budget=64 << 30, server_factory=None, **kw):
+        self.devices = list(devices)
+        make = server_factory or Server
+        self.servers = []
+        for d in self.devices:
+            extra = dict(kw)
+            if "stream_factory" not in extra and d is not None:
+                import torch
+                extra["stream_factory"] = (lambda dev=d: torch.cuda.Stream(device=dev))
+            self.servers.append(make(make_problem, options, slots=slots, hbm_budget=hbm_budget, device=d, **extra))
+        self.placement = {}
+
+    def serve(self, requests, realtime=True):
+        place, committed = place_operators(requests, self.servers[0]._estimate, len(self.servers))
+        self.placement = place
+        per = [[r for r in requests if place[r.op] == k] for k in range(len(self.servers))]
+        outs = [None] * len(self.servers)
+
+        def run(k):
+            outs[k] = self.servers[k].serve(per[k], realtime=realtime) if per[k] else dict(
+                requests=0, wall_s=0.0, latencies=[], peak_committed=0)
+
+        ths = [threading.Thread(target=run, args=(k,), daemon=True) for k in range(len(self.servers))]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        out = merge_stats(outs)
+        out["placement_committed_estimate"] = committed
+        return out
+
+    def close(self):
+        for s in self.servers:
+            s.close()
