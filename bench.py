@@ -544,6 +544,11 @@ def run_ours(args):
     avg = {k: round(statistics.mean(pp[k] for pp in parts_all), 2) for k in parts_all[0]}
 
     extras = None if args.no_extras else run_extras(sa, torch, dprob)
+    # a short serving pass (c4 workload, 128 requests): latency and throughput
+    serving = None
+    if not args.no_serving and ws == 1:
+        del B
+        serving = serving_pass(torch, 128, 6, 32, 256, 48, True)
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -573,6 +578,7 @@ def run_ours(args):
         "setup_phases_ms": setup_phases(prof),
         "kernel_profile_all": [[r["kind"], r["level"], r["launches"], round(r["ms"], 3)] for r in krows],
         "extras": extras,
+        "serving": serving,
     }
     if jobs is not None:
         res = jobs.collect(args.oracle_deadline)
@@ -736,24 +742,20 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # other modes
 # ---------------------------------------------------------------------------
-def run_serving(args):
-    """Serving workload: seeded Poisson-arrival requests on 2D/3D layered
+def serving_pass(torch, nreq, slots, hbm_gb, max2d, max3d, group, rank=0, ws=1):
+    """the serving workload: seeded Poisson-arrival requests on 2D/3D layered
     operators (contrast 10^U(2,10)), several right-hand sides per operator with
-    the hierarchy cached, HBM-admitted, FP32 V-cycle inside FP64 flexible CG.
-    The arrival rate is 0.8 x the throughput of a back-to-back warm-up run."""
+    the hierarchy cached, HBM-admitted, FP32 V-cycle inside FP64 flexible CG;
+    the arrival rate is 0.8 x the throughput of a back-to-back warm-up run.
+    group: single requests of different operators are solved together in
+    shared launches (sa_solve_group).  Under torchrun each rank serves the
+    operators placed on it and the latencies are gathered."""
     import numpy as np
-    import torch
 
     import gen
     from paper_2602_05686_gb300.serving import Request, Server, gather_stats, partition
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    nreq = args.requests
-    ops, reqs = gen.serving_requests(nreq, seed=11, max2d=args.max2d, max3d=args.max3d)
+    ops, reqs = gen.serving_requests(nreq, seed=11, max2d=max2d, max3d=max3d)
     t = time.perf_counter()
     probs = {k: gen.layered_serving(o["dim"], o["n_el"], o["contrast"]) for k, o in enumerate(ops)}
     gen_s = time.perf_counter() - t
@@ -769,9 +771,7 @@ def run_serving(args):
         return dict(theta=0.05, measure="material", precision="fp32", max_coarse=5000)
 
     def run(scale, realtime):
-        """all requests at the given arrival-time scale; under torchrun each
-        rank serves the operators placed on it and the stats are gathered"""
-        srv = Server(lambda op: probs[op], options, slots=args.slots, hbm_budget=args.hbm_gb << 30)
+        srv = Server(lambda op: probs[op], options, slots=slots, hbm_budget=hbm_gb << 30, group_solves=group)
         rs, tt = [], 0.0
         for k, r in enumerate(reqs):
             tt += r["gap"] * scale
@@ -782,26 +782,41 @@ def run_serving(args):
             dist.barrier()
         local_out = srv.serve(mine, realtime=realtime)
         srv.close()
-        out = gather_stats(local_out, ws)
-        return out, mine
+        return gather_stats(local_out, ws) if ws > 1 else local_out, mine
 
     warm, _ = run(0.0, False)
     rate = 0.8 * warm["throughput_rps"]
     out, rs = run(1.0 / rate, True)
     iters = [r.info.get("iters", 0) for r in rs]
+    return {"p50_s": round(out["p50_s"], 4), "p99_s": round(out["p99_s"], 4),
+            "req_per_s": round(out["throughput_rps"], 2), "arrival_rate_rps": round(rate, 2),
+            "warmup_req_per_s": round(warm["throughput_rps"], 2), "requests": nreq, "operators": len(ops),
+            "slots": slots, "group_solves": bool(group), "setups": out.get("setups"), "cache_hits": out.get("hits"),
+            "groups": out.get("groups"), "max_group": out.get("max_group"), "evictions": out.get("evictions"),
+            "failed": out.get("failed"), "mean_iters": round(float(np.mean(iters)), 1) if iters else None,
+            "max_rel_res": max((r.info.get("rel_res", 0.0) for r in rs), default=None),
+            "per_gpu_requests": out.get("per_device_requests"), "generation_s": round(gen_s, 1),
+            "workload": f"serving: {nreq} requests, 2D 16^2..{max2d}^2 and 3D 16^3..{max3d}^3 layered operators, "
+                        "contrast 1e2..1e10, 1-16 RHS per operator, FP32 V-cycle in FP64 flexible CG"}
+
+
+def run_serving(args):
+    """Serving workload (c4) on its own, one JSON line (p99 latency as the
+    value)."""
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    r = serving_pass(torch, args.requests, args.slots, args.hbm_gb, args.max2d, args.max3d, not args.no_group,
+                     rank, ws)
     if rank != 0:
         return
     res = {"metric": "serving latency p50/p99 (continuous batching, cached hierarchies)",
-           "value": round(out["p99_s"], 4), "unit": "s (p99 latency)", "higher_is_better": False,
-           "n_gpus": ws, "per_gpu_requests": out.get("per_device_requests"), "p50_s": round(out["p50_s"], 4), "p99_s": round(out["p99_s"], 4),
-           "throughput_rps": round(out["throughput_rps"], 2), "arrival_rate_rps": round(rate, 2),
-           "warmup_throughput_rps": round(warm["throughput_rps"], 2), "requests": nreq, "operators": len(ops),
-           "slots": args.slots, "setups": out["setups"], "cache_hits": out["hits"], "evictions": out["evictions"],
-           "failed": out["failed"], "mean_iters": round(float(np.mean(iters)), 1),
-           "max_rel_res": max(r.info.get("rel_res", 0.0) for r in rs), "generation_s": round(gen_s, 1),
-           "config": {"workload": f"serving: {nreq} requests, 2D 16^2..{args.max2d}^2 and 3D 16^3..{args.max3d}^3 "
-                                  "layered operators, contrast 1e2..1e10, 1-16 RHS per operator",
-                      "precision": "FP32 V-cycle in FP64 flexible CG", "tol": TOL}}
+           "value": r["p99_s"], "unit": "s (p99 latency)", "higher_is_better": False, "n_gpus": ws, **r,
+           "config": {"workload": r["workload"], "precision": "FP32 V-cycle in FP64 flexible CG", "tol": TOL}}
     print(json.dumps(res), flush=True)
 
 
@@ -872,6 +887,8 @@ def main():
     ap.add_argument("--hbm-gb", type=int, default=64)
     ap.add_argument("--max2d", type=int, default=512)
     ap.add_argument("--max3d", type=int, default=96)
+    ap.add_argument("--no-group", action="store_true", help="serving without group solves")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving pass of the default run")
     ap.add_argument("--annulus", action="store_true", help="run the annulus study (Sec. 4.2) instead")
     ap.add_argument("--annulus-refine", type=int, default=4)
     ap.add_argument("--sweep", action="store_true", help="run the two-domain theta sweep (Sec. 4.1) instead")

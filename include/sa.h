@@ -287,6 +287,30 @@ const char* sa_last_error(void);
 int64_t sa_launch_count(void);
 
 /*
+ * sa_solve_group: m independent problems -- m different handles, one
+ * right-hand side each -- solved together, every step in shared launches:
+ * each operator product, V-cycle kernel (all levels; the dense coarse
+ * solves of all problems together at the bottom of the cycle) and CG vector
+ * update is one launch covering every problem still iterating.  This is the
+ * continuous-batching form of the serving loop (requests for different
+ * operators in flight together); no counterpart in the paper (north-star
+ * extension; the method per problem is PCG / flexible CG as for sa_solve).
+ *   - hs[m]: distinct handles with the same precision setting, Chebyshev
+ *     degree and maxit, all on the current device; B[i], X[i]: n_i doubles
+ *     (host or device pointers; X[i] in: initial guess, out: solution).
+ *   - Each problem follows exactly the arithmetic of sa_solve: its iterations,
+ *     status and solution are bitwise those of sa_solve on that handle alone.
+ *   - Runs on hs[0]'s stream after the work already queued on every handle's
+ *     stream; the handles must not be used elsewhere until the call returns
+ *     (it synchronises before returning).  1 <= m <= 64.
+ *   - Returns SA_OK when every problem converged, else the first non-OK
+ *     problem status (per-problem status in infos[i].status; infos may be
+ *     NULL); SA_ERR_INVALID_ARG for duplicate handles or mixed settings.
+ */
+int sa_solve_group(int m, sa_handle* hs, const double* const* B, double* const* X, double tol,
+                   sa_solve_info* infos);
+
+/*
  * Single steps on caller-provided DEVICE buffers, for stepwise parity checks
  * and for callers that build their own pipeline.  Ordered on `stream`.
  *

@@ -19,7 +19,7 @@ MEASURE = {"classical": 0, "material": 1, "distance": 2}
 PRECISION = {"fp64": 0, "fp32": 1}
 DROP = {"pointwise": 0, "cut": 1}
 
-EXPORTED = ["sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle", "sa_hierarchy_stats",
+EXPORTED = ["sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_solve_group", "sa_vcycle", "sa_hierarchy_stats",
             "sa_level_sizes", "sa_level_format", "sa_export_level", "sa_export_strength", "sa_free",
             "sa_status_string", "sa_last_error", "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
             "sa_launch_count", "sa_strength_material_noalloc", "sa_serialized_size", "sa_serialize",
@@ -101,7 +101,8 @@ def lib(build_if_missing: bool = True):
         L.sa_serialized_size.argtypes = [P, P]
         L.sa_serialize.argtypes = [P, P, ctypes.c_uint64]
         L.sa_deserialize.argtypes = [P, ctypes.c_uint64, P, P]
-        for f in ("sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_vcycle",
+        L.sa_solve_group.argtypes = [I, P, P, P, D, P]
+        for f in ("sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_solve_group", "sa_vcycle",
                   "sa_hierarchy_stats", "sa_level_sizes", "sa_level_format", "sa_export_level",
                   "sa_export_strength", "sa_free",
                   "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
@@ -361,6 +362,31 @@ class Hierarchy:
             out["keep"] = out["keep"][:nnz]
         out["omega"], out["lam_omega"], out["cheb_lmax"], out["cheb_lmin"] = (float(v) for v in out["scalars"])
         return out
+
+
+def solve_group(hierarchies, rhs, tol=1e-8, x0=None, check=True):
+    """sa_solve_group: one right-hand side per hierarchy (distinct handles with
+    the same precision setting), all problems advanced together in shared
+    launches on the first hierarchy's stream.  rhs: list of CUDA tensors
+    (float64, n_i each); returns (list of solutions, list of info dicts)."""
+    torch = _torch()
+    m = len(hierarchies)
+    if m != len(rhs):
+        raise ValueError("solve_group: one right-hand side per hierarchy")
+    st0 = hierarchies[0].stream
+    B = [b.to(device="cuda", dtype=torch.float64).contiguous() for b in rhs]
+    with torch.cuda.stream(st0):
+        X = [torch.zeros_like(b) if x0 is None else x0[k].to(device="cuda", dtype=torch.float64).clone()
+             for k, b in enumerate(B)]
+    hs = (ctypes.c_void_p * m)(*[h.h.value for h in hierarchies])
+    bp = (ctypes.c_void_p * m)(*[b.data_ptr() for b in B])
+    xp = (ctypes.c_void_p * m)(*[x.data_ptr() for x in X])
+    infos = (SolveInfo * max(m, 1))()
+    st = lib().sa_solve_group(m, hs, bp, xp, float(tol), infos)
+    if check and st not in (OK, ERR_NO_CONVERGENCE):
+        _check(st, "sa_solve_group")
+    return X, [dict(status=int(infos[c].status), iters=infos[c].iters, rel_res=infos[c].rel_res_true,
+                    setup_ms=infos[c].setup_ms, solve_ms=infos[c].solve_ms) for c in range(m)]
 
 
 def strength(measure, dim, row_ptr, col, val, coords, sigma_inv, dirichlet, theta, stream=None):

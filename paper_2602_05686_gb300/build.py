@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsa_gb300.so")
-SOURCES = ["prim", "setup_exact", "graph", "spgemm", "solve", "dense", "vcycle", "block", "profile", "noalloc", "host"]
+SOURCES = ["prim", "setup_exact", "graph", "spgemm", "solve", "dense", "vcycle", "block", "group", "profile", "noalloc",
+           "host"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 PER_FILE = {"setup_exact": ["-fmad=false"]}

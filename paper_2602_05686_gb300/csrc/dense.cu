@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "profile.cuh"
+#include "group.cuh"
 #include "solve.cuh"
 
 namespace sa {
@@ -437,14 +438,12 @@ int dense_finish(DenseJob& job) {
 // ---------------------------------------------------------------------------
 constexpr int TRI_WARPS = 4;
 
+// the row i of one step (a block of TRI_WARPS warps per row)
 template <int MODE, int K>
-__global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_row(int64_t n, int64_t r0, int64_t r1,
-                                                            const double* __restrict__ M,
-                                                            const double* __restrict__ v,
-                                                            const double* __restrict__ rhs,
-                                                            double* __restrict__ out) {
+__device__ __forceinline__ void tri_row_at(int64_t n, int64_t r0, int64_t r1, const double* __restrict__ M,
+                                           const double* __restrict__ v, const double* __restrict__ rhs,
+                                           double* __restrict__ out, int64_t i) {
   __shared__ double sh[TRI_WARPS][K];
-  const int64_t i = r0 + blockIdx.x;
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
   const int64_t lo = MODE == 0 ? r0 : (MODE == 1 ? i : (MODE == 2 ? 0 : r1));
   const int64_t hi = MODE == 0 ? i + 1 : (MODE == 1 ? r1 : (MODE == 2 ? r0 : n));
@@ -485,6 +484,50 @@ __global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_row(int64_t n, int64_t r
     out[i * K + c] = MODE >= 2 ? rhs[i * K + c] - t : t;
   }
 }
+
+template <int MODE, int K>
+__global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_row(int64_t n, int64_t r0, int64_t r1,
+                                                            const double* __restrict__ M,
+                                                            const double* __restrict__ v,
+                                                            const double* __restrict__ rhs,
+                                                            double* __restrict__ out) {
+  tri_row_at<MODE, K>(n, r0, r1, M, v, rhs, out, r0 + blockIdx.x);
+}
+
+// the same step for several problems in one launch (group solve): block
+// blockIdx.x - blk0 of a segment takes that segment's row r0 + (blockIdx.x -
+// blk0), as its own launch would
+template <int MODE>
+__global__ void __launch_bounds__(TRI_WARPS * 32) k_g_tri(const GTri* __restrict__ d, int m) {
+  __shared__ int s_seg;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (d[mid].blk0 <= blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    s_seg = lo;
+  }
+  __syncthreads();
+  const GTri& D = d[s_seg];
+  tri_row_at<MODE, 1>(D.n, D.r0, D.r1, D.M, D.v, D.rhs, D.out, D.r0 + (int64_t)(blockIdx.x - D.blk0));
+}
+
+int launch_g_tri(cudaStream_t st, int mode, const GTri* d, int m, unsigned blocks) {
+  if (m <= 0 || blocks == 0) return SA_OK;
+  const unsigned T = TRI_WARPS * 32;
+  switch (mode) {
+    case 0: k_g_tri<0><<<blocks, T, 0, st>>>(d, m); break;
+    case 1: k_g_tri<1><<<blocks, T, 0, st>>>(d, m); break;
+    case 2: k_g_tri<2><<<blocks, T, 0, st>>>(d, m); break;
+    default: k_g_tri<3><<<blocks, T, 0, st>>>(d, m); break;
+  }
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int tri_threads() { return TRI_WARPS * 32; }
 
 template <int K>
 static int coarse_solve_k(cudaStream_t st, const CoarseView& F, const double* b, double* t, double* y, double* x) {

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "group.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
 #include "solve.cuh"
@@ -1456,6 +1457,550 @@ int sa_strength(sa_measure measure, int dim, int64_t n, int64_t nnz, const int64
                                         cnt.p));
   }
   return SA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// group solve (sa_solve_group): m problems with different operators, one
+// right-hand side each, advanced together.  Every step is one launch for all
+// problems still iterating (group.cuh); the arithmetic of each problem is the
+// host-driven one-vector CG's (cg_eager_dev), so a problem ends bitwise where
+// sa_solve ends.  The coarse solves of all problems run together at the
+// bottom of the group V-cycle.
+// ---------------------------------------------------------------------------
+namespace sa {
+
+// descriptor arrays of one group solve: built on the host, copied to the
+// device in one transfer whenever the set of iterating problems changes
+struct GArena {
+  std::vector<unsigned char> img;
+  Buf<unsigned char> dev;
+  Alloc* al = nullptr;
+  void clear() { img.clear(); }
+  template <typename D>
+  size_t put(const std::vector<D>& v) {
+    size_t off = (img.size() + 63) & ~size_t(63);
+    img.resize(off + sizeof(D) * v.size());
+    if (!v.empty()) memcpy(img.data() + off, v.data(), sizeof(D) * v.size());
+    return off;
+  }
+  int upload(cudaStream_t s) {
+    if (img.empty()) return SA_OK;
+    if ((size_t)dev.n < img.size()) {
+      dev.release();
+      SA_TRY(dev.alloc(al, (int64_t)img.size() + 4096));
+    }
+    SA_CUDA(cudaMemcpyAsync(dev.p, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+    return SA_OK;
+  }
+  template <typename D>
+  const D* at(size_t off) const { return reinterpret_cast<const D*>(dev.p + off); }
+};
+
+struct GLaunch {
+  int kind;  // 0 matrix rows, 1 elementwise, 2 coarse substitution
+  int op;    // op or substitution mode
+  size_t off;
+  int m;
+  unsigned blocks;
+};
+
+template <typename T>
+struct GroupVcycle {
+  std::vector<sa_handle> hs;
+  std::vector<VHier<T>*> vh;
+  std::vector<const double*> r64;  // cycle input per problem (the outer residual)
+  std::vector<GLaunch> launches;
+  std::vector<std::pair<int, int>> pending;  // (problem, coarsest level) waiting for the shared coarse solve
+
+  // level l for the problems `segs` that have it; returns per problem the
+  // level's output vector
+  void plan_level(GArena& ar, int l, const std::vector<int>& segs, std::vector<T*>& xout) {
+    std::vector<int> D;
+    for (int i : segs) {
+      if (l == (int)vh[i]->lev.size() - 1) {
+        pending.emplace_back(i, l);
+        xout[i] = vh[i]->lev[l]->x.p;  // written by the shared coarse solve
+      } else {
+        D.push_back(i);
+      }
+    }
+    if (D.empty()) {
+      flush_coarse(ar);
+      return;
+    }
+    const int deg = vh[D[0]]->deg;
+    std::vector<T*> xa(hs.size()), xb(hs.size());
+    std::vector<double> th(hs.size()), de(hs.size()), s1(hs.size()), rho(hs.size());
+    for (int i : D) {
+      VLevel<T>* L = vh[i]->lev[l];
+      th[i] = 0.5 * (L->lmax + L->lmin);
+      de[i] = 0.5 * (L->lmax - L->lmin);
+      s1[i] = th[i] / de[i];
+      xa[i] = L->x.p;
+      xb[i] = L->x2.p;
+    }
+    {  // first step from zero (fine level: entry from the FP64 residual)
+      std::vector<GVec<T>> v;
+      uint32_t blk = 0;
+      for (int i : D) {
+        VLevel<T>* L = vh[i]->lev[l];
+        GVec<T> g = {};
+        g.blk0 = blk;
+        g.n = L->n;
+        g.r64 = r64[i];
+        g.s = vh[i]->s0.p;
+        g.c2 = (T)(1.0 / th[i]);
+        g.b = L->b.p;
+        g.x = xa[i];
+        g.d = L->d.p;
+        v.push_back(g);
+        blk += g256(L->n);
+      }
+      launches.push_back({1, l == 0 ? GV_FINE_IN : GV_FIRST, ar.put(v), (int)v.size(), blk});
+    }
+    for (int i : D) rho[i] = 1.0 / s1[i];
+    for (int q = 1; q < deg; ++q) {
+      std::vector<GMat<T>> v;
+      uint32_t blk = 0;
+      for (int i : D) {
+        VLevel<T>* L = vh[i]->lev[l];
+        const double rn = 1.0 / (2.0 * s1[i] - rho[i]);
+        v.push_back(mat_desc(L->A, blk, L->b.p, xa[i], xb[i], L->d.p, (T)(rn * rho[i]), (T)(2.0 * rn / de[i]), 0));
+        std::swap(xa[i], xb[i]);
+        rho[i] = rn;
+      }
+      launches.push_back({0, GM_CHEB, ar.put(v), (int)v.size(), blk});
+    }
+    {
+      std::vector<GMat<T>> v;
+      uint32_t blk = 0;
+      for (int i : D) {
+        VLevel<T>* L = vh[i]->lev[l];
+        GMat<T> g = mat_desc(L->A, blk, L->b.p, xa[i], nullptr, nullptr, (T)0, (T)0, 0);
+        g.r = L->r.p;
+        v.push_back(g);
+      }
+      launches.push_back({0, GM_RESID, ar.put(v), (int)v.size(), blk});
+    }
+    {
+      std::vector<GMat<T>> v;
+      uint32_t blk = 0;
+      for (int i : D) {
+        VLevel<T>* L = vh[i]->lev[l];
+        v.push_back(mat_desc(L->R, blk, nullptr, L->r.p, vh[i]->lev[l + 1]->b.p, nullptr, (T)0, (T)0, 0));
+      }
+      launches.push_back({0, GM_SPMV, ar.put(v), (int)v.size(), blk});
+    }
+    std::vector<T*> xc(hs.size(), nullptr);
+    plan_level(ar, l + 1, D, xc);
+    {
+      std::vector<GMat<T>> v;
+      uint32_t blk = 0;
+      for (int i : D) {
+        VLevel<T>* L = vh[i]->lev[l];
+        v.push_back(mat_desc(L->P, blk, nullptr, xc[i], xa[i], nullptr, (T)0, (T)0, 0));
+      }
+      launches.push_back({0, GM_SPMV_ADD, ar.put(v), (int)v.size(), blk});
+    }
+    for (int i : D) rho[i] = 1.0 / s1[i];
+    for (int q = 0; q < deg; ++q) {
+      const int first = (q == 0);
+      const bool out = (l == 0 && q == deg - 1);
+      std::vector<GMat<T>> v;
+      uint32_t blk = 0;
+      for (int i : D) {
+        VLevel<T>* L = vh[i]->lev[l];
+        T c1 = (T)0, c2 = (T)(1.0 / th[i]);
+        double rn = rho[i];
+        if (!first) {
+          rn = 1.0 / (2.0 * s1[i] - rho[i]);
+          c1 = (T)(rn * rho[i]);
+          c2 = (T)(2.0 * rn / de[i]);
+        }
+        GMat<T> g = mat_desc(L->A, blk, L->b.p, xa[i], out ? nullptr : xb[i], L->d.p, c1, c2, first);
+        if (out) {
+          g.s = vh[i]->s0.p;
+          g.z = vh[i]->z.p;
+        } else {
+          std::swap(xa[i], xb[i]);
+        }
+        if (!first) rho[i] = rn;
+        v.push_back(g);
+      }
+      launches.push_back({0, out ? GM_CHEB_OUT : GM_CHEB, ar.put(v), (int)v.size(), blk});
+    }
+    for (int i : D) xout[i] = xa[i];
+  }
+
+  GMat<T> mat_desc(const Mat<T>& M, uint32_t& blk, const T* b, const T* xin, T* xo, T* d, T c1, T c2, int first) {
+    GMat<T> g = {};
+    g.blk0 = blk;
+    g.fmt = g_mat_fmt(M);
+    g.M = view(M);
+    g.b = b;
+    g.xin = xin;
+    g.xout = xo;
+    g.d = d;
+    g.c1 = c1;
+    g.c2 = c2;
+    g.first = first;
+    blk += g_mat_blocks(M);
+    return g;
+  }
+
+  // the coarse solves of every pending problem, together (block substitution
+  // of dense.cu, one launch per step for all problems that have the step)
+  void flush_coarse(GArena& ar) {
+    if (pending.empty()) return;
+    struct C { int i, l; bool direct; int64_t n; int nbk; const double* bin; double *t, *y, *x; CoarseView F; };
+    std::vector<C> cs;
+    int maxnbk = 0;
+    {
+      std::vector<GVec<T>> v;
+      uint32_t blk = 0;
+      for (auto& pr : pending) {
+        const int i = pr.first, l = pr.second;
+        VHier<T>* m = vh[i];
+        C c;
+        c.i = i; c.l = l; c.direct = (m->lev.size() == 1); c.F = m->cf; c.n = m->cf.n;
+        c.nbk = (int)((c.n + COARSE_BS - 1) / COARSE_BS);
+        c.bin = c.direct ? r64[i] : m->ct.p;
+        c.t = m->cs.p; c.y = m->cy.p; c.x = c.direct ? m->z.p : m->cx.p;
+        cs.push_back(c);
+        maxnbk = c.nbk > maxnbk ? c.nbk : maxnbk;
+        if (!c.direct) {
+          VLevel<T>* L = m->lev[l];
+          GVec<T> g = {};
+          g.blk0 = blk; g.n = L->n; g.s = L->sq.p; g.b = L->b.p; g.t = m->ct.p;
+          v.push_back(g);
+          blk += g256(L->n);
+        }
+      }
+      launches.push_back({1, GV_COARSE_IN, ar.put(v), (int)v.size(), blk});
+    }
+    for (int q = 0; q < maxnbk; ++q) {   // forward: t_K = b_K - L_{K,<K} y; y_K = W_KK t_K
+      for (int mode : {2, 0}) {
+        if (mode == 2 && q == 0) continue;
+        std::vector<GTri> v;
+        uint32_t blk = 0;
+        for (auto& c : cs) {
+          if (c.nbk <= q) continue;
+          const int64_t r0 = q * COARSE_BS, r1 = r0 + COARSE_BS < c.n ? r0 + COARSE_BS : c.n;
+          GTri g = {};
+          g.blk0 = blk; g.n = c.n; g.r0 = r0; g.r1 = r1;
+          if (mode == 2) { g.M = c.F.L; g.v = c.y; g.rhs = c.bin; g.out = c.t; }
+          else { g.M = c.F.W; g.v = q > 0 ? c.t : c.bin; g.rhs = nullptr; g.out = c.y; }
+          v.push_back(g);
+          blk += (uint32_t)(r1 - r0);
+        }
+        launches.push_back({2, mode, ar.put(v), (int)v.size(), blk});
+      }
+    }
+    for (int t = 0; t < maxnbk; ++t) {   // backward: t_K = y_K - L^T_{K,>K} x; x_K = W_KK^T t_K
+      for (int mode : {3, 1}) {
+        if (mode == 3 && t == 0) continue;
+        std::vector<GTri> v;
+        uint32_t blk = 0;
+        for (auto& c : cs) {
+          if (c.nbk <= t) continue;
+          const int q = c.nbk - 1 - t;
+          const int64_t r0 = q * COARSE_BS, r1 = r0 + COARSE_BS < c.n ? r0 + COARSE_BS : c.n;
+          GTri g = {};
+          g.blk0 = blk; g.n = c.n; g.r0 = r0; g.r1 = r1;
+          if (mode == 3) { g.M = c.F.LT; g.v = c.x; g.rhs = c.y; g.out = c.t; }
+          else { g.M = c.F.WT; g.v = t > 0 ? c.t : c.y; g.rhs = nullptr; g.out = c.x; }
+          v.push_back(g);
+          blk += (uint32_t)(r1 - r0);
+        }
+        launches.push_back({2, mode, ar.put(v), (int)v.size(), blk});
+      }
+    }
+    {
+      std::vector<GVec<T>> v;
+      uint32_t blk = 0;
+      for (auto& c : cs) {
+        if (c.direct) continue;
+        VLevel<T>* L = vh[c.i]->lev[c.l];
+        GVec<T> g = {};
+        g.blk0 = blk; g.n = L->n; g.s = L->sq.p; g.x = L->x.p; g.t = vh[c.i]->cx.p;
+        v.push_back(g);
+        blk += g256(L->n);
+      }
+      launches.push_back({1, GV_COARSE_OUT, ar.put(v), (int)v.size(), blk});
+    }
+    pending.clear();
+  }
+
+  void plan(GArena& ar, const std::vector<int>& act) {
+    launches.clear();
+    pending.clear();
+    std::vector<T*> xo(hs.size(), nullptr);
+    plan_level(ar, 0, act, xo);
+  }
+
+  int run(const GArena& ar, cudaStream_t st) const {
+    for (const GLaunch& g : launches) {
+      if (g.m == 0) continue;
+      if (g.kind == 0) SA_TRY(launch_g_mat<T>(st, g.op, ar.at<GMat<T>>(g.off), g.m, g.blocks));
+      else if (g.kind == 1) SA_TRY(launch_g_vec<T>(st, g.op, ar.at<GVec<T>>(g.off), g.m, g.blocks));
+      else SA_TRY(launch_g_tri(st, g.op, ar.at<GTri>(g.off), g.m, g.blocks));
+    }
+    return SA_OK;
+  }
+};
+
+template <typename T>
+static int cg_group(std::vector<sa_handle>& hs, std::vector<VHier<T>*>& vh, const double* const* B, double* const* X,
+                    double tol, sa_solve_info* infos, int* statuses) {
+  const int m = (int)hs.size();
+  cudaStream_t s = hs[0]->al.stream;
+  const int flexible = hs[0]->opt.precision == SA_PREC_FP32_VCYCLE;
+  const int maxit = hs[0]->opt.maxit;
+  auto t0 = std::chrono::steady_clock::now();
+  GArena ar;
+  ar.al = &hs[0]->al;
+  Buf<double> gath;
+  SA_TRY(gath.alloc(&hs[0]->al, 2 * GROUP_MAX));
+  std::vector<double> hg(2 * GROUP_MAX);
+  GroupVcycle<T> V;
+  V.hs = hs;
+  V.vh = vh;
+  for (int i = 0; i < m; ++i) V.r64.push_back(hs[i]->r.p);
+  for (int i = 0; i < m; ++i) {
+    SA_CUDA(cudaMemcpyAsync(hs[i]->bb.p, B[i], sizeof(double) * hs[i]->n, cudaMemcpyDefault, s));
+    SA_CUDA(cudaMemcpyAsync(hs[i]->xb.p, X[i], sizeof(double) * hs[i]->n, cudaMemcpyDefault, s));
+  }
+  // descriptor arrays for a set of problems
+  struct Ops {
+    size_t resid_r, resid_t, dots_rr, fin_dots, dots_tt, fin_dots4, spmv, fin_spmv, alpha, update, fin_upd, beta0,
+        beta, pup1, pup, dots_rz, gather;
+    unsigned rows;
+    int m;
+  };
+  auto build = [&](const std::vector<int>& set, Ops& o) {
+    std::vector<GCg> base;
+    uint32_t blk = 0;
+    for (int i : set) {
+      sa_handle h = hs[i];
+      GCg g = {};
+      g.blk0 = blk;
+      g.n = h->n;
+      g.sp = h->A0s.sp.p; g.ci = h->A0s.ci.p; g.v = h->A0s.v.p;
+      g.base = h->A0s.idx16 ? h->A0s.base.p : nullptr;
+      g.c16 = h->A0s.idx16 ? h->A0s.c16.p : nullptr;
+      g.cg = h->cg.p;
+      g.part = h->part.p;
+      base.push_back(g);
+      blk += g256(h->n);
+    }
+    o.rows = blk;
+    o.m = (int)set.size();
+    auto var = [&](auto fn) {
+      std::vector<GCg> v = base;
+      for (size_t k = 0; k < set.size(); ++k) fn(v[k], hs[set[k]], vh[set[k]]);
+      return ar.put(v);
+    };
+    o.resid_r = var([](GCg& g, sa_handle h, VHier<T>*) { g.in = h->xb.p; g.bvec = h->bb.p; g.out = h->r.p; });
+    o.resid_t = var([](GCg& g, sa_handle h, VHier<T>*) { g.in = h->xb.p; g.bvec = h->bb.p; g.out = h->t.p; });
+    o.dots_rr = var([](GCg& g, sa_handle h, VHier<T>*) { g.a0 = h->r.p; g.b0 = h->r.p; });
+    o.dots_tt = var([](GCg& g, sa_handle h, VHier<T>*) { g.a0 = h->t.p; g.b0 = h->t.p; });
+    o.dots_rz = var([&](GCg& g, sa_handle h, VHier<T>* w) {
+      g.a0 = h->r.p; g.b0 = w->z.p;
+      if (flexible) { g.a1 = w->z.p; g.b1 = h->rprev.p; }
+    });
+    o.fin_dots = var([](GCg& g, sa_handle h, VHier<T>*) { g.np = RED_BLOCKS; g.stride = RED_BLOCKS; g.dots = h->dots.p; });
+    o.fin_dots4 = var([](GCg& g, sa_handle h, VHier<T>*) { g.np = RED_BLOCKS; g.stride = RED_BLOCKS; g.dots = h->dots.p + 4; });
+    o.spmv = var([](GCg& g, sa_handle h, VHier<T>*) { g.in = h->p.p; g.out = h->q.p; });
+    o.fin_spmv = var([](GCg& g, sa_handle h, VHier<T>*) { g.np = (int)g256(h->n); g.stride = 0; g.dots = h->dots.p; });
+    o.alpha = var([](GCg& g, sa_handle h, VHier<T>*) { g.dots = h->dots.p; });
+    o.update = var([&](GCg& g, sa_handle h, VHier<T>*) {
+      g.x = h->xb.p; g.r = h->r.p; g.rprev = flexible ? h->rprev.p : nullptr; g.p = h->p.p; g.q = h->q.p;
+    });
+    o.fin_upd = var([](GCg& g, sa_handle h, VHier<T>*) { g.np = RED_BLOCKS; g.stride = 0; g.dots = h->dots.p + 4; });
+    o.beta0 = var([](GCg& g, sa_handle h, VHier<T>*) { g.dots = h->dots.p; g.flexible = -1; });
+    o.beta = var([&](GCg& g, sa_handle h, VHier<T>*) { g.dots = h->dots.p; g.flexible = flexible; });
+    o.pup1 = var([](GCg& g, sa_handle h, VHier<T>* w) { g.in = w->z.p; g.out = h->p.p; g.first = 1; });
+    o.pup = var([](GCg& g, sa_handle h, VHier<T>* w) { g.in = w->z.p; g.out = h->p.p; g.first = 0; });
+    o.gather = var([&](GCg& g, sa_handle h, VHier<T>*) { g.dots = h->dots.p + 4; g.gather = gath.p; });
+  };
+  auto L = [&](int op, size_t off, const Ops& o, unsigned blocks) {
+    return launch_g_cg(s, op, ar.at<GCg>(off), o.m, blocks);
+  };
+  // host copy of the gathered (r.r, breakdown) pairs of the problems in `set`
+  auto gather = [&](const Ops& o, size_t off) -> int {
+    SA_TRY(L(GC_GATHER, off, o, 0));
+    SA_CUDA(cudaMemcpyAsync(hg.data(), gath.p, sizeof(double) * 2 * o.m, cudaMemcpyDeviceToHost, s));
+    SA_CUDA(cudaStreamSynchronize(s));
+    return SA_OK;
+  };
+
+  std::vector<int> all(m);
+  for (int i = 0; i < m; ++i) all[i] = i;
+  std::vector<double> r0(m, 0.0);
+  std::vector<int> its(m, 0), st(m, SA_ERR_NO_CONVERGENCE), act;
+  Ops o;
+  ar.clear();
+  build(all, o);
+  SA_TRY(ar.upload(s));
+  SA_TRY(L(GC_RESID, o.resid_r, o, o.rows));
+  SA_TRY(L(GC_DOTS, o.dots_rr, o, 0));
+  SA_TRY(L(GC_FINISH, o.fin_dots, o, 0));
+  // gather reads dots + 4; the initial r.r sits in dots[0]: gather it by a
+  // finish into dots + 4 as well (the same sum)
+  SA_TRY(L(GC_FINISH, o.fin_dots4, o, 0));
+  SA_TRY(gather(o, o.gather));
+  for (int i = 0; i < m; ++i) {
+    r0[i] = sqrt(hg[2 * i]);
+    if (r0[i] > 0.0) act.push_back(i);
+    else st[i] = SA_OK;
+  }
+  int it = 0;
+  if (!act.empty()) {
+    ar.clear();
+    build(act, o);
+    V.plan(ar, act);
+    SA_TRY(ar.upload(s));
+    SA_TRY(V.run(ar, s));
+    SA_TRY(L(GC_PUPDATE, o.pup1, o, 0));
+    SA_TRY(L(GC_DOTS, o.dots_rz, o, 0));
+    SA_TRY(L(GC_FINISH, o.fin_dots, o, 0));
+    SA_TRY(L(GC_BETA, o.beta0, o, 0));
+    for (it = 1; it <= maxit && !act.empty(); ++it) {
+      SA_TRY(L(GC_SPMV_DOT, o.spmv, o, o.rows));
+      SA_TRY(L(GC_FINISH, o.fin_spmv, o, 0));
+      SA_TRY(L(GC_ALPHA, o.alpha, o, 0));
+      SA_TRY(L(GC_UPDATE, o.update, o, 0));
+      SA_TRY(L(GC_FINISH, o.fin_upd, o, 0));
+      SA_TRY(gather(o, o.gather));
+      std::vector<int> cand, keep;
+      for (size_t k = 0; k < act.size(); ++k) {
+        const int i = act[k];
+        its[i] = it;
+        if (hg[2 * k + 1] != 0.0) { st[i] = SA_ERR_BREAKDOWN; continue; }
+        if (sqrt(hg[2 * k]) <= tol * r0[i]) cand.push_back(i);
+        keep.push_back(i);
+      }
+      if (!cand.empty()) {
+        // confirm on the true residual; where it does not confirm, it
+        // replaces the recursive one
+        Ops oc;
+        const size_t mark = ar.img.size();
+        build(cand, oc);  // appended to the image of the iterating set and uploaded with it
+        SA_TRY(ar.upload(s));
+        SA_TRY(L(GC_RESID, oc.resid_t, oc, oc.rows));
+        SA_TRY(L(GC_DOTS, oc.dots_tt, oc, 0));
+        SA_TRY(L(GC_FINISH, oc.fin_dots4, oc, 0));
+        SA_TRY(gather(oc, oc.gather));
+        std::vector<int> still;
+        for (size_t k = 0; k < cand.size(); ++k) {
+          const int i = cand[k];
+          if (sqrt(hg[2 * k]) <= tol * r0[i]) st[i] = SA_OK;
+          else SA_CUDA(cudaMemcpyAsync(hs[i]->r.p, hs[i]->t.p, sizeof(double) * hs[i]->n, cudaMemcpyDeviceToDevice, s));
+        }
+        for (int i : keep)
+          if (st[i] != SA_OK) still.push_back(i);
+        keep.swap(still);
+        ar.img.resize(mark);  // the device copy of the prefix is unchanged
+      }
+      std::vector<int> next;
+      for (int i : keep)
+        if (it < maxit) next.push_back(i);  // at maxit the status stays SA_ERR_NO_CONVERGENCE
+      if (next.empty()) { act.clear(); break; }
+      if (next != act) {
+        act.swap(next);
+        ar.clear();
+        build(act, o);
+        V.plan(ar, act);
+        SA_TRY(ar.upload(s));
+      }
+      SA_TRY(V.run(ar, s));
+      SA_TRY(L(GC_DOTS, o.dots_rz, o, 0));
+      SA_TRY(L(GC_FINISH, o.fin_dots, o, 0));
+      SA_TRY(L(GC_BETA, o.beta, o, 0));
+      SA_TRY(L(GC_PUPDATE, o.pup, o, 0));
+    }
+  }
+  // true residuals at exit, the solutions
+  ar.clear();
+  build(all, o);
+  SA_TRY(ar.upload(s));
+  SA_TRY(L(GC_RESID, o.resid_t, o, o.rows));
+  SA_TRY(L(GC_DOTS, o.dots_tt, o, 0));
+  SA_TRY(L(GC_FINISH, o.fin_dots4, o, 0));
+  SA_TRY(gather(o, o.gather));
+  for (int i = 0; i < m; ++i)
+    SA_CUDA(cudaMemcpyAsync(X[i], hs[i]->xb.p, sizeof(double) * hs[i]->n, cudaMemcpyDefault, s));
+  SA_CUDA(cudaStreamSynchronize(s));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < m; ++i) {
+    statuses[i] = st[i];
+    if (infos) {
+      infos[i].iters = its[i];
+      infos[i].rel_res_true = r0[i] > 0.0 ? sqrt(hg[2 * i]) / r0[i] : 0.0;
+      infos[i].setup_ms = hs[i]->setup_ms;
+      infos[i].solve_ms = ms;
+      infos[i].status = st[i];
+    }
+  }
+  return SA_OK;
+}
+
+}  // namespace sa
+
+extern "C" {
+
+int sa_solve_group(int m, sa_handle* hs, const double* const* B, double* const* X, double tol,
+                   sa_solve_info* infos) {
+  if (m < 0 || m > sa::GROUP_MAX || (m > 0 && (!hs || !B || !X)) || !(tol > 0.0)) return SA_ERR_INVALID_ARG;
+  if (m == 0) return SA_OK;
+  std::vector<sa_handle> h(hs, hs + m);
+  for (int i = 0; i < m; ++i) {
+    if (!h[i] || !B[i] || !X[i]) return SA_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (h[j] == h[i]) {
+        sa::set_error_text("sa_solve_group: a handle appears twice (one right-hand side per handle)");
+        return SA_ERR_INVALID_ARG;
+      }
+    if (h[i]->opt.precision != h[0]->opt.precision || h[i]->opt.cheb_degree != h[0]->opt.cheb_degree ||
+        h[i]->opt.maxit != h[0]->opt.maxit) {
+      sa::set_error_text("sa_solve_group: handles differ in precision, Chebyshev degree or maxit");
+      return SA_ERR_INVALID_ARG;
+    }
+  }
+  // the group runs on the first handle's stream, after the other handles' work
+  cudaStream_t s = h[0]->al.stream;
+  for (int i = 1; i < m; ++i) {
+    if (h[i]->al.stream == s) continue;
+    cudaEvent_t e;
+    SA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    SA_CUDA(cudaEventRecord(e, h[i]->al.stream));
+    SA_CUDA(cudaStreamWaitEvent(s, e, 0));
+    cudaEventDestroy(e);
+  }
+  std::vector<int> sts(m, SA_OK);
+  int st;
+  if (h[0]->opt.precision == SA_PREC_FP32_VCYCLE) {
+    std::vector<sa::VHier<float>*> v;
+    for (auto x : h) {
+      if (!x->v32) return SA_ERR_INVALID_ARG;
+      v.push_back(x->v32);
+    }
+    st = sa::cg_group<float>(h, v, B, X, tol, infos, sts.data());
+  } else {
+    std::vector<sa::VHier<double>*> v;
+    for (auto x : h) {
+      if (!x->v64) return SA_ERR_INVALID_ARG;
+      v.push_back(x->v64);
+    }
+    st = sa::cg_group<double>(h, v, B, X, tol, infos, sts.data());
+  }
+  if (st != SA_OK) return st;
+  int worst = SA_OK;
+  for (int i = 0; i < m; ++i)
+    if (sts[i] != SA_OK && worst == SA_OK) worst = sts[i];
+  return worst;
 }
 
 }  // extern "C"

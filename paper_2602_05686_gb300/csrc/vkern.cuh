@@ -194,10 +194,14 @@ static unsigned mat_grid(const Mat<T>& M) {
 // reduced by shuffles (every lane of the warp reaches the shuffles), rows of
 // the long-row bin by a warp each.  The sums do not depend on the unroll.
 // Returns true for the thread that owns the row.
+// row_apply_at takes the launch-local block index explicitly (blk), so a
+// launch that covers several matrices one after another (the group solve)
+// gives every row exactly the threads and arithmetic of its own launch.
 template <typename T, int SW>
-__device__ __forceinline__ bool row_apply(const MatView<T>& M, const T* __restrict__ x, T& out, int64_t& row) {
+__device__ __forceinline__ bool row_apply_at(const MatView<T>& M, const T* __restrict__ x, T& out, int64_t& row,
+                                             unsigned blk) {
   if constexpr (SW == -2) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gt = (int64_t)blk * blockDim.x + threadIdx.x;
     const int64_t sl = gt >> 6;
     const int r = (int)((gt & 63) >> 1), h = (int)(gt & 1);
     const int64_t i = sl * 32 + r;
@@ -210,15 +214,15 @@ __device__ __forceinline__ bool row_apply(const MatView<T>& M, const T* __restri
     out = acc;
     return i < M.n && h == 0;
   } else if constexpr (SW == 0) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gt = (int64_t)blk * blockDim.x + threadIdx.x;
     row = gt;
     if (gt >= M.n) return false;
     out = M.c16 ? sell_row16<T>(M.p, M.base, M.c16, M.v, x, gt) : sell_row<T>(M.p, M.ci, M.v, x, gt);
     return true;
   } else {
-    if (blockIdx.x < M.nlb) {
+    if (blk < M.nlb) {
       // warp-uniform: one long row per warp
-      const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+      const int64_t w = ((int64_t)blk * blockDim.x + threadIdx.x) >> 5;
       if (w >= M.nlong) return false;
       const int lane = (int)(threadIdx.x & 31);
       const int64_t i = M.lrows[w];
@@ -229,7 +233,7 @@ __device__ __forceinline__ bool row_apply(const MatView<T>& M, const T* __restri
       out = acc;
       return lane == 0;
     }
-    const int64_t gt = (int64_t)(blockIdx.x - M.nlb) * blockDim.x + threadIdx.x;
+    const int64_t gt = (int64_t)(blk - M.nlb) * blockDim.x + threadIdx.x;
     const int64_t i = gt / SW;
     const int sl = (int)(gt % SW);
     row = i;
@@ -247,6 +251,11 @@ __device__ __forceinline__ bool row_apply(const MatView<T>& M, const T* __restri
     out = acc;
     return own;
   }
+}
+
+template <typename T, int SW>
+__device__ __forceinline__ bool row_apply(const MatView<T>& M, const T* __restrict__ x, T& out, int64_t& row) {
+  return row_apply_at<T, SW>(M, x, out, row, blockIdx.x);
 }
 
 // Chebyshev direction d = first ? c2 r : c1 d + c2 r with r = b - y, written

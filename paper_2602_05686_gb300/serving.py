@@ -18,7 +18,13 @@ instead of running the setup.
 Requests for the same operator that are waiting together are served as one
 multi-right-hand-side job (up to `batch` columns, sa_solve_batch): every
 operator product, V-cycle and vector update of the job is one launch for all
-its columns.  Every numerical step runs in the CUDA library; this module only
+its columns.  With group_solves=True, single-request jobs of DIFFERENT
+operators whose hierarchies are ready are solved together by one executor
+thread (sa_solve_group): every operator product, V-cycle kernel (coarse
+solves included) and CG update is one launch for all of them, which is where
+small problems, whose launches are mostly empty, gain.  A group is formed
+from whatever is ready when the executor is free; requests that become ready
+during a group solve form the next one.  Every numerical step runs in the CUDA library; this module only
 schedules.
 Results do not depend on the schedule: every kernel of the library is
 deterministic and a column of a multi-right-hand-side solve equals the
@@ -79,10 +85,25 @@ class Server:
     make_problem(op) -> problem dict; options(op) -> Hierarchy keyword args."""
 
     def __init__(self, make_problem, options, slots=4, hbm_budget=64 << 30, tol=1e-8, hierarchy_factory=None,
-                 stream_factory=None, store_dir=None, store_key=None, hierarchy_loader=None, batch=8, device=None):
+                 stream_factory=None, store_dir=None, store_key=None, hierarchy_loader=None, batch=8, device=None,
+                 group_solves=False, group_solver=None, group_max=64):
         # device: the CUDA device this server's slots run on (made current in
         # every slot thread); None keeps the caller's current device
         self.device = device
+        # group_solves: single-request jobs of different operators are solved
+        # together (group_solver(hierarchies, rhs, tol) -> (xs, infos))
+        self.group_solves = bool(group_solves)
+        if self.group_solves and group_solver is None:
+            from .api import solve_group
+
+            def group_solver(hs, rhs, tol):
+                return solve_group(hs, rhs, tol=tol, check=False)
+        self.group_solver = group_solver
+        self.group_max = max(1, min(64, int(group_max)))
+        self._ready = []            # (entry, request, event) waiting for the group executor
+        self._gcv = threading.Condition()
+        self._gthread = None
+        self._gstop = False
         if hierarchy_factory is None:
             from .api import Hierarchy as hierarchy_factory
         if hierarchy_loader is None and store_dir is not None:
@@ -108,7 +129,7 @@ class Server:
         self.free_slots = list(range(slots))
         self.batch = max(1, int(batch))
         self.stats = dict(admitted=0, setups=0, hits=0, evictions=0, peak_committed=0, loads=0, stores=0, jobs=0,
-                          batched=0)
+                          batched=0, groups=0, grouped=0, max_group=0)
         self._problems = {}
         self.building = {}  # op -> threading.Event of an in-flight setup
 
@@ -235,15 +256,18 @@ class Server:
                 if hasattr(rhs[0], "to") and stream is not None and hasattr(stream, "cuda_stream"):
                     rhs = [v.to(device="cuda", non_blocking=True) for v in rhs]
                     stream.synchronize()  # the cached handle may run on another slot's stream
-                with entry.lock:
-                    if len(job) == 1:
-                        x, info = entry.h.solve(rhs[0], tol=self.tol, check=False)
-                        results = [(x, info)]
-                    else:
-                        import torch
-                        B = torch.stack(rhs) if hasattr(rhs[0], "to") else rhs
-                        X, infos = entry.h.solve_batch(B, tol=self.tol, check=False)
-                        results = [(X[c], infos[c]) for c in range(len(job))]
+                if len(job) == 1 and self.group_solves:
+                    results = [self._group_solve(entry, rhs[0])]
+                else:
+                    with entry.lock:
+                        if len(job) == 1:
+                            x, info = entry.h.solve(rhs[0], tol=self.tol, check=False)
+                            results = [(x, info)]
+                        else:
+                            import torch
+                            B = torch.stack(rhs) if hasattr(rhs[0], "to") else rhs
+                            X, infos = entry.h.solve_batch(B, tol=self.tol, check=False)
+                            results = [(X[c], infos[c]) for c in range(len(job))]
                 for r, (x, info) in zip(job, results):
                     r.result = x
                     r.info.update(info)
@@ -262,6 +286,70 @@ class Server:
                     entry.last = done
                 self.free_slots.append(slot)
                 self.cv.notify_all()
+
+    # -- group solves -----------------------------------------------------------
+    def _group_solve(self, entry, rhs):
+        """hands (entry, rhs) to the group executor and waits for its result"""
+        item = {"entry": entry, "rhs": rhs, "done": threading.Event(), "res": None, "err": None}
+        with self._gcv:
+            if self._gthread is None:
+                self._gstop = False
+                self._gthread = threading.Thread(target=self._group_loop, daemon=True)
+                self._gthread.start()
+            self._ready.append(item)
+            self._gcv.notify_all()
+        item["done"].wait()
+        if item["err"] is not None:
+            raise item["err"]
+        return item["res"]
+
+    def _group_loop(self):
+        """the executor: solves everything ready (one request per operator) in
+        one group solve, then the next group"""
+        if self.device is not None:
+            import torch
+            torch.cuda.set_device(self.device)
+        while True:
+            with self._gcv:
+                while not self._ready and not self._gstop:
+                    self._gcv.wait(timeout=0.05)
+                if self._gstop and not self._ready:
+                    return
+                group, rest, seen = [], [], set()
+                for it in self._ready:
+                    if id(it["entry"]) in seen or len(group) >= self.group_max:
+                        rest.append(it)
+                    else:
+                        seen.add(id(it["entry"]))
+                        group.append(it)
+                self._ready = rest
+            locks = [it["entry"].lock for it in group]
+            for lk in locks:
+                lk.acquire()
+            try:
+                xs, infos = self.group_solver([it["entry"].h for it in group], [it["rhs"] for it in group], self.tol)
+                for it, x, info in zip(group, xs, infos):
+                    it["res"] = (x, info)
+            except Exception as e:  # every member of a failed group retires with the error
+                for it in group:
+                    it["err"] = e
+            finally:
+                for lk in locks:
+                    lk.release()
+            with self.cv:
+                self.stats["groups"] += 1
+                self.stats["grouped"] += len(group)
+                self.stats["max_group"] = max(self.stats["max_group"], len(group))
+            for it in group:
+                it["done"].set()
+
+    def _stop_group(self):
+        with self._gcv:
+            self._gstop = True
+            self._gcv.notify_all()
+        if self._gthread is not None:
+            self._gthread.join(timeout=30)
+        self._gthread = None
 
     # -- the loop -----------------------------------------------------------
     def serve(self, requests, realtime=True):
@@ -329,6 +417,7 @@ class Server:
                     failed=sum(1 for r in requests if r.status not in (0,)), latencies=lat)
 
     def close(self):
+        self._stop_group()
         for e in self.cache.values():
             e.h.free()
         self.cache.clear()

@@ -42,8 +42,9 @@ def test_alone_equals_mix(env):
     from paper_2602_05686_gb300.serving import Request, Server
     ops, reqs, probs, rhs = _setup(torch, gen)
 
-    def run(slots, gaps):
-        srv = Server(lambda op: probs[op], _options, slots=slots, hbm_budget=8 << 30)
+    def run(slots, gaps, group=False, batch=8):
+        srv = Server(lambda op: probs[op], _options, slots=slots, hbm_budget=8 << 30, group_solves=group,
+                     batch=batch)
         rs = []
         t = 0.0
         for k, r in enumerate(reqs):
@@ -74,6 +75,16 @@ def test_alone_equals_mix(env):
     assert out0["failed"] == 0 and out0["batched"] > 0 and out0["jobs"] < len(reqs)
     for k in alone:
         assert alone[k][1] == mix0[k][1] and np.array_equal(alone[k][0], mix0[k][0]), k
+    # different operators in shared launches (group solves): still bitwise
+    # the request alone
+    outg, mixg = run(slots=6, gaps=0.0, group=True, batch=1)
+    assert outg["failed"] == 0 and outg["grouped"] == len(reqs) and outg["max_group"] > 1
+    for k in alone:
+        assert alone[k][1] == mixg[k][1] and np.array_equal(alone[k][0], mixg[k][0]), k
+    outr, mixr = run(slots=4, gaps=0.002, group=True)
+    assert outr["failed"] == 0
+    for k in alone:
+        assert alone[k][1] == mixr[k][1] and np.array_equal(alone[k][0], mixr[k][0]), k
 
 
 def test_small_budget_evicts_but_stays_correct(env):

@@ -231,3 +231,27 @@ def test_same_operator_requests_share_one_job():
     out1 = s1.serve(reqs([0, 0, 1]), realtime=False)
     s1.close()
     assert out1["jobs"] == 3 and out1["batched"] == 0
+
+
+def test_group_executor_solves_distinct_operators_together():
+    """group_solves: ready single-request jobs of different operators go to one
+    group call (one request per operator per group)"""
+    FakeHierarchy.live = FakeHierarchy.peak = 0
+    calls = []
+
+    def group_solver(hs, rhs, tol):
+        calls.append(len(hs))
+        assert len({id(h) for h in hs}) == len(hs)   # distinct operators
+        time.sleep(0.01)
+        return [[v * 2 for v in b] for b in rhs], [{"status": 0, "iters": 3, "rel_res": 1e-9} for _ in hs]
+
+    probs = {op: {"n": 10, "nnz": 30, "bytes": 100} for op in range(6)}
+    s = Server(lambda op: probs[op], lambda op: {}, slots=6, hbm_budget=10_000, hierarchy_factory=FakeHierarchy,
+               stream_factory=lambda: None, group_solves=True, group_solver=group_solver, batch=1)
+    s._estimate = lambda op: 100
+    rs = reqs([0, 1, 2, 3, 4, 5, 0, 1, 2, 3])
+    out = s.serve(rs, realtime=False)
+    assert out["failed"] == 0 and out["requests"] == 10
+    assert all(r.result == [2.0 * r.rid, 2.0] for r in rs)
+    assert out["grouped"] == 10 and sum(calls) == 10 and max(calls) > 1 and out["groups"] == len(calls)
+    s.close()
