@@ -117,11 +117,14 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
-    """hash of the sources that define the V-cycle and outer-product kernels
-    (a recorded ncu traffic figure is used only while they are unchanged)"""
+def kernel_source_hash(kernel=""):
+    """hash of the sources that define a kernel family (a recorded ncu traffic
+    figure is used only while they are unchanged): the K-column kernels
+    (names starting with b) live in block.cu with the structures of
+    vcycle.cuh, the one-vector V-cycle kernels in vcycle.cu and vkern.cuh"""
+    files = ("block.cu", "vcycle.cuh") if kernel.startswith("b") else ("vcycle.cu", "vkern.cuh")
     h = hashlib.sha256()
-    for f in ("vcycle.cu", "vkern.cuh", "block.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2602_05686_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -134,7 +137,7 @@ def traffic_for(kernel, workload):
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
         e = t.get(f"{kernel}@{workload}")
-        if e and e.get("source_hash") == kernel_source_hash():
+        if e and e.get("source_hash") == kernel_source_hash(kernel):
             return float(e["bytes_per_launch"])
     except Exception:
         pass
