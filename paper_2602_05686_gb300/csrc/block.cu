@@ -38,14 +38,60 @@ __device__ __forceinline__ void ldvec(const T* __restrict__ p, T (&v)[K]) {
   }
 }
 
+// Reduction of the K per-lane partial sums over the W lanes of one row.  The
+// one-vector kernels add a row's lane sums by the butterfly xor W/2, ..., 1;
+// here every exchange also halves the columns a lane carries (a lane keeps
+// the lower or upper half and receives its partner's values of that half),
+// so each column is added in exactly the butterfly's tree -- bitwise the
+// one-vector sum -- with K/2 + K/4 + ... additions per lane instead of
+// K log2(W).  On return the lane holds the sums of columns c0 .. c0+V-1 in
+// acc[0 .. V); V = K/W when K >= W, else 1 (then lanes whose low bits
+// (lane mod W/K) are not zero hold copies).
+template <typename T, int K, int W>
+__device__ __forceinline__ int lane_reduce(T (&acc)[K], int lane, int& c0) {
+  int V = K;
+  c0 = 0;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    if (V > 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int j = 0; j < K / 2; ++j) {
+        if (j < V / 2) {
+          const T send = up ? acc[j] : acc[j + V / 2];
+          const T keep = up ? acc[j + V / 2] : acc[j];
+          acc[j] = keep + __shfl_xor_sync(FULL, send, o, W);
+        }
+      }
+      if (up) c0 += V / 2;
+      V /= 2;
+    } else {
+      acc[0] += __shfl_xor_sync(FULL, acc[0], o, W);
+    }
+  }
+  return V;
+}
+
+// the row product of this thread's row for K interleaved columns; returns the
+// number of columns this thread writes (0: none), their sums in acc[0 .. nw)
+// being columns c0 .. c0+nw-1 of `row`.  Entries are loaded U at a time
+// (values and columns first, then the gathers) and added in entry order, so
+// every column's sum is the one-vector kernel's.
+template <typename T, int K>
+struct BUnroll {
+  static constexpr int U = 2;
+};
+
 template <typename T, int SW, int K>
-__device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restrict__ X, T (&acc)[K], int64_t& row) {
+__device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restrict__ X, T (&acc)[K], int64_t& row,
+                                          int& c0) {
+  constexpr int U = BUnroll<T, K>::U;
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
   for (int c = 0; c < K; ++c) acc[c] = (T)0;
-  T xv[K];
+  c0 = 0;
   if constexpr (SW == -2) {
-    // two lanes per SELL row: even and odd entries, one shuffle
+    // two lanes per SELL row: even and odd entries
     const int64_t sl = gt >> 6;
     const int r = (int)((gt & 63) >> 1), h = (int)(gt & 1);
     const int64_t i = sl * 32 + r;
@@ -53,7 +99,24 @@ __device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restr
     if (i < M.n) {
       const int64_t e = M.p[sl + 1];
       const T* __restrict__ xs = M.c16 ? X + (int64_t)M.base[sl] * K : X;
-      for (int64_t p = M.p[sl] + 32 * h + r; p < e; p += 64) {
+      int64_t p = M.p[sl] + 32 * h + r;
+      for (; p + 64 * (U - 1) < e; p += 64 * U) {
+        T a[U], xv[U][K];
+        int64_t cc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          a[u] = __ldcs(&M.v[p + 64 * u]);
+          cc[u] = M.c16 ? (int64_t)__ldcs(&M.c16[p + 64 * u]) : (int64_t)__ldcs(&M.ci[p + 64 * u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) ldvec<T, K>(xs + cc[u] * K, xv[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int j = 0; j < K; ++j) acc[j] += a[u] * xv[u][j];
+      }
+      for (; p < e; p += 64) {
+        T xv[K];
         const T a = __ldcs(&M.v[p]);
         const int64_t c = M.c16 ? (int64_t)__ldcs(&M.c16[p]) : (int64_t)__ldcs(&M.ci[p]);
         ldvec<T, K>(xs + c * K, xv);
@@ -61,52 +124,75 @@ __device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restr
         for (int j = 0; j < K; ++j) acc[j] += a * xv[j];
       }
     }
-#pragma unroll
-    for (int j = 0; j < K; ++j) acc[j] += __shfl_xor_sync(FULL, acc[j], 1);
-    return i < M.n && h == 0;
+    const int v = lane_reduce<T, K, 2>(acc, h, c0);
+    return i < M.n ? v : 0;
   } else if constexpr (SW == 0) {
     row = gt;
-    if (gt >= M.n) return false;
+    if (gt >= M.n) return 0;
     const int64_t sl = gt >> 5, r = gt & 31;
     const int64_t b = M.p[sl], e = M.p[sl + 1];
-    if (M.c16) {
-      const T* __restrict__ xs = X + (int64_t)M.base[sl] * K;
-      for (int64_t p = b + r; p < e; p += 32) {
-        const T a = __ldcs(&M.v[p]);
-        ldvec<T, K>(xs + (int64_t)__ldcs(&M.c16[p]) * K, xv);
+    const T* __restrict__ xs = M.c16 ? X + (int64_t)M.base[sl] * K : X;
+    int64_t p = b + r;
+    for (; p + 32 * (U - 1) < e; p += 32 * U) {
+      T a[U], xv[U][K];
+      int64_t cc[U];
 #pragma unroll
-        for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
+      for (int u = 0; u < U; ++u) {
+        a[u] = __ldcs(&M.v[p + 32 * u]);
+        cc[u] = M.c16 ? (int64_t)__ldcs(&M.c16[p + 32 * u]) : (int64_t)__ldcs(&M.ci[p + 32 * u]);
       }
-    } else {
-      for (int64_t p = b + r; p < e; p += 32) {
-        const T a = __ldcs(&M.v[p]);
-        ldvec<T, K>(X + (int64_t)__ldcs(&M.ci[p]) * K, xv);
 #pragma unroll
-        for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
-      }
+      for (int u = 0; u < U; ++u) ldvec<T, K>(xs + cc[u] * K, xv[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] += a[u] * xv[u][c];
     }
-    return true;
+    for (; p < e; p += 32) {
+      T xv[K];
+      const T a = __ldcs(&M.v[p]);
+      const int64_t c = M.c16 ? (int64_t)__ldcs(&M.c16[p]) : (int64_t)__ldcs(&M.ci[p]);
+      ldvec<T, K>(xs + c * K, xv);
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc[j] += a * xv[j];
+    }
+    return K;
   } else {
     if (blockIdx.x < M.nlb) {
       // the long-row bin: one row per warp (warp-uniform), lane-strided
-      // sums and the 32-lane shuffle tree of the one-vector kernel
+      // sums and the 32-lane tree of the one-vector kernel
       const int64_t w = gt >> 5;
-      if (w >= M.nlong) return false;
+      if (w >= M.nlong) return 0;
       const int lane = (int)(threadIdx.x & 31);
       const int64_t i = M.lrows[w];
       row = i;
       const int64_t e = M.p[i + 1];
-      for (int64_t q = M.p[i] + lane; q < e; q += 32) {
+      int64_t q = M.p[i] + lane;
+      for (; q + 32 * (U - 1) < e; q += 32 * U) {
+        T a[U], xv[U][K];
+        int64_t cc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          a[u] = M.v[q + 32 * u];
+          cc[u] = M.ci[q + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) ldvec<T, K>(X + cc[u] * K, xv[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < K; ++c) acc[c] += a[u] * xv[u][c];
+      }
+      for (; q < e; q += 32) {
+        T xv[K];
         const T a = M.v[q];
         ldvec<T, K>(X + (int64_t)M.ci[q] * K, xv);
 #pragma unroll
         for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
       }
-#pragma unroll
-      for (int c = 0; c < K; ++c)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(FULL, acc[c], o);
-      return lane == 0;
+      const int v = lane_reduce<T, K, 32>(acc, lane, c0);
+      constexpr int copies = K >= 32 ? 1 : 32 / K;   // lanes holding the same columns
+      return (lane & (copies - 1)) == 0 ? v : 0;
     }
     const int64_t g = (int64_t)(blockIdx.x - M.nlb) * blockDim.x + threadIdx.x;
     const int64_t i = g / SW;
@@ -116,8 +202,25 @@ __device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restr
     if (i < M.n) {
       const int64_t b = M.p[i], e = M.p[i + 1];
       if (e - b <= M.lt) {
-        own = sl == 0;
-        for (int64_t q = b + sl; q < e; q += SW) {
+        own = true;
+        int64_t q = b + sl;
+        for (; q + SW * (U - 1) < e; q += SW * U) {
+          T a[U], xv[U][K];
+          int64_t cc[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            a[u] = M.v[q + SW * u];
+            cc[u] = M.ci[q + SW * u];
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) ldvec<T, K>(X + cc[u] * K, xv[u]);
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < K; ++c) acc[c] += a[u] * xv[u][c];
+        }
+        for (; q < e; q += SW) {
+          T xv[K];
           const T a = M.v[q];
           ldvec<T, K>(X + (int64_t)M.ci[q] * K, xv);
 #pragma unroll
@@ -125,11 +228,13 @@ __device__ __forceinline__ bool brow_apply(const MatView<T>& M, const T* __restr
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < K; ++c)
-#pragma unroll
-      for (int o = SW / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(FULL, acc[c], o, SW);
-    return own;
+    if constexpr (SW == 1) {
+      return own ? K : 0;
+    } else {
+      const int v = lane_reduce<T, K, SW>(acc, sl, c0);
+      constexpr int copies = K >= SW ? 1 : SW / K;
+      return own && (sl & (copies - 1)) == 0 ? v : 0;
+    }
   }
 }
 
@@ -138,13 +243,16 @@ __global__ void k_bvc_cheb(MatView<T> A, const T* __restrict__ b, const T* __res
                            T* __restrict__ d, T c1, T c2, int first) {
   T y[K];
   int64_t i;
-  if (!brow_apply<T, SW, K>(A, xin, y, i)) return;
-  const int64_t o = i * K;
+  int c0;
+  const int nw = brow_apply<T, SW, K>(A, xin, y, i, c0);
+  const int64_t o = i * K + c0;
 #pragma unroll
-  for (int c = 0; c < K; ++c) {
-    const T dn = cheb_dir<T>(b[o + c], y[c], first ? (T)0 : d[o + c], c1, c2, first);
-    d[o + c] = dn;
-    xout[o + c] = xin[o + c] + dn;
+  for (int j = 0; j < K; ++j) {
+    if (j < nw) {
+      const T dn = cheb_dir<T>(b[o + j], y[j], first ? (T)0 : d[o + j], c1, c2, first);
+      d[o + j] = dn;
+      xout[o + j] = xin[o + j] + dn;
+    }
   }
 }
 
@@ -152,30 +260,36 @@ template <typename T, int SW, int K>
 __global__ void k_bvc_residual(MatView<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
   T y[K];
   int64_t i;
-  if (!brow_apply<T, SW, K>(A, x, y, i)) return;
-  const int64_t o = i * K;
+  int c0;
+  const int nw = brow_apply<T, SW, K>(A, x, y, i, c0);
+  const int64_t o = i * K + c0;
 #pragma unroll
-  for (int c = 0; c < K; ++c) r[o + c] = b[o + c] - y[c];
+  for (int j = 0; j < K; ++j)
+    if (j < nw) r[o + j] = b[o + j] - y[j];
 }
 
 template <typename T, int SW, int K>
 __global__ void k_bvc_spmv(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
   T y[K];
   int64_t i;
-  if (!brow_apply<T, SW, K>(A, x, y, i)) return;
-  const int64_t o = i * K;
+  int c0;
+  const int nw = brow_apply<T, SW, K>(A, x, y, i, c0);
+  const int64_t o = i * K + c0;
 #pragma unroll
-  for (int c = 0; c < K; ++c) out[o + c] = y[c];
+  for (int j = 0; j < K; ++j)
+    if (j < nw) out[o + j] = y[j];
 }
 
 template <typename T, int SW, int K>
 __global__ void k_bvc_spmv_add(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
   T y[K];
   int64_t i;
-  if (!brow_apply<T, SW, K>(A, x, y, i)) return;
-  const int64_t o = i * K;
+  int c0;
+  const int nw = brow_apply<T, SW, K>(A, x, y, i, c0);
+  const int64_t o = i * K + c0;
 #pragma unroll
-  for (int c = 0; c < K; ++c) out[o + c] += y[c];
+  for (int j = 0; j < K; ++j)
+    if (j < nw) out[o + j] += y[j];
 }
 
 template <typename T, int SW, int K>
@@ -184,13 +298,17 @@ __global__ void k_bvc_cheb_out(MatView<T> A, const T* __restrict__ b, const T* _
                                double* __restrict__ z) {
   T y[K];
   int64_t i;
-  if (!brow_apply<T, SW, K>(A, xin, y, i)) return;
-  const int64_t o = i * K;
+  int c0;
+  const int nw = brow_apply<T, SW, K>(A, xin, y, i, c0);
+  if (nw == 0) return;
+  const int64_t o = i * K + c0;
   const double si = s[i];
 #pragma unroll
-  for (int c = 0; c < K; ++c) {
-    const T dn = cheb_dir<T>(b[o + c], y[c], first ? (T)0 : d[o + c], c1, c2, first);
-    z[o + c] = si * (double)(xin[o + c] + dn);
+  for (int j = 0; j < K; ++j) {
+    if (j < nw) {
+      const T dn = cheb_dir<T>(b[o + j], y[j], first ? (T)0 : d[o + j], c1, c2, first);
+      z[o + j] = si * (double)(xin[o + j] + dn);
+    }
   }
 }
 
@@ -389,9 +507,10 @@ __global__ void k_bsell_spmv_dot(MatView<double> A, const double* __restrict__ P
                                  double* __restrict__ part) {
   double y[K], c[K];
   int64_t i;
+  int c0;
 #pragma unroll
   for (int j = 0; j < K; ++j) c[j] = 0.0;
-  if (brow_apply<double, 0, K>(A, P, y, i)) {
+  if (brow_apply<double, 0, K>(A, P, y, i, c0)) {
     const int64_t o = i * K;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -401,10 +520,16 @@ __global__ void k_bsell_spmv_dot(MatView<double> A, const double* __restrict__ P
   }
   __shared__ double sh[K][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // the warp sums of the K columns by the exchanging butterfly (each
+  // column's tree is warp_sum's); lane c * (32 / K) ends with column c
+  {
+    int cc;
+    const int v = lane_reduce<double, K, 32>(c, lane, cc);
+    constexpr int copies = K >= 32 ? 1 : 32 / K;
+    if ((lane & (copies - 1)) == 0)
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    const double t = warp_sum(c[j]);
-    if (lane == 0) sh[j][w] = t;
+      for (int j = 0; j < K; ++j)
+        if (j < v) sh[cc + j][w] = c[j];
   }
   __syncthreads();
   if (w == 0) {
@@ -422,7 +547,8 @@ __global__ void k_bsell_res64(MatView<double> A, const double* __restrict__ B, c
                               double* __restrict__ R) {
   double y[K];
   int64_t i;
-  if (!brow_apply<double, 0, K>(A, X, y, i)) return;
+  int c0;
+  if (!brow_apply<double, 0, K>(A, X, y, i, c0)) return;
   const int64_t o = i * K;
 #pragma unroll
   for (int j = 0; j < K; ++j) R[o + j] = B[o + j] - y[j];
