@@ -356,6 +356,49 @@ def setup_phases(prof):
     return {k: round(v, 2) for k, v in sorted(out.items(), key=lambda kv: -kv[1])}
 
 
+def setup_roofline(phases_ms, sizes, peak):
+    """algorithmic bytes of each setup phase (what it must move at least once,
+    summed over the coarsening levels: CSR values 8 B, columns 4 B, row
+    pointers 8 B; see the phase list below) against its measured stream time.
+    sizes: per level dicts of n, nnz, nnz_P, nc, nnz_gc (level_sizes)."""
+    by = {}
+
+    def add(k, b):
+        by[k] = by.get(k, 0.0) + b
+
+    L = len(sizes)
+    for l, z in enumerate(sizes):
+        n, nnz, nP, nc, ngc = z["n"], z["nnz"], z["nnz_P"], z["nc"], z["nnz_gc"]
+        if l < L - 1:
+            nnz_c = sizes[l + 1]["nnz"]
+            add("strength", 12 * nnz + 1 * nnz + 8 * (n + 1) + 16 * n)            # A in, keep + counts out
+            add("graph", 5 * nnz + 8 * n + 4 * ngc + 8 * (n + 1))                 # keep, columns in; G_C out
+            add("mis2", 4 * ngc + 8 * (n + 1) + 16 * n)                            # one sweep of G_C and tags
+            add("aggregate", 4 * ngc + 8 * (n + 1) + 8 * n)
+            add("filter", 13 * nnz + 8 * (n + 1) + 12 * (ngc + n) + 16 * n)        # A, keep in; A_F, D~ out
+            add("omega", 10 * (12 * (ngc + n) + 24 * n))                           # ten products with A_F
+            add("smooth_p", 12 * (ngc + n) + 4 * n + 12 * nP + 8 * (n + 1))        # A_F, agg in; P out
+            add("transpose", 2 * (12 * nP) + 8 * (n + 1) + 8 * (nc + 1))           # P in, R out
+            add("galerkin", 12 * nnz + 2 * 12 * nP + 12 * nnz_c + 8 * (nc + 1))   # A, P, R in; A_c out
+            add("aux", 0)
+        add("cheb_bounds", 10 * (12 * nnz + 24 * n) if l < L - 1 else 0)
+        add("sell", 12 * nnz + 10 * nnz)                                            # CSR in, SELL copy out
+    out = {}
+    for k, ms in phases_ms.items():
+        if k in by and by[k] > 0 and ms > 0:
+            gbs = by[k] / (ms * 1e-3) / 1e9
+            out[k] = {"ms": ms, "algorithmic_GB": round(by[k] / 1e9, 3), "GBs": round(gbs, 1),
+                      "frac_of_hbm": round(gbs / peak, 3)}
+    if sizes:
+        nL = sizes[-1]["n"]
+        ms = phases_ms.get("dense")
+        if ms:
+            fl = nL ** 3 / 3.0
+            out["dense"] = {"ms": ms, "flops": fl, "TFLOPs": round(fl / (ms * 1e-3) / 1e12, 4),
+                            "note": "coarse Cholesky factor (n_L^3/3), overlapped with other setup work"}
+    return out
+
+
 def fp64_flops(kind, level, nnz0, n0, K):
     """FP64 FLOPs per launch of a level-0 FP64 kernel: one FMA per stored
     entry and column plus the row updates"""
@@ -474,6 +517,9 @@ def run_ours(args):
     prof = sa.profile_read()
     sa.profile_enable(False)
     ms_step_prof = t2.elapsed_time(t3)
+    hh = sa.Hierarchy(dprob, theta=CLS_THETA, measure="classical", precision="fp64")
+    lsizes = [hh.level_sizes(l) for l in range(hh.stats()["levels"])]
+    hh.free()
     x64_0 = sols[0][0].cpu().numpy()
     x32_0 = sols[1][0].cpu().numpy()
     del sols
@@ -579,6 +625,7 @@ def run_ours(args):
         "kernel_profile_top": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}
                                for r in krows[:10]],
         "setup_phases_ms": setup_phases(prof),
+        "setup_roofline": setup_roofline(setup_phases(prof), lsizes, peak),
         "kernel_profile_all": [[r["kind"], r["level"], r["launches"], round(r["ms"], 3)] for r in krows],
         "extras": extras,
         "serving": serving,

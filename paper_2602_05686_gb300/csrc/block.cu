@@ -77,15 +77,18 @@ __device__ __forceinline__ int lane_reduce(T (&acc)[K], int lane, int& c0) {
 // being columns c0 .. c0+nw-1 of `row`.  Entries are loaded U at a time
 // (values and columns first, then the gathers) and added in entry order, so
 // every column's sum is the one-vector kernel's.
-template <typename T, int K>
+// entries per load round: one on SELL rows of one lane (measured: more
+// registers cost the level-0 FP32 step more occupancy than the extra loads in
+// flight gain), two on CSR lanes and two-lane SELL rows
+template <typename T, int SW>
 struct BUnroll {
-  static constexpr int U = 2;
+  static constexpr int U = SW == 0 ? 1 : 2;
 };
 
 template <typename T, int SW, int K>
 __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restrict__ X, T (&acc)[K], int64_t& row,
                                           int& c0) {
-  constexpr int U = BUnroll<T, K>::U;
+  constexpr int U = BUnroll<T, SW>::U;
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
   for (int c = 0; c < K; ++c) acc[c] = (T)0;

@@ -366,10 +366,18 @@ __global__ void k_bdots(int64_t n, int k, const double* __restrict__ a0, const d
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = i * k;
 #pragma unroll
-    for (int c = 0; c < KB; ++c) {
+    for (int c = 0; c < KB; c += 2) {
       if (c < k) {
-        acc[c] = fma(a0[o + c], b0[o + c], acc[c]);
-        if (a1) acc[KB + c] = fma(a1[o + c], b1[o + c], acc[KB + c]);
+        const double2 a = *reinterpret_cast<const double2*>(a0 + o + c);
+        const double2 b = *reinterpret_cast<const double2*>(b0 + o + c);
+        acc[c] = fma(a.x, b.x, acc[c]);
+        acc[c + 1] = fma(a.y, b.y, acc[c + 1]);
+        if (a1) {
+          const double2 e = *reinterpret_cast<const double2*>(a1 + o + c);
+          const double2 f = *reinterpret_cast<const double2*>(b1 + o + c);
+          acc[KB + c] = fma(e.x, f.x, acc[KB + c]);
+          acc[KB + c + 1] = fma(e.y, f.y, acc[KB + c + 1]);
+        }
       }
     }
   }
@@ -424,19 +432,35 @@ __global__ void k_bcg_update(int64_t n, int k, const CgScalars* __restrict__ s, 
     alpha[c] = c < k ? s[c].alpha : 0.0;
     acc[c] = 0.0;
   }
+  // k is even (2, 4 or 8) and rows of the interleaved blocks are 16-byte
+  // aligned: columns move in pairs (double2), each column updated and summed
+  // exactly as in the one-vector kernel
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = i * k;
 #pragma unroll
-    for (int c = 0; c < KB; ++c) {
+    for (int c = 0; c < KB; c += 2) {
       if (c < k) {
-        double ri = r[o + c];
-        if (on[c]) {
-          if (rprev) rprev[o + c] = ri;
-          x[o + c] = fma(alpha[c], p[o + c], x[o + c]);
-          ri = fma(-alpha[c], q[o + c], ri);
-          r[o + c] = ri;
+        const double2 r2 = *reinterpret_cast<const double2*>(r + o + c);
+        double ri[2] = {r2.x, r2.y};
+        if (on[c] || on[c + 1]) {
+          const double2 p2 = *reinterpret_cast<const double2*>(p + o + c);
+          const double2 q2 = *reinterpret_cast<const double2*>(q + o + c);
+          const double2 x2 = *reinterpret_cast<const double2*>(x + o + c);
+          const double pv[2] = {p2.x, p2.y}, qv[2] = {q2.x, q2.y};
+          double xv[2] = {x2.x, x2.y};
+          if (rprev) *reinterpret_cast<double2*>(rprev + o + c) = r2;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (on[c + h]) {
+              xv[h] = fma(alpha[c + h], pv[h], xv[h]);
+              ri[h] = fma(-alpha[c + h], qv[h], ri[h]);
+            }
+          }
+          *reinterpret_cast<double2*>(x + o + c) = make_double2(xv[0], xv[1]);
+          *reinterpret_cast<double2*>(r + o + c) = make_double2(ri[0], ri[1]);
         }
-        acc[c] = fma(ri, ri, acc[c]);
+        acc[c] = fma(ri[0], ri[0], acc[c]);
+        acc[c + 1] = fma(ri[1], ri[1], acc[c + 1]);
       }
     }
   }
@@ -472,8 +496,18 @@ __global__ void k_bcg_pupdate(int64_t n, int k, const CgScalars* __restrict__ s,
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = i * k;
 #pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (on[c]) p[o + c] = first ? z[o + c] : fma(beta[c], p[o + c], z[o + c]);
+    for (int c = 0; c < KB; c += 2) {
+      if (c < k && (on[c] || on[c + 1])) {
+        const double2 z2 = *reinterpret_cast<const double2*>(z + o + c);
+        const double2 p2 = *reinterpret_cast<const double2*>(p + o + c);
+        double pv[2] = {p2.x, p2.y};
+        const double zv[2] = {z2.x, z2.y};
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (on[c + h]) pv[h] = first ? zv[h] : fma(beta[c + h], pv[h], zv[h]);
+        *reinterpret_cast<double2*>(p + o + c) = make_double2(pv[0], pv[1]);
+      }
+    }
   }
 }
 
@@ -490,7 +524,7 @@ __global__ void k_interleave(int64_t n, int k, int K, const double* __restrict__
 
 int launch_bdots(cudaStream_t st, int64_t n, int k, const double* a0, const double* b0, const double* a1,
                  const double* b1, double* part, double* out) {
-  if (k < 1 || k > KB) return SA_ERR_INVALID_ARG;
+  if (k < 2 || k > KB || (k & 1)) return SA_ERR_INVALID_ARG;  // column pairs
   k_bdots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, a0, b0, a1, b1, part);
   SA_LAUNCHED();
   k_bdots_finish<2 * KB><<<1, 1024, 0, st>>>(part, RED_BLOCKS, RED_BLOCKS, out);
@@ -514,6 +548,7 @@ int launch_bcg_alpha(cudaStream_t st, int k, CgScalars* s, const double* dots, c
 
 int launch_bcg_update(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* p,
                       const double* q, double* x, double* r, double* rprev, double* part) {
+  if (k < 2 || k > KB || (k & 1)) return SA_ERR_INVALID_ARG;  // column pairs
   k_bcg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, s, active, p, q, x, r, rprev, part);
   SA_LAUNCHED();
   return SA_OK;
@@ -527,6 +562,7 @@ int launch_bcg_beta(cudaStream_t st, int k, CgScalars* s, const double* dots, in
 
 int launch_bcg_pupdate(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* z,
                        double* p, int first) {
+  if (k < 2 || k > KB || (k & 1)) return SA_ERR_INVALID_ARG;  // column pairs
   k_bcg_pupdate<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, s, active, z, p, first);
   SA_LAUNCHED();
   return SA_OK;
