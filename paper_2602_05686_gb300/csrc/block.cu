@@ -197,46 +197,99 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
       constexpr int copies = K >= 32 ? 1 : 32 / K;   // lanes holding the same columns
       return (lane & (copies - 1)) == 0 ? v : 0;
     }
-    const int64_t g = (int64_t)(blockIdx.x - M.nlb) * blockDim.x + threadIdx.x;
-    const int64_t i = g / SW;
-    const int sl = (int)(g % SW);
-    row = i;
-    bool own = false;
-    if (i < M.n) {
+    if constexpr (sizeof(T) == 8) {
+      // regular rows: K threads per row, thread c taking column c of every
+      // entry (the K values of a gathered row of X are contiguous, so the
+      // row's threads read them together).  The one-vector kernel's SW lanes
+      // are kept as SW partial sums per thread -- entry q goes to partial
+      // (q - b) mod SW, in entry order -- and added in its butterfly order,
+      // so the column's sum is bitwise the one-vector sum.
+      const int64_t g = (int64_t)(blockIdx.x - M.nlb) * blockDim.x + threadIdx.x;
+      const int64_t i = g / K;
+      const int c = (int)(g % K);
+      row = i;
+      if (i >= M.n) return 0;
       const int64_t b = M.p[i], e = M.p[i + 1];
-      if (e - b <= M.lt) {
-        own = true;
-        int64_t q = b + sl;
-        for (; q + SW * (U - 1) < e; q += SW * U) {
-          T a[U], xv[U][K];
-          int64_t cc[U];
+      if (e - b > M.lt) return 0;  // in the long-row bin
+      constexpr int UC = SW == 1 ? 4 : 2;  // rounds of SW entries loaded together
+      T part[SW];
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            a[u] = M.v[q + SW * u];
-            cc[u] = M.ci[q + SW * u];
-          }
+      for (int h = 0; h < SW; ++h) part[h] = (T)0;
+      int64_t q = b;
+      for (; q + SW * UC - 1 < e; q += SW * UC) {
+        // SW * UC consecutive entries: partial h takes entries q + h + SW u
+        T a[SW * UC], xv[SW * UC];
+        int32_t cc[SW * UC];
 #pragma unroll
-          for (int u = 0; u < U; ++u) ldvec<T, K>(X + cc[u] * K, xv[u]);
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < K; ++c) acc[c] += a[u] * xv[u][c];
+        for (int t = 0; t < SW * UC; ++t) {
+          a[t] = M.v[q + t];
+          cc[t] = M.ci[q + t];
         }
-        for (; q < e; q += SW) {
-          T xv[K];
-          const T a = M.v[q];
-          ldvec<T, K>(X + (int64_t)M.ci[q] * K, xv);
 #pragma unroll
-          for (int c = 0; c < K; ++c) acc[c] += a * xv[c];
+        for (int t = 0; t < SW * UC; ++t) xv[t] = __ldg(&X[(int64_t)cc[t] * K + c]);
+#pragma unroll
+        for (int u = 0; u < UC; ++u)
+#pragma unroll
+          for (int h = 0; h < SW; ++h) part[h] += a[u * SW + h] * xv[u * SW + h];
+      }
+      for (int h = 0; q < e; ++q, h = (h + 1 == SW ? 0 : h + 1)) {
+        // q - b is a multiple of SW at the loop entry, so h = (q - b) mod SW
+#pragma unroll
+        for (int hh = 0; hh < SW; ++hh)
+          if (hh == h) part[hh] += M.v[q] * __ldg(&X[(int64_t)M.ci[q] * K + c]);
+      }
+      // the butterfly of the SW lanes: offsets SW/2, ..., 1, lower lane first
+#pragma unroll
+      for (int o = SW / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int h = 0; h < o; ++h) part[h] = part[h] + part[h + o];
+      acc[0] = part[0];
+      c0 = c;
+      return 1;
+    } else {
+      // FP32 (bandwidth bound, not FP64-issue bound): SW lanes per row as in
+      // the one-vector kernel, the K column sums reduced by lane_reduce
+      const int64_t g = (int64_t)(blockIdx.x - M.nlb) * blockDim.x + threadIdx.x;
+      const int64_t i = g / SW;
+      const int sl = (int)(g % SW);
+      row = i;
+      bool own = false;
+      if (i < M.n) {
+        const int64_t b = M.p[i], e = M.p[i + 1];
+        if (e - b <= M.lt) {
+          own = true;
+          int64_t q = b + sl;
+          for (; q + SW * (U - 1) < e; q += SW * U) {
+            T a[U], xv[U][K];
+            int64_t cc[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              a[u] = M.v[q + SW * u];
+              cc[u] = M.ci[q + SW * u];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) ldvec<T, K>(X + cc[u] * K, xv[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+              for (int cc2 = 0; cc2 < K; ++cc2) acc[cc2] += a[u] * xv[u][cc2];
+          }
+          for (; q < e; q += SW) {
+            T xv[K];
+            const T a = M.v[q];
+            ldvec<T, K>(X + (int64_t)M.ci[q] * K, xv);
+#pragma unroll
+            for (int cc2 = 0; cc2 < K; ++cc2) acc[cc2] += a * xv[cc2];
+          }
         }
       }
-    }
-    if constexpr (SW == 1) {
-      return own ? K : 0;
-    } else {
-      const int v = lane_reduce<T, K, SW>(acc, sl, c0);
-      constexpr int copies = K >= SW ? 1 : SW / K;
-      return own && (sl & (copies - 1)) == 0 ? v : 0;
+      if constexpr (SW == 1) {
+        return own ? K : 0;
+      } else {
+        const int v = lane_reduce<T, K, SW>(acc, sl, c0);
+        constexpr int copies = K >= SW ? 1 : SW / K;
+        return own && (sl & (copies - 1)) == 0 ? v : 0;
+      }
     }
   }
 }
@@ -357,7 +410,7 @@ __global__ void k_bcoarse_out(int64_t n, int K, const double* __restrict__ x, co
 #define BMAT_SW(Kern, KK, M, st, ...)                                                    \
   do {                                                                                   \
     const MatView<T> _mv = view(M);                                                      \
-    const unsigned _g = mat_grid(M);                                                     \
+    const unsigned _g = bmat_grid(M, KK);                                                \
     if ((M).sw == 0 && (M).sell_lanes == 2) Kern<T, -2, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
     else if ((M).sw == 0) Kern<T, 0, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
     else if ((M).sw == 1) Kern<T, 1, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
@@ -395,6 +448,14 @@ static int block_alloc(Alloc& al, VHier<T>* m) {
   SA_TRY(m->kz.alloc(&al, m->lev[0]->n * KMAX_BLOCK));
   m->kready = 1;
   return SA_OK;
+}
+
+// blocks of a K-column launch: SELL and FP32 CSR as the one-vector launch;
+// FP64 CSR: the long-row bin's blocks, then K threads per regular row
+template <typename T>
+static unsigned bmat_grid(const Mat<T>& M, int K) {
+  if (M.sw == 0 || sizeof(T) == 4) return mat_grid(M);
+  return blocks_for(M.n * (int64_t)K, 256) + (M.nlong > 0 ? long_blocks(M.nlong) : 0u);
 }
 
 // one profiled launch (CUDA events around it when profiling is on)

@@ -42,3 +42,20 @@ def test_oracle_jobs_report_parity_and_sample():
     rows = {r["measure"]: r for r in res[0]["rows"]}
     assert set(rows) == {"material", "classical"}
     assert all(r["status"] == 0 and r["rel_res"] <= 1e-8 and r["iters"] > 0 for r in rows.values())
+
+
+def test_setup_roofline_bytes_and_fraction():
+    """algorithmic bytes of the setup phases from the level sizes: a two-level
+    hierarchy by hand"""
+    sys.path.insert(0, ROOT)
+    import bench
+    sizes = [dict(n=1000, nnz=27000, nnz_P=3000, nc=100, nnz_gc=20000),
+             dict(n=100, nnz=2700, nnz_P=0, nc=0, nnz_gc=0)]
+    r = bench.setup_roofline({"galerkin": 1.0, "strength": 0.5, "dense": 2.0, "cheb_bounds": 1.0}, sizes, 1000.0)
+    # Galerkin: A (12 B per entry) in, P and R (12 B per entry each) in, A_c out, coarse row pointers
+    g = 12 * 27000 + 24 * 3000 + 12 * 2700 + 8 * 101
+    assert r["galerkin"]["algorithmic_GB"] == round(g / 1e9, 3)
+    assert abs(r["galerkin"]["GBs"] - g / 1e-3 / 1e9) < 0.1
+    assert r["strength"]["frac_of_hbm"] == round((13 * 27000 + 8 * 1001 + 16 * 1000) / 0.5e-3 / 1e9 / 1000.0, 3)
+    assert r["cheb_bounds"]["algorithmic_GB"] == round(10 * (12 * 27000 + 24 * 1000) / 1e9, 3)
+    assert r["dense"]["flops"] == 100 ** 3 / 3.0
