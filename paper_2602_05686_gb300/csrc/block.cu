@@ -294,8 +294,16 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
   }
 }
 
+// resident blocks per SM asked of the compiler: FP32 rows are latency bound
+// and gain from occupancy (6 blocks: 40 registers); FP64 rows keep the
+// 64-register budget they have without a bound (4 blocks)
+template <typename T>
+struct BOcc {
+  static constexpr int B = sizeof(T) == 4 ? 6 : 4;
+};
+
 template <typename T, int SW, int K>
-__global__ void k_bvc_cheb(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+__global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_cheb(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
                            T* __restrict__ d, T c1, T c2, int first) {
   T y[K];
   int64_t i;
@@ -313,7 +321,7 @@ __global__ void k_bvc_cheb(MatView<T> A, const T* __restrict__ b, const T* __res
 }
 
 template <typename T, int SW, int K>
-__global__ void k_bvc_residual(MatView<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
+__global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_residual(MatView<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
   T y[K];
   int64_t i;
   int c0;
@@ -349,7 +357,7 @@ __global__ void k_bvc_spmv_add(MatView<T> A, const T* __restrict__ x, T* __restr
 }
 
 template <typename T, int SW, int K>
-__global__ void k_bvc_cheb_out(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin,
+__global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_cheb_out(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin,
                                const T* __restrict__ d, T c1, T c2, int first, const double* __restrict__ s,
                                double* __restrict__ z) {
   T y[K];
