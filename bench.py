@@ -62,6 +62,19 @@ METRIC = ("time-to-1e-8 residual as throughput: dofs x right-hand sides solved p
 UNIT = "MDoF-solves/s"
 
 
+# the paper's own figures for its battery model (Sec. 4.3; CPU cluster, FP64
+# assumed, different problems and aggregation code): context for the line,
+# not a target
+PAPER_CONTEXT = {
+    "source": "arXiv 2602.05686, Sec. 4.3, thermal battery model (Trilinos/MueLu CG, FP64 assumed)",
+    "cg_iterations_16x_radial_refinement": {"classical_sa_theta_0.04": 34, "material_theta_0.08": 17},
+    "smoother_complexity_same_runs": {"classical_sa_theta_0.04": 1.32, "material_theta_0.08": 1.70},
+    "solve_s_n_3.25e7": {"hardware": "Eclipse: 2x18-core Intel Broadwell E5-2695 per node",
+                         "1024_ranks": {"classical_sa_theta_0.04": 0.58, "material_theta_0.08": 0.35},
+                         "4096_ranks": {"classical_sa": 0.26, "material": 0.17}},
+}
+
+
 def workload_desc(n_el):
     n = (n_el + 1) ** 3
     return (f"inclusions: Q1 hex {n_el}^3 ({n / 1e6:.2f}M dofs), seeded spheres sigma=1e6 in diag(1,1,1e-2), "
@@ -607,6 +620,7 @@ def run_ours(args):
         "kernel_profile_all": [[r["kind"], r["level"], r["launches"], round(r["ms"], 3)] for r in krows],
         "extras": extras,
         "serving": serving,
+        "paper_context": PAPER_CONTEXT,
     }
     if jobs is not None:
         res = jobs.collect(args.oracle_deadline)
