@@ -116,3 +116,24 @@ def test_group_rejects_duplicates_and_mixed_settings(sa, gen_mod):
     assert L.sa_solve_group(0, None, None, None, 1e-8, None) == 0
     for h in hs:
         h.free()
+
+
+def test_group_with_host_buffers(sa, gen_mod):
+    """right-hand sides and solutions in host memory (copied inside the call)"""
+    import torch
+    hs, bs = build(sa, gen_mod, "fp64")
+    sub = [0, 2, 4]
+    B = [bs[k].cpu().numpy().copy() for k in sub]
+    X = [np.zeros_like(b) for b in B]
+    L = sa.lib()
+    m = len(sub)
+    hp = (ctypes.c_void_p * m)(*[hs[k].h.value for k in sub])
+    bp = (ctypes.c_void_p * m)(*[b.ctypes.data for b in B])
+    xp = (ctypes.c_void_p * m)(*[x.ctypes.data for x in X])
+    infos = (sa.SolveInfo * m)()
+    assert L.sa_solve_group(m, hp, bp, xp, 1e-8, infos) == 0
+    Xd, _ = sa.solve_group([hs[k] for k in sub], [bs[k] for k in sub])
+    for j in range(m):
+        assert np.array_equal(X[j], Xd[j].cpu().numpy()) and infos[j].status == 0
+    for h in hs:
+        h.free()
