@@ -110,7 +110,11 @@ typedef struct {
  *   NULL = stream-ordered cudaMallocAsync/cudaFreeAsync on `stream`, from the
  *   current device's default pool, whose release threshold the library raises
  *   so that freed memory stays cached for later setups in this process (pass
- *   an allocator to keep memory elsewhere).
+ *   an allocator to keep memory elsewhere).  A block the allocator returns
+ *   must start on a 256-byte boundary (as cudaMalloc's do): the solve
+ *   kernels move whole rows of their multi-column blocks with 32-byte
+ *   vector accesses.  A misaligned block is handed back to `dealloc` and
+ *   the call fails with SA_ERR_OOM and an error text saying so.
  */
 typedef struct {
   double theta;
@@ -175,6 +179,16 @@ int sa_solve(sa_handle h, const double* b, double* x, double tol, sa_solve_info*
  * the V-cycle's n_l x 8 vectors) are allocated on the first call.
  */
 int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos);
+
+/*
+ * sa_solve_batch from the zero initial guess (the usual case of Sec. 4's
+ * solves): X is output only -- nothing is read from it, and no host buffer
+ * of zeros is filled or copied to the device; the device copy of the
+ * initial guess is zero-filled in place.  Same arguments, statuses and
+ * results as sa_solve_batch with X zero on entry (bitwise).  No counterpart
+ * in the paper.
+ */
+int sa_solve_batch_zero(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos);
 
 /*
  * Switches the solve form of an existing hierarchy (the FP32 copies of the

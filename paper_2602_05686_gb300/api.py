@@ -19,7 +19,7 @@ MEASURE = {"classical": 0, "material": 1, "distance": 2}
 PRECISION = {"fp64": 0, "fp32": 1}
 DROP = {"pointwise": 0, "cut": 1}
 
-EXPORTED = ["sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_solve_group", "sa_vcycle", "sa_hierarchy_stats",
+EXPORTED = ["sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_solve_batch_zero", "sa_solve_group", "sa_vcycle", "sa_hierarchy_stats",
             "sa_level_sizes", "sa_level_format", "sa_export_level", "sa_export_strength", "sa_free",
             "sa_status_string", "sa_last_error", "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
             "sa_launch_count", "sa_strength_material_noalloc", "sa_serialized_size", "sa_serialize",
@@ -79,6 +79,7 @@ def lib(build_if_missing: bool = True):
         L.sa_setup.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)]
         L.sa_solve.argtypes = [P, P, P, D, ctypes.POINTER(SolveInfo)]
         L.sa_solve_batch.argtypes = [P, I, P, P, D, ctypes.POINTER(SolveInfo)]
+        L.sa_solve_batch_zero.argtypes = [P, I, P, P, D, ctypes.POINTER(SolveInfo)]
         L.sa_vcycle.argtypes = [P, P, P]
         L.sa_hierarchy_stats.argtypes = [P, P, P, P, P, P]
         L.sa_level_sizes.argtypes = [P, I, P]
@@ -102,7 +103,8 @@ def lib(build_if_missing: bool = True):
         L.sa_serialize.argtypes = [P, P, ctypes.c_uint64]
         L.sa_deserialize.argtypes = [P, ctypes.c_uint64, P, P]
         L.sa_solve_group.argtypes = [I, P, P, P, D, P]
-        for f in ("sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_solve_group", "sa_vcycle",
+        for f in ("sa_default_options", "sa_setup", "sa_solve", "sa_solve_batch", "sa_solve_batch_zero",
+                  "sa_solve_group", "sa_vcycle",
                   "sa_hierarchy_stats", "sa_level_sizes", "sa_level_format", "sa_export_level",
                   "sa_export_strength", "sa_free",
                   "sa_strength", "sa_set_precision", "sa_profile_enable", "sa_profile_read",
@@ -272,14 +274,15 @@ class Hierarchy:
         launch; each column ends bitwise where solve() on it ends).  B: (k, n)
         CUDA tensor (float64) or numpy array; returns (X of the same kind,
         list of per-column info dicts).  Host path: `out` (a C-contiguous
-        float64 (k, n) numpy array, e.g. a view of pinned memory) receives X;
-        it is zeroed first unless X0 is given."""
+        float64 (k, n) numpy array, e.g. a view of pinned memory) receives X.
+        Without X0 the solve starts from zero through sa_solve_batch_zero (X
+        is output only: no buffer of zeros is filled or copied)."""
         torch = self.torch
         if isinstance(B, torch.Tensor):
             B = B.to(device="cuda", dtype=torch.float64).contiguous()
             k = int(B.shape[0])
             with torch.cuda.stream(self.stream):
-                X = torch.zeros_like(B) if X0 is None else X0.to(device="cuda", dtype=torch.float64).clone()
+                X = torch.empty_like(B) if X0 is None else X0.to(device="cuda", dtype=torch.float64).clone()
             bp, xp = B.data_ptr(), X.data_ptr()
         else:
             B = np.ascontiguousarray(B, np.float64)
@@ -288,12 +291,14 @@ class Hierarchy:
                 if out.shape != B.shape or out.dtype != np.float64 or not out.flags.c_contiguous:
                     raise ValueError("solve_batch: out must be a C-contiguous float64 array shaped like B")
                 X = out
-                X[...] = 0.0 if X0 is None else X0
+                if X0 is not None:
+                    X[...] = X0
             else:
-                X = np.zeros_like(B) if X0 is None else np.array(X0, np.float64)
+                X = np.empty_like(B) if X0 is None else np.array(X0, np.float64)
             bp, xp = B.ctypes.data, X.ctypes.data
         infos = (SolveInfo * max(k, 1))()
-        st = lib().sa_solve_batch(self.h, k, bp, xp, float(tol), infos)
+        entry = lib().sa_solve_batch_zero if X0 is None else lib().sa_solve_batch
+        st = entry(self.h, k, bp, xp, float(tol), infos)
         if check and st not in (OK, ERR_NO_CONVERGENCE):
             _check(st, "sa_solve_batch")
         return X, [dict(status=int(infos[c].status), iters=infos[c].iters, rel_res=infos[c].rel_res_true,

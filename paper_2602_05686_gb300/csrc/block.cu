@@ -14,27 +14,110 @@
 
 namespace sa {
 
-// the K values of one row of an interleaved block
+// One row of an interleaved block (its K values, K * sizeof(T) contiguous
+// bytes, aligned to that size) moves as whole vectors: 32-byte accesses
+// (sm_100 and later) where the row fills one or two of them, else the widest
+// that fits.  Element-wise accesses at the 32-byte row stride make every warp
+// instruction touch eight 128-byte lines for 128 useful bytes and leave the
+// stores as partial-sector writes; measured on the 8-column FP32 Chebyshev
+// step at 320^3 that cost 1.6x in time.  Buffers start on 256-byte
+// boundaries (the allocator contract).
+//   ld_row_nc: data read-only for the whole launch (gathered x, b)
+//   ld_row:    coherent load (a vector the launch also writes, as d)
 template <typename T, int K>
-__device__ __forceinline__ void ldvec(const T* __restrict__ p, T (&v)[K]) {
-  if constexpr (sizeof(T) == 4 && K % 4 == 0) {
+__device__ __forceinline__ void ld_row_nc(const T* __restrict__ p, T (&v)[K]) {
+  if constexpr (sizeof(T) == 4 && K == 8) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+  } else if constexpr (sizeof(T) == 8 && K % 4 == 0) {
 #pragma unroll
-    for (int q = 0; q < K / 4; ++q) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + q);
-      v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-    }
+    for (int q = 0; q < K / 4; ++q)
+      asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+          : "=d"(v[4 * q]), "=d"(v[4 * q + 1]), "=d"(v[4 * q + 2]), "=d"(v[4 * q + 3])
+          : "l"(p + 4 * q));
+  } else if constexpr (sizeof(T) == 4 && K == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
   } else if constexpr (sizeof(T) == 4 && K == 2) {
     const float2 t = __ldg(reinterpret_cast<const float2*>(p));
     v[0] = t.x; v[1] = t.y;
-  } else if constexpr (sizeof(T) == 8 && K % 2 == 0) {
+  } else if constexpr (sizeof(T) == 8 && K == 2) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = __ldg(p + c);
+  }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void ld_row(const T* p, T (&v)[K]) {
+  if constexpr (sizeof(T) == 4 && K == 8) {
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p)
+                 : "memory");
+  } else if constexpr (sizeof(T) == 8 && K % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < K / 4; ++q)
+      asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+                   : "=d"(v[4 * q]), "=d"(v[4 * q + 1]), "=d"(v[4 * q + 2]), "=d"(v[4 * q + 3])
+                   : "l"(p + 4 * q)
+                   : "memory");
+  } else if constexpr (sizeof(T) == 4 && K == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (sizeof(T) == 4 && K == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else if constexpr (sizeof(T) == 8 && K == 2) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = p[c];
+  }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void st_row(T* p, const T (&v)[K]) {
+  if constexpr (sizeof(T) == 4 && K == 8) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+  } else if constexpr (sizeof(T) == 8 && K % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < K / 4; ++q)
+      asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 4 * q), "d"(v[4 * q]), "d"(v[4 * q + 1]),
+                   "d"(v[4 * q + 2]), "d"(v[4 * q + 3])
+                   : "memory");
+  } else if constexpr (sizeof(T) == 4 && K == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (sizeof(T) == 4 && K == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (sizeof(T) == 8 && K == 2) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < K; ++c) p[c] = v[c];
+  }
+}
+
+// the K values of one gathered row: one 256-bit load for eight FP32
+// columns; 128-bit pairs for FP64 (their kernels are FP64-issue bound, and
+// a 256-bit load's four results held at once cost the CSR kernels
+// registers and occupancy)
+template <typename T, int K>
+__device__ __forceinline__ void ldvec(const T* __restrict__ p, T (&v)[K]) {
+  if constexpr (sizeof(T) == 8 && K % 2 == 0) {
 #pragma unroll
     for (int q = 0; q < K / 2; ++q) {
       const double2 t = __ldg(reinterpret_cast<const double2*>(p) + q);
       v[2 * q] = t.x; v[2 * q + 1] = t.y;
     }
   } else {
-#pragma unroll
-    for (int c = 0; c < K; ++c) v[c] = __ldg(p + c);
+    ld_row_nc<T, K>(p, v);
   }
 }
 
@@ -294,6 +377,17 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
   }
 }
 
+// columns a thread of the regular rows writes (when it writes any): the
+// whole row on SELL rows of one lane and FP32 CSR rows of one thread, half
+// on two-lane SELL rows, K / lanes on FP32 CSR lanes, one on FP64 CSR (a
+// thread per column).  The epilogues move these as one vector where it is
+// more than one column; the long-row bin (one column per lane) and FP64 CSR
+// keep element stores (the branch would cost those kernels registers).
+template <typename T, int SW, int K>
+struct BCols {
+  static constexpr int V = SW == 0 ? K : SW == -2 ? K / 2 : (sizeof(T) == 8 ? 1 : (K >= SW ? K / SW : 1));
+};
+
 // resident blocks per SM asked of the compiler: FP32 rows are latency bound
 // and gain from occupancy (6 blocks: 40 registers); FP64 rows keep the
 // 64-register budget they have without a bound (4 blocks)
@@ -310,6 +404,28 @@ __global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_cheb(MatView<T> A, cons
   int c0;
   const int nw = brow_apply<T, SW, K>(A, xin, y, i, c0);
   const int64_t o = i * K + c0;
+  constexpr int NW = BCols<T, SW, K>::V;
+  if constexpr (NW > 1) {
+    if (nw == NW) {
+      T bb[NW], xx[NW], dd[NW], xo[NW];
+      ld_row_nc<T, NW>(b + o, bb);
+      ld_row_nc<T, NW>(xin + o, xx);
+      if (first) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) dd[j] = (T)0;
+      } else {
+        ld_row<T, NW>(d + o, dd);
+      }
+#pragma unroll
+      for (int j = 0; j < NW; ++j) {
+        dd[j] = cheb_dir<T>(bb[j], y[j], dd[j], c1, c2, first);
+        xo[j] = xx[j] + dd[j];
+      }
+      st_row<T, NW>(d + o, dd);
+      st_row<T, NW>(xout + o, xo);
+      return;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     if (j < nw) {
@@ -327,6 +443,17 @@ __global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_residual(MatView<T> A, 
   int c0;
   const int nw = brow_apply<T, SW, K>(A, x, y, i, c0);
   const int64_t o = i * K + c0;
+  constexpr int NW = BCols<T, SW, K>::V;
+  if constexpr (NW > 1) {
+    if (nw == NW) {
+      T bb[NW];
+      ld_row_nc<T, NW>(b + o, bb);
+#pragma unroll
+      for (int j = 0; j < NW; ++j) bb[j] = bb[j] - y[j];
+      st_row<T, NW>(r + o, bb);
+      return;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < K; ++j)
     if (j < nw) r[o + j] = b[o + j] - y[j];
@@ -339,6 +466,16 @@ __global__ void k_bvc_spmv(MatView<T> A, const T* __restrict__ x, T* __restrict_
   int c0;
   const int nw = brow_apply<T, SW, K>(A, x, y, i, c0);
   const int64_t o = i * K + c0;
+  constexpr int NW = BCols<T, SW, K>::V;
+  if constexpr (NW > 1) {
+    if (nw == NW) {
+      T t[NW];
+#pragma unroll
+      for (int j = 0; j < NW; ++j) t[j] = y[j];
+      st_row<T, NW>(out + o, t);
+      return;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < K; ++j)
     if (j < nw) out[o + j] = y[j];
@@ -351,6 +488,17 @@ __global__ void k_bvc_spmv_add(MatView<T> A, const T* __restrict__ x, T* __restr
   int c0;
   const int nw = brow_apply<T, SW, K>(A, x, y, i, c0);
   const int64_t o = i * K + c0;
+  constexpr int NW = BCols<T, SW, K>::V;
+  if constexpr (NW > 1) {
+    if (nw == NW) {
+      T t[NW];
+      ld_row<T, NW>(out + o, t);
+#pragma unroll
+      for (int j = 0; j < NW; ++j) t[j] += y[j];
+      st_row<T, NW>(out + o, t);
+      return;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < K; ++j)
     if (j < nw) out[o + j] += y[j];
@@ -367,6 +515,25 @@ __global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_cheb_out(MatView<T> A, 
   if (nw == 0) return;
   const int64_t o = i * K + c0;
   const double si = s[i];
+  constexpr int NW = BCols<T, SW, K>::V;
+  if constexpr (NW > 1) {
+    if (nw == NW) {
+      T bb[NW], xx[NW], dd[NW];
+      double zz[NW];
+      ld_row_nc<T, NW>(b + o, bb);
+      ld_row_nc<T, NW>(xin + o, xx);
+      if (first) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) dd[j] = (T)0;
+      } else {
+        ld_row_nc<T, NW>(d + o, dd);
+      }
+#pragma unroll
+      for (int j = 0; j < NW; ++j) zz[j] = si * (double)(xx[j] + cheb_dir<T>(bb[j], y[j], dd[j], c1, c2, first));
+      st_row<double, NW>(z + o, zz);
+      return;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     if (j < nw) {
@@ -584,11 +751,11 @@ __global__ void k_bsell_spmv_dot(MatView<double> A, const double* __restrict__ P
   for (int j = 0; j < K; ++j) c[j] = 0.0;
   if (brow_apply<double, 0, K>(A, P, y, i, c0)) {
     const int64_t o = i * K;
+    double pp[K];
+    ld_row_nc<double, K>(P + o, pp);
+    st_row<double, K>(Q + o, y);
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-      Q[o + j] = y[j];
-      c[j] = y[j] * P[o + j];
-    }
+    for (int j = 0; j < K; ++j) c[j] = y[j] * pp[j];
   }
   __shared__ double sh[K][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -622,8 +789,11 @@ __global__ void k_bsell_res64(MatView<double> A, const double* __restrict__ B, c
   int c0;
   if (!brow_apply<double, 0, K>(A, X, y, i, c0)) return;
   const int64_t o = i * K;
+  double bb[K];
+  ld_row_nc<double, K>(B + o, bb);
 #pragma unroll
-  for (int j = 0; j < K; ++j) R[o + j] = B[o + j] - y[j];
+  for (int j = 0; j < K; ++j) bb[j] = bb[j] - y[j];
+  st_row<double, K>(R + o, bb);
 }
 
 static MatView<double> sell_view(const Sell<double>& A) {

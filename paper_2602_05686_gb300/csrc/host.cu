@@ -58,6 +58,7 @@ struct sa_handle_s {
   sa::Buf<double> r, p, q, rprev, t, part, dots, xb, bb;
   sa::Buf<sa::CgScalars> cg;
   double* host_pin = nullptr;  // pinned readback buffer
+  int zero_guess = 0;          // set for one sa_solve_batch_zero call: x is output only
   sa::VHier<double>* v64 = nullptr;  // FP64 V-cycle on the scaled hierarchy
   sa::VHier<float>* v32 = nullptr;   // FP32 V-cycle on the scaled hierarchy
   double setup_ms = 0;
@@ -292,13 +293,21 @@ struct HostScal {
   double rr, pad0, pad1;
 };
 
+// the initial guess into a device buffer: copied from x (host or device), or
+// zero-filled on the device when the call has no initial guess
+static int copy_in_guess(sa_handle h, double* dst, const double* x, size_t bytes) {
+  if (h->zero_guess) SA_CUDA(cudaMemsetAsync(dst, 0, bytes, h->al.stream));
+  else SA_CUDA(cudaMemcpyAsync(dst, x, bytes, cudaMemcpyDefault, h->al.stream));
+  return SA_OK;
+}
+
 // CG / flexible CG on device buffers b, x (Sec. 4), host-driven: one
 // readback per iteration.  Used when profiling (events bracket every launch).
 static int cg_eager_dev(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info);
 static int cg_eager(sa_handle h, const double* b, double* x, double tol, sa_solve_info* info) {
   cudaStream_t s = h->al.stream;
   SA_CUDA(cudaMemcpyAsync(h->bb.p, b, sizeof(double) * h->n, cudaMemcpyDefault, s));
-  SA_CUDA(cudaMemcpyAsync(h->xb.p, x, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  SA_TRY(copy_in_guess(h, h->xb.p, x, sizeof(double) * h->n));
   int st = cg_eager_dev(h, h->bb.p, h->xb.p, tol, info);
   SA_CUDA(cudaMemcpyAsync(x, h->xb.p, sizeof(double) * h->n, cudaMemcpyDefault, s));
   SA_CUDA(cudaStreamSynchronize(s));
@@ -485,7 +494,7 @@ static int cg_graph(sa_handle h, const double* b, double* x, double tol, sa_solv
   double* hp = h->host_pin;
   auto t0 = std::chrono::steady_clock::now();
   SA_CUDA(cudaMemcpyAsync(h->bb.p, b, sizeof(double) * n, cudaMemcpyDefault, s));
-  SA_CUDA(cudaMemcpyAsync(h->xb.p, x, sizeof(double) * n, cudaMemcpyDefault, s));
+  SA_TRY(copy_in_guess(h, h->xb.p, x, sizeof(double) * n));
   int status = SA_ERR_NO_CONVERGENCE, it = 0;
   SA_TRY(op_residual(h, h->bb.p, h->xb.p, h->r.p));
   SA_TRY(launch_dots(s, n, h->r.p, h->r.p, nullptr, nullptr, nullptr, nullptr, h->part.p, h->dots.p));
@@ -619,8 +628,12 @@ static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, 
   // inputs: column-major (host or device) -> interleaved
   SA_CUDA(cudaMemcpyAsync(h->kStage.p, B, sizeof(double) * n * k, cudaMemcpyDefault, s));
   SA_TRY(launch_interleave(s, n, k, K, h->kStage.p, Bb, 1));
-  SA_CUDA(cudaMemcpyAsync(h->kStage.p, X, sizeof(double) * n * k, cudaMemcpyDefault, s));
-  SA_TRY(launch_interleave(s, n, k, K, h->kStage.p, Xb, 1));
+  if (h->zero_guess) {
+    SA_CUDA(cudaMemsetAsync(Xb, 0, sizeof(double) * n * K, s));  // what interleaving zeros gives
+  } else {
+    SA_CUDA(cudaMemcpyAsync(h->kStage.p, X, sizeof(double) * n * k, cudaMemcpyDefault, s));
+    SA_TRY(launch_interleave(s, n, k, K, h->kStage.p, Xb, 1));
+  }
   // host view of the columns
   double r0[KMAX_BLOCK], hb[2 * KMAX_BLOCK];
   int act[KMAX_BLOCK], its[KMAX_BLOCK], st[KMAX_BLOCK];
@@ -961,6 +974,14 @@ int sa_solve_batch(sa_handle h, int k, const double* B, double* X, double tol, s
     }
   }
   return worst;
+}
+
+int sa_solve_batch_zero(sa_handle h, int k, const double* B, double* X, double tol, sa_solve_info* infos) {
+  if (!h) return SA_ERR_INVALID_ARG;
+  h->zero_guess = 1;
+  const int st = sa_solve_batch(h, k, B, X, tol, infos);
+  h->zero_guess = 0;
+  return st;
 }
 
 int sa_set_precision(sa_handle h, sa_precision p) {

@@ -51,6 +51,13 @@ int Alloc::get(void** p, size_t bytes) {
   if (fn_alloc) {
     *p = fn_alloc(bytes, ctx);
     if (!*p) return SA_ERR_OOM;
+    if (reinterpret_cast<uintptr_t>(*p) & 255u) {
+      // the block kernels' 32-byte row accesses need aligned buffers
+      if (fn_free) fn_free(*p, ctx);
+      *p = nullptr;
+      set_error_text("allocator callback returned a block not aligned to 256 bytes");
+      return SA_ERR_OOM;
+    }
   } else {
     keep_pool_memory();
     cudaError_t e = cudaMallocAsync(p, bytes, stream);

@@ -445,3 +445,107 @@ def test_annulus_study_matches_oracle(sa, orc, gen_mod):
         assert r["status"] == 0 and r["rel_res"] <= 1e-8, r
         assert abs(r["iters"] - oi["iters"]) <= 1 and r["levels"] == o.nlev, (r, oi)
         assert r["op_complexity"] == pytest.approx(o.operator_complexity(), abs=1e-3)
+
+
+def _raw_handle(sa, p, t, o):
+    import ctypes
+    pr = sa.Problem()
+    pr.dim, pr.n, pr.nnz = 3, p["n"], p["nnz"]
+    pr.row_ptr, pr.col, pr.val = t["row_ptr"].data_ptr(), t["col"].data_ptr(), t["val"].data_ptr()
+    pr.coords = t["coords"].data_ptr()
+    hh = ctypes.c_void_p()
+    st = sa.lib().sa_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(hh))
+    return st, hh
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_caller_allocator_alignment(sa, gen_mod, precision):
+    """a caller allocator's blocks must start on 256-byte boundaries (the
+    block kernels move whole rows with 32-byte accesses): aligned blocks give
+    bitwise the default allocator's solve; blocks offset by 64 bytes are
+    refused at the first allocation, before any kernel runs on them"""
+    import ctypes
+    import torch
+    p = gen_mod.battery_3d(12, 12, 24)
+    t = {k: torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("row_ptr", "col", "val", "coords")}
+    L = sa.lib()
+    live = {}
+
+    def make(offset):
+        @sa.api._ALLOC
+        def alloc(nbytes, ctx):
+            buf = torch.empty(int(nbytes) + 512, dtype=torch.uint8, device="cuda")
+            base = (buf.data_ptr() + 255) // 256 * 256
+            ptr = base + offset
+            live[ptr] = buf
+            return ptr
+
+        @sa.api._FREE
+        def free(ptr, ctx):
+            live.pop(ptr, None)
+
+        return alloc, free
+
+    def opts(alloc=None, free=None):
+        o = sa.default_options()
+        o.max_coarse = 100
+        o.measure = 0
+        o.precision = precision
+        o.stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        if alloc is not None:
+            o.alloc, o.dealloc = alloc, free
+        return o
+
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((8, p["n"]))
+    B[:, p["dir_mask"] == 1] = 0.0
+    Bd = torch.from_numpy(B).cuda().contiguous()
+    res = []
+    cbs = make(0)
+    for o in (opts(), opts(*cbs)):
+        st, hh = _raw_handle(sa, p, t, o)
+        assert st == 0 and hh.value
+        Xd = torch.zeros_like(Bd)
+        infos = (sa.SolveInfo * 8)()
+        assert L.sa_solve_batch(hh, 8, Bd.data_ptr(), Xd.data_ptr(), 1e-8, infos) == 0
+        torch.cuda.synchronize()
+        res.append((Xd.cpu(), [infos[c].iters for c in range(8)]))
+        L.sa_free(hh)
+    assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+    assert not live  # every block handed back
+    bad = make(64)
+    st, hh = _raw_handle(sa, p, t, opts(*bad))
+    assert st == -2 and not hh.value
+    assert b"256 bytes" in sa.lib().sa_last_error()
+    assert not live
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_zero_guess_batch_equals_explicit_zeros(sa, gen_mod, precision):
+    """sa_solve_batch_zero (X output only) ends bitwise where sa_solve_batch
+    from an X of zeros ends: one column, a partial block and a full block,
+    device and host buffers"""
+    import ctypes
+    import torch
+    p = gen_mod.battery_3d(12, 12, 24)
+    h = sa.Hierarchy(p, theta=0.05, measure="classical", max_coarse=100, precision=precision)
+    rng = np.random.default_rng(5)
+    L = sa.lib()
+    for k in (1, 3, 8):
+        B = rng.standard_normal((k, p["n"]))
+        B[:, p["dir_mask"] == 1] = 0.0
+        Bd = torch.from_numpy(B).cuda().contiguous()
+        ref = torch.zeros_like(Bd)
+        i0 = (sa.SolveInfo * k)()
+        assert L.sa_solve_batch(h.h, k, Bd.data_ptr(), ref.data_ptr(), 1e-8, i0) == 0
+        got = torch.full_like(Bd, float("nan"))  # never read
+        i1 = (sa.SolveInfo * k)()
+        assert L.sa_solve_batch_zero(h.h, k, Bd.data_ptr(), got.data_ptr(), 1e-8, i1) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(ref, got), k
+        assert [i0[c].iters for c in range(k)] == [i1[c].iters for c in range(k)]
+        Xh, infos = h.solve_batch(B)  # host buffers, no initial guess
+        assert np.array_equal(Xh, ref.cpu().numpy())
+        assert [d["iters"] for d in infos] == [i0[c].iters for c in range(k)]
+    h.free()
+    del ctypes
