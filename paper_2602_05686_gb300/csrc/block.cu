@@ -246,7 +246,10 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
   } else {
     if (blockIdx.x < M.nlb) {
       // the long-row bin: one row per warp (warp-uniform), lane-strided
-      // sums and the 32-lane tree of the one-vector kernel
+      // sums and the 32-lane tree of the one-vector kernel (one entry per
+      // load round for FP64: the K accumulators and gathered values of a
+      // second would cost the CSR kernels their occupancy)
+      constexpr int U = sizeof(T) == 8 ? 1 : BUnroll<T, SW>::U;
       const int64_t w = gt >> 5;
       if (w >= M.nlong) return 0;
       const int lane = (int)(threadIdx.x & 31);
@@ -294,32 +297,33 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
       if (i >= M.n) return 0;
       const int64_t b = M.p[i], e = M.p[i + 1];
       if (e - b > M.lt) return 0;  // in the long-row bin
-      constexpr int UC = SW == 1 ? 4 : 2;  // rounds of SW entries loaded together
+      // rounds of R = SW * UC consecutive entries (SW on CSR lanes, four on
+      // one-thread rows), the last one predicated so that a short row's
+      // loads go out together: entry q + t of a round goes to partial t mod SW
+      // (q - b is a multiple of SW), each partial adding in entry order.
+      // Measured against rounds of 2 SW with a one-entry tail (prolongator
+      // rows of 4.5 entries: 1.46x faster; rows of 59 and 75 entries: equal).
+      constexpr int UC = SW == 1 ? 4 : 1;
+      constexpr int R = SW * UC;
       T part[SW];
 #pragma unroll
       for (int h = 0; h < SW; ++h) part[h] = (T)0;
-      int64_t q = b;
-      for (; q + SW * UC - 1 < e; q += SW * UC) {
-        // SW * UC consecutive entries: partial h takes entries q + h + SW u
-        T a[SW * UC], xv[SW * UC];
-        int32_t cc[SW * UC];
+      for (int64_t q = b; q < e; q += R) {
+        T a[R], xv[R];
+        int32_t cc[R];
 #pragma unroll
-        for (int t = 0; t < SW * UC; ++t) {
-          a[t] = M.v[q + t];
-          cc[t] = M.ci[q + t];
+        for (int t = 0; t < R; ++t) {
+          const bool in = q + t < e;
+          a[t] = in ? M.v[q + t] : (T)0;
+          cc[t] = in ? M.ci[q + t] : 0;
         }
 #pragma unroll
-        for (int t = 0; t < SW * UC; ++t) xv[t] = __ldg(&X[(int64_t)cc[t] * K + c]);
+        for (int t = 0; t < R; ++t) xv[t] = q + t < e ? __ldg(&X[(int64_t)cc[t] * K + c]) : (T)0;
 #pragma unroll
         for (int u = 0; u < UC; ++u)
 #pragma unroll
-          for (int h = 0; h < SW; ++h) part[h] += a[u * SW + h] * xv[u * SW + h];
-      }
-      for (int h = 0; q < e; ++q, h = (h + 1 == SW ? 0 : h + 1)) {
-        // q - b is a multiple of SW at the loop entry, so h = (q - b) mod SW
-#pragma unroll
-        for (int hh = 0; hh < SW; ++hh)
-          if (hh == h) part[hh] += M.v[q] * __ldg(&X[(int64_t)M.ci[q] * K + c]);
+          for (int h = 0; h < SW; ++h)
+            if (q + u * SW + h < e) part[h] += a[u * SW + h] * xv[u * SW + h];
       }
       // the butterfly of the SW lanes: offsets SW/2, ..., 1, lower lane first
 #pragma unroll
@@ -389,15 +393,18 @@ struct BCols {
 };
 
 // resident blocks per SM asked of the compiler: FP32 rows are latency bound
-// and gain from occupancy (6 blocks: 40 registers); FP64 rows keep the
-// 64-register budget they have without a bound (4 blocks)
-template <typename T>
+// and gain from occupancy (6 blocks: 40 registers); the FP64 CSR rows (a
+// thread per column) too, but their long-row bin holds eight accumulators
+// and an entry's gathered values, which spill below 48 registers (5 blocks;
+// measured within 1 % of 6 on the regular rows); FP64 SELL rows keep them in
+// 64 registers (4 blocks)
+template <typename T, int SW>
 struct BOcc {
-  static constexpr int B = sizeof(T) == 4 ? 6 : 4;
+  static constexpr int B = sizeof(T) == 4 ? 6 : (SW >= 1 ? 5 : 4);
 };
 
 template <typename T, int SW, int K>
-__global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_cheb(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+__global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_cheb(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
                            T* __restrict__ d, T c1, T c2, int first) {
   T y[K];
   int64_t i;
@@ -437,7 +444,7 @@ __global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_cheb(MatView<T> A, cons
 }
 
 template <typename T, int SW, int K>
-__global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_residual(MatView<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
+__global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_residual(MatView<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
   T y[K];
   int64_t i;
   int c0;
@@ -460,7 +467,7 @@ __global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_residual(MatView<T> A, 
 }
 
 template <typename T, int SW, int K>
-__global__ void k_bvc_spmv(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
+__global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_spmv(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
   T y[K];
   int64_t i;
   int c0;
@@ -482,7 +489,7 @@ __global__ void k_bvc_spmv(MatView<T> A, const T* __restrict__ x, T* __restrict_
 }
 
 template <typename T, int SW, int K>
-__global__ void k_bvc_spmv_add(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
+__global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_spmv_add(MatView<T> A, const T* __restrict__ x, T* __restrict__ out) {
   T y[K];
   int64_t i;
   int c0;
@@ -505,7 +512,7 @@ __global__ void k_bvc_spmv_add(MatView<T> A, const T* __restrict__ x, T* __restr
 }
 
 template <typename T, int SW, int K>
-__global__ void __launch_bounds__(256, BOcc<T>::B) k_bvc_cheb_out(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin,
+__global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_cheb_out(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin,
                                const T* __restrict__ d, T c1, T c2, int first, const double* __restrict__ s,
                                double* __restrict__ z) {
   T y[K];

@@ -187,14 +187,20 @@ __global__ void k_long_fill(int64_t n, const int64_t* __restrict__ rp, int64_t l
 
 // SELL-32 (one thread per row, one FMA per stored entry) if it stores at most
 // 25 % padding; else CSR with CSR_LANES lanes per row (one for matrices of at
-// most three entries per row on average), and the rows longer
-// than LONG_ROW entries in the long-row bin (a warp per row, launched first).
-// On the coarse levels of the stretched battery stack a few rows are 10-40x
-// longer than the rest: a few lanes per row keep the FP64 shuffle additions
-// and idle lanes down (the FP64 pipe is the scarce unit), the bin keeps the
-// long rows from holding the launch.  Measured on its material hierarchy
-// against 8 lanes, 8 lanes with a bin, and 4 lanes with bins from 32 to
-// 128 entries, this was the fastest for both value types.
+// most three entries per row on average), and the outlier rows -- longer than
+// LONG_ROW_FACTOR times the mean row length and than LONG_ROW entries -- in
+// the long-row bin (a warp per row, launched first).  On the coarse levels of
+// the stretched battery stack a few rows are 10-40x longer than the rest: a
+// few lanes per row keep the FP64 shuffle additions and idle lanes down (the
+// FP64 pipe is the scarce unit), the bin keeps the long rows from holding the
+// launch.  Measured on its material hierarchy against 8 lanes, 8 lanes with a
+// bin, and 4 lanes with bins from 32 to 128 entries, 4 lanes with a bin was
+// the fastest for both value types.  The bin's threshold is relative because
+// of the several-column kernels: there a warp-per-row sum of eight columns
+// adds about half again the FMAs in shuffle additions, and on the 320^3
+// inclusions hierarchy a fixed 64 put 24-86 % of the coarse operators' rows
+// and 74 % of the restriction's in the bin (measured on rows of 59 and 75
+// entries: a thread per column took 0.43x and 0.61x the warp-per-row time).
 
 template <typename T>
 int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v,
@@ -234,8 +240,9 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
   M.sw = short_rows ? 1 : CSR_LANES;
   M.nlong = 0;
   M.lt = INT64_MAX;
-  if ((int64_t)max_width > LONG_ROW) {
-    M.lt = LONG_ROW;
+  const int64_t lt = std::max<int64_t>(LONG_ROW, LONG_ROW_FACTOR * ((nnz + n - 1) / n));
+  if ((int64_t)max_width > lt) {
+    M.lt = lt;
     Buf<int64_t> cnt;
     SA_TRY(cnt.alloc(&al, n + 1));
     SA_TRY(memset_d(cnt.p, 0, sizeof(int64_t), s));

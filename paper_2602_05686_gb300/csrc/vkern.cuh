@@ -118,10 +118,12 @@ struct MatView {
   unsigned nlb;
 };
 
-// CSR storage of a V-cycle matrix: lanes per row, and the entry count above
-// which a row is in the long-row bin (a warp per row)
+// CSR storage of a V-cycle matrix: lanes per row; a row is in the long-row
+// bin (a warp per row) above max(LONG_ROW, LONG_ROW_FACTOR x the mean row
+// length) entries
 constexpr int CSR_LANES = 4;
 constexpr int64_t LONG_ROW = 64;
+constexpr int64_t LONG_ROW_FACTOR = 4;
 // SELL-32 matrices with fewer rows take two lanes per row (one thread per
 // row leaves too few warps to cover the load latency)
 constexpr int64_t SELL2_ROWS = int64_t(1) << 19;
