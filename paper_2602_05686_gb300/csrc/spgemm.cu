@@ -10,6 +10,8 @@
 // and add, so the values do not depend on scheduling.  Rows whose distinct
 // column count exceeds the table go to a block-per-row path with a dense
 // accumulator in global scratch memory.
+#include <stdlib.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -100,7 +102,11 @@ __global__ void __launch_bounds__(SG_WARPS * 32)
 k_spgemm_fill(int64_t n, const int32_t* __restrict__ rows, const int64_t* __restrict__ Arp,
               const int32_t* __restrict__ Aci, const double* __restrict__ Av, const int64_t* __restrict__ Brp,
               const int32_t* __restrict__ Bci, const double* __restrict__ Bv, const int64_t* __restrict__ Crp,
-              int32_t* __restrict__ Cci, double* __restrict__ Cv, const uint8_t* __restrict__ isbig, int upper_only) {
+              int32_t* __restrict__ Cci, double* __restrict__ Cv, const uint8_t* __restrict__ isbig, int upper_only,
+              int32_t* __restrict__ defer, unsigned long long* __restrict__ ndefer, int64_t* __restrict__ cnt) {
+  // one-pass mode (isbig NULL): Crp holds each row's upper-bound offset, a
+  // row wider than the table goes to `defer` (the big tier), the distinct
+  // count of every other row to cnt[i + 1]
   __shared__ int32_t keys_all[SG_WARPS][HB];
   __shared__ int32_t rank_all[SG_WARPS][HB];
   __shared__ int32_t cols_all[SG_WARPS][HCAP];
@@ -113,8 +119,12 @@ k_spgemm_fill(int64_t n, const int32_t* __restrict__ rows, const int64_t* __rest
   double* acc = acc_all[w];
   for (int64_t t = global_warp(); t < n; t += warp_stride()) {
     const int64_t i = rows ? rows[t] : t;
-    if (isbig[i]) continue;  // warp-uniform
+    if (isbig && isbig[i]) continue;  // warp-uniform
     const int c = warp_build_row(i, Arp, Aci, Brp, Bci, keys, &wcount_all[w]);
+    if (!isbig && lane == 0) {
+      if (c < 0) defer[atomicAdd(ndefer, 1ull)] = (int32_t)i;
+      else cnt[i + 1] = c;
+    }
     if (c <= 0) continue;
     // compact the keys (slot order), remember each key's slot
     int out = 0;
@@ -243,13 +253,17 @@ __global__ void __launch_bounds__(TB)
 k_spgemm_tfill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
                const double* __restrict__ Av, const int64_t* __restrict__ Brp, const int32_t* __restrict__ Bci,
                const double* __restrict__ Bv, const int64_t* __restrict__ Crp, int32_t* __restrict__ Cci,
-               double* __restrict__ Cv, const uint8_t* __restrict__ ismid, int upper_only) {
+               double* __restrict__ Cv, const uint8_t* __restrict__ ismid, int upper_only,
+               int32_t* __restrict__ defer, unsigned long long* __restrict__ ndefer, int64_t* __restrict__ cnt) {
+  // one-pass mode (ismid NULL): Crp holds each row's upper-bound offset, a
+  // row with more than TCAP distinct columns goes to `defer` (the warp
+  // tier), the distinct count of every other row to cnt[i + 1]
   __shared__ int32_t cols_all[TCAP * TB];
   __shared__ double vals_all[TCAP * TB];
   int32_t* cols = cols_all + threadIdx.x;
   double* vals = vals_all + threadIdx.x;
   const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-  if (i >= n || ismid[i]) return;
+  if (i >= n || (ismid && ismid[i])) return;
   const int32_t jmin = upper_only ? (int32_t)i : INT32_MIN;
   int c = 0;
   const int64_t e = Arp[i + 1];
@@ -274,7 +288,10 @@ k_spgemm_tfill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __rest
         const int32_t j = Bci[q];
         const int pos = tlower(cols, c, j);
         if (!(pos < c && cols[pos * TB] == j)) {
-          if (c == TCAP) return;  // cannot happen: the count held this row
+          if (c == TCAP) {  // two-phase: cannot happen (the count held this row)
+            if (!ismid) defer[atomicAdd(ndefer, 1ull)] = (int32_t)i;
+            return;
+          }
           for (int t = c; t > pos; --t) {
             cols[t * TB] = cols[(t - 1) * TB];
             vals[t * TB] = vals[(t - 1) * TB];
@@ -292,6 +309,7 @@ k_spgemm_tfill(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __rest
     Cci[cb + t] = cols[t * TB];
     Cv[cb + t] = vals[t * TB];
   }
+  if (!ismid) cnt[i + 1] = c;
 }
 
 // ---------------------------------------------------------------------------
@@ -354,7 +372,7 @@ k_spgemm_big(int phase, int64_t nbig, const int32_t* __restrict__ big, int64_t m
       }
       run += tot;
     }
-    if (!phase && threadIdx.x == 0) cnt[i + 1] = run;
+    if (cnt && threadIdx.x == 0) cnt[i + 1] = run;  // count pass, or the one-pass fill
     // release the stamps of this row
     for (int64_t j = threadIdx.x; j < m; j += blockDim.x)
       if (stamp[j] == i) stamp[j] = -1;
@@ -367,26 +385,38 @@ __global__ void k_mark_big(int64_t nbig, const int32_t* __restrict__ big, uint8_
   if (t < nbig) isbig[big[t]] = 1;
 }
 
-int run_spgemm(Alloc& al, int64_t n, int64_t m, int64_t kdim, const int64_t* Arp, const int32_t* Aci,
-               const double* Av, const int64_t* Brp, const int32_t* Bci, const double* Bv, Buf<int64_t>& Crp,
-               Buf<int32_t>& Cci, Buf<double>& Cv, int64_t* nnzC, int upper_only) {
-  cudaStream_t s = al.stream;
-  SA_TRY(Crp.alloc(&al, n + 1));
-  SA_TRY(memset_d(Crp.p, 0, Crp.bytes(), s));
-  *nnzC = 0;
-  if (n <= 0) {
-    SA_TRY(Cci.alloc(&al, 0));
-    SA_TRY(Cv.alloc(&al, 0));
-    return SA_OK;
+// products of each row of A B (an upper bound of its distinct columns)
+__global__ void k_spgemm_pcount(int64_t n, const int64_t* __restrict__ Arp, const int32_t* __restrict__ Aci,
+                                const int64_t* __restrict__ Brp, int64_t* __restrict__ ub) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t t = 0;
+  for (int64_t p = Arp[i]; p < Arp[i + 1]; ++p) {
+    const int32_t k = Aci[p];
+    t += Brp[k + 1] - Brp[k];
   }
-  // tier choice by the expected products per row, (nnz(A)/n) (nnz(B)/kdim),
-  // an upper bound of the distinct columns (FE products repeat columns
-  // about 8 times: 90 products per row give about 11 distinct columns in the
-  // aggregation prolongators); wide products go straight to the warp tier
-  int64_t nnzA = 0, nnzB = 0;
-  SA_TRY(copy_d2h(&nnzA, Arp + n, sizeof(int64_t), s));
-  if (kdim > 0) SA_TRY(copy_d2h(&nnzB, Brp + kdim, sizeof(int64_t), s));
-  const bool thread_tier = kdim > 0 && ((double)nnzA / (double)n) * ((double)nnzB / (double)kdim) <= 256.0;
+  ub[i + 1] = t;
+}
+
+// rows from their upper-bound slots to the packed CSR (a warp per row)
+__global__ void k_spgemm_compact(int64_t n, const int64_t* __restrict__ ub, const int32_t* __restrict__ uci,
+                                 const double* __restrict__ uv, const int64_t* __restrict__ Crp,
+                                 int32_t* __restrict__ Cci, double* __restrict__ Cv) {
+  const int lane = lane_id();
+  for (int64_t i = global_warp(); i < n; i += warp_stride()) {
+    const int64_t src = ub[i], dst = Crp[i], c = Crp[i + 1] - dst;
+    for (int64_t t = lane; t < c; t += 32) {
+      Cci[dst + t] = uci[src + t];
+      Cv[dst + t] = uv[src + t];
+    }
+  }
+}
+
+static int spgemm_two_phase(Alloc& al, int64_t n, int64_t m, const int64_t* Arp, const int32_t* Aci,
+                            const double* Av, const int64_t* Brp, const int32_t* Bci, const double* Bv,
+                            Buf<int64_t>& Crp, Buf<int32_t>& Cci, Buf<double>& Cv, int64_t* nnzC, int upper_only,
+                            bool thread_tier) {
+  cudaStream_t s = al.stream;
   Buf<int32_t> big, midl;
   Buf<unsigned long long> nbig_d, nmid_d;
   Buf<uint8_t> isbig, ismid;
@@ -441,12 +471,12 @@ int run_spgemm(Alloc& al, int64_t n, int64_t m, int64_t kdim, const int64_t* Arp
   SA_TRY(Cv.alloc(&al, *nnzC));
   if (thread_tier) {
     k_spgemm_tfill<<<blocks_for(n, TB), TB, 0, s>>>(n, Arp, Aci, Av, Brp, Bci, Bv, Crp.p, Cci.p, Cv.p, ismid.p,
-                                                    upper_only);
+                                                    upper_only, nullptr, nullptr, nullptr);
     SA_LAUNCHED();
   }
   if (nwarp > 0) {
     k_spgemm_fill<<<warp_rows_grid(nwarp, SG_WARPS * 32), SG_WARPS * 32, 0, s>>>(
-        nwarp, wrows, Arp, Aci, Av, Brp, Bci, Bv, Crp.p, Cci.p, Cv.p, isbig.p, upper_only);
+        nwarp, wrows, Arp, Aci, Av, Brp, Bci, Bv, Crp.p, Cci.p, Cv.p, isbig.p, upper_only, nullptr, nullptr, nullptr);
     SA_LAUNCHED();
   }
   if (nbig > 0) {
@@ -455,6 +485,109 @@ int run_spgemm(Alloc& al, int64_t n, int64_t m, int64_t kdim, const int64_t* Arp
     SA_LAUNCHED();
   }
   return SA_OK;
+}
+
+// One pass: every row is filled once into slots sized by its product count
+// (ub, exclusive offsets), its distinct count recorded, and the rows are then
+// packed.  Same tiers, same per-entry arithmetic and column order as the
+// two-phase form (bitwise the same C); the count pass over every product is
+// saved for 12 bytes of scratch per product.
+static int spgemm_one_pass(Alloc& al, int64_t n, int64_t m, const int64_t* Arp, const int32_t* Aci,
+                           const double* Av, const int64_t* Brp, const int32_t* Bci, const double* Bv,
+                           const int64_t* ub, int64_t ubtot, Buf<int64_t>& Crp, Buf<int32_t>& Cci, Buf<double>& Cv,
+                           int64_t* nnzC, int upper_only, bool thread_tier) {
+  cudaStream_t s = al.stream;
+  Buf<int32_t> uci, defw, defb;
+  Buf<double> uv;
+  Buf<unsigned long long> nd;
+  SA_TRY(uci.alloc(&al, ubtot));
+  SA_TRY(uv.alloc(&al, ubtot));
+  SA_TRY(defw.alloc(&al, n));
+  SA_TRY(defb.alloc(&al, n));
+  SA_TRY(nd.alloc(&al, 2));
+  SA_TRY(memset_d(nd.p, 0, nd.bytes(), s));
+  int64_t nwarp = n;
+  const int32_t* wrows = nullptr;
+  if (thread_tier) {
+    k_spgemm_tfill<<<blocks_for(n, TB), TB, 0, s>>>(n, Arp, Aci, Av, Brp, Bci, Bv, ub, uci.p, uv.p, nullptr,
+                                                    upper_only, defw.p, nd.p, Crp.p);
+    SA_LAUNCHED();
+    unsigned long long h = 0;
+    SA_TRY(copy_d2h(&h, nd.p, sizeof(h), s));
+    nwarp = (int64_t)h;
+    wrows = defw.p;
+  }
+  unsigned long long nbig = 0;
+  if (nwarp > 0) {
+    k_spgemm_fill<<<warp_rows_grid(nwarp, SG_WARPS * 32), SG_WARPS * 32, 0, s>>>(
+        nwarp, wrows, Arp, Aci, Av, Brp, Bci, Bv, ub, uci.p, uv.p, nullptr, upper_only, defb.p, nd.p + 1, Crp.p);
+    SA_LAUNCHED();
+    SA_TRY(copy_d2h(&nbig, nd.p + 1, sizeof(nbig), s));
+  }
+  if (nbig > 0) {
+    const unsigned gbig = (unsigned)(nbig < 64 ? nbig : 64);
+    Buf<int32_t> stamp;
+    Buf<double> dacc;
+    SA_TRY(stamp.alloc(&al, (int64_t)gbig * m));
+    SA_TRY(dacc.alloc(&al, (int64_t)gbig * m));
+    SA_TRY(memset_d(stamp.p, 0xff, stamp.bytes(), s));
+    k_spgemm_big<<<gbig, BIG_THREADS, 0, s>>>(1, (int64_t)nbig, defb.p, m, Arp, Aci, Av, Brp, Bci, Bv, Crp.p, ub,
+                                                uci.p, uv.p, stamp.p, dacc.p);
+    SA_LAUNCHED();
+  }
+  SA_TRY(scan_inplace(al, Crp.p + 1, n));
+  SA_TRY(copy_d2h(nnzC, Crp.p + n, sizeof(int64_t), s));
+  SA_TRY(Cci.alloc(&al, *nnzC));
+  SA_TRY(Cv.alloc(&al, *nnzC));
+  k_spgemm_compact<<<warp_rows_grid(n), 256, 0, s>>>(n, ub, uci.p, uv.p, Crp.p, Cci.p, Cv.p);
+  SA_LAUNCHED();
+  return SA_OK;
+}
+
+int run_spgemm(Alloc& al, int64_t n, int64_t m, int64_t kdim, const int64_t* Arp, const int32_t* Aci,
+               const double* Av, const int64_t* Brp, const int32_t* Bci, const double* Bv, Buf<int64_t>& Crp,
+               Buf<int32_t>& Cci, Buf<double>& Cv, int64_t* nnzC, int upper_only) {
+  cudaStream_t s = al.stream;
+  SA_TRY(Crp.alloc(&al, n + 1));
+  SA_TRY(memset_d(Crp.p, 0, Crp.bytes(), s));
+  *nnzC = 0;
+  if (n <= 0) {
+    SA_TRY(Cci.alloc(&al, 0));
+    SA_TRY(Cv.alloc(&al, 0));
+    return SA_OK;
+  }
+  // tier choice by the expected products per row, (nnz(A)/n) (nnz(B)/kdim),
+  // an upper bound of the distinct columns (FE products repeat columns
+  // about 8 times: 90 products per row give about 11 distinct columns in the
+  // aggregation prolongators); wide products go straight to the warp tier
+  int64_t nnzA = 0, nnzB = 0;
+  SA_TRY(copy_d2h(&nnzA, Arp + n, sizeof(int64_t), s));
+  if (kdim > 0) SA_TRY(copy_d2h(&nnzB, Brp + kdim, sizeof(int64_t), s));
+  const bool thread_tier = kdim > 0 && ((double)nnzA / (double)n) * ((double)nnzB / (double)kdim) <= 256.0;
+  // one pass when the upper-bound slots (12 bytes per product) fit in half
+  // of the device's free memory, else count then fill (SA_SPGEMM_PASSES=2
+  // in the environment forces the latter, for its tests)
+  const char* passes = getenv("SA_SPGEMM_PASSES");
+  if (passes && passes[0] == '2')
+    return spgemm_two_phase(al, n, m, Arp, Aci, Av, Brp, Bci, Bv, Crp, Cci, Cv, nnzC, upper_only, thread_tier);
+  Buf<int64_t> ub;
+  SA_TRY(ub.alloc(&al, n + 1));
+  SA_TRY(memset_d(ub.p, 0, sizeof(int64_t), s));
+  k_spgemm_pcount<<<blocks_for(n, 256), 256, 0, s>>>(n, Arp, Aci, Brp, ub.p);
+  SA_LAUNCHED();
+  SA_TRY(scan_inplace(al, ub.p + 1, n));
+  int64_t ubtot = 0;
+  SA_TRY(copy_d2h(&ubtot, ub.p + n, sizeof(int64_t), s));
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = 0;
+  }
+  if ((double)ubtot * 12.0 <= 0.5 * (double)fr)
+    return spgemm_one_pass(al, n, m, Arp, Aci, Av, Brp, Bci, Bv, ub.p, ubtot, Crp, Cci, Cv, nnzC, upper_only,
+                           thread_tier);
+  ub.release();
+  return spgemm_two_phase(al, n, m, Arp, Aci, Av, Brp, Bci, Bv, Crp, Cci, Cv, nnzC, upper_only, thread_tier);
 }
 
 // ---------------------------------------------------------------------------

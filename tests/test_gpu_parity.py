@@ -560,3 +560,23 @@ def test_zero_guess_batch_equals_explicit_zeros(sa, gen_mod, precision):
         assert [d["iters"] for d in infos] == [i0[c].iters for c in range(k)]
     h.free()
     del ctypes
+
+
+@pytest.mark.parametrize("measure", ["material", "classical"])
+def test_spgemm_one_pass_equals_two_phase(sa, gen_mod, measure, monkeypatch):
+    """the one-pass SpGEMM (rows filled once into product-count slots, then
+    packed) and the count-then-fill form build the same hierarchy bit for
+    bit: every level's aggregates, P and A"""
+    p = gen_mod.battery_3d(24, 24, 48)
+    h1 = sa.Hierarchy(p, theta=0.05, measure=measure, max_coarse=100)
+    monkeypatch.setenv("SA_SPGEMM_PASSES", "2")
+    h2 = sa.Hierarchy(p, theta=0.05, measure=measure, max_coarse=100)
+    monkeypatch.delenv("SA_SPGEMM_PASSES")
+    n1, n2 = h1.stats()["levels"], h2.stats()["levels"]
+    assert n1 == n2 and n1 >= 3
+    for l in range(n1):
+        a, b = h1.export_level(l), h2.export_level(l)
+        for k in ("agg", "P_rp", "P_ci", "P_v", "A_rp", "A_ci", "A_v"):
+            assert np.array_equal(a[k], b[k]), (l, k)
+    h1.free()
+    h2.free()
