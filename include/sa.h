@@ -393,7 +393,8 @@ int sa_strength_material_noalloc(int dim, int64_t n, int64_t nnz, const int64_t*
  * coarse factor, 26 SELL packing, 27 Galerkin A*P, 28 Galerkin R*(AP); the
  * K-column kernels of sa_solve_batch: 29-33 FP64 Chebyshev step, residual,
  * restriction, prolongation, first step, 34 dense coarse solve, 35-39 the
- * same five in FP32, 40 outer FP64 product with the p.q partials), level,
+ * same five in FP32, 40 outer FP64 product with the p.q partials, 41 CG
+ * vector updates and dot products on K columns), level,
  * launches, total milliseconds, and
  * total algorithmic bytes (bytes the kernel must move at least once; 0 for
  * the setup phases).  *rows receives the number of

@@ -416,7 +416,7 @@ PROFILE_KINDS = ["cheb64", "resid64", "restrict64", "prolong64", "first64", "cg_
                  "setup_omega", "setup_smooth_p", "setup_transpose", "setup_galerkin", "setup_aux",
                  "setup_cheb_bounds", "setup_dense", "setup_sell", "setup_galerkin_ap", "setup_galerkin_rap",
                  "bcheb64", "bresid64", "brestrict64", "bprolong64", "bfirst64", "bcoarse",
-                 "bcheb32", "bresid32", "brestrict32", "bprolong32", "bfirst32", "bcg_spmv"]
+                 "bcheb32", "bresid32", "brestrict32", "bprolong32", "bfirst32", "bcg_spmv", "bcg_vec"]
 
 
 def profile_enable(on=True):

@@ -625,6 +625,7 @@ static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, 
   double* R = h->kR.p; double* P = h->kP.p; double* Q = h->kQ.p; double* Rp = h->kRp.p;
   double* T = h->kT.p; double* Xb = h->kX.p; double* Bb = h->kB.p;
   double* part = h->kpart.p; double* dots = h->kdots.p;
+  const double vb = 8.0 * (double)n * K;  // bytes of one n x K block
   // inputs: column-major (host or device) -> interleaved
   SA_CUDA(cudaMemcpyAsync(h->kStage.p, B, sizeof(double) * n * k, cudaMemcpyDefault, s));
   SA_TRY(launch_interleave(s, n, k, K, h->kStage.p, Bb, 1));
@@ -639,7 +640,7 @@ static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, 
   int act[KMAX_BLOCK], its[KMAX_BLOCK], st[KMAX_BLOCK];
   struct { double rr[KMAX_BLOCK]; CgScalars S[KMAX_BLOCK]; } hr;
   SA_TRY(launch_bsell_residual64(s, h->A0s, K, Bb, Xb, R));
-  SA_TRY(launch_bdots(s, n, K, R, R, nullptr, nullptr, part, dots));
+  PROF(PK_B_CG_VEC, 0, 2 * vb, launch_bdots(s, n, K, R, R, nullptr, nullptr, part, dots));
   SA_CUDA(cudaMemcpyAsync(hb, dots, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
   SA_CUDA(cudaStreamSynchronize(s));
   int nact = 0;
@@ -655,15 +656,16 @@ static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, 
     // first iteration
     double* Z = nullptr;
     SA_TRY(precondition_block(h, K, R, &Z));
-    SA_TRY(launch_bcg_pupdate(s, n, K, h->kS.p, h->kact.p, Z, P, 1));
-    SA_TRY(launch_bdots(s, n, K, R, Z, nullptr, nullptr, part, dots));
+    PROF(PK_B_CG_VEC, 0, 2 * vb, launch_bcg_pupdate(s, n, K, h->kS.p, h->kact.p, Z, P, 1));
+    PROF(PK_B_CG_VEC, 0, 2 * vb, launch_bdots(s, n, K, R, Z, nullptr, nullptr, part, dots));
     SA_TRY(launch_bcg_beta(s, K, h->kS.p, dots, -1, h->kact.p));
     for (int it = 1;; ++it) {
       int np = 0;
       SA_TRY(launch_bsell_spmv_dot(s, h->A0s, K, P, Q, part, &np));
       SA_TRY(launch_bfinish(s, part, np, K, dots));
       SA_TRY(launch_bcg_alpha(s, K, h->kS.p, dots, h->kact.p));
-      SA_TRY(launch_bcg_update(s, n, K, h->kS.p, h->kact.p, P, Q, Xb, R, flexible ? Rp : nullptr, part));
+      PROF(PK_B_CG_VEC, 0, (flexible ? 7 : 6) * vb,
+           launch_bcg_update(s, n, K, h->kS.p, h->kact.p, P, Q, Xb, R, flexible ? Rp : nullptr, part));
       SA_TRY(launch_bfinish(s, part, RED_BLOCKS, K, dots + 2 * KMAX_BLOCK));
       SA_CUDA(cudaMemcpyAsync(hr.rr, dots + 2 * KMAX_BLOCK, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
       SA_CUDA(cudaMemcpyAsync(hr.S, h->kS.p, sizeof(CgScalars) * K, cudaMemcpyDeviceToHost, s));
@@ -701,9 +703,10 @@ static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, 
       SA_CUDA(cudaMemcpyAsync(h->kact.p, act, sizeof(int) * K, cudaMemcpyHostToDevice, s));
       if (nact == 0) break;
       SA_TRY(precondition_block(h, K, R, &Z));
-      SA_TRY(launch_bdots(s, n, K, R, Z, flexible ? Z : nullptr, flexible ? Rp : nullptr, part, dots));
+      PROF(PK_B_CG_VEC, 0, (flexible ? 3 : 2) * vb,
+           launch_bdots(s, n, K, R, Z, flexible ? Z : nullptr, flexible ? Rp : nullptr, part, dots));
       SA_TRY(launch_bcg_beta(s, K, h->kS.p, dots, flexible, h->kact.p));
-      SA_TRY(launch_bcg_pupdate(s, n, K, h->kS.p, h->kact.p, Z, P, 0));
+      PROF(PK_B_CG_VEC, 0, 3 * vb, launch_bcg_pupdate(s, n, K, h->kS.p, h->kact.p, Z, P, 0));
     }
   }
   // true residuals at exit and the solutions

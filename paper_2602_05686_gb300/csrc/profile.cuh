@@ -50,7 +50,8 @@ enum ProfKind {
   PK_B_PROLONG32 = 38,
   PK_B_FIRST32 = 39,
   PK_B_CG_SPMV = 40,   // Q = A P on K columns with the p.q partials (FP64 SELL)
-  PK_NKINDS = 41
+  PK_B_CG_VEC = 41,    // CG vector updates and dot products on K columns
+  PK_NKINDS = 42
 };
 
 bool prof_on();

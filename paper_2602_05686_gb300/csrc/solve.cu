@@ -358,30 +358,59 @@ int launch_cg_pupdate(cudaStream_t st, int64_t n, const CgScalars* s, const doub
 // ---------------------------------------------------------------------------
 constexpr int KB = KMAX_BLOCK;
 
-__global__ void k_bdots(int64_t n, int k, const double* __restrict__ a0, const double* __restrict__ b0,
-                        const double* __restrict__ a1, const double* __restrict__ b1, double* __restrict__ part) {
-  double acc[2 * KB];
+// Rows of an interleaved n x KK block move as whole vectors, in groups of
+// G = 4 columns (one 256-bit access; rows on 32-byte boundaries) or G = 2
+// (KK = 2: one 128-bit access).  Element-wise pieces at the row stride leave
+// every warp store writing partial sectors.  The kernels keep the one-vector
+// kernels' grid, per-thread stride and reduction trees (each column's
+// arithmetic is theirs) and fit two 512-thread blocks per SM (64 registers):
+// the per-column scalars are read from shared memory, not held.
+template <int G>
+__device__ __forceinline__ void ldgrp(const double* p, double (&v)[G]) {
+  if constexpr (G == 4) {
+    asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p) : "memory");
+  } else {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  }
+}
+template <int G>
+__device__ __forceinline__ void stgrp(double* p, const double (&v)[G]) {
+  if constexpr (G == 4) {
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3]) : "memory");
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+}
+
+// NV = KB: one dot per column (a1 unused); NV = 2 KB: two (a0.b0, a1.b1)
+template <int KK, int NV>
+__global__ void __launch_bounds__(RED_THREADS, 2) k_bdots(int64_t n, const double* __restrict__ a0,
+                                                          const double* __restrict__ b0, const double* __restrict__ a1,
+                                                          const double* __restrict__ b1, double* __restrict__ part) {
+  constexpr int G = KK >= 4 ? 4 : 2;
+  double acc[NV];
 #pragma unroll
-  for (int c = 0; c < 2 * KB; ++c) acc[c] = 0.0;
+  for (int c = 0; c < NV; ++c) acc[c] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = i * k;
+    const int64_t o = i * KK;
 #pragma unroll
-    for (int c = 0; c < KB; c += 2) {
-      if (c < k) {
-        const double2 a = *reinterpret_cast<const double2*>(a0 + o + c);
-        const double2 b = *reinterpret_cast<const double2*>(b0 + o + c);
-        acc[c] = fma(a.x, b.x, acc[c]);
-        acc[c + 1] = fma(a.y, b.y, acc[c + 1]);
-        if (a1) {
-          const double2 e = *reinterpret_cast<const double2*>(a1 + o + c);
-          const double2 f = *reinterpret_cast<const double2*>(b1 + o + c);
-          acc[KB + c] = fma(e.x, f.x, acc[KB + c]);
-          acc[KB + c + 1] = fma(e.y, f.y, acc[KB + c + 1]);
-        }
+    for (int g = 0; g < KK; g += G) {
+      double a[G], b[G];
+      ldgrp<G>(a0 + o + g, a);
+      ldgrp<G>(b0 + o + g, b);
+#pragma unroll
+      for (int h = 0; h < G; ++h) acc[g + h] = fma(a[h], b[h], acc[g + h]);
+      if constexpr (NV == 2 * KB) {
+        ldgrp<G>(a1 + o + g, a);
+        ldgrp<G>(b1 + o + g, b);
+#pragma unroll
+        for (int h = 0; h < G; ++h) acc[KB + g + h] = fma(a[h], b[h], acc[KB + g + h]);
       }
     }
   }
-  block_sum_to<2 * KB>(acc, part, RED_BLOCKS);
+  block_sum_to<NV>(acc, part, RED_BLOCKS);
 }
 
 // out[v] = sum over np partials of value v (stride `stride`), in index order,
@@ -421,47 +450,52 @@ __global__ void k_bcg_alpha(int k, CgScalars* __restrict__ s, const double* __re
   S.alpha = S.rz / pq;
 }
 
-__global__ void k_bcg_update(int64_t n, int k, const CgScalars* __restrict__ s, const int* __restrict__ active,
-                             const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
-                             double* __restrict__ r, double* __restrict__ rprev, double* __restrict__ part) {
-  double alpha[KB], acc[KB];
-  bool on[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    on[c] = c < k && active[c];
-    alpha[c] = c < k ? s[c].alpha : 0.0;
-    acc[c] = 0.0;
+template <int KK>
+__global__ void __launch_bounds__(RED_THREADS, 2)
+    k_bcg_update(const int64_t n, const CgScalars* __restrict__ s, const int* __restrict__ active,
+                 const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                 double* __restrict__ r, double* __restrict__ rprev, double* __restrict__ part) {
+  constexpr int G = KK >= 4 ? 4 : 2;
+  __shared__ double alpha[KB];
+  __shared__ int on[KB];
+  if (threadIdx.x < KB) {
+    const int c = threadIdx.x;
+    on[c] = c < KK && active[c];
+    alpha[c] = c < KK ? s[c].alpha : 0.0;
   }
-  // k is even (2, 4 or 8) and rows of the interleaved blocks are 16-byte
-  // aligned: columns move in pairs (double2), each column updated and summed
-  // exactly as in the one-vector kernel
+  __syncthreads();
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < KK; ++c) any |= on[c] != 0;
+  double acc[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) acc[c] = 0.0;
+  // each column updated and summed exactly as in the one-vector kernel; a
+  // frozen column's values are written back unchanged
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = i * k;
+    const int64_t o = i * KK;
 #pragma unroll
-    for (int c = 0; c < KB; c += 2) {
-      if (c < k) {
-        const double2 r2 = *reinterpret_cast<const double2*>(r + o + c);
-        double ri[2] = {r2.x, r2.y};
-        if (on[c] || on[c + 1]) {
-          const double2 p2 = *reinterpret_cast<const double2*>(p + o + c);
-          const double2 q2 = *reinterpret_cast<const double2*>(q + o + c);
-          const double2 x2 = *reinterpret_cast<const double2*>(x + o + c);
-          const double pv[2] = {p2.x, p2.y}, qv[2] = {q2.x, q2.y};
-          double xv[2] = {x2.x, x2.y};
-          if (rprev) *reinterpret_cast<double2*>(rprev + o + c) = r2;
+    for (int g = 0; g < KK; g += G) {
+      // r with q, then x with p: two groups live at a time
+      double rv[G];
+      ldgrp<G>(r + o + g, rv);
+      if (any) {
+        double u[G], v[G];
+        if (rprev) stgrp<G>(rprev + o + g, rv);
+        ldgrp<G>(q + o + g, u);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (on[c + h]) {
-              xv[h] = fma(alpha[c + h], pv[h], xv[h]);
-              ri[h] = fma(-alpha[c + h], qv[h], ri[h]);
-            }
-          }
-          *reinterpret_cast<double2*>(x + o + c) = make_double2(xv[0], xv[1]);
-          *reinterpret_cast<double2*>(r + o + c) = make_double2(ri[0], ri[1]);
-        }
-        acc[c] = fma(ri[0], ri[0], acc[c]);
-        acc[c + 1] = fma(ri[1], ri[1], acc[c + 1]);
+        for (int h = 0; h < G; ++h)
+          if (on[g + h]) rv[h] = fma(-alpha[g + h], u[h], rv[h]);
+        stgrp<G>(r + o + g, rv);
+        ldgrp<G>(x + o + g, u);
+        ldgrp<G>(p + o + g, v);
+#pragma unroll
+        for (int h = 0; h < G; ++h)
+          if (on[g + h]) u[h] = fma(alpha[g + h], v[h], u[h]);
+        stgrp<G>(x + o + g, u);
       }
+#pragma unroll
+      for (int h = 0; h < G; ++h) acc[g + h] = fma(rv[h], rv[h], acc[g + h]);
     }
   }
   block_sum_to<KB>(acc, part, RED_BLOCKS);
@@ -484,29 +518,34 @@ __global__ void k_bcg_beta(int k, CgScalars* __restrict__ s, const double* __res
   S.rz = rz_new;
 }
 
-__global__ void k_bcg_pupdate(int64_t n, int k, const CgScalars* __restrict__ s, const int* __restrict__ active,
-                              const double* __restrict__ z, double* __restrict__ p, int first) {
-  double beta[KB];
-  bool on[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    on[c] = c < k && active[c];
-    beta[c] = c < k ? s[c].beta : 0.0;
+template <int KK>
+__global__ void __launch_bounds__(RED_THREADS, 2)
+    k_bcg_pupdate(int64_t n, const CgScalars* __restrict__ s, const int* __restrict__ active,
+                  const double* __restrict__ z, double* __restrict__ p, int first) {
+  constexpr int G = KK >= 4 ? 4 : 2;
+  __shared__ double beta[KB];
+  __shared__ int on[KB];
+  if (threadIdx.x < KB) {
+    const int c = threadIdx.x;
+    on[c] = c < KK && active[c];
+    beta[c] = c < KK ? s[c].beta : 0.0;
   }
+  __syncthreads();
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < KK; ++c) any |= on[c] != 0;
+  if (!any) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = i * k;
+    const int64_t o = i * KK;
 #pragma unroll
-    for (int c = 0; c < KB; c += 2) {
-      if (c < k && (on[c] || on[c + 1])) {
-        const double2 z2 = *reinterpret_cast<const double2*>(z + o + c);
-        const double2 p2 = *reinterpret_cast<const double2*>(p + o + c);
-        double pv[2] = {p2.x, p2.y};
-        const double zv[2] = {z2.x, z2.y};
+    for (int g = 0; g < KK; g += G) {
+      double zv[G], pv[G];
+      ldgrp<G>(z + o + g, zv);
+      ldgrp<G>(p + o + g, pv);
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-          if (on[c + h]) pv[h] = first ? zv[h] : fma(beta[c + h], pv[h], zv[h]);
-        *reinterpret_cast<double2*>(p + o + c) = make_double2(pv[0], pv[1]);
-      }
+      for (int h = 0; h < G; ++h)
+        if (on[g + h]) pv[h] = first ? zv[h] : fma(beta[g + h], pv[h], zv[h]);
+      stgrp<G>(p + o + g, pv);
     }
   }
 }
@@ -524,10 +563,21 @@ __global__ void k_interleave(int64_t n, int k, int K, const double* __restrict__
 
 int launch_bdots(cudaStream_t st, int64_t n, int k, const double* a0, const double* b0, const double* a1,
                  const double* b1, double* part, double* out) {
-  if (k < 2 || k > KB || (k & 1)) return SA_ERR_INVALID_ARG;  // column pairs
-  k_bdots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, a0, b0, a1, b1, part);
-  SA_LAUNCHED();
-  k_bdots_finish<2 * KB><<<1, 1024, 0, st>>>(part, RED_BLOCKS, RED_BLOCKS, out);
+  if (k != 2 && k != 4 && k != 8) return SA_ERR_INVALID_ARG;  // whole-row vectors
+  // one dot per column, or two (a1 . b1 into out[KB + c])
+  if (a1) {
+    if (k == 2) k_bdots<2, 2 * KB><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, a0, b0, a1, b1, part);
+    else if (k == 4) k_bdots<4, 2 * KB><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, a0, b0, a1, b1, part);
+    else k_bdots<8, 2 * KB><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, a0, b0, a1, b1, part);
+    SA_LAUNCHED();
+    k_bdots_finish<2 * KB><<<1, 1024, 0, st>>>(part, RED_BLOCKS, RED_BLOCKS, out);
+  } else {
+    if (k == 2) k_bdots<2, KB><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, a0, b0, a1, b1, part);
+    else if (k == 4) k_bdots<4, KB><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, a0, b0, a1, b1, part);
+    else k_bdots<8, KB><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, a0, b0, a1, b1, part);
+    SA_LAUNCHED();
+    k_bdots_finish<KB><<<1, 1024, 0, st>>>(part, RED_BLOCKS, RED_BLOCKS, out);
+  }
   SA_LAUNCHED();
   return SA_OK;
 }
@@ -548,8 +598,10 @@ int launch_bcg_alpha(cudaStream_t st, int k, CgScalars* s, const double* dots, c
 
 int launch_bcg_update(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* p,
                       const double* q, double* x, double* r, double* rprev, double* part) {
-  if (k < 2 || k > KB || (k & 1)) return SA_ERR_INVALID_ARG;  // column pairs
-  k_bcg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, s, active, p, q, x, r, rprev, part);
+  if (k != 2 && k != 4 && k != 8) return SA_ERR_INVALID_ARG;  // whole-row vectors
+  if (k == 2) k_bcg_update<2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, active, p, q, x, r, rprev, part);
+  else if (k == 4) k_bcg_update<4><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, active, p, q, x, r, rprev, part);
+  else k_bcg_update<8><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, active, p, q, x, r, rprev, part);
   SA_LAUNCHED();
   return SA_OK;
 }
@@ -562,8 +614,10 @@ int launch_bcg_beta(cudaStream_t st, int k, CgScalars* s, const double* dots, in
 
 int launch_bcg_pupdate(cudaStream_t st, int64_t n, int k, const CgScalars* s, const int* active, const double* z,
                        double* p, int first) {
-  if (k < 2 || k > KB || (k & 1)) return SA_ERR_INVALID_ARG;  // column pairs
-  k_bcg_pupdate<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, s, active, z, p, first);
+  if (k != 2 && k != 4 && k != 8) return SA_ERR_INVALID_ARG;  // whole-row vectors
+  if (k == 2) k_bcg_pupdate<2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, active, z, p, first);
+  else if (k == 4) k_bcg_pupdate<4><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, active, z, p, first);
+  else k_bcg_pupdate<8><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, active, z, p, first);
   SA_LAUNCHED();
   return SA_OK;
 }

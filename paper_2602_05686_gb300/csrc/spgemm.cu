@@ -563,12 +563,16 @@ int run_spgemm(Alloc& al, int64_t n, int64_t m, int64_t kdim, const int64_t* Arp
   int64_t nnzA = 0, nnzB = 0;
   SA_TRY(copy_d2h(&nnzA, Arp + n, sizeof(int64_t), s));
   if (kdim > 0) SA_TRY(copy_d2h(&nnzB, Brp + kdim, sizeof(int64_t), s));
-  const bool thread_tier = kdim > 0 && ((double)nnzA / (double)n) * ((double)nnzB / (double)kdim) <= 256.0;
-  // one pass when the upper-bound slots (12 bytes per product) fit in half
-  // of the device's free memory, else count then fill (SA_SPGEMM_PASSES=2
-  // in the environment forces the latter, for its tests)
+  const double per_row = kdim > 0 ? ((double)nnzA / (double)n) * ((double)nnzB / (double)kdim) : 0.0;
+  const bool thread_tier = kdim > 0 && per_row <= 256.0;
+  // one pass for wide products (48 or more per row expected: the Galerkin
+  // products; measured slower than count-then-fill at 27 per row, the
+  // smoothed prolongator, where the count pass is cheap) when the
+  // upper-bound slots (12 bytes per product) fit in half of the device's free
+  // memory; else count then fill (SA_SPGEMM_PASSES=2 in the environment
+  // forces that, for its tests)
   const char* passes = getenv("SA_SPGEMM_PASSES");
-  if (passes && passes[0] == '2')
+  if ((passes && passes[0] == '2') || per_row < 48.0)
     return spgemm_two_phase(al, n, m, Arp, Aci, Av, Brp, Bci, Bv, Crp, Cci, Cv, nnzC, upper_only, thread_tier);
   Buf<int64_t> ub;
   SA_TRY(ub.alloc(&al, n + 1));
