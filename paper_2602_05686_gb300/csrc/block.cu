@@ -163,14 +163,6 @@ __device__ __forceinline__ int lane_reduce(T (&acc)[K], int lane, int& c0) {
 // entries per load round: one on SELL rows of one lane (measured: more
 // registers cost the level-0 FP32 step more occupancy than the extra loads in
 // flight gain), two on CSR lanes and two-lane SELL rows
-// SW code of the FP32 block kernels' row-thread form of CSR_LANES matrices
-// with at most SW_ROWS_MEAN entries per row on average (FP64 keeps its
-// thread per column: the code maps to CSR_LANES there, never dispatched)
-constexpr int SW_ROWS = -4;
-constexpr int64_t SW_ROWS_MEAN = 8;
-template <typename T>
-constexpr int rows_code() { return sizeof(T) == 4 ? SW_ROWS : CSR_LANES; }
-
 template <typename T, int SW>
 struct BUnroll {
   static constexpr int U = SW == 0 ? 1 : 2;
@@ -252,8 +244,6 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
     }
     return K;
   } else {
-    // SW_ROWS: CSR stored for CSR_LANES lanes, the lanes' sums kept by one thread
-    constexpr int W = SW == SW_ROWS ? CSR_LANES : SW;
     if (blockIdx.x < M.nlb) {
       // the long-row bin: one row per warp (warp-uniform), lane-strided
       // sums and the 32-lane tree of the one-vector kernel (one entry per
@@ -293,54 +283,40 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
       constexpr int copies = K >= 32 ? 1 : 32 / K;   // lanes holding the same columns
       return (lane & (copies - 1)) == 0 ? v : 0;
     }
-    if constexpr (SW == SW_ROWS) {
-      // FP32 rows of short CSR matrices (prolongators): one thread per row
-      // holds the W lane sums of all K columns -- entry q to lane sum
-      // (q - b) mod W, in entry order -- and adds them in the lanes'
-      // butterfly order, so each column is the one-vector sum; one 256-bit
-      // gather per entry and a whole-row epilogue.  Measured on a
+    if constexpr (sizeof(T) == 4 && SW == 1) {
+      // FP32 rows of one-thread CSR matrices (the prolongators, at most
+      // SHORT_ROW_MEAN entries per row on average): one thread per row, the
+      // entries in rounds of four loaded together (the last one predicated),
+      // each entry's K products added in entry order -- the one-vector
+      // kernel's sum -- with one 256-bit gather per entry.  Measured on a
       // prolongator-shaped operator (4 entries per row, 320^3 -> 120^3):
-      // 0.79 ms against 1.67 ms for W lanes per row with the exchanging
-      // butterfly (and 3.5 ms for a thread per column); on rows of 60-75
-      // entries the lanes are the faster form, so the dispatch keeps them
-      // there.
+      // 0.79 ms against 1.67 ms for four lanes per row with the exchanging
+      // butterfly and 3.5 ms for a thread per column.
       const int64_t i = (int64_t)(blockIdx.x - M.nlb) * blockDim.x + threadIdx.x;
       row = i;
       if (i >= M.n) return 0;
       const int64_t b = M.p[i], e = M.p[i + 1];
       if (e - b > M.lt) return 0;  // in the long-row bin
-      T part[W][K];
+      constexpr int R = 4;
+      for (int64_t q = b; q < e; q += R) {
+        T a[R];
+        int32_t cc[R];
 #pragma unroll
-      for (int h = 0; h < W; ++h)
-#pragma unroll
-        for (int j = 0; j < K; ++j) part[h][j] = (T)0;
-      for (int64_t q = b; q < e; q += W) {
-        T a[W];
-        int32_t cc[W];
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
+        for (int t = 0; t < R; ++t) {
           const bool in = q + t < e;
           a[t] = in ? M.v[q + t] : (T)0;
           cc[t] = in ? M.ci[q + t] : 0;
         }
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
+        for (int t = 0; t < R; ++t) {
           if (q + t < e) {
             T xv[K];
             ldvec<T, K>(X + (int64_t)cc[t] * K, xv);
 #pragma unroll
-            for (int j = 0; j < K; ++j) part[t][j] += a[t] * xv[j];
+            for (int j = 0; j < K; ++j) acc[j] += a[t] * xv[j];
           }
         }
       }
-#pragma unroll
-      for (int o = W / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int h = 0; h < o; ++h)
-#pragma unroll
-          for (int j = 0; j < K; ++j) part[h][j] = part[h][j] + part[h + o][j];
-#pragma unroll
-      for (int j = 0; j < K; ++j) acc[j] = part[0][j];
       c0 = 0;
       return K;
     } else if constexpr (sizeof(T) == 8) {
@@ -450,7 +426,7 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
 template <typename T, int SW, int K>
 struct BCols {
   static constexpr int V =
-      (SW == 0 || SW == SW_ROWS) ? K : SW == -2 ? K / 2 : (sizeof(T) == 8 ? 1 : (K >= SW ? K / SW : 1));
+      SW == 0 ? K : SW == -2 ? K / 2 : (sizeof(T) == 8 ? 1 : (K >= SW ? K / SW : 1));
 };
 
 // resident blocks per SM asked of the compiler: FP32 rows are latency bound
@@ -461,7 +437,7 @@ struct BCols {
 // 64 registers (4 blocks)
 template <typename T, int SW>
 struct BOcc {
-  static constexpr int B = sizeof(T) == 4 ? (SW == SW_ROWS ? 4 : 6) : (SW >= 1 ? 5 : 4);
+  static constexpr int B = sizeof(T) == 4 ? 6 : (SW >= 1 ? 5 : 4);
 };
 
 template <typename T, int SW, int K>
@@ -657,7 +633,6 @@ __global__ void k_bcoarse_out(int64_t n, int K, const double* __restrict__ x, co
     if ((M).sw == 0 && (M).sell_lanes == 2) Kern<T, -2, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
     else if ((M).sw == 0) Kern<T, 0, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
     else if ((M).sw == 1) Kern<T, 1, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
-    else if (rows_form(M)) Kern<T, rows_code<T>(), KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
     else Kern<T, CSR_LANES, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                   \
   } while (0)
 
@@ -696,15 +671,8 @@ static int block_alloc(Alloc& al, VHier<T>* m) {
 
 // blocks of a K-column launch: SELL and FP32 CSR as the one-vector launch;
 // FP64 CSR: the long-row bin's blocks, then K threads per regular row
-// the row-thread form: FP32 CSR-lane matrices of short rows
-template <typename T>
-static bool rows_form(const Mat<T>& M) {
-  return sizeof(T) == 4 && M.sw == CSR_LANES && M.nnz <= SW_ROWS_MEAN * M.n;
-}
-
 template <typename T>
 static unsigned bmat_grid(const Mat<T>& M, int K) {
-  if (rows_form(M)) return blocks_for(M.n, 256) + (M.nlong > 0 ? long_blocks(M.nlong) : 0u);
   if (M.sw == 0 || sizeof(T) == 4) return mat_grid(M);
   return blocks_for(M.n * (int64_t)K, 256) + (M.nlong > 0 ? long_blocks(M.nlong) : 0u);
 }

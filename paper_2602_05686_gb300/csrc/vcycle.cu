@@ -227,7 +227,7 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
   // short rows (prolongators): SELL also above 25 % padding when its padding
   // costs fewer bytes than the CSR row pointers it saves (value + 32-bit
   // column per padded entry against 8 bytes per row less a slice pointer)
-  const bool short_rows = (double)nnz <= 3.0 * (double)n;
+  const bool short_rows = (double)nnz <= (double)SHORT_ROW_MEAN * (double)n;
   const bool sell_smaller =
       short_rows && (double)(sizeof(T) + 4) * (double)(stored - nnz) < 8.0 * (double)(n - M.nslices);
   if (n == 0 || (double)stored <= 1.25 * (double)nnz || sell_smaller) {
@@ -235,8 +235,11 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
     M.sell_lanes = n < SELL2_ROWS ? 2 : 1;
     return build_sell<T>(al, n, nnz, rp, ci, v, left, right, M.sell);
   }
-  // prolongators hold 1-3 entries per row: one thread per row there (no
-  // idle lanes, no shuffle additions)
+  // prolongators hold 1-8 entries per row: one thread per row there (no
+  // idle lanes, no shuffle additions, and one partial sum per column in the
+  // several-column kernels: with four lanes' partial sums the FP64 level-0
+  // prolongation of the 320^3 inclusions stack spent 2.5x its products in
+  // FP64 instructions -- 88 % of the FP64 pipe in ncu)
   M.sw = short_rows ? 1 : CSR_LANES;
   M.nlong = 0;
   M.lt = INT64_MAX;

@@ -124,6 +124,9 @@ struct MatView {
 constexpr int CSR_LANES = 4;
 constexpr int64_t LONG_ROW = 64;
 constexpr int64_t LONG_ROW_FACTOR = 4;
+// CSR matrices with at most this many entries per row on average (the
+// prolongators) take one thread per row
+constexpr int64_t SHORT_ROW_MEAN = 8;
 // SELL-32 matrices with fewer rows take two lanes per row (one thread per
 // row leaves too few warps to cover the load latency)
 constexpr int64_t SELL2_ROWS = int64_t(1) << 19;
