@@ -844,24 +844,13 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
   DenseJob dj;
   dj.level = nlev - 1;
   SA_TRY(dense_start(al, Lc.n, Lc.rp.p, Lc.ci.p, Lc.v.p, h->cf, dj));
-  // a15: smoother data (Chebyshev bounds from 10 power steps on D^-1/2 A D^-1/2)
+  // a15: smoother data: the V-cycle's copies of every level (values
+  // D^-1/2 A D^-1/2, SELL-32 or CSR), then the Chebyshev bounds from 10
+  // power steps on those copies (the product in its fastest form)
   for (int l = 0; l < nlev; ++l) {
-    PHASE_BEGIN(PK_S_CHEB, l);
     Level& L = *h->lev[l];
     SA_TRY(L.dinv.alloc(&al, L.n));
     SA_TRY(launch_reciprocal(s, L.n, L.diag.p, L.dinv.p));
-    if (l + 1 < nlev) {
-      Buf<double> sc, lam;
-      SA_TRY(sc.alloc(&al, L.n));
-      SA_TRY(lam.alloc(&al, 1));
-      SA_TRY(launch_rsqrt_scale(s, L.n, L.diag.p, sc.p));
-      SA_TRY(run_power(al, L.n, L.rp.p, L.ci.p, L.v.p, sc.p, o->power_iters, (uint32_t)(2 * l + 2), o->seed, lam.p));
-      double hl = 0;
-      SA_TRY(copy_d2h(&hl, lam.p, sizeof(double), s));
-      L.lmax = o->cheb_boost * hl;
-      L.lmin = L.lmax / o->cheb_ratio;
-    }
-    PHASE_END(PK_S_CHEB);
   }
   SA_TRY(alloc_workspace(h));
   PHASE_BEGIN(PK_S_SELL, 0);
@@ -872,6 +861,20 @@ static int setup_impl(const sa_problem* P, const sa_options* o, sa_handle h) {
     SA_TRY(vh_build<double>(al, in.data(), nlev, o->cheb_degree, coarse_view(h->cf, h->nL), &h->v64));
   }
   PHASE_END(PK_S_SELL);
+  for (int l = 0; l + 1 < nlev; ++l) {
+    PHASE_BEGIN(PK_S_CHEB, l);
+    Level& L = *h->lev[l];
+    Buf<double> lam;
+    SA_TRY(lam.alloc(&al, 1));
+    SA_TRY(vh_power(al, h->v64, l, o->power_iters, (uint32_t)(2 * l + 2), o->seed, lam.p));
+    double hl = 0;
+    SA_TRY(copy_d2h(&hl, lam.p, sizeof(double), s));
+    L.lmax = o->cheb_boost * hl;
+    L.lmin = L.lmax / o->cheb_ratio;
+    h->v64->lev[l]->lmax = L.lmax;
+    h->v64->lev[l]->lmin = L.lmin;
+    PHASE_END(PK_S_CHEB);
+  }
   if (o->precision == SA_PREC_FP32_VCYCLE) SA_TRY(build_mixed(h));
   SA_TRY(dense_finish(dj));
   SA_CUDA(cudaStreamSynchronize(s));

@@ -1,6 +1,8 @@
 // Host-side launchers of the library's kernels (one declaration per step).
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace sa {
@@ -69,6 +71,10 @@ struct PowerScratch;
 // the hash-uniform start (tag, seed); result in *lam_dev (device scalar)
 int run_power(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* s,
               int steps, uint32_t tag, uint32_t seed, double* lam_dev);
+// the same iteration on an operator given by its product: apply(y, w)
+// writes w = M y (the V-cycle's pre-scaled copy of D^-1/2 A D^-1/2)
+int run_power_op(Alloc& al, int64_t n, int steps, uint32_t tag, uint32_t seed, double* lam_dev,
+                 const std::function<int(const double*, double*)>& apply);
 int launch_rsqrt_scale(cudaStream_t s, int64_t n, const double* d, double* out);  // 1/sqrt(d), inf -> 0
 int launch_reciprocal(cudaStream_t s, int64_t n, const double* d, double* out);
 int launch_omega(cudaStream_t s, const double* lam_dev, double omega_sym, double* omega_dev);

@@ -3,6 +3,8 @@
 // scalars.  The V-cycle itself lives in vcycle.cu.
 #include <math.h>
 
+#include <functional>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "solve.cuh"
@@ -25,7 +27,7 @@ namespace sa {
 __global__ void k_power_prep(int64_t n, const double* __restrict__ X, const double* __restrict__ s,
                              const double* __restrict__ sc, double* __restrict__ y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = s[i] * (X[i] * sc[4]);
+  if (i < n) y[i] = s ? s[i] * (X[i] * sc[4]) : X[i] * sc[4];  // s NULL: a pre-scaled operator
 }
 
 // w_i = s_i * sum_p a_p y_j
@@ -72,10 +74,25 @@ __global__ void k_dots(int64_t n, const double* __restrict__ a0, const double* _
                        const double* __restrict__ a1, const double* __restrict__ b1, const double* __restrict__ a2,
                        const double* __restrict__ b2, double* __restrict__ part) {
   double acc[3] = {0.0, 0.0, 0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    acc[0] = fma(a0[i], b0[i], acc[0]);
-    if (a1) acc[1] = fma(a1[i], b1[i], acc[1]);
-    if (a2) acc[2] = fma(a2[i], b2[i], acc[2]);
+  // two grid-stride elements per trip, their loads issued together and
+  // added in the grid-stride order (the sums do not depend on the unroll)
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * st) {
+    const int64_t j = i + st;
+    const bool two = j < n;
+    const double u0 = a0[i], v0 = b0[i], u1 = two ? a0[j] : 0.0, v1 = two ? b0[j] : 0.0;
+    acc[0] = fma(u0, v0, acc[0]);
+    if (two) acc[0] = fma(u1, v1, acc[0]);
+    if (a1) {
+      const double e0 = a1[i], f0 = b1[i], e1 = two ? a1[j] : 0.0, f1 = two ? b1[j] : 0.0;
+      acc[1] = fma(e0, f0, acc[1]);
+      if (two) acc[1] = fma(e1, f1, acc[1]);
+    }
+    if (a2) {
+      const double e0 = a2[i], f0 = b2[i], e1 = two ? a2[j] : 0.0, f1 = two ? b2[j] : 0.0;
+      acc[2] = fma(e0, f0, acc[2]);
+      if (two) acc[2] = fma(e1, f1, acc[2]);
+    }
   }
   block_sum_to<3>(acc, part, RED_BLOCKS);
 }
@@ -246,6 +263,35 @@ int run_power(Alloc& al, int64_t n, const int64_t* rp, const int32_t* ci, const 
   return SA_OK;
 }
 
+int run_power_op(Alloc& al, int64_t n, int steps, uint32_t tag, uint32_t seed, double* lam_dev,
+                 const std::function<int(const double*, double*)>& apply) {
+  cudaStream_t st = al.stream;
+  if (n <= 0) return SA_OK;
+  Buf<double> x, w, y, part, sc;
+  SA_TRY(x.alloc(&al, n));
+  SA_TRY(w.alloc(&al, n));
+  SA_TRY(y.alloc(&al, n));
+  SA_TRY(part.alloc(&al, 3 * RED_BLOCKS));
+  SA_TRY(sc.alloc(&al, 5));
+  const double init[5] = {0.0, 0.0, 1.0, 0.0, 1.0};
+  SA_CUDA(cudaMemcpyAsync(sc.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  k_start_vector<<<blocks_for(n, 256), 256, 0, st>>>(n, tag, seed, x.p);
+  SA_LAUNCHED();
+  double* X = x.p;
+  double* W = w.p;
+  for (int it = 0; it < steps; ++it) {
+    k_power_prep<<<blocks_for(n, 256), 256, 0, st>>>(n, X, nullptr, sc.p, y.p);
+    SA_LAUNCHED();
+    SA_TRY(apply(y.p, W));
+    k_power_dots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, W, X, sc.p, part.p);
+    SA_LAUNCHED();
+    k_power_finish<<<1, 1024, 0, st>>>(part.p, sc.p, lam_dev);
+    SA_LAUNCHED();
+    double* t = X; X = W; W = t;
+  }
+  return SA_OK;
+}
+
 int launch_rsqrt_scale(cudaStream_t s, int64_t n, const double* d, double* out) {
   if (n <= 0) return SA_OK;
   k_rsqrt_scale<<<blocks_for(n, 256), 256, 0, s>>>(n, d, out);
@@ -284,13 +330,35 @@ __global__ void k_cg_update(int64_t n, const CgScalars* __restrict__ s, const do
                             double* __restrict__ rprev, double* __restrict__ part) {
   const double alpha = s->alpha;
   double acc[1] = {0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double ri = r[i];
-    if (rprev) rprev[i] = ri;
-    x[i] = fma(alpha, p[i], x[i]);
-    ri = fma(-alpha, q[i], ri);
-    r[i] = ri;
-    acc[0] = fma(ri, ri, acc[0]);
+  // two grid-stride elements per trip (loads together; r.r added in the
+  // grid-stride order)
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * st) {
+    const int64_t j = i + st;
+    const bool two = j < n;
+    double r0 = r[i];
+    const double p0 = p[i], q0 = q[i], x0 = x[i];
+    double r1 = 0.0, p1 = 0.0, q1 = 0.0, x1 = 0.0;
+    if (two) {
+      r1 = r[j];
+      p1 = p[j];
+      q1 = q[j];
+      x1 = x[j];
+    }
+    if (rprev) {
+      rprev[i] = r0;
+      if (two) rprev[j] = r1;
+    }
+    x[i] = fma(alpha, p0, x0);
+    r0 = fma(-alpha, q0, r0);
+    r[i] = r0;
+    acc[0] = fma(r0, r0, acc[0]);
+    if (two) {
+      x[j] = fma(alpha, p1, x1);
+      r1 = fma(-alpha, q1, r1);
+      r[j] = r1;
+      acc[0] = fma(r1, r1, acc[0]);
+    }
   }
   block_sum_to<1>(acc, part, 0);
 }
@@ -313,8 +381,15 @@ __global__ void k_cg_beta(CgScalars* __restrict__ s, const double* __restrict__ 
 __global__ void k_cg_pupdate(int64_t n, const CgScalars* __restrict__ s, const double* __restrict__ z,
                              double* __restrict__ p, int first) {
   const double beta = s->beta;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * st) {
+    const int64_t j = i + st;
+    const bool two = j < n;
+    const double z0 = z[i], p0 = first ? 0.0 : p[i];
+    const double z1 = two ? z[j] : 0.0, p1 = (two && !first) ? p[j] : 0.0;
+    p[i] = first ? z0 : fma(beta, p0, z0);
+    if (two) p[j] = first ? z1 : fma(beta, p1, z1);
+  }
 }
 
 int launch_finish(cudaStream_t st, const double* part, int np, double* out) {

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "kernels.cuh"
 #include "profile.cuh"
 #include "solve.cuh"
 #include "vcycle.cuh"
@@ -408,6 +409,20 @@ __global__ void k_vc_fine_in(int64_t n, const double* __restrict__ r, const doub
     else if ((M).sw == 1) K<T, 1><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                 \
     else K<T, CSR_LANES><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                          \
   } while (0)
+
+// spectral-radius estimate of level l's operator D^-1/2 A D^-1/2 by `steps`
+// power steps on the V-cycle's own (pre-scaled) copy, so the bounds come
+// from the fastest form of the product (a15: Chebyshev bounds, Sec. 4)
+int vh_power(Alloc& al, VHier<double>* m, int l, int steps, uint32_t tag, uint32_t seed, double* lam_dev) {
+  using T = double;
+  const Mat<T>& A = m->lev[l]->A;
+  cudaStream_t st = al.stream;
+  return run_power_op(al, m->lev[l]->n, steps, tag, seed, lam_dev, [&](const double* y, double* w) {
+    LAUNCH_MAT(k_vc_spmv, A, st, y, w);
+    SA_LAUNCHED();
+    return SA_OK;
+  });
+}
 
 template <typename T>
 __global__ void k_coarse_in(int64_t n, const T* __restrict__ b, const double* __restrict__ sq,

@@ -104,6 +104,9 @@ int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32
 template <typename T>
 int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const CoarseView& cf,
              VHier<T>** out);
+// largest eigenvalue estimate of level l's scaled operator by power steps
+// on the hierarchy's copy (result in the device scalar *lam_dev)
+int vh_power(Alloc& al, VHier<double>* m, int l, int steps, uint32_t tag, uint32_t seed, double* lam_dev);
 // z = D^-1/2 V~(D^-1/2 r); *z points to hierarchy-owned FP64 memory
 template <typename T>
 int vh_vcycle(VHier<T>* m, cudaStream_t s, const double* r, double** z);
