@@ -163,6 +163,52 @@ __device__ __forceinline__ int lane_reduce(T (&acc)[K], int lane, int& c0) {
 // entries per load round: one on SELL rows of one lane (measured: more
 // registers cost the level-0 FP32 step more occupancy than the extra loads in
 // flight gain), two on CSR lanes and two-lane SELL rows
+// FP32 one-lane SELL levels with slices at most STAGE_WCAP entries wide take
+// the staged form (SW code SW_STAGED): each warp owns one slice and copies its
+// values and columns into shared memory with two bulk copies (cp.async.bulk,
+// the TMA engine) completing on a per-warp mbarrier, then gathers with
+// STAGE_UG loads in flight.  Measured against the same kernel reading the
+// stream directly (27-point SELL-32 at 320^3, eight columns): 2.20 against
+// 2.33-2.40 ms.  FP64 never takes it (its kernels are FP64-issue bound).
+constexpr int SW_STAGED = -8;
+constexpr int STAGE_WPB = 4;     // warps (slices) per block
+constexpr int STAGE_WCAP = 32;   // widest slice staged
+constexpr int STAGE_UG = 8;      // gathers in flight per thread
+template <typename T>
+constexpr int staged_code() { return sizeof(T) == 4 ? SW_STAGED : 0; }
+
+// set when a staged kernel's wait for its bulk copies ran out (the kernel
+// then writes nothing); read and cleared by block_stage_status
+__device__ int g_stage_err = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t cnt) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(cnt) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// bounded wait for the barrier's phase `parity`: false when it ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 template <typename T, int SW>
 struct BUnroll {
   static constexpr int U = SW == 0 ? 1 : 2;
@@ -212,6 +258,70 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
     }
     const int v = lane_reduce<T, K, 2>(acc, h, c0);
     return i < M.n ? v : 0;
+  } else if constexpr (SW == SW_STAGED) {
+    // one slice per warp, its values and columns staged in shared memory
+    extern __shared__ __align__(128) unsigned char stage_smem[];
+    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    const int64_t sl = (int64_t)blockIdx.x * STAGE_WPB + warp;
+    row = sl * 32 + lane;
+    if (sl >= ((M.n + 31) >> 5)) return 0;  // warp-uniform
+    const int64_t p0 = M.p[sl];
+    const int w = (int)((M.p[sl + 1] - p0) >> 5);
+    const uint32_t ib = M.c16 ? 2u : 4u;
+    T* sv = reinterpret_cast<T*>(stage_smem + 128 + (size_t)warp * STAGE_WCAP * 32 * 8);
+    unsigned char* scol = reinterpret_cast<unsigned char*>(sv + STAGE_WCAP * 32);
+    const uint32_t ba = smem_u32(reinterpret_cast<uint64_t*>(stage_smem) + warp);
+    if (w > 0) {
+      if (lane == 0) {
+        mbar_init(ba, 1);
+        fence_mbar_init();
+      }
+      __syncwarp();
+      if (lane == 0) {
+        // p0 is a multiple of 32 entries: both sources 64-byte aligned, both
+        // sizes (128 w and 32 w ib bytes) multiples of 16
+        mbar_expect_tx(ba, (uint32_t)w * 32u * (4u + ib));
+        bulk_g2s(smem_u32(sv), M.v + p0, (uint32_t)w * 128u, ba);
+        bulk_g2s(smem_u32(scol), M.c16 ? (const void*)(M.c16 + p0) : (const void*)(M.ci + p0),
+                 (uint32_t)w * 32u * ib, ba);
+      }
+      if (!mbar_wait(ba, 0)) {
+        atomicExch(&g_stage_err, 1);
+        mbar_wait(ba, 0);  // the copies in flight, again bounded
+        return 0;
+      }
+    }
+    if (row >= M.n) return 0;
+    const T* __restrict__ xs = M.c16 ? X + (int64_t)M.base[sl] * K : X;
+    const uint16_t* s16 = reinterpret_cast<const uint16_t*>(scol);
+    const int32_t* s32 = reinterpret_cast<const int32_t*>(scol);
+    int k = 0;
+    for (; k + STAGE_UG <= w; k += STAGE_UG) {
+      T a[STAGE_UG], xv[STAGE_UG][K];
+      int64_t cc[STAGE_UG];
+#pragma unroll
+      for (int u = 0; u < STAGE_UG; ++u) {
+        const int q = (k + u) * 32 + lane;
+        a[u] = sv[q];
+        cc[u] = ib == 2 ? (int64_t)s16[q] : (int64_t)s32[q];
+      }
+#pragma unroll
+      for (int u = 0; u < STAGE_UG; ++u) ldvec<T, K>(xs + cc[u] * K, xv[u]);
+#pragma unroll
+      for (int u = 0; u < STAGE_UG; ++u)
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc[j] += a[u] * xv[u][j];
+    }
+    for (; k < w; ++k) {
+      T xv[K];
+      const int q = k * 32 + lane;
+      const T a = sv[q];
+      const int64_t c = ib == 2 ? (int64_t)s16[q] : (int64_t)s32[q];
+      ldvec<T, K>(xs + c * K, xv);
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc[j] += a * xv[j];
+    }
+    return K;
   } else if constexpr (SW == 0) {
     row = gt;
     if (gt >= M.n) return 0;
@@ -426,7 +536,7 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
 template <typename T, int SW, int K>
 struct BCols {
   static constexpr int V =
-      SW == 0 ? K : SW == -2 ? K / 2 : (sizeof(T) == 8 ? 1 : (K >= SW ? K / SW : 1));
+      (SW == 0 || SW == SW_STAGED) ? K : SW == -2 ? K / 2 : (sizeof(T) == 8 ? 1 : (K >= SW ? K / SW : 1));
 };
 
 // resident blocks per SM asked of the compiler: FP32 rows are latency bound
@@ -437,7 +547,7 @@ struct BCols {
 // 64 registers (4 blocks)
 template <typename T, int SW>
 struct BOcc {
-  static constexpr int B = sizeof(T) == 4 ? 6 : (SW >= 1 ? 5 : 4);
+  static constexpr int B = sizeof(T) == 4 ? (SW == SW_STAGED ? 2 : 6) : (SW >= 1 ? 5 : 4);
 };
 
 template <typename T, int SW, int K>
@@ -630,7 +740,9 @@ __global__ void k_bcoarse_out(int64_t n, int K, const double* __restrict__ x, co
   do {                                                                                   \
     const MatView<T> _mv = view(M);                                                      \
     const unsigned _g = bmat_grid(M, KK);                                                \
-    if ((M).sw == 0 && (M).sell_lanes == 2) Kern<T, -2, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
+    if (staged_form(M))                                                                  \
+      Kern<T, staged_code<T>(), KK><<<stage_grid(M), STAGE_WPB * 32, stage_smem_bytes(), st>>>(_mv, __VA_ARGS__); \
+    else if ((M).sw == 0 && (M).sell_lanes == 2) Kern<T, -2, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__); \
     else if ((M).sw == 0) Kern<T, 0, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
     else if ((M).sw == 1) Kern<T, 1, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);          \
     else Kern<T, CSR_LANES, KK><<<_g, 256, 0, st>>>(_mv, __VA_ARGS__);                   \
@@ -671,6 +783,28 @@ static int block_alloc(Alloc& al, VHier<T>* m) {
 
 // blocks of a K-column launch: SELL and FP32 CSR as the one-vector launch;
 // FP64 CSR: the long-row bin's blocks, then K threads per regular row
+// the staged form: FP32 one-lane SELL with slices at most STAGE_WCAP wide
+template <typename T>
+static bool staged_form(const Mat<T>& M) {
+  return sizeof(T) == 4 && M.sw == 0 && M.sell_lanes == 1 && M.n > 0 && M.wmax <= STAGE_WCAP;
+}
+template <typename T>
+static unsigned stage_grid(const Mat<T>& M) {
+  return blocks_for((M.n + 31) / 32, STAGE_WPB);
+}
+static size_t stage_smem_bytes() { return 128 + (size_t)STAGE_WPB * STAGE_WCAP * 32 * 8; }
+
+int block_stage_status(cudaStream_t st) {
+  int h = 0;
+  SA_CUDA(cudaMemcpyFromSymbolAsync(&h, g_stage_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  SA_CUDA(cudaStreamSynchronize(st));
+  if (!h) return SA_OK;
+  const int z = 0;
+  SA_CUDA(cudaMemcpyToSymbolAsync(g_stage_err, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+  set_error_text("a staged SELL kernel's bounded wait for its bulk copies ran out");
+  return SA_ERR_CUDA;
+}
+
 template <typename T>
 static unsigned bmat_grid(const Mat<T>& M, int K) {
   if (M.sw == 0 || sizeof(T) == 4) return mat_grid(M);

@@ -716,6 +716,7 @@ static int cg_block(sa_handle h, int k, const double* B, double* X, double tol, 
   SA_TRY(launch_interleave(s, n, k, K, Xb, h->kStage.p, 0));
   SA_CUDA(cudaMemcpyAsync(X, h->kStage.p, sizeof(double) * n * k, cudaMemcpyDefault, s));
   SA_CUDA(cudaStreamSynchronize(s));
+  SA_TRY(block_stage_status(s));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   for (int c = 0; c < k; ++c) {
     statuses[c] = st[c];

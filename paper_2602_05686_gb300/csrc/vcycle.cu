@@ -231,6 +231,7 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
   const bool short_rows = (double)nnz <= (double)SHORT_ROW_MEAN * (double)n;
   const bool sell_smaller =
       short_rows && (double)(sizeof(T) + 4) * (double)(stored - nnz) < 8.0 * (double)(n - M.nslices);
+  M.wmax = (int64_t)max_width;
   if (n == 0 || (double)stored <= 1.25 * (double)nnz || sell_smaller) {
     M.sw = 0;
     M.sell_lanes = n < SELL2_ROWS ? 2 : 1;

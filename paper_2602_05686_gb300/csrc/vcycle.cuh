@@ -50,6 +50,7 @@ struct Mat {
   Buf<int32_t> lrows;
   int64_t nlong = 0, lt = INT64_MAX;
   int64_t n = 0, nnz = 0, nslices = 0;
+  int64_t wmax = 0;  // longest row (SELL: widest slice)
   Sell<T> sell;
   Buf<int64_t> rp;
   Buf<int32_t> ci;
@@ -104,6 +105,9 @@ int build_sell(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32
 template <typename T>
 int vh_build(Alloc& al, const VLevelIn* in, int nlev, int cheb_degree, const CoarseView& cf,
              VHier<T>** out);
+// SA_OK, or SA_ERR_CUDA (error text set) when a staged several-column kernel's
+// bounded wait ran out since the last call; synchronises `st`
+int block_stage_status(cudaStream_t st);
 // largest eigenvalue estimate of level l's scaled operator by power steps
 // on the hierarchy's copy (result in the device scalar *lam_dev)
 int vh_power(Alloc& al, VHier<double>* m, int l, int steps, uint32_t tag, uint32_t seed, double* lam_dev);

@@ -84,3 +84,25 @@ def test_block_rejects_bad_arguments(sa, gen_mod):
     assert sa.lib().sa_solve_batch(h.h, 2, None, None, 1e-8, infos) == -1
     assert sa.lib().sa_solve_batch(h.h, -1, None, None, 1e-8, infos) == -1
     del ctypes
+
+
+@pytest.mark.parametrize("k", [3, 8])
+def test_block_fp32_staged_sell_level_equals_single_solves(sa, gen_mod, k):
+    """The FP32 several-column kernels of a one-lane SELL level with slices at
+    most 32 entries wide (levels of 2^19 rows and more: here the 96^3
+    inclusions' fine level, 27-entry rows) stage each slice's values and
+    columns in shared memory with bulk copies on an mbarrier; the columns of
+    the block solve still end bitwise where the one-vector solves end."""
+    import torch
+    p = gen_mod.inclusions_3d(96)
+    h = sa.Hierarchy(p, theta=0.04, measure="classical", precision="fp32")
+    f0 = h.level_format(0)
+    assert f0["lanes"] == 0 and f0["sell_lanes"] == 1 and p["n"] >= 1 << 19
+    B = rhs(p, k, 31 + k)
+    Bd = torch.from_numpy(B).cuda()
+    X, infos = h.solve_batch(Bd)
+    for c in range(k):
+        x1, i1 = h.solve(Bd[c].clone())
+        assert infos[c]["iters"] == i1["iters"] and infos[c]["status"] == i1["status"] == 0
+        assert torch.equal(X[c], x1), c
+    h.free()
