@@ -448,7 +448,8 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
       // loads go out together: entry q + t of a round goes to partial t mod SW
       // (q - b is a multiple of SW), each partial adding in entry order.
       // Measured against rounds of 2 SW with a one-entry tail (prolongator
-      // rows of 4.5 entries: 1.46x faster; rows of 59 and 75 entries: equal).
+      // rows of 4.5 entries: 1.46x faster; rows of 59 and 75 entries: equal);
+      // rounds of two on one-thread rows measured no faster than four.
       constexpr int UC = SW == 1 ? 4 : 1;
       constexpr int R = SW * UC;
       T part[SW];
@@ -551,8 +552,10 @@ struct BOcc {
 };
 
 template <typename T, int SW, int K>
+// d_in and d_out may be one buffer (each thread reads and writes its own row);
+// d_in may also be x_in's buffer (after the first step, where x_1 = d_1)
 __global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_cheb(MatView<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
-                           T* __restrict__ d, T c1, T c2, int first) {
+                           const T* din, T* dout, T c1, T c2, int first) {
   T y[K];
   int64_t i;
   int c0;
@@ -568,14 +571,14 @@ __global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_cheb(MatView<T> A, 
 #pragma unroll
         for (int j = 0; j < NW; ++j) dd[j] = (T)0;
       } else {
-        ld_row<T, NW>(d + o, dd);
+        ld_row<T, NW>(din + o, dd);
       }
 #pragma unroll
       for (int j = 0; j < NW; ++j) {
         dd[j] = cheb_dir<T>(bb[j], y[j], dd[j], c1, c2, first);
         xo[j] = xx[j] + dd[j];
       }
-      st_row<T, NW>(d + o, dd);
+      st_row<T, NW>(dout + o, dd);
       st_row<T, NW>(xout + o, xo);
       return;
     }
@@ -583,8 +586,8 @@ __global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_cheb(MatView<T> A, 
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     if (j < nw) {
-      const T dn = cheb_dir<T>(b[o + j], y[j], first ? (T)0 : d[o + j], c1, c2, first);
-      d[o + j] = dn;
+      const T dn = cheb_dir<T>(b[o + j], y[j], first ? (T)0 : din[o + j], c1, c2, first);
+      dout[o + j] = dn;
       xout[o + j] = xin[o + j] + dn;
     }
   }
@@ -698,27 +701,22 @@ __global__ void __launch_bounds__(256, BOcc<T, SW>::B) k_bvc_cheb_out(MatView<T>
 }
 
 // elementwise forms over the n*K elements
+// (the first step's iterate x_1 equals its direction d_1: only d is written)
 template <typename T>
 __global__ void k_bvc_fine_in(int64_t n, int K, const double* __restrict__ r, const double* __restrict__ s, T c2,
-                              T* __restrict__ b, T* __restrict__ x, T* __restrict__ d) {
+                              T* __restrict__ b, T* __restrict__ d) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n * K) {
     const T bi = (T)(s[e / K] * r[e]);
     b[e] = bi;
-    const T dn = c2 * bi;
-    d[e] = dn;
-    x[e] = dn;
+    d[e] = c2 * bi;
   }
 }
 
 template <typename T>
-__global__ void k_bvc_first(int64_t nk, const T* __restrict__ b, T c2, T* __restrict__ x, T* __restrict__ d) {
+__global__ void k_bvc_first(int64_t nk, const T* __restrict__ b, T c2, T* __restrict__ d) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nk) {
-    const T dn = c2 * b[e];
-    d[e] = dn;
-    x[e] = dn;
-  }
+  if (e < nk) d[e] = c2 * b[e];
 }
 
 template <typename T>
@@ -845,26 +843,41 @@ static int mv_block(VHier<T>* m, cudaStream_t st, int l, int K, const double* r6
   const int deg = m->deg;
   const double th = 0.5 * (L->lmax + L->lmin), de = 0.5 * (L->lmax - L->lmin);
   const double s1 = th / de;
-  T* xa = L->kx.p;
-  T* xb = L->kx2.p;
   const Mat<T>& A = L->A;
+  // the first step writes b and d_1 = x_1 into kd; the next step reads both
+  // from there and writes d into kx2 and x into kx (then in place / ping-pong)
   if (l == 0) {
-    BPROF(K_FST, l, 8.0 * K * n + 8.0 * n + 3.0 * S * K * n,
-          (k_bvc_fine_in<T><<<g256(nk), 256, 0, st>>>(n, K, r64, m->s0.p, (T)(1.0 / th), L->kb.p, xa, L->kd.p)));
+    BPROF(K_FST, l, 8.0 * K * n + 8.0 * n + 2.0 * S * K * n,
+          (k_bvc_fine_in<T><<<g256(nk), 256, 0, st>>>(n, K, r64, m->s0.p, (T)(1.0 / th), L->kb.p, L->kd.p)));
   } else {
-    BPROF(K_FST, l, 3.0 * S * K * n,
-          (k_bvc_first<T><<<g256(nk), 256, 0, st>>>(nk, L->kb.p, (T)(1.0 / th), xa, L->kd.p)));
+    BPROF(K_FST, l, 2.0 * S * K * n, (k_bvc_first<T><<<g256(nk), 256, 0, st>>>(nk, L->kb.p, (T)(1.0 / th), L->kd.p)));
   }
   SA_LAUNCHED();
+  T* x = L->kd.p;  // the iterate
+  T* d = L->kd.p;  // the direction
   const double b_chebK = b_mat(A) + 5.0 * S * K * n;
   double rho = 1.0 / s1;
   for (int q = 1; q < deg; ++q) {
     double rn = 1.0 / (2.0 * s1 - rho);
-    BPROF(K_CHEB, l, b_chebK,
-          LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, L->kd.p, (T)(rn * rho), (T)(2.0 * rn / de), 0));
-    T* t = xa; xa = xb; xb = t;
+    T* xn = q == 1 ? L->kx.p : (x == L->kx.p ? L->kd.p : L->kx.p);
+    T* dn = q == 1 ? L->kx2.p : d;
+    BPROF(K_CHEB, l, q == 1 ? b_chebK - S * K * n : b_chebK,
+          LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, x, xn, d, dn, (T)(rn * rho), (T)(2.0 * rn / de), 0));
+    x = xn;
+    d = dn;
     rho = rn;
   }
+  // post-smoothing buffers: the direction and the other iterate, both not x
+  T* post[2];
+  {
+    int k2 = 0;
+    T* cand[3] = {L->kx2.p, L->kd.p, L->kx.p};
+    for (int c = 0; c < 3 && k2 < 2; ++c)
+      if (cand[c] != x) post[k2++] = cand[c];
+  }
+  T* xa = x;
+  T* xb = post[1];
+  T* dp = post[0];
   VLevel<T>* C = m->lev[l + 1];
   BPROF(K_RES, l, b_mat(A) + 3.0 * S * K * n, LAUNCH_BMAT(k_bvc_residual, A, st, K, L->kb.p, xa, L->kr.p));
   BPROF(K_RST, l, b_mat(L->R) + S * K * (n + C->n), LAUNCH_BMAT(k_bvc_spmv, L->R, st, K, L->kr.p, C->kb.p));
@@ -885,9 +898,9 @@ static int mv_block(VHier<T>* m, cudaStream_t st, int l, int K, const double* r6
       // the last step reads b, x, d and the scaling, and writes the FP64
       // output block in place of x and d
       BPROF(K_CHEB, l, b_mat(A) + 3.0 * S * K * n + 8.0 * K * n + 8.0 * n,
-            LAUNCH_BMAT(k_bvc_cheb_out, A, st, K, L->kb.p, xa, L->kd.p, c1, c2, first, m->s0.p, m->kz.p));
+            LAUNCH_BMAT(k_bvc_cheb_out, A, st, K, L->kb.p, xa, dp, c1, c2, first, m->s0.p, m->kz.p));
     } else {
-      BPROF(K_CHEB, l, b_chebK, LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, L->kd.p, c1, c2, first));
+      BPROF(K_CHEB, l, b_chebK, LAUNCH_BMAT(k_bvc_cheb, A, st, K, L->kb.p, xa, xb, dp, dp, c1, c2, first));
       T* t = xa; xa = xb; xb = t;
     }
     if (!first) rho = rn;
