@@ -640,6 +640,16 @@ def run_ours(args):
         par = [r for r in res if r["kind"] == "parity"]
         if par:
             result["oracle_parity"] = parity_report(par, extras, infos, x64_0, x32_0)
+        # the oracle at full size on this workload (its parity solve: setup and
+        # one FP64 PCG solve, measured in this run), beside the bounded sample
+        full = result.get("oracle_parity", {}).get("c5", {}).get("classical")
+        if full and result.get("cpu_baseline") and full.get("oracle_solve_s"):
+            n5 = result["config"]["dofs"]
+            ts = full["oracle_setup_s"] + full["oracle_solve_s"]
+            result["cpu_baseline"]["full_size"] = {
+                "measured": "full size, same run: classical setup + one FP64 PCG solve (right-hand side 0), one thread",
+                "dofs": n5, "setup_s": full["oracle_setup_s"], "solve_s_one_rhs": full["oracle_solve_s"],
+                "iters": full["iters_oracle"], "value_one_rhs": round(n5 / ts / 1e6, 5), "unit": UNIT}
         jobs.cleanup()
     # the end-to-end pass runs after the oracle processes have finished, so
     # that their host-memory traffic does not share the host with its copies
