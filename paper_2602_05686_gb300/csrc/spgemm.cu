@@ -17,12 +17,16 @@
 
 namespace sa {
 
-constexpr int HB = 512;             // hash slots per warp
-constexpr int HCAP = 384;           // max distinct columns on the warp path
+// table sizes: hash slots per warp and the distinct columns the warp tier
+// holds (the Galerkin rows hold about 60; rows above go to the block tier),
+// and (below) TCAP for the thread tier -- sized so that more warps stay
+// resident (shared memory per warp is what limits the tiers)
+constexpr int HB = 256;             // hash slots per warp
+constexpr int HCAP = 192;           // max distinct columns on the warp path
 constexpr int SG_WARPS = 4;         // warps per CTA
 constexpr int BIG_THREADS = 512;
 
-__device__ __forceinline__ int hslot(int32_t j) { return (int)(((uint32_t)j * 0x9E3779B1u) >> 23); }  // 9 bits
+__device__ __forceinline__ int hslot(int32_t j) { return (int)(((uint32_t)j * 0x9E3779B1u) >> 24); }  // 8 bits
 
 // insert j; returns 1 if newly inserted, 0 if present, -1 if the table is full
 __device__ __forceinline__ int hinsert(int32_t* keys, int32_t j) {
@@ -188,7 +192,7 @@ k_spgemm_fill(int64_t n, const int32_t* __restrict__ rows, const int64_t* __rest
 // rows with more than TCAP distinct columns go to the warp tier
 // ---------------------------------------------------------------------------
 constexpr int TB = 128;
-constexpr int TCAP = 32;
+constexpr int TCAP = 24;
 constexpr int TG = 4;  // A entries whose B rows are looked up together
 
 __device__ __forceinline__ int tlower(const int32_t* cols, int c, int32_t j) {
