@@ -86,15 +86,17 @@ def test_block_rejects_bad_arguments(sa, gen_mod):
     del ctypes
 
 
-@pytest.mark.parametrize("k", [3, 8])
-def test_block_fp32_staged_sell_level_equals_single_solves(sa, gen_mod, k):
+@pytest.mark.parametrize("n_el,k", [(96, 3), (96, 8), (200, 8)])
+def test_block_fp32_staged_sell_level_equals_single_solves(sa, gen_mod, n_el, k):
     """The FP32 several-column kernels of a one-lane SELL level with slices at
-    most 32 entries wide (levels of 2^19 rows and more: here the 96^3
-    inclusions' fine level, 27-entry rows) stage each slice's values and
-    columns in shared memory with bulk copies on an mbarrier; the columns of
-    the block solve still end bitwise where the one-vector solves end."""
+    most 32 entries wide (levels of 2^19 rows and more: here the inclusions'
+    fine level, 27-entry rows) stage each slice's values and columns in shared
+    memory with bulk copies on an mbarrier; the columns of the block solve
+    still end bitwise where the one-vector solves end.  96^3 stores 16-bit
+    column offsets (slice spans below 2^16), 200^3 32-bit columns (a plane of
+    201^2 rows makes the span 2 x 40401)."""
     import torch
-    p = gen_mod.inclusions_3d(96)
+    p = gen_mod.inclusions_3d(n_el)
     h = sa.Hierarchy(p, theta=0.04, measure="classical", precision="fp32")
     f0 = h.level_format(0)
     assert f0["lanes"] == 0 and f0["sell_lanes"] == 1 and p["n"] >= 1 << 19
