@@ -393,15 +393,18 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
       constexpr int copies = K >= 32 ? 1 : 32 / K;   // lanes holding the same columns
       return (lane & (copies - 1)) == 0 ? v : 0;
     }
-    if constexpr (sizeof(T) == 4 && SW == 1) {
-      // FP32 rows of one-thread CSR matrices (the prolongators, at most
+    if constexpr (SW == 1) {
+      // rows of one-thread CSR matrices (the prolongators, at most
       // SHORT_ROW_MEAN entries per row on average): one thread per row, the
       // entries in rounds of four loaded together (the last one predicated),
       // each entry's K products added in entry order -- the one-vector
-      // kernel's sum -- with one 256-bit gather per entry.  Measured on a
-      // prolongator-shaped operator (4 entries per row, 320^3 -> 120^3):
-      // 0.79 ms against 1.67 ms for four lanes per row with the exchanging
-      // butterfly and 3.5 ms for a thread per column.
+      // kernel's sum -- with the row's K values of a gathered x_j as one
+      // 256-bit load (FP32) or 128-bit pairs (FP64).  Measured on a
+      // prolongator-shaped operator (4 entries per row, 320^3 -> 120^3),
+      // FP32: 0.79 ms against 1.67 ms for four lanes per row with the
+      // exchanging butterfly and 3.5 ms for a thread per column; FP64: with
+      // one partial sum per column a thread per column pays K-fold loads and
+      // the predicated rounds in FP64 issue slots.
       const int64_t i = (int64_t)(blockIdx.x - M.nlb) * blockDim.x + threadIdx.x;
       row = i;
       if (i >= M.n) return 0;
@@ -537,18 +540,18 @@ __device__ __forceinline__ int brow_apply(const MatView<T>& M, const T* __restri
 template <typename T, int SW, int K>
 struct BCols {
   static constexpr int V =
-      (SW == 0 || SW == SW_STAGED) ? K : SW == -2 ? K / 2 : (sizeof(T) == 8 ? 1 : (K >= SW ? K / SW : 1));
+      (SW == 0 || SW == SW_STAGED || SW == 1) ? K : SW == -2 ? K / 2 : (sizeof(T) == 8 ? 1 : (K >= SW ? K / SW : 1));
 };
 
 // resident blocks per SM asked of the compiler: FP32 rows are latency bound
-// and gain from occupancy (6 blocks: 40 registers); the FP64 CSR rows (a
-// thread per column) too, but their long-row bin holds eight accumulators
+// and gain from occupancy (6 blocks: 40 registers); the FP64 CSR-lane rows
+// (a thread per column) too, but their long-row bin holds eight accumulators
 // and an entry's gathered values, which spill below 48 registers (5 blocks;
-// measured within 1 % of 6 on the regular rows); FP64 SELL rows keep them in
-// 64 registers (4 blocks)
+// measured within 1 % of 6 on the regular rows); FP64 SELL rows and FP64
+// one-thread CSR rows (a thread per row) keep them in 64 registers (4 blocks)
 template <typename T, int SW>
 struct BOcc {
-  static constexpr int B = sizeof(T) == 4 ? (SW == SW_STAGED ? 2 : 6) : (SW >= 1 ? 5 : 4);
+  static constexpr int B = sizeof(T) == 4 ? (SW == SW_STAGED ? 2 : 6) : (SW > 1 ? 5 : 4);
 };
 
 template <typename T, int SW, int K>
@@ -805,7 +808,7 @@ int block_stage_status(cudaStream_t st) {
 
 template <typename T>
 static unsigned bmat_grid(const Mat<T>& M, int K) {
-  if (M.sw == 0 || sizeof(T) == 4) return mat_grid(M);
+  if (M.sw == 0 || M.sw == 1 || sizeof(T) == 4) return mat_grid(M);
   return blocks_for(M.n * (int64_t)K, 256) + (M.nlong > 0 ? long_blocks(M.nlong) : 0u);
 }
 
