@@ -307,7 +307,7 @@ int64_t sa_launch_count(void);
  * solves of all problems together at the bottom of the cycle) and CG vector
  * update is one launch covering every problem still iterating.  This is the
  * continuous-batching form of the serving loop (requests for different
- * operators in flight together); no counterpart in the paper (north-star
+ * operators in flight together); no counterpart in the paper (a serving
  * extension; the method per problem is PCG / flexible CG as for sa_solve).
  *   - hs[m]: distinct handles with the same precision setting, Chebyshev
  *     degree and maxit, all on the current device; B[i], X[i]: n_i doubles
