@@ -186,6 +186,57 @@ __global__ void k_long_fill(int64_t n, const int64_t* __restrict__ rp, int64_t l
   if (i < n && rp[i + 1] - rp[i] > lt) lrows[cnt[i]] = (int32_t)i;
 }
 
+// the row order of a one-thread CSR matrix: one block of ROW_ORDER_WIN
+// threads per window of as many rows, a thread per row.  Key = the row's
+// length (rows of ROW_ORDER_LEN - 1 or more entries share the last key; the
+// threads past n take no key).  A row's place in the window is the number of
+// rows with a smaller key, plus those with its key in lower warps, plus those
+// with its key in lower lanes of its warp: a stable counting sort.
+__global__ void __launch_bounds__(ROW_ORDER_WIN) k_row_order(int64_t n, const int64_t* __restrict__ rp,
+                                                             int32_t* __restrict__ perm) {
+  constexpr int NW = ROW_ORDER_WIN / 32;
+  constexpr int PER_LANE = ROW_ORDER_LEN * NW / 32;
+  __shared__ int s_cnt[ROW_ORDER_LEN * NW];  // [key][warp], then the exclusive prefix in that order
+  const int64_t base = (int64_t)blockIdx.x * ROW_ORDER_WIN;
+  const int64_t i = base + threadIdx.x;
+  const int w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  int key = ROW_ORDER_LEN;  // no row
+  if (i < n) {
+    const int64_t len = rp[i + 1] - rp[i];
+    key = len < ROW_ORDER_LEN - 1 ? (int)len : ROW_ORDER_LEN - 1;
+  }
+  for (int t = threadIdx.x; t < ROW_ORDER_LEN * NW; t += blockDim.x) s_cnt[t] = 0;
+  __syncthreads();
+  const unsigned same = __match_any_sync(FULL, key);
+  const int rank = __popc(same & ((1u << lane) - 1u));
+  if (key < ROW_ORDER_LEN && rank == 0) s_cnt[key * NW + w] = __popc(same);
+  __syncthreads();
+  if (w == 0) {
+    // lane l scans the PER_LANE consecutive counts from l * PER_LANE
+    int loc[PER_LANE];
+    int sum = 0;
+#pragma unroll
+    for (int q = 0; q < PER_LANE; ++q) {
+      loc[q] = s_cnt[lane * PER_LANE + q];
+      sum += loc[q];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += u;
+    }
+    int run = inc - sum;
+#pragma unroll
+    for (int q = 0; q < PER_LANE; ++q) {
+      s_cnt[lane * PER_LANE + q] = run;
+      run += loc[q];
+    }
+  }
+  __syncthreads();
+  if (key < ROW_ORDER_LEN) perm[base + s_cnt[key * NW + w] + rank] = (int32_t)i;
+}
+
 // SELL-32 (one thread per row, one FMA per stored entry) if it stores at most
 // 25 % padding; else CSR with CSR_LANES lanes per row (one for matrices of at
 // most three entries per row on average), and the outlier rows -- longer than
@@ -262,6 +313,11 @@ int build_mat(Alloc& al, int64_t n, int64_t nnz, const int64_t* rp, const int32_
     } else {
       M.lt = INT64_MAX;
     }
+  }
+  if (M.sw == 1 && sizeof(T) == 8) {  // FP64 rows only: see the several-column kernels
+    SA_TRY(M.perm.alloc(&al, n));
+    k_row_order<<<(unsigned)((n + ROW_ORDER_WIN - 1) / ROW_ORDER_WIN), ROW_ORDER_WIN, 0, s>>>(n, rp, M.perm.p);
+    SA_LAUNCHED();
   }
   SA_TRY(M.rp.alloc(&al, n + 1));
   SA_TRY(M.ci.alloc(&al, nnz));

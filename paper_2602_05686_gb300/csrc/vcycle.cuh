@@ -55,6 +55,10 @@ struct Mat {
   Buf<int64_t> rp;
   Buf<int32_t> ci;
   Buf<T> v;
+  // FP64 one-thread CSR (sw == 1): the rows grouped by length inside
+  // windows of ROW_ORDER_WIN rows -- the order in which the several-column
+  // kernels take them (else empty)
+  Buf<int32_t> perm;
 };
 
 template <typename T>

@@ -116,6 +116,9 @@ struct MatView {
   int64_t nlong;
   int64_t lt;
   unsigned nlb;
+  // one-thread CSR rows: the launch order of the several-column kernels
+  // (thread t takes row perm[t]; NULL: row t)
+  const int32_t* perm;
 };
 
 // CSR storage of a V-cycle matrix: lanes per row; a row is in the long-row
@@ -127,6 +130,11 @@ constexpr int64_t LONG_ROW_FACTOR = 4;
 // CSR matrices with at most this many entries per row on average (the
 // prolongators) take one thread per row
 constexpr int64_t SHORT_ROW_MEAN = 8;
+// their FP64 rows are taken by the several-column kernels grouped by length
+// (0 .. ROW_ORDER_LEN - 2 entries, longer rows together) inside windows of
+// ROW_ORDER_WIN consecutive rows, ascending row index within a length
+constexpr int ROW_ORDER_WIN = 1024;
+constexpr int ROW_ORDER_LEN = 16;
 // SELL-32 matrices with fewer rows take two lanes per row (one thread per
 // row leaves too few warps to cover the load latency)
 constexpr int64_t SELL2_ROWS = int64_t(1) << 19;
@@ -172,11 +180,13 @@ static MatView<T> view(const Mat<T>& M) {
   m.nlong = 0;
   m.lt = INT64_MAX;
   m.nlb = 0;
+  m.perm = nullptr;
   if (M.sw == 0) {
     m.p = M.sell.sp.p; m.ci = M.sell.ci.p; m.v = M.sell.v.p;
     if (M.sell.idx16) { m.base = M.sell.base.p; m.c16 = M.sell.c16.p; }
   } else {
     m.p = M.rp.p; m.ci = M.ci.p; m.v = M.v.p;
+    if (M.sw == 1) m.perm = M.perm.p;
     if (M.nlong > 0) {
       m.lrows = M.lrows.p;
       m.nlong = M.nlong;
