@@ -59,3 +59,35 @@ def test_setup_roofline_bytes_and_fraction():
     assert r["strength"]["frac_of_hbm"] == round((13 * 27000 + 8 * 1001 + 16 * 1000) / 0.5e-3 / 1e9 / 1000.0, 3)
     assert r["cheb_bounds"]["algorithmic_GB"] == round(10 * (12 * 27000 + 24 * 1000) / 1e9, 3)
     assert r["dense"]["flops"] == 100 ** 3 / 3.0
+
+
+def test_traffic_record_only_for_unchanged_sources(tmp_path, monkeypatch):
+    """a recorded ncu DRAM figure enters the line only while the sources of
+    its kernel family hash as when it was taken"""
+    sys.path.insert(0, ROOT)
+    import bench
+    hb, h1 = bench.kernel_source_hash("bcheb64"), bench.kernel_source_hash("cheb64")
+    assert len(hb) == 16 and hb == bench.kernel_source_hash("bcg_spmv") and hb != h1
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps({"bcheb64_level0@w": {"bytes_per_launch": 123, "source_hash": hb},
+                             "cheb64_level0@w": {"bytes_per_launch": 45, "source_hash": hb}}))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.traffic_for("bcheb64_level0", "w") == 123.0
+    assert bench.traffic_for("bcheb64_level0", "other") is None
+    assert bench.traffic_for("cheb64_level0", "w") is None      # one-vector family: other sources
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda kernel="": "0" * 16)
+    assert bench.traffic_for("bcheb64_level0", "w") is None
+
+
+def test_fp64_flops_of_level0_kernels():
+    """two flops per stored entry and column plus the row updates; level-0
+    FP64 kernels only.  The 320^3 inclusions Chebyshev step: the figure the
+    bench line reports per launch"""
+    sys.path.insert(0, ROOT)
+    import bench
+    nnz, n = bench.inclusions_nnz(320), 321 ** 3
+    assert bench.fp64_flops("bcheb64", 0, nnz, n, 8) == 15480424984.0
+    assert bench.fp64_flops("bcheb64", 0, nnz, n, 8) == 8 * bench.fp64_flops("cheb64", 0, nnz, n, 1)
+    assert bench.fp64_flops("bresid64", 0, 100, 10, 4) == 4 * (200 + 10)
+    assert bench.fp64_flops("bcheb64", 1, nnz, n, 8) is None
+    assert bench.fp64_flops("bcheb32", 0, nnz, n, 8) is None
