@@ -473,6 +473,44 @@ def test_vcycle_is_symmetric_positive(orc, gen_mod):
     assert v @ Mv > 0 and u @ Mu > 0
 
 
+@pytest.mark.parametrize("measure", ["classical", "material"])
+def test_vcycle_equals_its_error_propagation_operator(orc, gen_mod, measure):
+    # Algorithm 1 with a stationary smoother, written as a matrix: with
+    # p_l = T_k((theta_l I - D_l^-1 A_l) / delta_l) / T_k(theta_l / delta_l)
+    # the Chebyshev error polynomial, E_l = I - P_l M_{l+1} P_l^T A_l the
+    # coarse-grid correction and M_L = A_L^-1 on the coarsest level, one
+    # V-cycle from x = 0 is M_l = (I - p_l E_l p_l) A_l^-1.  Built densely
+    # from the exported levels and compared column by column with the
+    # oracle's cycle (catches a dropped smoothing pass, a wrong sign of the
+    # correction, R != P^T, or a wrong Chebyshev interval on any level).
+    p = gen_mod.layered_2d(12, contrast=1e-2)
+    h = orc.Hierarchy(p, 0.08, measure, max_coarse=12)
+    assert h.nlev >= 3
+    lv = [h.level(l) for l in range(h.nlev)]
+    A = [sp.csr_matrix((d["A_v"], d["A_ci"], d["A_rp"]), shape=(d["n"], d["n"])).toarray() for d in lv]
+    P = [sp.csr_matrix((d["P_v"], d["P_ci"], d["P_rp"]), shape=(d["n"], d["nc"])).toarray() for d in lv[:-1]]
+    def cycle(l, Mc, post=True, sign=1.0):
+        n = A[l].shape[0]
+        th = 0.5 * (lv[l]["cheb_lmax"] + lv[l]["cheb_lmin"])
+        de = 0.5 * (lv[l]["cheb_lmax"] - lv[l]["cheb_lmin"])
+        Y = (th * np.eye(n) - A[l] / np.diag(A[l])[:, None]) / de
+        pl = (2 * Y @ Y - np.eye(n)) / (2 * (th / de) ** 2 - 1)      # T_2(Y) / T_2(theta / delta)
+        E = np.eye(n) - sign * P[l] @ Mc @ P[l].T @ A[l]
+        err = pl @ E @ pl if post else E @ pl
+        return np.linalg.solve(A[l].T, (np.eye(n) - err).T).T          # (I - p E p) A^-1
+
+    Ms = [None] * h.nlev
+    Ms[-1] = np.linalg.inv(A[-1])
+    for l in range(h.nlev - 2, -1, -1):
+        Ms[l] = cycle(l, Ms[l + 1])
+    V = np.column_stack([h.vcycle(e) for e in np.eye(p["n"])])
+    tol = 1e-9 * np.abs(Ms[0]).max()
+    np.testing.assert_allclose(V, Ms[0], rtol=0, atol=tol)
+    # the plausible slips are far outside that bar
+    for wrong in (cycle(0, Ms[1], post=False), cycle(0, Ms[1], sign=-1.0), cycle(0, np.linalg.inv(A[1]))):
+        assert np.abs(V - wrong).max() > 1e4 * tol
+
+
 def test_flexible_cg_converges(orc, gen_mod):
     p = gen_mod.layered_2d(32)
     h = orc.Hierarchy(p, 0.08, "material", max_coarse=64)
