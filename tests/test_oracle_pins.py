@@ -473,6 +473,33 @@ def test_vcycle_is_symmetric_positive(orc, gen_mod):
     assert v @ Mv > 0 and u @ Mu > 0
 
 
+@pytest.mark.parametrize("case", ["layered", "voronoi", "battery"])
+def test_smoother_and_damping_intervals(orc, gen_mod, case):
+    # Sec. 4 / Sec. 2.2 readings: lambda_max = 1.1 x (10 power steps on
+    # D^-1/2 A D^-1/2, D = diag A), lambda_min = lambda_max / 30; omega =
+    # (4/3) / lambda~ with lambda~ from power steps under the 1-norm diagonal.
+    # A power estimate never exceeds the spectral radius of the symmetric
+    # scaled matrix, and ten steps come close (dense eigenvalues here); under
+    # the 1-norm diagonal the radius is at most 1 (Gershgorin).  Scaling the
+    # smoother's operator by the 1-norm diagonal, dropping the boost or
+    # changing the ratio fails one of these.
+    p = {"layered": lambda: gen_mod.layered_2d(16), "voronoi": lambda: gen_mod.voronoi_3d(6, nseeds=4, seed=6),
+         "battery": lambda: gen_mod.battery_3d(8, 8, 16)}[case]()
+    for measure in ("classical", "material"):
+        h = orc.Hierarchy(p, 0.05, measure, max_coarse=20)
+        assert h.nlev >= 2
+        for l in range(h.nlev - 1):
+            d = h.level(l)
+            A = sp.csr_matrix((d["A_v"], d["A_ci"], d["A_rp"]), shape=(d["n"],) * 2).toarray()
+            s = 1 / np.sqrt(np.diag(A))
+            lam = np.linalg.eigvalsh(s[:, None] * A * s[None, :]).max()
+            est = d["cheb_lmax"] / 1.1
+            assert 0.8 * lam <= est <= lam * (1 + 1e-12), (measure, l, est / lam)
+            assert d["cheb_lmax"] / d["cheb_lmin"] == pytest.approx(30.0, rel=4e-16)
+            assert d["omega"] * d["lam_omega"] == pytest.approx(4.0 / 3.0, rel=4e-16)
+            assert 0.5 < d["lam_omega"] <= 1 + 1e-12
+
+
 @pytest.mark.parametrize("measure", ["classical", "material"])
 def test_vcycle_equals_its_error_propagation_operator(orc, gen_mod, measure):
     # Algorithm 1 with a stationary smoother, written as a matrix: with
