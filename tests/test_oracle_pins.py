@@ -473,6 +473,34 @@ def test_vcycle_is_symmetric_positive(orc, gen_mod):
     assert v @ Mv > 0 and u @ Mu > 0
 
 
+def test_stop_rule(orc, gen_mod):
+    # Sec. 4 stop rule (reading 10): coarsen while n_l > max_coarse and fewer
+    # than max_levels levels exist; a coarsening that would keep more than
+    # 0.9 n_l unknowns makes level l the coarsest
+    p = gen_mod.layered_2d(32)
+    for mc in (64, 10):
+        h = orc.Hierarchy(p, 0.08, "material", max_coarse=mc)
+        n = [h.level(l)["n"] for l in range(h.nlev)]
+        assert all(x > mc for x in n[:-1]) and n[-1] <= mc, n
+        assert all(b <= 0.9 * a for a, b in zip(n, n[1:])), n
+    deep = orc.Hierarchy(p, 0.08, "material", max_coarse=10)
+    cut = orc.Hierarchy(p, 0.08, "material", max_coarse=10, max_levels=2)
+    assert deep.nlev > 2 and cut.nlev == 2 and cut.level(1)["n"] == deep.level(1)["n"] > 10
+    # theta = 0.9: no off-diagonal is strong, so every free node would be an
+    # aggregate of its own (n - #Dirichlet > 0.9 n): the fine level is the
+    # coarsest and the cycle is the direct solve
+    rp, ci, v, n0 = p["row_ptr"], p["col"], p["val"], p["n"]
+    dm = orc.dirichlet(n0, rp, ci, v)
+    keep = orc.strength_classical(n0, rp, ci, v, dm, 0.9)
+    grp, gci = orc.filtered_graph(n0, rp, ci, keep, dm)
+    nc, _ = orc.aggregate(n0, grp, gci, dm, orc.mis2(n0, grp, gci, dm, 0, 0))
+    assert nc == n0 - int(dm.sum()) and nc > 0.9 * n0
+    one = orc.Hierarchy(p, 0.9, "classical", max_coarse=64)
+    assert one.nlev == 1 and one.status == 0
+    x, info = one.solve(p["b"], tol=1e-10)
+    assert info["status"] == 0 and info["iters"] <= 2
+
+
 @pytest.mark.parametrize("case", ["layered", "voronoi", "battery"])
 def test_smoother_and_damping_intervals(orc, gen_mod, case):
     # Sec. 4 / Sec. 2.2 readings: lambda_max = 1.1 x (10 power steps on
